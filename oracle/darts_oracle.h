@@ -1,0 +1,141 @@
+/*
+ * darts_oracle.h -- plain FP64 CPU oracle for DARTS transient path tracing.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may include, link or
+ * call this code; it exists so that tests, the smoke check and the CPU
+ * baseline leg of the benchmark can compare the CUDA library against an
+ * independent, slow, obviously-correct restatement of the method:
+ *   He, Du, Jiang, Jin, "DARTS: Diffusion Approximated Residual Time Sampling
+ *   for Time-of-flight Rendering in Homogeneous Scattering Media" (2024).
+ *
+ * Everything is double precision.  The oracle shares no code, header, table
+ * or constant generator with the CUDA path; only the scene description (plain
+ * numbers) is common.
+ */
+#ifndef DARTS_ORACLE_H
+#define DARTS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Rendering methods. */
+enum { ORC_DARTS = 0, ORC_PLAIN_UNIFORM_T = 1, ORC_VANILLA_DIRECT = 2 };
+
+/* Per-path event codes written to decisions[k*4+0] (low nibble). */
+enum {
+  ORC_EV_NONE = 0,      /* vertex not reached                                */
+  ORC_EV_EARLY = 1,     /* residual bound below straight-line distance (Sec.5.2) */
+  ORC_EV_SCATTER = 2,   /* connection made (maybe empty), walk continued     */
+  ORC_EV_ESCAPE = 3,    /* Bernoulli medium event failed: ray leaves medium  */
+  ORC_EV_INVALID = 4,   /* every RIS candidate non-causal: path ends          */
+  ORC_EV_MAXDEPTH = 5   /* k+1 == max_bounces after the connection            */
+};
+
+/* Path-level flags (bit mask) reported by the per-path debug routine. */
+enum {
+  ORC_FLAG_NEAR_DEGENERATE = 1, /* a connection had (S-C)/C < 2^-12            */
+  ORC_FLAG_SMALL_TPRIME = 2     /* a RIS candidate had t' < 2^-6 (t_max-t_min) */
+};
+
+typedef struct {
+  /* medium (Eq. 9, Eq. 12): sigma_s, sigma_a, Henyey-Greenstein g, v = c/eta */
+  double sigma_s, sigma_a, g, v;
+  /* medium box [lo, hi] (axis aligned, no surfaces) */
+  double lo[3], hi[3];
+  /* isotropic point pulse emitter: position, start time t0, energy */
+  double xe[3];
+  double t0, energy;
+  /* isotropic point fluence sensor */
+  double xs[3];
+  /* time gate [t_min, t_max) split into n_bins equal bins */
+  double t_min, t_max;
+  int32_t n_bins;
+  int32_t max_bounces;          /* K: scattering vertices per path, incl. control vertex */
+  int32_t ris_m;                /* N_RIS candidates (Eq. 15)                 */
+  int32_t n_rho, n_s, n_mu;     /* direction table: C/S cells, S cells, cos bins */
+  double mis_alpha;             /* alpha of Eq. 19                           */
+  uint64_t seed;                /* Philox key                                */
+  uint32_t stream;              /* Philox stream word                        */
+  int32_t sensor_uniform_only;  /* 1: no EDA at the sensor vertex            */
+  uint64_t paths_per_element;   /* N_e, the per-bin weight is n_bins / N_e   */
+} orc_scene;
+
+/* Philox4x32-10 block (Salmon et al., SC'11). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Uniform double in [0,1) from a 32-bit word: (x >> 8) * 2^-24. */
+double orc_u01(uint32_t x);
+
+/* log of the transient diffusion Green's function, Eq. 9. */
+double orc_log_phi(double r, double tprime, double sigma_s, double sigma_a,
+                   double g, double v);
+
+/* Henyey-Greenstein density on the sphere and its inversion sampler. */
+double orc_hg_pdf(double mu, double g);
+double orc_hg_sample(double g, double xi);
+
+/* Polar distance of Eq. 18 / Eq. 21 and the control-vertex density of Eq. 22
+ * (Jacobian-corrected): given S, C and mu, return t; r1 = S - t; p(t). */
+void orc_ellipse(double S, double C, double mu, double* t, double* r1);
+double orc_control_pdf(double pS, double S, double C, double mu, double r1);
+
+/* n-point Gauss-Legendre rule on [-1, 1] by Newton iteration. */
+void orc_gauss_legendre(int n, double* x, double* w);
+
+/* Radical inverse in base 2 of i (van der Corput), the first Sobol dimension. */
+double orc_radical_inverse2(uint32_t i);
+
+/* Elliptical DA direction table (Eq. 16-18): CDF rows [n_rho*n_s][n_mu+1].
+ * Rows are ordered row = i_rho * n_s + i_s. */
+int orc_build_table(const orc_scene* sc, double* cdf);
+/* Unnormalised integral of one mu-bin of one table cell.  mode 0: the fixed
+ * Gauss-Legendre rule of the table; mode 1: adaptive Gauss-Kronrod in both
+ * dimensions (used to pin the fixed rule). */
+double orc_table_bin_integral(const orc_scene* sc, int row, int mu_bin, int mode);
+
+/* Table cell lookup from (C, S_M). */
+int orc_table_row(const orc_scene* sc, double C, double SM, double* margin);
+
+/* Trace `count` paths with ids first .. first+count-1 one by one.
+ * contrib[i]: the path's summed contribution (before the per-bin weight);
+ * bin[i]: the time bin the path is dedicated to (DARTS) or -1;
+ * decisions[i*K*4 + k*4 + j] (optional): per-vertex decision bytes;
+ * margin[i*K + k] (optional): smallest relative distance to a decision
+ * threshold met at vertex k; flags[i] (optional): ORC_FLAG_* bits;
+ * nbounce[i] (optional): vertices visited.  cdf may be NULL for methods
+ * other than DARTS.  Returns 0 on success. */
+int orc_trace_paths(const orc_scene* sc, int method, const double* cdf,
+                    uint64_t first, uint32_t count, double* contrib,
+                    int32_t* bin, uint8_t* decisions, double* margin,
+                    int32_t* flags, int32_t* nbounce);
+
+/* Distance step (Eq. 12-15) of vertex k from an explicit state, for tests:
+ * candidate distances, validity, log RIS weights, selected index (-1 when
+ * the ray escapes or every candidate is invalid) and the throughput factor.
+ * Returns 0 = escape, 1 = moved, 2 = all invalid. */
+int orc_ris_step(const orc_scene* sc, uint64_t id, int k, const double x[3], const double w[3],
+                 double SM, double dm, double* d_out, double* lw_out, int32_t* valid_out,
+                 int32_t* sel_out, double* factor_out);
+
+/* Full histogram render of n_paths paths starting at path id `offset`,
+ * split over n_threads POSIX threads; hist/sumsq are [n_bins] and are
+ * overwritten.  stats (optional, 8 doubles): paths, vertices, connections,
+ * nonempty connections, RIS candidates, early exits, all-invalid stops,
+ * escapes. */
+int orc_render(const orc_scene* sc, int method, const double* cdf,
+               uint64_t n_paths, uint64_t offset, int n_threads,
+               double* hist, double* sumsq, double* stats);
+
+/* Path-replay score of the DARTS estimator (detached sampling):
+ * grad[3] += sum over paths of dLdh[bin] * w_b * sum_v c_v * s_v, with s_v the
+ * derivative of log f w.r.t. (sigma_s, sigma_a, g). */
+int orc_adjoint(const orc_scene* sc, const double* cdf, uint64_t n_paths,
+                uint64_t offset, int n_threads, const double* dLdh,
+                double* grad3, double* grad3_sq);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,164 @@
+"""Scene and sampling descriptions, plus the seeded synthetic workloads.
+
+This module holds plain numbers only: it performs none of the method's
+arithmetic, so both the CUDA library binding and the CPU oracle used by the
+tests can take their inputs from it.
+
+The quantities follow the statement of the problem in the DARTS paper
+(He et al. 2024): a homogeneous medium (sigma_s, sigma_a, Henyey-Greenstein g,
+speed of light v = c/eta inside the medium, Eq. 3 and Eq. 9), pulse emitters
+with start times (Eq. 1, t_e), a sensor, a time gate split into equal bins,
+a path budget and a seed.  Lengths and times share units with v = 1
+(Eq. 3 treats path length and time as interchangeable).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+# Methods (values are the ones of the C-ABI enum darts_method).
+DARTS = 0
+PLAIN_UNIFORM_T = 1
+VANILLA_DIRECT = 2
+METHOD_NAMES = {DARTS: "darts", PLAIN_UNIFORM_T: "plain_uniform_t", VANILLA_DIRECT: "vanilla_direct"}
+
+# Sampling flags (C-ABI DARTS_FLAG_*).
+FLAG_SENSOR_UNIFORM_ONLY = 1 << 0
+FLAG_REBUILD_TABLE = 1 << 1
+
+Vec3 = Tuple[float, float, float]
+
+
+@dataclass
+class Medium:
+    sigma_s: float
+    sigma_a: float
+    g: float
+    v: float = 1.0
+
+
+@dataclass
+class Emitter:
+    pos: Vec3
+    t0: float = 0.0
+    energy: float = 1.0
+
+
+@dataclass
+class Sensor:
+    """Isotropic point fluence detector (one sensor element)."""
+    pos: Vec3
+
+
+@dataclass
+class Gate:
+    t_min: float
+    t_max: float
+    n_bins: int
+
+
+@dataclass
+class Geometry:
+    """Axis-aligned medium box [lo, hi]; no surfaces."""
+    lo: Vec3 = (0.0, 0.0, 0.0)
+    hi: Vec3 = (1.0, 1.0, 1.0)
+
+
+@dataclass
+class Scene:
+    medium: Medium
+    geometry: Geometry
+    emitters: List[Emitter]
+    sensor: Sensor
+    gate: Gate
+
+
+@dataclass
+class Sampling:
+    seed: int = 0
+    paths_per_element: int = 1 << 16
+    max_bounces: int = 50
+    ris_m: int = 8
+    table_n_rho: int = 16
+    table_n_s: int = 8
+    table_n_mu: int = 256
+    mis_alpha: float = 0.5
+    method: int = DARTS
+    flags: int = 0
+    stream: int = 0
+
+
+def slab_scene(sigma_s=1.0, sigma_a=0.01, g=0.7, v=1.0, side=1.0, n_bins=256,
+               t_min=0.8, t_max=6.0) -> Scene:
+    """The medium-only cube of side `side` with emitter and sensor on its axis.
+
+    Emitter at (0.5, 0.5, 0.1)*side, t0 = 0, unit energy; point sensor at
+    (0.5, 0.5, 0.9)*side; gate [t_min, t_max)*side split into n_bins bins.
+    side = 1 with the defaults is the 2^16-path parity workload.
+    """
+    s = float(side)
+    return Scene(
+        medium=Medium(sigma_s, sigma_a, g, v),
+        geometry=Geometry((0.0, 0.0, 0.0), (s, s, s)),
+        emitters=[Emitter((0.5 * s, 0.5 * s, 0.1 * s), 0.0, 1.0)],
+        sensor=Sensor((0.5 * s, 0.5 * s, 0.9 * s)),
+        gate=Gate(t_min * s, t_max * s, n_bins),
+    )
+
+
+def cube_workload(paths: int = 1 << 16, seed: int = 0) -> Tuple[Scene, Sampling]:
+    """Unit cube, sigma_s = 1, sigma_a = 0.01, g = 0.7, 256 bins on [0.8, 6),
+    `paths` paths from `seed`, 50 bounces, 8 RIS candidates, 16x8x256 table."""
+    return slab_scene(), Sampling(seed=seed, paths_per_element=paths)
+
+
+def infinite_scene(sigma_s, sigma_a, g, separation=1.0, n_bins=64, t_min=None,
+                   t_max=None, half_width=1.0e4) -> Scene:
+    """Emitter and sensor `separation` apart inside a box so large that no
+    path reaches its walls within the gate (an infinite medium in practice)."""
+    c = separation
+    t_min = c if t_min is None else t_min
+    t_max = 6.0 * c if t_max is None else t_max
+    h = float(half_width)
+    return Scene(
+        medium=Medium(sigma_s, sigma_a, g, 1.0),
+        geometry=Geometry((-h, -h, -h), (h, h, h)),
+        emitters=[Emitter((0.0, 0.0, 0.0), 0.0, 1.0)],
+        sensor=Sensor((0.0, 0.0, float(c))),
+        gate=Gate(float(t_min), float(t_max), n_bins),
+    )
+
+
+def batched_media(n_media: int = 256, seed: int = 0, n_bins: int = 128,
+                  log2_budget: Tuple[float, float] = (12.0, 20.0)) -> List[Tuple[Scene, Sampling]]:
+    """Independent slab media with uneven path budgets.
+
+    Per medium: sigma_s log-uniform in [0.1, 10], albedo uniform in
+    [0.5, 0.999], g uniform in [-0.3, 0.9], cube side uniform in [0.5, 4],
+    path budget 2^U[12, 20] rounded to an integer; 128 bins.
+    """
+    rs = np.random.default_rng(np.random.SeedSequence([seed, 0x0D47]))
+    out = []
+    for i in range(n_media):
+        sigma_s = float(10.0 ** rs.uniform(-1.0, 1.0))
+        albedo = float(rs.uniform(0.5, 0.999))
+        g = float(rs.uniform(-0.3, 0.9))
+        side = float(rs.uniform(0.5, 4.0))
+        budget = int(round(2.0 ** rs.uniform(*log2_budget)))
+        sigma_a = sigma_s * (1.0 - albedo) / albedo
+        sc = slab_scene(sigma_s, sigma_a, g, 1.0, side, n_bins)
+        sp = Sampling(seed=seed, paths_per_element=budget, stream=i)
+        out.append((sc, sp))
+    return out
+
+
+def with_paths(sp: Sampling, n: int) -> Sampling:
+    return replace(sp, paths_per_element=int(n))
+
+
+def total_paths(sc: Scene, sp: Sampling) -> int:
+    """Number of paths one render call traces (one sensor element)."""
+    return int(sp.paths_per_element)
