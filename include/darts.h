@@ -1,0 +1,229 @@
+/*
+ * darts.h -- C ABI of libdarts: GB300 (sm_103a) DARTS transient path tracing.
+ *
+ * DARTS (He, Du, Jiang, Jin, "Diffusion Approximated Residual Time Sampling
+ * for Time-of-flight Rendering in Homogeneous Scattering Media", 2024) traces
+ * paths from a sensor through a homogeneous medium.  Each path:
+ *   - samples free-path distances by resampled importance sampling with the
+ *     transient diffusion approximation as target (Sec. 4, Eq. 9-15);
+ *   - samples directions from the tabulated elliptical DA distribution by
+ *     inverse CDF, mixed with phase sampling by one-sample MIS (Sec. 5.1,
+ *     Eq. 16-19);
+ *   - connects every vertex to the emitter through an elliptical control
+ *     vertex whose total path length lies in the path's time bin (Sec. 5.2,
+ *     Eq. 18-22);
+ *   - adds its contribution to a per-pixel time-bin histogram (Eq. 1, Eq. 4).
+ *
+ * Conventions
+ *   - Plain C types only.  Pointers named *_dev are CUDA device pointers
+ *     (cudaMalloc / torch CUDA tensors on the context's device); *_host are
+ *     host pointers.  The caller owns every buffer it passes.
+ *   - Calls are asynchronous and ordered on the context's stream unless
+ *     stated otherwise.  Errors found on the device (non-finite values,
+ *     bounded waits that expired) are reported by darts_sync().
+ *   - Lengths and times share units: a path of length l takes l / v time
+ *     (Eq. 3, v = c / eta).  Histogram bins hold time-integrated fluence per
+ *     unit emitted energy (not a rate: divide by the bin width for one).
+ *   - Functions never throw; they return a darts_status.  The message of the
+ *     last failure on a context is available from darts_last_error().
+ */
+#ifndef DARTS_H
+#define DARTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DARTS_OK = 0,
+  DARTS_ERR_INVALID_ARG = 1, /* a parameter outside its domain or a NULL required pointer */
+  DARTS_ERR_CUDA = 2,        /* a CUDA runtime call failed                               */
+  DARTS_ERR_OOM = 3,         /* device memory could not be allocated                     */
+  DARTS_ERR_NUMERIC = 4,     /* a kernel produced a non-finite contribution              */
+  DARTS_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired                       */
+  DARTS_ERR_UNSUPPORTED = 6  /* a feature this build does not implement                  */
+} darts_status;
+
+typedef enum {
+  DARTS_METHOD_DARTS = 0,           /* Sec. 4-5: DA-RIS distance, EDA+MIS direction, ellipse */
+  DARTS_METHOD_PLAIN_UNIFORM_T = 1, /* Eq. 21 with uniform P (Jarabo et al.): uniform
+                                       temporal control vertex, free flight, HG      */
+  DARTS_METHOD_VANILLA_DIRECT = 2   /* Sec. 5.2 "vanilla": direct shadow connections  */
+} darts_method;
+
+/* sampling.flags */
+#define DARTS_FLAG_SENSOR_UNIFORM_ONLY (1u << 0) /* no EDA at the sensor vertex        */
+#define DARTS_FLAG_REBUILD_TABLE (1u << 1)       /* rebuild the direction table even on a cache hit */
+
+typedef struct darts_ctx darts_ctx;
+
+/* Homogeneous medium (Eq. 9): scattering and absorption coefficients,
+ * Henyey-Greenstein anisotropy g (|g| < 1), speed of light v = c/eta. */
+typedef struct {
+  double sigma_s, sigma_a, g, v;
+} darts_medium;
+
+/* Isotropic point pulse emitter (Eq. 1: L_e with start time t_e). */
+typedef struct {
+  double pos[3];
+  double t0;     /* start time of the pulse */
+  double energy; /* emitted energy; radiant intensity energy / (4 pi) */
+} darts_emitter;
+
+/* Isotropic point fluence sensor (one sensor element). */
+typedef struct {
+  double pos[3];
+} darts_sensor;
+
+/* Time gate [t_min, t_max) in n_bins equal bins. */
+typedef struct {
+  double t_min, t_max;
+  int32_t n_bins;
+} darts_gate;
+
+/* The medium fills the axis-aligned box [lo, hi]; there are no surfaces. */
+typedef struct {
+  double lo[3], hi[3];
+} darts_geometry;
+
+typedef struct {
+  darts_medium medium;
+  darts_geometry geom;
+  const darts_emitter* emitters; /* host array; this build supports n_emitters == 1 */
+  int32_t n_emitters;
+  darts_sensor sensor;
+  darts_gate gate;
+} darts_scene;
+
+typedef struct {
+  uint64_t seed;              /* Philox key                                           */
+  uint64_t paths_per_element; /* path budget N_e of this call (>= 0)                  */
+  int32_t max_bounces;        /* K: scattering vertices per path incl. the control vertex, 1..1024 */
+  int32_t ris_m;              /* RIS candidates N_RIS (Eq. 15), 1..32; 8 in the paper */
+  int32_t table_n_rho;        /* direction table: C/S cells (Sec. 5.1), >= 1          */
+  int32_t table_n_s;          /* direction table: S cells (octaves below S_max), >= 1 */
+  int32_t table_n_mu;         /* direction table: cos-theta bins, 2..1024; 256 in the paper */
+  double mis_alpha;           /* alpha of Eq. 19, > 0; 0.5 in the paper               */
+  int32_t method;             /* darts_method                                         */
+  uint32_t flags;             /* DARTS_FLAG_*                                         */
+  uint32_t stream;            /* Philox stream word (independent sub-streams)         */
+} darts_sampling;
+
+/* Optional per-path probe of darts_render: for the paths with local index
+ * first, first + stride, ... (count of them, local index = path id minus
+ * path_offset) the kernel writes the path's unweighted contribution and its
+ * bin.  Lets callers check sampled paths of a full-size launch. */
+typedef struct {
+  uint64_t first;
+  uint64_t stride; /* >= 1 */
+  uint32_t count;
+  float* contrib_dev;  /* [count] */
+  int32_t* bin_dev;    /* [count] */
+} darts_probe;
+
+/* Counters of the last darts_render on a context. */
+typedef struct {
+  uint64_t paths;
+  uint64_t vertices;             /* path vertices visited                          */
+  uint64_t connections_nonempty; /* control vertices sampled                       */
+  uint64_t distance_steps;       /* RIS distance steps (each evaluates ris_m candidates) */
+  uint64_t early_exits;          /* Sec. 5.2 residual-bound terminations          */
+  uint64_t all_invalid;          /* RIS steps whose candidates were all non-causal */
+  uint64_t escapes;              /* rays that left the medium                      */
+  uint64_t fp64_ellipse;         /* near-degenerate ellipse solves done in FP64     */
+  uint64_t fp64_phi;             /* small-t' DA exponents done in FP64              */
+} darts_stats;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `cuda_device`; `cuda_stream` is a
+ * cudaStream_t (NULL = the legacy default stream).  Allocates the context's
+ * scratch (counters, status word, block partials).  *out is NULL on error. */
+darts_status darts_create(darts_ctx** out, int cuda_device, void* cuda_stream);
+
+/* Release the context and its device memory (waits for its stream). */
+darts_status darts_destroy(darts_ctx* ctx);
+
+/* Change the stream later calls are ordered on. */
+darts_status darts_set_stream(darts_ctx* ctx, void* cuda_stream);
+
+/* Static, never-NULL description of a status code. */
+const char* darts_status_string(darts_status s);
+
+/* Copy the last error message of ctx (NUL-terminated, truncated to n). */
+darts_status darts_last_error(const darts_ctx* ctx, char* buf, size_t n);
+
+/* Wait for the context's stream and report device-side errors recorded by
+ * earlier kernels (DARTS_ERR_NUMERIC, DARTS_ERR_TIMEOUT); clears them. */
+darts_status darts_sync(darts_ctx* ctx);
+
+/* ---- the hot path ------------------------------------------------------- */
+
+/* Build the elliptical DA direction table (Sec. 5.1, Eq. 16-18) of the
+ * scene's medium and gate on the GPU: rows = table_n_rho * table_n_s
+ * conditioning cells (C/S uniform on [0,1); S log-spaced over 8 octaves below
+ * S_max = v (t_max - t0)), each a normalised CDF over table_n_mu equal
+ * cos-theta bins of [-1, 1].  Output cdf_dev: float [rows][row_stride] with
+ * row_stride = table_n_mu + 1 rounded up to a multiple of 4; entry j < n_mu+1
+ * is the CDF at the j-th bin edge (0 ... 1).  Caller-owned, overwritten. */
+darts_status darts_build_table(darts_ctx* ctx, const darts_scene* scene,
+                               const darts_sampling* sampling, float* cdf_dev);
+
+/* Row stride (floats) of the table written by darts_build_table. */
+int32_t darts_table_row_stride(int32_t table_n_mu);
+
+/* Render sampling->paths_per_element paths with ids path_offset .. +N-1 and
+ * write the histogram estimate hist_dev[n_bins] (double, overwritten):
+ * DARTS dedicates each path to one bin (Sec. 6.2) and weights it by
+ * n_bins / N; the baselines bin each contribution by its time and weight it
+ * by 1 / N.  sumsq_dev (optional, [n_bins]) receives the sum over paths of
+ * the squared weighted per-path bin contribution (for standard errors).
+ * Builds the direction table first when the context's cache misses.
+ * probe may be NULL. */
+darts_status darts_render(darts_ctx* ctx, const darts_scene* scene,
+                          const darts_sampling* sampling, double* hist_dev,
+                          double* sumsq_dev, uint64_t path_offset,
+                          const darts_probe* probe);
+
+/* darts_render into HOST buffers: the histogram (and optional sums of
+ * squares) are copied back and the stream is synchronised before return. */
+darts_status darts_render_host(darts_ctx* ctx, const darts_scene* scene,
+                               const darts_sampling* sampling, double* hist_host,
+                               double* sumsq_host, uint64_t path_offset);
+
+/* Counters of the last render on this context (synchronises the stream). */
+darts_status darts_get_stats(darts_ctx* ctx, darts_stats* out);
+
+/* Kernel timing: when enabled, every darts_render records a pair of CUDA
+ * events on the context's stream immediately around the path kernel launch
+ * (the direction-table kernel and the small scratch resets are outside).
+ * darts_last_kernel_ms() synchronises on the stop event and returns the
+ * elapsed time of the most recent path kernel in milliseconds. */
+darts_status darts_set_kernel_timing(darts_ctx* ctx, int enable);
+darts_status darts_last_kernel_ms(darts_ctx* ctx, float* ms);
+
+/* ---- checking ------------------------------------------------------------ */
+
+/* Trace paths first .. first+count-1 one per thread-slot of the render kernel
+ * and record, per path: the unweighted contribution, the bin, the number of
+ * vertices visited and four decision bytes per vertex
+ * [event | nonempty<<4, RIS index, MIS choice, cos bin] in
+ * decisions_dev[count][max_bounces][4] (0xFF = not taken).  Any output may be
+ * NULL.  Uses the same kernel code as darts_render. */
+darts_status darts_debug_paths(darts_ctx* ctx, const darts_scene* scene,
+                               const darts_sampling* sampling, uint64_t first,
+                               uint32_t count, float* contrib_dev, int32_t* bin_dev,
+                               int32_t* nvert_dev, uint8_t* decisions_dev);
+
+/* Philox4x32-10 blocks of the library's generator: out_dev[i*4..i*4+3] for
+ * counter ctr_dev[i*4..i*4+3] and key (seed lo, seed hi); n blocks. */
+darts_status darts_debug_philox(darts_ctx* ctx, const uint32_t* ctr_dev, uint64_t seed,
+                                uint32_t n, uint32_t* out_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DARTS_H */

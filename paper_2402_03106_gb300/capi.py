@@ -1,0 +1,337 @@
+"""Thin ctypes binding of libdarts (include/darts.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Device memory and streams come from PyTorch.  The functions named
+``darts_*`` mirror the C entry points one to one; ``Context`` and the
+helpers below them allocate output tensors and convert the scene objects of
+``scenes.py`` into the C structs.
+
+The library is loaded from this package's directory; when it is missing the
+import of this module still works but every call raises, so no path can
+fall back silently to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import torch
+
+from . import scenes as S
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdarts.so")
+
+DARTS_OK = 0
+STATUS_NAMES = {0: "DARTS_OK", 1: "DARTS_ERR_INVALID_ARG", 2: "DARTS_ERR_CUDA", 3: "DARTS_ERR_OOM",
+                4: "DARTS_ERR_NUMERIC", 5: "DARTS_ERR_TIMEOUT", 6: "DARTS_ERR_UNSUPPORTED"}
+
+EXPORTED = ("darts_create", "darts_destroy", "darts_set_stream", "darts_status_string",
+            "darts_last_error", "darts_sync", "darts_build_table", "darts_table_row_stride",
+            "darts_render", "darts_render_host", "darts_get_stats", "darts_debug_paths",
+            "darts_debug_philox", "darts_set_kernel_timing", "darts_last_kernel_ms")
+
+
+class DartsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class darts_medium(C.Structure):
+    _fields_ = [("sigma_s", C.c_double), ("sigma_a", C.c_double), ("g", C.c_double), ("v", C.c_double)]
+
+
+class darts_emitter(C.Structure):
+    _fields_ = [("pos", C.c_double * 3), ("t0", C.c_double), ("energy", C.c_double)]
+
+
+class darts_sensor(C.Structure):
+    _fields_ = [("pos", C.c_double * 3)]
+
+
+class darts_gate(C.Structure):
+    _fields_ = [("t_min", C.c_double), ("t_max", C.c_double), ("n_bins", C.c_int32)]
+
+
+class darts_geometry(C.Structure):
+    _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3)]
+
+
+class darts_scene(C.Structure):
+    _fields_ = [("medium", darts_medium), ("geom", darts_geometry),
+                ("emitters", C.POINTER(darts_emitter)), ("n_emitters", C.c_int32),
+                ("sensor", darts_sensor), ("gate", darts_gate)]
+
+
+class darts_sampling(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("paths_per_element", C.c_uint64),
+                ("max_bounces", C.c_int32), ("ris_m", C.c_int32),
+                ("table_n_rho", C.c_int32), ("table_n_s", C.c_int32), ("table_n_mu", C.c_int32),
+                ("mis_alpha", C.c_double), ("method", C.c_int32), ("flags", C.c_uint32),
+                ("stream", C.c_uint32)]
+
+
+class darts_probe(C.Structure):
+    _fields_ = [("first", C.c_uint64), ("stride", C.c_uint64), ("count", C.c_uint32),
+                ("contrib_dev", C.c_void_p), ("bin_dev", C.c_void_p)]
+
+
+class darts_stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in (
+        "paths", "vertices", "connections_nonempty", "distance_steps", "early_exits",
+        "all_invalid", "escapes", "fp64_ellipse", "fp64_phi")]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH):
+    """Load libdarts.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = C.CDLL(path)
+        vp, st = C.c_void_p, C.c_int
+        sc_p, sp_p = C.POINTER(darts_scene), C.POINTER(darts_sampling)
+        lib.darts_create.argtypes = [C.POINTER(vp), C.c_int, vp]
+        lib.darts_destroy.argtypes = [vp]
+        lib.darts_set_stream.argtypes = [vp, vp]
+        lib.darts_status_string.argtypes = [st]
+        lib.darts_status_string.restype = C.c_char_p
+        lib.darts_last_error.argtypes = [vp, C.c_char_p, C.c_size_t]
+        lib.darts_sync.argtypes = [vp]
+        lib.darts_build_table.argtypes = [vp, sc_p, sp_p, vp]
+        lib.darts_table_row_stride.argtypes = [C.c_int32]
+        lib.darts_table_row_stride.restype = C.c_int32
+        lib.darts_render.argtypes = [vp, sc_p, sp_p, vp, vp, C.c_uint64, C.POINTER(darts_probe)]
+        lib.darts_render_host.argtypes = [vp, sc_p, sp_p, vp, vp, C.c_uint64]
+        lib.darts_get_stats.argtypes = [vp, C.POINTER(darts_stats)]
+        lib.darts_debug_paths.argtypes = [vp, sc_p, sp_p, C.c_uint64, C.c_uint32, vp, vp, vp, vp]
+        lib.darts_debug_philox.argtypes = [vp, vp, C.c_uint64, C.c_uint32, vp]
+        lib.darts_set_kernel_timing.argtypes = [vp, C.c_int]
+        lib.darts_last_kernel_ms.argtypes = [vp, C.POINTER(C.c_float)]
+        for name in EXPORTED:
+            if name not in ("darts_status_string", "darts_table_row_stride"):
+                getattr(lib, name).restype = st
+        _lib = lib
+        return lib
+
+
+# ----------------------------------------------------------------------------
+# Scene conversion
+# ----------------------------------------------------------------------------
+def to_c_scene(scene: S.Scene):
+    """Return (darts_scene, keepalive) for a scenes.Scene."""
+    n = len(scene.emitters)
+    arr = (darts_emitter * max(n, 1))()
+    for i, e in enumerate(scene.emitters):
+        arr[i].pos[:] = [float(x) for x in e.pos]
+        arr[i].t0 = float(e.t0)
+        arr[i].energy = float(e.energy)
+    cs = darts_scene()
+    m = scene.medium
+    cs.medium = darts_medium(float(m.sigma_s), float(m.sigma_a), float(m.g), float(m.v))
+    cs.geom.lo[:] = [float(x) for x in scene.geometry.lo]
+    cs.geom.hi[:] = [float(x) for x in scene.geometry.hi]
+    cs.emitters = C.cast(arr, C.POINTER(darts_emitter))
+    cs.n_emitters = n
+    cs.sensor.pos[:] = [float(x) for x in scene.sensor.pos]
+    cs.gate = darts_gate(float(scene.gate.t_min), float(scene.gate.t_max), int(scene.gate.n_bins))
+    return cs, arr
+
+
+def to_c_sampling(sp: S.Sampling) -> darts_sampling:
+    c = darts_sampling()
+    c.seed = int(sp.seed) & 0xFFFFFFFFFFFFFFFF
+    c.paths_per_element = int(sp.paths_per_element)
+    c.max_bounces = int(sp.max_bounces)
+    c.ris_m = int(sp.ris_m)
+    c.table_n_rho, c.table_n_s, c.table_n_mu = int(sp.table_n_rho), int(sp.table_n_s), int(sp.table_n_mu)
+    c.mis_alpha = float(sp.mis_alpha)
+    c.method = int(sp.method)
+    c.flags = int(sp.flags)
+    c.stream = int(sp.stream) & 0xFFFFFFFF
+    return c
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+# ----------------------------------------------------------------------------
+# One-to-one wrappers of the C entry points
+# ----------------------------------------------------------------------------
+def _check(ctx_handle, status: int):
+    if status != DARTS_OK:
+        lib = load()
+        msg = C.create_string_buffer(512)
+        if ctx_handle:
+            lib.darts_last_error(ctx_handle, msg, 512)
+        raise DartsError(status, msg.value.decode() or lib.darts_status_string(status).decode())
+
+
+def darts_create(device: int = 0, stream=None):
+    h = C.c_void_p()
+    _check(None, load().darts_create(C.byref(h), int(device), stream))
+    return h
+
+
+def darts_destroy(h):
+    _check(None, load().darts_destroy(h))
+
+
+def darts_set_stream(h, stream):
+    _check(h, load().darts_set_stream(h, stream))
+
+
+def darts_sync(h):
+    _check(h, load().darts_sync(h))
+
+
+def darts_table_row_stride(n_mu: int) -> int:
+    return int(load().darts_table_row_stride(int(n_mu)))
+
+
+def darts_build_table(h, scene, sampling, cdf: torch.Tensor):
+    cs, keep = to_c_scene(scene)
+    _check(h, load().darts_build_table(h, C.byref(cs), C.byref(to_c_sampling(sampling)), _ptr(cdf)))
+
+
+def darts_render(h, scene, sampling, hist: torch.Tensor, sumsq: Optional[torch.Tensor] = None,
+                 path_offset: int = 0, probe: Optional[darts_probe] = None):
+    cs, keep = to_c_scene(scene)
+    _check(h, load().darts_render(h, C.byref(cs), C.byref(to_c_sampling(sampling)), _ptr(hist),
+                                  _ptr(sumsq), int(path_offset),
+                                  C.byref(probe) if probe is not None else None))
+
+
+def darts_render_host(h, scene, sampling, hist_host: torch.Tensor,
+                      sumsq_host: Optional[torch.Tensor] = None, path_offset: int = 0):
+    cs, keep = to_c_scene(scene)
+    _check(h, load().darts_render_host(h, C.byref(cs), C.byref(to_c_sampling(sampling)),
+                                       _ptr(hist_host), _ptr(sumsq_host), int(path_offset)))
+
+
+def darts_get_stats(h) -> dict:
+    st = darts_stats()
+    _check(h, load().darts_get_stats(h, C.byref(st)))
+    return {n: int(getattr(st, n)) for n, _ in darts_stats._fields_}
+
+
+def darts_debug_paths(h, scene, sampling, first, count, contrib, bins, nvert, decisions):
+    cs, keep = to_c_scene(scene)
+    _check(h, load().darts_debug_paths(h, C.byref(cs), C.byref(to_c_sampling(sampling)),
+                                       int(first), int(count), _ptr(contrib), _ptr(bins),
+                                       _ptr(nvert), _ptr(decisions)))
+
+
+def darts_debug_philox(h, ctr: torch.Tensor, seed: int, out: torch.Tensor):
+    _check(h, load().darts_debug_philox(h, _ptr(ctr), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                        int(ctr.numel() // 4), _ptr(out)))
+
+
+def darts_set_kernel_timing(h, enable: bool):
+    _check(h, load().darts_set_kernel_timing(h, 1 if enable else 0))
+
+
+def darts_last_kernel_ms(h) -> float:
+    ms = C.c_float()
+    _check(h, load().darts_last_kernel_ms(h, C.byref(ms)))
+    return float(ms.value)
+
+
+# ----------------------------------------------------------------------------
+# Convenience layer
+# ----------------------------------------------------------------------------
+class Context:
+    """A libdarts context on one CUDA device, ordered on a torch stream."""
+
+    def __init__(self, device: int = 0, stream: Optional[torch.cuda.Stream] = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libdarts needs a CUDA device")
+        self.device = int(device)
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        self.h = darts_create(self.device, C.c_void_p(self.stream.cuda_stream))
+
+    def close(self):
+        if self.h:
+            darts_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self.stream = stream
+        darts_set_stream(self.h, C.c_void_p(stream.cuda_stream))
+
+    def sync(self):
+        darts_sync(self.h)
+
+    def _dev(self):
+        return torch.device("cuda", self.device)
+
+    def render(self, scene, sampling, sumsq: bool = False, path_offset: int = 0,
+               out: Optional[torch.Tensor] = None, probe: Optional[darts_probe] = None):
+        B = scene.gate.n_bins
+        hist = out if out is not None else torch.empty(B, dtype=torch.float64, device=self._dev())
+        sq = torch.empty(B, dtype=torch.float64, device=self._dev()) if sumsq else None
+        darts_render(self.h, scene, sampling, hist, sq, path_offset, probe)
+        return (hist, sq) if sumsq else hist
+
+    def render_host(self, scene, sampling, hist_host: torch.Tensor,
+                    sumsq_host: Optional[torch.Tensor] = None, path_offset: int = 0):
+        darts_render_host(self.h, scene, sampling, hist_host, sumsq_host, path_offset)
+        return hist_host
+
+    def build_table(self, scene, sampling) -> torch.Tensor:
+        rows = sampling.table_n_rho * sampling.table_n_s
+        stride = darts_table_row_stride(sampling.table_n_mu)
+        cdf = torch.empty(rows, stride, dtype=torch.float32, device=self._dev())
+        darts_build_table(self.h, scene, sampling, cdf)
+        return cdf
+
+    def set_kernel_timing(self, enable: bool):
+        darts_set_kernel_timing(self.h, enable)
+
+    def last_kernel_ms(self) -> float:
+        return darts_last_kernel_ms(self.h)
+
+    def stats(self) -> dict:
+        return darts_get_stats(self.h)
+
+    def debug_paths(self, scene, sampling, first: int, count: int) -> dict:
+        dev = self._dev()
+        K = sampling.max_bounces
+        out = dict(contrib=torch.zeros(count, dtype=torch.float32, device=dev),
+                   bin=torch.zeros(count, dtype=torch.int32, device=dev),
+                   nvert=torch.zeros(count, dtype=torch.int32, device=dev),
+                   decisions=torch.zeros(count, K, 4, dtype=torch.uint8, device=dev))
+        darts_debug_paths(self.h, scene, sampling, first, count, out["contrib"], out["bin"],
+                          out["nvert"], out["decisions"])
+        return out
+
+    def probe(self, first: int, stride: int, count: int):
+        dev = self._dev()
+        c = torch.zeros(count, dtype=torch.float32, device=dev)
+        b = torch.full((count,), -1, dtype=torch.int32, device=dev)
+        p = darts_probe(int(first), int(stride), int(count), c.data_ptr(), b.data_ptr())
+        return p, c, b
+
+    def philox(self, ctr, seed: int) -> torch.Tensor:
+        ctr = torch.as_tensor(ctr, dtype=torch.int64).reshape(-1).to(torch.uint32)
+        ctr = ctr.to(self._dev())
+        out = torch.zeros_like(ctr)
+        darts_debug_philox(self.h, ctr, seed, out)
+        return out

@@ -1,0 +1,537 @@
+// capi.cu -- host side of libdarts: contexts, validation, the table cache and
+// the C entry points declared in include/darts.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "darts.h"
+#include "darts_device.cuh"
+#include "darts_internal.h"
+
+using namespace darts;
+
+struct darts_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  int smem_optin = 0;
+  // scratch: [0] path counter, [1] ticket|status, [2 .. 2+kStatCount) stats
+  unsigned long long* scratch = nullptr;
+  double* partials = nullptr;  // block partials, grown on demand
+  size_t partials_bytes = 0;
+  double* acc = nullptr;       // global accumulator (no-tile mode)
+  size_t acc_bytes = 0;
+  double* host_hist = nullptr; // device histogram for darts_render_host
+  size_t host_hist_bytes = 0;
+  // direction-table cache
+  float* table = nullptr;
+  size_t table_bytes = 0;
+  bool table_valid = false;
+  double table_key[9] = {0};
+  // launch shape
+  int block = 512;
+  // kernel timing
+  bool timing = false;
+  bool timed = false;
+  cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+  char err[512] = {0};
+};
+
+namespace {
+
+darts_status fail(darts_ctx* c, darts_status s, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return s;
+}
+
+darts_status cuda_fail(darts_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) return fail(c, DARTS_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(c, DARTS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                              \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+  } while (0)
+
+// Grow a device buffer to at least `bytes`.
+cudaError_t ensure(void** ptr, size_t* cap, size_t bytes) {
+  if (*cap >= bytes && *ptr) return cudaSuccess;
+  if (*ptr) cudaFree(*ptr);
+  *ptr = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e == cudaSuccess) *cap = bytes;
+  return e;
+}
+
+// n-point Gauss-Legendre nodes/weights on [-1, 1]: Newton iteration on the
+// three-term recurrence of the Legendre polynomials.
+void gauss_legendre(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), pp = 1.0;
+    for (int it = 0; it < 64; ++it) {
+      double p1 = 1.0, p2 = 0.0;
+      for (int j = 1; j <= n; ++j) {
+        const double p3 = p2;
+        p2 = p1;
+        p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+      }
+      pp = n * (z * p1 - p2) / (z * z - 1.0);
+      const double z1 = z;
+      z = z1 - p1 / pp;
+      if (std::fabs(z - z1) < 1e-15) break;
+    }
+    x[i] = -z;
+    w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+  }
+}
+
+int row_stride_of(int n_mu) { return ((n_mu + 1) + 3) / 4 * 4; }
+
+darts_status validate(darts_ctx* ctx, const darts_scene* sc, const darts_sampling* sp) {
+  if (!sc || !sp) return fail(ctx, DARTS_ERR_INVALID_ARG, "scene and sampling must not be NULL");
+  const darts_medium& m = sc->medium;
+  if (!(m.sigma_s >= 0.0) || !(m.sigma_a >= 0.0) || !(m.sigma_s + m.sigma_a > 0.0))
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "need sigma_s >= 0, sigma_a >= 0, sigma_t > 0");
+  if (!(std::fabs(m.g) < 1.0)) return fail(ctx, DARTS_ERR_INVALID_ARG, "need |g| < 1");
+  if (!(m.v > 0.0) || !std::isfinite(m.v)) return fail(ctx, DARTS_ERR_INVALID_ARG, "need v > 0");
+  if (sc->gate.n_bins < 1) return fail(ctx, DARTS_ERR_INVALID_ARG, "need n_bins >= 1");
+  if (!(sc->gate.t_max > sc->gate.t_min)) return fail(ctx, DARTS_ERR_INVALID_ARG, "need t_max > t_min");
+  for (int i = 0; i < 3; ++i)
+    if (!(sc->geom.hi[i] > sc->geom.lo[i])) return fail(ctx, DARTS_ERR_INVALID_ARG, "empty medium box");
+  if (sc->n_emitters < 1 || !sc->emitters) return fail(ctx, DARTS_ERR_INVALID_ARG, "need an emitter");
+  if (sc->n_emitters != 1) return fail(ctx, DARTS_ERR_UNSUPPORTED, "this build supports one emitter");
+  const darts_emitter& e = sc->emitters[0];
+  if (!(e.energy >= 0.0) || !std::isfinite(e.t0)) return fail(ctx, DARTS_ERR_INVALID_ARG, "bad emitter");
+  for (int i = 0; i < 3; ++i) {
+    if (!(e.pos[i] >= sc->geom.lo[i] && e.pos[i] <= sc->geom.hi[i]))
+      return fail(ctx, DARTS_ERR_INVALID_ARG, "emitter outside the medium box");
+    if (!(sc->sensor.pos[i] >= sc->geom.lo[i] && sc->sensor.pos[i] <= sc->geom.hi[i]))
+      return fail(ctx, DARTS_ERR_INVALID_ARG, "sensor outside the medium box");
+  }
+  if (!(sc->gate.t_max > e.t0)) return fail(ctx, DARTS_ERR_INVALID_ARG, "gate ends before the pulse");
+  if (sp->max_bounces < 1 || sp->max_bounces > 1024)
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "max_bounces must be in 1..1024");
+  if (sp->ris_m < 1 || sp->ris_m > trace_max_m())
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "ris_m must be in 1..%d", trace_max_m());
+  if (sp->table_n_rho < 1 || sp->table_n_s < 1 || sp->table_n_mu < 2 || sp->table_n_mu > 1024)
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "table dims: n_rho >= 1, n_s >= 1, 2 <= n_mu <= 1024");
+  if (!(sp->mis_alpha > 0.0) || !std::isfinite(sp->mis_alpha))
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "mis_alpha must be > 0");
+  if (sp->method < DARTS_METHOD_DARTS || sp->method > DARTS_METHOD_VANILLA_DIRECT)
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "unknown method %d", sp->method);
+  return DARTS_OK;
+}
+
+void make_table_params(const darts_scene* sc, const darts_sampling* sp, TableParams* tp) {
+  const darts_medium& m = sc->medium;
+  const double D = 1.0 / (3.0 * (m.sigma_a + m.sigma_s * (1.0 - m.g)));
+  tp->sigma_t = (float)(m.sigma_s + m.sigma_a);
+  tp->sigma_a = (float)m.sigma_a;
+  tp->v = (float)m.v;
+  tp->phi_k0 = (float)(std::log(m.v) - 1.5 * std::log(4.0 * M_PI * m.v * D));
+  tp->phi_invk = (float)(1.0 / (4.0 * m.v * D));
+  tp->sa_v = (float)(m.sigma_a * m.v);
+  tp->smax = (float)(m.v * (sc->gate.t_max - sc->emitters[0].t0));
+  tp->n_rho = sp->table_n_rho;
+  tp->n_s = sp->table_n_s;
+  tp->n_mu = sp->table_n_mu;
+  tp->row_stride = row_stride_of(sp->table_n_mu);
+  double x[kMaxTabTNodes], w[kMaxTabTNodes];
+  gauss_legendre(kMaxTabMuNodes, x, w);
+  for (int i = 0; i < kMaxTabMuNodes; ++i) {
+    tp->mu_x[i] = (float)x[i];
+    tp->mu_w[i] = (float)w[i];
+  }
+  gauss_legendre(kMaxTabTNodes, x, w);
+  for (int i = 0; i < kMaxTabTNodes; ++i) {
+    tp->t_x[i] = (float)x[i];
+    tp->t_w[i] = (float)w[i];
+  }
+}
+
+void table_key(const darts_scene* sc, const darts_sampling* sp, double key[9]) {
+  key[0] = sc->medium.sigma_s;
+  key[1] = sc->medium.sigma_a;
+  key[2] = sc->medium.g;
+  key[3] = sc->medium.v;
+  key[4] = sc->gate.t_max - sc->emitters[0].t0;
+  key[5] = sp->table_n_rho;
+  key[6] = sp->table_n_s;
+  key[7] = sp->table_n_mu;
+  key[8] = 1.0;
+}
+
+// Build (or reuse) the context's cached table for this scene.
+darts_status ensure_table(darts_ctx* ctx, const darts_scene* sc, const darts_sampling* sp) {
+  double key[9];
+  table_key(sc, sp, key);
+  const bool hit = ctx->table_valid && std::memcmp(key, ctx->table_key, sizeof(key)) == 0 &&
+                   !(sp->flags & DARTS_FLAG_REBUILD_TABLE);
+  if (hit) return DARTS_OK;
+  TableParams tp;
+  make_table_params(sc, sp, &tp);
+  const size_t bytes = (size_t)tp.n_rho * tp.n_s * tp.row_stride * sizeof(float);
+  CK(ensure((void**)&ctx->table, &ctx->table_bytes, bytes), "table allocation");
+  tp.cdf = ctx->table;
+  CK(launch_table(tp, ctx->stream), "table kernel launch");
+  std::memcpy(ctx->table_key, key, sizeof(key));
+  ctx->table_valid = true;
+  return DARTS_OK;
+}
+
+void make_trace_params(darts_ctx* ctx, const darts_scene* sc, const darts_sampling* sp,
+                       TraceParams* P) {
+  std::memset(P, 0, sizeof(*P));
+  const darts_medium& m = sc->medium;
+  const darts_emitter& e = sc->emitters[0];
+  const double st = m.sigma_s + m.sigma_a;
+  const double D = 1.0 / (3.0 * (m.sigma_a + m.sigma_s * (1.0 - m.g)));
+  P->sigma_s = (float)m.sigma_s;
+  P->sigma_t = (float)st;
+  P->albedo = (float)(m.sigma_s / st);
+  P->sa_v = (float)(m.sigma_a * m.v);
+  P->v = (float)m.v;
+  P->inv_v = (float)(1.0 / m.v);
+  P->phi_k0_d = std::log(m.v) - 1.5 * std::log(4.0 * M_PI * m.v * D);
+  P->phi_invk_d = 1.0 / (4.0 * m.v * D);
+  P->sa_v_d = m.sigma_a * m.v;
+  P->inv_v_d = 1.0 / m.v;
+  P->phi_k0 = (float)P->phi_k0_d;
+  P->phi_invk = (float)P->phi_invk_d;
+  P->g = (float)m.g;
+  P->hg_a = (float)((1.0 - m.g * m.g) / (4.0 * M_PI));
+  P->hg_b = (float)(1.0 + m.g * m.g);
+  P->hg_c = (float)(2.0 * m.g);
+  for (int i = 0; i < 3; ++i) {
+    P->lo[i] = (float)sc->geom.lo[i];
+    P->hi[i] = (float)sc->geom.hi[i];
+    P->xe[i] = (float)e.pos[i];
+    P->xs[i] = (float)sc->sensor.pos[i];
+  }
+  P->Ie = (float)(e.energy / (4.0 * M_PI));
+  const darts_gate& G = sc->gate;
+  P->n_bins = G.n_bins;
+  P->S_gate_lo = (float)(m.v * (G.t_min - e.t0));
+  P->S_gate_hi = (float)(m.v * (G.t_max - e.t0));
+  P->S_bin = (float)(m.v * (G.t_max - G.t_min) / G.n_bins);
+  P->inv_S_bin = (float)(G.n_bins / (m.v * (G.t_max - G.t_min)));
+  P->tiny_s = (float)(m.v * (G.t_max - G.t_min) / 64.0);
+  P->n_rho = sp->table_n_rho;
+  P->n_s = sp->table_n_s;
+  P->n_mu = sp->table_n_mu;
+  P->row_stride = row_stride_of(sp->table_n_mu);
+  P->rows = sp->table_n_rho * sp->table_n_s;
+  P->inv_smax = (float)(1.0 / (m.v * (G.t_max - e.t0)));
+  P->n_s_over_8 = (float)(sp->table_n_s / 8.0);
+  P->mu_scale = (float)(sp->table_n_mu / 2.0);
+  P->mis_alpha = (float)sp->mis_alpha;
+  P->uniform_sensor = (sp->flags & DARTS_FLAG_SENSOR_UNIFORM_ONLY) ? 1 : 0;
+  P->table = ctx->table;
+  P->K = sp->max_bounces;
+  P->M = sp->ris_m;
+  P->key0 = (uint32_t)sp->seed;
+  P->key1 = (uint32_t)(sp->seed >> 32);
+  P->stream = sp->stream;
+  // bin offset of the (single) sensor element: Philox at the element counter
+  const U4 r = philox4x32_10(0u, 0u, sp->stream, (kVertexElement << 8) | 0u, P->key0, P->key1);
+  double oe = std::floor((double)(r.x >> 8) * (1.0 / 16777216.0) * G.n_bins);
+  if (oe >= G.n_bins) oe = G.n_bins - 1;
+  P->o_e = (uint32_t)oe;
+  const double ne = (double)std::max<uint64_t>(sp->paths_per_element, 1);
+  P->wb = (float)(sp->method == DARTS_METHOD_DARTS ? G.n_bins / ne : 1.0 / ne);
+  P->stats = ctx->scratch + 2;
+  P->counter = ctx->scratch;
+  P->ticket = reinterpret_cast<unsigned int*>(ctx->scratch + 1);
+  P->status = reinterpret_cast<unsigned int*>(ctx->scratch + 1) + 1;
+}
+
+// Common launch of the path kernel for render and debug.
+darts_status run_trace(darts_ctx* ctx, const darts_scene* sc, const darts_sampling* sp,
+                       TraceParams& P, bool debug) {
+  const int block = ctx->block;
+  const int grid = ctx->sm_count;
+  bool tile = true;
+  size_t smem = trace_smem_bytes(sp->method, P, block, tile);
+  if (smem > (size_t)ctx->smem_optin) {
+    tile = false;
+    smem = trace_smem_bytes(sp->method, P, block, tile);
+  }
+  if (smem > (size_t)ctx->smem_optin)
+    return fail(ctx, DARTS_ERR_UNSUPPORTED, "direction table of %zu bytes exceeds shared memory", smem);
+  const size_t pbytes = (size_t)grid * 2 * P.n_bins * sizeof(double);
+  CK(ensure((void**)&ctx->partials, &ctx->partials_bytes, pbytes), "partials allocation");
+  P.partials = ctx->partials;
+  if (!tile) {
+    CK(ensure((void**)&ctx->acc, &ctx->acc_bytes, 2 * P.n_bins * sizeof(double)), "accumulator");
+    CK(cudaMemsetAsync(ctx->acc, 0, 2 * P.n_bins * sizeof(double), ctx->stream), "memset");
+    P.acc = ctx->acc;
+  }
+  // zero the path counter and the statistics (ticket and status persist)
+  CK(cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), ctx->stream), "memset");
+  CK(cudaMemsetAsync(ctx->scratch + 2, 0, kStatCount * sizeof(unsigned long long), ctx->stream), "memset");
+  (void)sc;
+  if (ctx->timing) CK(cudaEventRecord(ctx->ev_start, ctx->stream), "event record");
+  CK(launch_trace(sp->method, P, grid, block, debug, tile, smem, ctx->stream), "trace kernel launch");
+  if (ctx->timing) {
+    CK(cudaEventRecord(ctx->ev_stop, ctx->stream), "event record");
+    ctx->timed = true;
+  }
+  return DARTS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* darts_status_string(darts_status s) {
+  switch (s) {
+    case DARTS_OK: return "ok";
+    case DARTS_ERR_INVALID_ARG: return "invalid argument";
+    case DARTS_ERR_CUDA: return "CUDA error";
+    case DARTS_ERR_OOM: return "out of device memory";
+    case DARTS_ERR_NUMERIC: return "non-finite value produced on the device";
+    case DARTS_ERR_TIMEOUT: return "bounded device wait expired";
+    case DARTS_ERR_UNSUPPORTED: return "unsupported by this build";
+  }
+  return "unknown status";
+}
+
+darts_status darts_create(darts_ctx** out, int cuda_device, void* cuda_stream) {
+  if (!out) return DARTS_ERR_INVALID_ARG;
+  *out = nullptr;
+  darts_ctx* ctx = new (std::nothrow) darts_ctx();
+  if (!ctx) return DARTS_ERR_OOM;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || cuda_device < 0 || cuda_device >= n) {
+    delete ctx;
+    return e != cudaSuccess ? DARTS_ERR_CUDA : DARTS_ERR_INVALID_ARG;
+  }
+  ctx->device = cuda_device;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  if (cudaSetDevice(cuda_device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, cuda_device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cuda_device) != cudaSuccess) {
+    delete ctx;
+    return DARTS_ERR_CUDA;
+  }
+  ctx->smem_optin -= 1024;  // static shared memory of the path kernel
+  const size_t sbytes = (2 + kStatCount) * sizeof(unsigned long long);
+  e = cudaMalloc((void**)&ctx->scratch, sbytes);
+  if (e == cudaSuccess) e = cudaMemset(ctx->scratch, 0, sbytes);
+  if (e != cudaSuccess) {
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    delete ctx;
+    return e == cudaErrorMemoryAllocation ? DARTS_ERR_OOM : DARTS_ERR_CUDA;
+  }
+  *out = ctx;
+  return DARTS_OK;
+}
+
+darts_status darts_destroy(darts_ctx* ctx) {
+  if (!ctx) return DARTS_ERR_INVALID_ARG;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->scratch);
+  cudaFree(ctx->partials);
+  cudaFree(ctx->acc);
+  cudaFree(ctx->table);
+  cudaFree(ctx->host_hist);
+  if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+  if (ctx->ev_stop) cudaEventDestroy(ctx->ev_stop);
+  delete ctx;
+  return DARTS_OK;
+}
+
+darts_status darts_set_stream(darts_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return DARTS_ERR_INVALID_ARG;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  return DARTS_OK;
+}
+
+darts_status darts_last_error(const darts_ctx* ctx, char* buf, size_t n) {
+  if (!ctx || !buf || n == 0) return DARTS_ERR_INVALID_ARG;
+  std::snprintf(buf, n, "%s", ctx->err);
+  return DARTS_OK;
+}
+
+darts_status darts_sync(darts_ctx* ctx) {
+  if (!ctx) return DARTS_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  unsigned int st[2] = {0, 0};
+  CK(cudaMemcpy(st, ctx->scratch + 1, sizeof(st), cudaMemcpyDeviceToHost), "status read");
+  if (st[1]) {
+    CK(cudaMemset(reinterpret_cast<unsigned int*>(ctx->scratch + 1) + 1, 0, sizeof(unsigned int)), "status clear");
+    if (st[1] & 2u) return fail(ctx, DARTS_ERR_TIMEOUT, "a bounded device wait expired");
+    return fail(ctx, DARTS_ERR_NUMERIC, "a kernel produced a non-finite contribution");
+  }
+  return DARTS_OK;
+}
+
+darts_status darts_set_kernel_timing(darts_ctx* ctx, int enable) {
+  if (!ctx) return DARTS_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (enable && !ctx->ev_start) {
+    CK(cudaEventCreate(&ctx->ev_start), "event create");
+    CK(cudaEventCreate(&ctx->ev_stop), "event create");
+  }
+  ctx->timing = enable != 0;
+  ctx->timed = false;
+  return DARTS_OK;
+}
+
+darts_status darts_last_kernel_ms(darts_ctx* ctx, float* ms) {
+  if (!ctx || !ms) return DARTS_ERR_INVALID_ARG;
+  if (!ctx->timed) return fail(ctx, DARTS_ERR_INVALID_ARG, "no timed kernel: enable timing and render first");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  CK(cudaEventSynchronize(ctx->ev_stop), "event synchronize");
+  CK(cudaEventElapsedTime(ms, ctx->ev_start, ctx->ev_stop), "event elapsed time");
+  return DARTS_OK;
+}
+
+int32_t darts_table_row_stride(int32_t table_n_mu) { return row_stride_of(table_n_mu); }
+
+darts_status darts_build_table(darts_ctx* ctx, const darts_scene* scene,
+                               const darts_sampling* sampling, float* cdf_dev) {
+  if (!ctx) return DARTS_ERR_INVALID_ARG;
+  darts_status s = validate(ctx, scene, sampling);
+  if (s != DARTS_OK) return s;
+  if (!cdf_dev) return fail(ctx, DARTS_ERR_INVALID_ARG, "cdf_dev must not be NULL");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  TableParams tp;
+  make_table_params(scene, sampling, &tp);
+  tp.cdf = cdf_dev;
+  CK(launch_table(tp, ctx->stream), "table kernel launch");
+  return DARTS_OK;
+}
+
+darts_status darts_render(darts_ctx* ctx, const darts_scene* scene, const darts_sampling* sampling,
+                          double* hist_dev, double* sumsq_dev, uint64_t path_offset,
+                          const darts_probe* probe) {
+  if (!ctx) return DARTS_ERR_INVALID_ARG;
+  darts_status s = validate(ctx, scene, sampling);
+  if (s != DARTS_OK) return s;
+  if (!hist_dev) return fail(ctx, DARTS_ERR_INVALID_ARG, "hist_dev must not be NULL");
+  if (probe && (probe->stride == 0 || (probe->count && (!probe->contrib_dev || !probe->bin_dev))))
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "probe needs stride >= 1 and output buffers");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const size_t hb = (size_t)scene->gate.n_bins * sizeof(double);
+  if (sampling->paths_per_element == 0) {
+    CK(cudaMemsetAsync(hist_dev, 0, hb, ctx->stream), "memset");
+    if (sumsq_dev) CK(cudaMemsetAsync(sumsq_dev, 0, hb, ctx->stream), "memset");
+    CK(cudaMemsetAsync(ctx->scratch + 2, 0, kStatCount * sizeof(unsigned long long), ctx->stream), "memset");
+    return DARTS_OK;
+  }
+  if (sampling->method == DARTS_METHOD_DARTS) {
+    s = ensure_table(ctx, scene, sampling);
+    if (s != DARTS_OK) return s;
+  }
+  TraceParams P;
+  make_trace_params(ctx, scene, sampling, &P);
+  P.N = sampling->paths_per_element;
+  P.path_offset = path_offset;
+  P.hist = hist_dev;
+  P.sumsq = sumsq_dev;
+  if (probe && probe->count) {
+    P.probe_first = probe->first;
+    P.probe_stride = probe->stride;
+    P.probe_count = probe->count;
+    P.probe_c = probe->contrib_dev;
+    P.probe_b = probe->bin_dev;
+  }
+  return run_trace(ctx, scene, sampling, P, false);
+}
+
+darts_status darts_render_host(darts_ctx* ctx, const darts_scene* scene,
+                               const darts_sampling* sampling, double* hist_host,
+                               double* sumsq_host, uint64_t path_offset) {
+  if (!ctx) return DARTS_ERR_INVALID_ARG;
+  if (!hist_host) return fail(ctx, DARTS_ERR_INVALID_ARG, "hist_host must not be NULL");
+  darts_status s = validate(ctx, scene, sampling);
+  if (s != DARTS_OK) return s;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const size_t hb = (size_t)scene->gate.n_bins * sizeof(double);
+  CK(ensure((void**)&ctx->host_hist, &ctx->host_hist_bytes, 2 * hb), "histogram allocation");
+  s = darts_render(ctx, scene, sampling, ctx->host_hist, sumsq_host ? ctx->host_hist + scene->gate.n_bins : nullptr,
+                   path_offset, nullptr);
+  if (s != DARTS_OK) return s;
+  CK(cudaMemcpyAsync(hist_host, ctx->host_hist, hb, cudaMemcpyDeviceToHost, ctx->stream), "histogram copy");
+  if (sumsq_host)
+    CK(cudaMemcpyAsync(sumsq_host, ctx->host_hist + scene->gate.n_bins, hb, cudaMemcpyDeviceToHost, ctx->stream),
+       "histogram copy");
+  return darts_sync(ctx);
+}
+
+darts_status darts_get_stats(darts_ctx* ctx, darts_stats* out) {
+  if (!ctx || !out) return DARTS_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  unsigned long long v[2 + kStatCount];
+  CK(cudaMemcpy(v, ctx->scratch, sizeof(v), cudaMemcpyDeviceToHost), "stats read");
+  const unsigned long long* s = v + 2;
+  out->paths = v[0];
+  out->vertices = s[0];
+  out->connections_nonempty = s[1];
+  out->distance_steps = s[2];
+  out->early_exits = s[3];
+  out->all_invalid = s[4];
+  out->escapes = s[5];
+  out->fp64_ellipse = s[6];
+  out->fp64_phi = s[7];
+  return DARTS_OK;
+}
+
+darts_status darts_debug_paths(darts_ctx* ctx, const darts_scene* scene,
+                               const darts_sampling* sampling, uint64_t first, uint32_t count,
+                               float* contrib_dev, int32_t* bin_dev, int32_t* nvert_dev,
+                               uint8_t* decisions_dev) {
+  if (!ctx) return DARTS_ERR_INVALID_ARG;
+  darts_status s = validate(ctx, scene, sampling);
+  if (s != DARTS_OK) return s;
+  if (!contrib_dev || !bin_dev || !nvert_dev || !decisions_dev)
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "debug outputs must not be NULL");
+  if (count == 0) return DARTS_OK;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (sampling->method == DARTS_METHOD_DARTS) {
+    s = ensure_table(ctx, scene, sampling);
+    if (s != DARTS_OK) return s;
+  }
+  TraceParams P;
+  make_trace_params(ctx, scene, sampling, &P);
+  P.N = count;
+  P.path_offset = first;
+  CK(ensure((void**)&ctx->host_hist, &ctx->host_hist_bytes, 2 * (size_t)scene->gate.n_bins * sizeof(double)),
+     "histogram allocation");
+  P.hist = ctx->host_hist;
+  P.sumsq = nullptr;
+  P.dbg_c = contrib_dev;
+  P.dbg_b = bin_dev;
+  P.dbg_n = nvert_dev;
+  P.dbg_dec = decisions_dev;
+  CK(cudaMemsetAsync(decisions_dev, 0xFF, (size_t)count * sampling->max_bounces * 4, ctx->stream), "memset");
+  return run_trace(ctx, scene, sampling, P, true);
+}
+
+darts_status darts_debug_philox(darts_ctx* ctx, const uint32_t* ctr_dev, uint64_t seed, uint32_t n,
+                                uint32_t* out_dev) {
+  if (!ctx || (n && (!ctr_dev || !out_dev))) return DARTS_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  CK(launch_philox(ctr_dev, (uint32_t)seed, (uint32_t)(seed >> 32), n, out_dev, ctx->stream), "philox launch");
+  return DARTS_OK;
+}
+
+}  // extern "C"

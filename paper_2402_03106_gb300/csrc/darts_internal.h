@@ -1,0 +1,88 @@
+// darts_internal.h -- parameter blocks and launchers shared by the library's
+// translation units (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace darts {
+
+constexpr int kMaxTabMuNodes = 4;   // Gauss-Legendre nodes per cos-theta bin
+constexpr int kMaxTabTNodes = 32;   // Gauss-Legendre nodes per t-panel (two panels)
+constexpr int kStatCount = 9;       // darts_stats fields after `paths`
+constexpr int kPathChunk = 64;      // paths a warp claims from the global counter
+
+// Elliptical DA table build (Sec. 5.1, Eq. 16-18).
+struct TableParams {
+  float sigma_t, sigma_a, v;
+  float phi_k0;    // log v - 1.5 log(4 pi v D)
+  float phi_invk;  // 1 / (4 v D)
+  float sa_v;      // sigma_a v
+  float smax;      // v (t_max - t0)
+  int n_rho, n_s, n_mu, row_stride;
+  float mu_x[kMaxTabMuNodes], mu_w[kMaxTabMuNodes];
+  float t_x[kMaxTabTNodes], t_w[kMaxTabTNodes];
+  float* cdf;      // [rows][row_stride]
+};
+
+// Path kernels.  Everything the step functions read, in FP32 unless noted.
+struct TraceParams {
+  // medium
+  float sigma_s, sigma_t, albedo, sa_v, v, inv_v;
+  float phi_k0, phi_invk;          // Eq. 9 in log form, see TableParams
+  float hg_a, hg_b, hg_c, g;       // HG constants (hg_eval) and g
+  double phi_k0_d, phi_invk_d, sa_v_d, inv_v_d;  // the same, FP64 (small-t' branch)
+  // geometry
+  float lo[3], hi[3], xe[3], xs[3];
+  float Ie;                        // energy / (4 pi)
+  // gate, in length units relative to the pulse start
+  float S_gate_lo;                 // v (t_min - t0)
+  float S_bin;                     // v (t_max - t_min) / n_bins
+  float inv_S_bin;
+  float S_gate_hi;                 // v (t_max - t0)
+  float tiny_s;                    // 2^-6 v (t_max - t_min): small-t' threshold
+  int n_bins;
+  // direction table
+  int n_rho, n_s, n_mu, row_stride, rows;
+  float inv_smax, n_s_over_8, mu_scale;  // 1/S_max, n_s / 8, n_mu / 2
+  float mis_alpha;
+  int uniform_sensor;
+  const float* table;              // [rows][row_stride]
+  // sampling
+  int K, M;
+  uint32_t key0, key1, stream;
+  uint32_t o_e;                    // bin offset of the sensor element
+  unsigned long long N;            // paths in this launch (local index 0..N-1)
+  unsigned long long path_offset;  // global id = path_offset + local index
+  float wb;                        // weight per path contribution (DARTS n_bins/N_e, else 1/N_e)
+  // outputs and scratch
+  double* hist;                    // [n_bins]
+  double* sumsq;                   // [n_bins] or null
+  double* partials;                // [grid][2][n_bins]
+  double* acc;                     // [2][n_bins] global accumulator (no-tile mode)
+  unsigned long long* counter;     // path counter
+  unsigned int* ticket;            // last-block ticket
+  unsigned int* status;            // device status word (bit 0: non-finite)
+  unsigned long long* stats;       // [kStatCount]
+  // per-path probe (sampled paths of a full launch)
+  unsigned long long probe_first, probe_stride;
+  unsigned int probe_count;
+  float* probe_c;
+  int* probe_b;
+  // debug (decision traces), local index < N
+  float* dbg_c;
+  int* dbg_b;
+  int* dbg_n;
+  uint8_t* dbg_dec;                // [N][K][4]
+};
+
+// Launchers (stream-ordered; return the launch's cudaError_t).
+cudaError_t launch_table(const TableParams& p, cudaStream_t s);
+cudaError_t launch_trace(int method, const TraceParams& p, int grid, int block, bool debug,
+                         bool tile, size_t smem, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t n,
+                          uint32_t* out, cudaStream_t s);
+size_t trace_smem_bytes(int method, const TraceParams& p, int block, bool tile);
+int trace_max_m();
+
+}  // namespace darts

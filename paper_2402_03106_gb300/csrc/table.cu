@@ -1,0 +1,128 @@
+// table.cu -- elliptical DA direction table on the GPU (Sec. 5.1, Eq. 16-18).
+//
+// For one conditioning cell (C/S = rho, S) the unnormalised density of the
+// direction cosine mu to the major axis x_k -> x_e is
+//   F(mu) = int_0^{t_M(mu)} exp(-sigma_t t) Phi(r(t, mu), (S - t)/v) dt,
+//   r^2 = C^2 + t^2 - 2 C t mu,  t_M = (S^2 - C^2) / (2 (S - C mu))  (Eq. 18),
+// with Phi the transient DA Green's function of Eq. 9 (the paper's MC
+// integration replaced by a fixed Gauss-Legendre rule: 4 nodes per mu-bin, two
+// 32-node panels in t split at the closest approach t = C mu when it lies
+// inside the ellipse).  Each CTA integrates one row, turns the bin integrals
+// into a normalised CDF by a block scan and writes it.
+#include <cfloat>
+
+#include "darts_device.cuh"
+#include "darts_internal.h"
+
+namespace darts {
+namespace {
+
+constexpr int kTableThreads = 256;
+constexpr int kMaxMu = 1024;
+
+__device__ __forceinline__ float warp_incl_scan(float v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float n = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(kTableThreads) eda_table_kernel(const TableParams P) {
+  __shared__ float logF[kMaxMu];
+  __shared__ float wsum[kTableThreads / 32];
+  __shared__ float wmax[kTableThreads / 32];
+  const int row = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int i_rho = row / P.n_s, i_s = row - i_rho * P.n_s;
+  const float rho = (i_rho + 0.5f) / P.n_rho;
+  const float S = P.smax * exp2f(-8.0f + 8.0f * (i_s + 0.5f) / P.n_s);
+  const float C = rho * S;
+  const float SmC = S * (1.0f - rho);  // S - C
+  const float h = 2.0f / P.n_mu;
+  const int per = (P.n_mu + kTableThreads - 1) / kTableThreads;
+
+  float local_max = -FLT_MAX;
+  for (int q = 0; q < per; ++q) {
+    const int i = tid * per + q;
+    if (i >= P.n_mu) break;
+    float m = -FLT_MAX, s = 0.0f;
+    for (int a = 0; a < kMaxTabMuNodes; ++a) {
+      const float xa1 = P.mu_x[a] + 1.0f;
+      const float onem = h * ((float)(P.n_mu - i) - 0.5f * xa1);  // 1 - mu
+      const float mu = 1.0f - onem;
+      const float tM = SmC * (S + C) / (2.0f * fmaf(C, onem, SmC));
+      const float cmu = C * mu;
+      const float split = (cmu > 0.0f && cmu < tM) ? cmu : 0.5f * tM;
+      const float wa = 0.5f * h * P.mu_w[a];
+#pragma unroll 1
+      for (int panel = 0; panel < 2; ++panel) {
+        const float lo = panel == 0 ? 0.0f : split;
+        const float hw = 0.5f * ((panel == 0 ? split : tM) - lo);
+#pragma unroll 4
+        for (int b = 0; b < kMaxTabTNodes; ++b) {
+          const float t = fmaf(hw, P.t_x[b] + 1.0f, lo);
+          const float tc = t - C;
+          const float r2 = fmaf(tc, tc, 2.0f * C * t * onem);
+          const float tp = (S - t) * (1.0f / P.v);  // t' > 0 inside the ellipse
+          const float li = P.phi_k0 - 1.5f * __logf(tp) - __fdividef(r2 * P.phi_invk, tp) -
+                           P.sa_v * tp - P.sigma_t * t;
+          const float mn = fmaxf(m, li);
+          s = fmaf(s, __expf(m - mn), wa * hw * P.t_w[b] * __expf(li - mn));
+          m = mn;
+        }
+      }
+    }
+    const float lf = m + __logf(s);
+    logF[i] = lf;
+    local_max = fmaxf(local_max, lf);
+  }
+  // row maximum of log F
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) local_max = fmaxf(local_max, __shfl_xor_sync(0xFFFFFFFFu, local_max, o));
+  if (lane == 0) wmax[warp] = local_max;
+  __syncthreads();
+  float M = wmax[0];
+  for (int w = 1; w < kTableThreads / 32; ++w) M = fmaxf(M, wmax[w]);
+
+  // per-thread run of consecutive bins, then a block-wide exclusive scan
+  float run[4];
+  float tsum = 0.0f;
+  for (int q = 0; q < per; ++q) {
+    const int i = tid * per + q;
+    const float f = (i < P.n_mu) ? __expf(logF[i] - M) : 0.0f;
+    tsum += f;
+    run[q] = tsum;
+  }
+  const float incl = warp_incl_scan(tsum, lane);
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  float woff = 0.0f, total = 0.0f;
+  for (int w = 0; w < kTableThreads / 32; ++w) {
+    if (w < warp) woff += wsum[w];
+    total += wsum[w];
+  }
+  const float excl = woff + incl - tsum;
+  float* out = P.cdf + (size_t)row * P.row_stride;
+  const bool good = total > 0.0f && isfinite(total);
+  const float inv = good ? 1.0f / total : 0.0f;
+  for (int q = 0; q < per; ++q) {
+    const int i = tid * per + q;
+    if (i >= P.n_mu) break;
+    const float v = good ? (excl + run[q]) * inv : (float)(i + 1) / P.n_mu;
+    out[i + 1] = (i + 1 == P.n_mu) ? 1.0f : fminf(v, 1.0f);
+  }
+  if (tid == 0) out[0] = 0.0f;
+  for (int j = P.n_mu + 1 + tid; j < P.row_stride; j += kTableThreads) out[j] = 1.0f;
+}
+
+}  // namespace
+
+cudaError_t launch_table(const TableParams& p, cudaStream_t s) {
+  if (p.n_mu > kMaxMu || p.n_mu > 4 * kTableThreads) return cudaErrorInvalidValue;
+  eda_table_kernel<<<p.n_rho * p.n_s, kTableThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace darts

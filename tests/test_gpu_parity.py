@@ -1,0 +1,302 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances:
+  * Philox blocks, bin assignment, per-path decision traces: bit-exact
+    (a trace may differ only where the oracle met a decision within 1e-3 of
+    its threshold -- FP32 and FP64 then legitimately take different sides --
+    and on at most 1 % of paths);
+  * direction tables: |cdf_gpu - cdf_oracle| <= 1e-5;
+  * per-path contributions of paths with identical traces: relative 1e-4;
+  * histograms at matched seeds: relative L2 <= 1e-3 and every bin within
+    3 standard errors.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_2402_03106_gb300 import scenes as S  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+NEAR_TIE = 1e-3
+REL_PATH = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2402_03106_gb300 import capi
+    c = capi.Context(0)
+    yield c
+    c.close()
+
+
+def compare_paths(gpu, ref, K):
+    """Return (same_trace mask, rel error array, report dict)."""
+    gb = gpu["bin"].cpu().numpy()
+    gn = gpu["nvert"].cpu().numpy()
+    gd = gpu["decisions"].cpu().numpy()
+    gc = gpu["contrib"].cpu().numpy().astype(np.float64)
+    n = len(gb)
+    assert np.array_equal(gb, ref["bin"]), "bin assignment differs"
+    same = np.zeros(n, bool)
+    first_diff = np.full(n, -1)
+    for i in range(n):
+        nv = ref["nvert"][i]
+        if gn[i] == nv and np.array_equal(gd[i, :nv], ref["decisions"][i, :nv]):
+            same[i] = True
+        else:
+            m = min(gn[i], nv)
+            diff = np.nonzero(np.any(gd[i, :m] != ref["decisions"][i, :m], axis=1))[0]
+            first_diff[i] = diff[0] if len(diff) else m - 1
+    rc = ref["contrib"]
+    rel = np.abs(gc - rc) / np.maximum(np.abs(rc), 1e-300)
+    rel[(rc == 0) & (gc == 0)] = 0.0
+    flips = np.nonzero(~same)[0]
+    margins = np.array([ref["margin"][i, : first_diff[i] + 1].min() for i in flips]) if len(flips) else np.array([])
+    return same, rel, dict(flips=flips, margins=margins, first_diff=first_diff)
+
+
+def check_paths(gpu, ref, K, rel_tol=REL_PATH, max_flip_frac=0.01):
+    same, rel, rep = compare_paths(gpu, ref, K)
+    n = len(same)
+    assert (~same).sum() <= max(2, max_flip_frac * n), f"{(~same).sum()} of {n} traces differ"
+    if len(rep["margins"]):
+        assert rep["margins"].max() < NEAR_TIE, f"trace flip away from a tie: {rep['margins']}"
+    nd = (ref["flags"] & O.FLAG_NEAR_DEGENERATE) != 0
+    ok = same & ~nd
+    bad = np.nonzero(ok & (rel > rel_tol))[0]
+    assert len(bad) == 0, f"{len(bad)} paths beyond {rel_tol}: worst {rel[ok].max():.3e}"
+    # near-degenerate ellipses (S - C < 2^-12 C) depend on FP32 path state; bound them loosely
+    if np.any(same & nd):
+        assert rel[same & nd].max() < 1e-2
+    return same, rel
+
+
+# ---------------------------------------------------------------------------
+def test_philox_bit_exact(ctx):
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64)
+    ctr[0] = 0
+    ctr[1] = 2 ** 32 - 1
+    for seed in (0, 123456789, 2 ** 63 + 5):
+        out = ctx.philox(ctr.astype(np.int64), seed).cpu().to(torch.int64).numpy().reshape(-1, 4)
+        key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+        for i in range(0, 4096, 97):
+            assert O.philox([int(x) for x in ctr[i]], key) == out[i].tolist()
+
+
+TABLE_CASES = [
+    S.cube_workload(),
+    (S.slab_scene(10.0, 0.1, -0.3, side=4.0, n_bins=128), S.Sampling()),
+    (S.slab_scene(0.1, 0.05, 0.9, side=0.5, n_bins=128), S.Sampling()),
+    (S.slab_scene(2.0, 0.5, 0.0, side=1.0, n_bins=16), S.Sampling(table_n_rho=5, table_n_s=3, table_n_mu=37)),
+]
+
+
+@pytest.mark.parametrize("case", range(len(TABLE_CASES)))
+def test_direction_table_matches_oracle(ctx, case):
+    sc, sp = TABLE_CASES[case]
+    cdf = ctx.build_table(sc, sp).cpu().numpy().astype(np.float64)
+    ref = O.build_table(sc, sp)
+    nb = sp.table_n_mu
+    np.testing.assert_allclose(cdf[:, : nb + 1], ref, atol=1e-5, rtol=0)
+    assert np.all(cdf[:, 0] == 0.0) and np.all(cdf[:, nb] == 1.0)
+
+
+@pytest.mark.parametrize("K", [1, 3, 50])
+def test_darts_per_path_parity(ctx, K):
+    sc, sp = S.cube_workload(paths=1 << 16, seed=2)
+    sp.max_bounces = K
+    n = 4096
+    gpu = ctx.debug_paths(sc, sp, 12345, n)
+    torch.cuda.synchronize()
+    ref = O.trace_paths(sc, sp, 12345, n)
+    check_paths(gpu, ref, K)
+
+
+def test_darts_per_path_parity_dense_medium(ctx):
+    """Many scattering events per path: sigma_s = 8 in a unit cube."""
+    sc = S.slab_scene(8.0, 0.05, 0.5, n_bins=64, t_min=0.8, t_max=6.0)
+    sp = S.Sampling(seed=9, paths_per_element=1 << 14, max_bounces=50)
+    n = 2048
+    gpu = ctx.debug_paths(sc, sp, 0, n)
+    ref = O.trace_paths(sc, sp, 0, n)
+    check_paths(gpu, ref, 50, max_flip_frac=0.03)
+
+
+@pytest.mark.parametrize("method", [S.PLAIN_UNIFORM_T, S.VANILLA_DIRECT])
+def test_baseline_per_path_parity(ctx, method):
+    sc, sp = S.cube_workload(paths=1 << 14, seed=4)
+    sp.method = method
+    n = 4096
+    gpu = ctx.debug_paths(sc, sp, 0, n)
+    ref = O.trace_paths(sc, sp, 0, n, method=method)
+    check_paths(gpu, ref, sp.max_bounces)
+
+
+@pytest.mark.parametrize("method", [S.DARTS, S.PLAIN_UNIFORM_T, S.VANILLA_DIRECT])
+def test_histogram_parity_matched_seeds(ctx, method):
+    sc, sp = S.cube_workload(paths=1 << 16, seed=0)
+    sp.method = method
+    hist, sq = ctx.render(sc, sp, sumsq=True)
+    ctx.sync()
+    h = hist.cpu().numpy()
+    href, sqref, _ = O.render(sc, sp, method)
+    per_bin = (1 << 16) / 256 if method == S.DARTS else (1 << 16)
+    se = O.standard_error(href, sqref, per_bin)
+    l2 = np.linalg.norm(h - href) / np.linalg.norm(href)
+    assert l2 < 1e-3, l2
+    assert np.all(np.abs(h - href) <= 3 * se + 1e-12 * np.abs(href).max())
+    np.testing.assert_allclose(sq.cpu().numpy().sum(), sqref.sum(), rtol=1e-2)
+
+
+def test_full_size_sampled_paths(ctx):
+    """2^24 paths in the benchmark's launch configuration; 2048 sampled paths
+    recomputed one by one by the oracle."""
+    sc, sp = S.cube_workload(paths=1 << 24, seed=0)
+    stride = (1 << 24) // 2048
+    probe, pc, pb = ctx.probe(first=7, stride=stride, count=2048)
+    ctx.render(sc, sp, probe=probe)
+    ctx.sync()
+    ids = 7 + stride * np.arange(2048)
+    c_ref = np.zeros(2048)
+    b_ref = np.zeros(2048, np.int64)
+    flags = np.zeros(2048, np.int64)
+    for i, pid in enumerate(ids):
+        r = O.trace_paths(sc, sp, int(pid), 1)
+        c_ref[i], b_ref[i], flags[i] = r["contrib"][0], r["bin"][0], r["flags"][0]
+    assert np.array_equal(pb.cpu().numpy(), b_ref)
+    gc = pc.cpu().numpy().astype(np.float64)
+    rel = np.abs(gc - c_ref) / np.maximum(np.abs(c_ref), 1e-300)
+    rel[(c_ref == 0) & (gc == 0)] = 0
+    # paths whose trace flipped near a tie differ entirely; allow 1 %
+    assert np.mean(rel > REL_PATH) <= 0.01, np.sort(rel)[-10:]
+    st = ctx.stats()
+    assert st["paths"] >= 1 << 24
+
+
+def test_stats_match_oracle_counts(ctx):
+    sc, sp = S.cube_workload(paths=1 << 15, seed=5)
+    ctx.render(sc, sp)
+    st = ctx.stats()
+    _, _, ost = O.render(sc, sp, O.ORC_DARTS)
+    assert abs(st["vertices"] - ost["vertices"]) <= 0.002 * ost["vertices"]
+    assert abs(st["connections_nonempty"] - ost["connections_nonempty"]) <= 0.002 * ost["connections_nonempty"] + 5
+    assert abs(st["escapes"] - ost["escapes"]) <= 0.002 * ost["escapes"] + 5
+
+
+# ---------------------------------------------------------------------------
+# Edge cases
+# ---------------------------------------------------------------------------
+def test_empty_render_writes_zeros(ctx):
+    sc, sp = S.cube_workload(paths=0)
+    h = ctx.render(sc, sp)
+    ctx.sync()
+    assert torch.all(h == 0)
+
+
+@pytest.mark.parametrize("n", [1, 255, 256 * 3 + 77])
+def test_ragged_path_counts(ctx, n):
+    sc, sp = S.cube_workload(paths=n, seed=11)
+    h = ctx.render(sc, sp).cpu().numpy()
+    ctx.sync()
+    href, _, _ = O.render(sc, sp, O.ORC_DARTS)
+    assert np.array_equal(h != 0, href != 0) or np.linalg.norm(h - href) <= 1e-3 * np.linalg.norm(href)
+    np.testing.assert_allclose(h, href, rtol=1e-3, atol=1e-6 * max(href.max(), 1e-30))
+
+
+def test_gate_before_straight_line_time_is_zero(ctx):
+    sc = S.slab_scene(n_bins=4, t_min=0.2, t_max=0.7)
+    for m in (S.DARTS, S.PLAIN_UNIFORM_T, S.VANILLA_DIRECT):
+        sp = S.Sampling(seed=0, paths_per_element=4096, method=m)
+        h = ctx.render(sc, sp)
+        ctx.sync()
+        assert torch.all(h == 0)
+    st = ctx.stats()
+    assert st["vertices"] > 0
+
+
+def test_render_host_matches_device(ctx):
+    sc, sp = S.cube_workload(paths=1 << 14, seed=3)
+    h_dev = ctx.render(sc, sp).cpu()
+    ctx.sync()
+    hh = torch.zeros(256, dtype=torch.float64).pin_memory()
+    ctx.render_host(sc, sp, hh)
+    # path-to-block assignment is dynamic: equal up to FP64 summation order
+    torch.testing.assert_close(hh, h_dev, rtol=1e-6, atol=1e-15)
+
+
+def test_other_ris_m_and_table_dims(ctx):
+    sc, _ = S.cube_workload()
+    sp = S.Sampling(seed=8, paths_per_element=1 << 12, ris_m=5, table_n_rho=7, table_n_s=5,
+                    table_n_mu=100, max_bounces=10)
+    gpu = ctx.debug_paths(sc, sp, 0, 1024)
+    ref = O.trace_paths(sc, sp, 0, 1024)
+    check_paths(gpu, ref, 10)
+
+
+def test_invalid_arguments_are_rejected(ctx):
+    from paper_2402_03106_gb300 import capi
+    sc, sp = S.cube_workload(paths=16)
+    bad = [
+        ("sigma", lambda s, p: setattr(s.medium, "sigma_s", 0.0) or setattr(s.medium, "sigma_a", 0.0)),
+        ("g", lambda s, p: setattr(s.medium, "g", 1.0)),
+        ("bins", lambda s, p: setattr(s.gate, "n_bins", 0)),
+        ("gate", lambda s, p: setattr(s.gate, "t_max", s.gate.t_min)),
+        ("K", lambda s, p: setattr(p, "max_bounces", 0)),
+        ("M", lambda s, p: setattr(p, "ris_m", 33)),
+        ("alpha", lambda s, p: setattr(p, "mis_alpha", 0.0)),
+        ("emitter", lambda s, p: setattr(s.emitters[0], "pos", (2.0, 0.5, 0.5))),
+        ("method", lambda s, p: setattr(p, "method", 7)),
+    ]
+    import copy
+    for name, mut in bad:
+        s2, p2 = copy.deepcopy(sc), copy.deepcopy(sp)
+        mut(s2, p2)
+        with pytest.raises(capi.DartsError) as ei:
+            ctx.render(s2, p2)
+        assert ei.value.status == 1, name
+    s2 = copy.deepcopy(sc)
+    s2.emitters = s2.emitters * 2
+    with pytest.raises(capi.DartsError) as ei:
+        ctx.render(s2, sp)
+    assert ei.value.status == 6
+    ctx.sync()
+
+
+# ---------------------------------------------------------------------------
+# Physics on the GPU (statistical)
+# ---------------------------------------------------------------------------
+def test_gpu_single_scatter_closed_form(ctx):
+    sc = S.infinite_scene(1.0, 0.01, 0.7, separation=1.0, n_bins=12, t_min=1.02, t_max=3.0)
+    ref = O.single_scatter_bins(sc)
+    n = 1 << 22
+    sp = S.Sampling(seed=11, paths_per_element=n, max_bounces=1)
+    for m in (S.DARTS, S.PLAIN_UNIFORM_T):
+        sp.method = m
+        h, sq = ctx.render(sc, sp, sumsq=True)
+        ctx.sync()
+        h, sq = h.cpu().numpy(), sq.cpu().numpy()
+        se = O.standard_error(h, sq, n / 12 if m == S.DARTS else n)
+        z = (h - ref) / se
+        assert np.max(np.abs(z)) < 5.0, (m, z)
+
+
+def test_gpu_darts_agrees_with_plain_pt(ctx):
+    sc, _ = S.cube_workload()
+    n = 1 << 22
+    hd, sd = ctx.render(sc, S.Sampling(seed=1, paths_per_element=n), sumsq=True)
+    hp, spq = ctx.render(sc, S.Sampling(seed=2, paths_per_element=n, method=S.PLAIN_UNIFORM_T), sumsq=True)
+    ctx.sync()
+    hd, sd, hp, spq = (t.cpu().numpy() for t in (hd, sd, hp, spq))
+    se = np.sqrt(O.standard_error(hd, sd, n / 256) ** 2 + O.standard_error(hp, spq, n) ** 2)
+    z = (hd - hp) / np.maximum(se, 1e-300)
+    good = se > 0
+    assert np.median(np.abs(z[1:][good[1:]])) < 1.5
+    assert np.mean(np.abs(z[1:][good[1:]]) > 4) < 0.02
