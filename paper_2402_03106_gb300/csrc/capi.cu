@@ -122,6 +122,11 @@ darts_status validate(darts_ctx* ctx, const darts_scene* sc, const darts_samplin
       return fail(ctx, DARTS_ERR_INVALID_ARG, "sensor outside the medium box");
   }
   if (!(sc->gate.t_max > e.t0)) return fail(ctx, DARTS_ERR_INVALID_ARG, "gate ends before the pulse");
+  {
+    double d2 = 0.0;
+    for (int i = 0; i < 3; ++i) d2 += (sc->sensor.pos[i] - e.pos[i]) * (sc->sensor.pos[i] - e.pos[i]);
+    if (!(d2 > 0.0)) return fail(ctx, DARTS_ERR_INVALID_ARG, "sensor coincides with the emitter");
+  }
   if (sp->max_bounces < 1 || sp->max_bounces > 1024)
     return fail(ctx, DARTS_ERR_INVALID_ARG, "max_bounces must be in 1..1024");
   if (sp->ris_m < 1 || sp->ris_m > trace_max_m())
