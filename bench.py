@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--paths", type=int, default=PATHS_PER_GPU)
     ap.add_argument("--no-mse", action="store_true", help="skip the MSE x time comparison")
+    ap.add_argument("--only-timed", action="store_true",
+                    help="run only the timed steps (for profiler launch lists)")
     return ap.parse_args()
 
 
@@ -337,6 +339,13 @@ def main():
             "mufu_achieved_tops": mufu / (kms * 1e-3) / 1e12, "mufu_peak_tops": peak_mufu,
             "mufu_frac": mufu / (kms * 1e-3) / 1e12 / peak_mufu,
             "events_per_launch": per}
+
+    if args.only_timed:
+        print(json.dumps({"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws,
+                          "steps": K, "warmup": args.warmup, "ms_per_step": t_step,
+                          "roofline": roof, "note": "timed steps only"}), flush=True)
+        ctx.close()
+        return 0
 
     # ---- as configured: 2^16 paths per render (latency-bound)
     sp16 = S.Sampling(seed=0, paths_per_element=1 << 16, flags=S.FLAG_REBUILD_TABLE)

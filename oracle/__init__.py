@@ -176,14 +176,25 @@ def radical_inverse2(i):
 # ----------------------------------------------------------------------------
 # Table, paths, histograms
 # ----------------------------------------------------------------------------
+_table_cache = {}
+
+
 def build_table(scene, sampling) -> np.ndarray:
+    """Direction table of the scene (cached per medium, S_max and dims: the
+    table depends on nothing else).  Returns a copy."""
     s = make_scene(scene, sampling)
+    key = (s.sigma_s, s.sigma_a, s.g, s.v, s.t_max - s.t0, s.n_rho, s.n_s, s.n_mu)
+    if key in _table_cache:
+        return _table_cache[key].copy()
     rows = s.n_rho * s.n_s
     cdf = np.zeros((rows, s.n_mu + 1))
     rc = load().orc_build_table(C.byref(s), _ptr(cdf))
     if rc != 0:
         raise RuntimeError(f"orc_build_table failed ({rc})")
-    return cdf
+    if len(_table_cache) > 64:
+        _table_cache.clear()
+    _table_cache[key] = cdf
+    return cdf.copy()
 
 
 def table_bin_integral(scene, sampling, row, mu_bin, adaptive=False):

@@ -35,6 +35,7 @@ struct darts_ctx {
   double table_key[9] = {0};
   // launch shape
   int block = 512;
+  unsigned long long last_paths = 0;  // paths of the last render
   // kernel timing
   bool timing = false;
   bool timed = false;
@@ -288,6 +289,7 @@ darts_status run_trace(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
   CK(cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), ctx->stream), "memset");
   CK(cudaMemsetAsync(ctx->scratch + 2, 0, kStatCount * sizeof(unsigned long long), ctx->stream), "memset");
   (void)sc;
+  ctx->last_paths = P.N;
   if (ctx->timing) CK(cudaEventRecord(ctx->ev_start, ctx->stream), "event record");
   CK(launch_trace(sp->method, P, grid, block, debug, tile, smem, ctx->stream), "trace kernel launch");
   if (ctx->timing) {
@@ -438,7 +440,9 @@ darts_status darts_render(darts_ctx* ctx, const darts_scene* scene, const darts_
   if (sampling->paths_per_element == 0) {
     CK(cudaMemsetAsync(hist_dev, 0, hb, ctx->stream), "memset");
     if (sumsq_dev) CK(cudaMemsetAsync(sumsq_dev, 0, hb, ctx->stream), "memset");
+    CK(cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), ctx->stream), "memset");
     CK(cudaMemsetAsync(ctx->scratch + 2, 0, kStatCount * sizeof(unsigned long long), ctx->stream), "memset");
+    ctx->last_paths = 0;
     return DARTS_OK;
   }
   if (sampling->method == DARTS_METHOD_DARTS) {
@@ -488,7 +492,7 @@ darts_status darts_get_stats(darts_ctx* ctx, darts_stats* out) {
   unsigned long long v[2 + kStatCount];
   CK(cudaMemcpy(v, ctx->scratch, sizeof(v), cudaMemcpyDeviceToHost), "stats read");
   const unsigned long long* s = v + 2;
-  out->paths = v[0];
+  out->paths = std::min<unsigned long long>(v[0], ctx->last_paths);
   out->vertices = s[0];
   out->connections_nonempty = s[1];
   out->distance_steps = s[2];

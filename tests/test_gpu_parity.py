@@ -153,7 +153,13 @@ def test_histogram_parity_matched_seeds(ctx, method):
     l2 = np.linalg.norm(h - href) / np.linalg.norm(href)
     assert l2 < 1e-3, l2
     assert np.all(np.abs(h - href) <= 3 * se + 1e-12 * np.abs(href).max())
-    np.testing.assert_allclose(sq.cpu().numpy().sum(), sqref.sum(), rtol=1e-2)
+    if method == S.DARTS:
+        # one commit per DARTS path: the per-path squares are exact.  The
+        # baselines square each connection (a path hitting a bin twice is not
+        # merged), so their sums of squares are checked only for consistency.
+        np.testing.assert_allclose(sq.cpu().numpy(), sqref, rtol=1e-3, atol=1e-12 * sqref.max())
+    else:
+        assert np.all(sq.cpu().numpy() >= 0) and sq.cpu().numpy().sum() <= 1.0001 * sqref.sum()
 
 
 def test_full_size_sampled_paths(ctx):
@@ -165,11 +171,12 @@ def test_full_size_sampled_paths(ctx):
     ctx.render(sc, sp, probe=probe)
     ctx.sync()
     ids = 7 + stride * np.arange(2048)
+    cdf = O.build_table(sc, sp)
     c_ref = np.zeros(2048)
     b_ref = np.zeros(2048, np.int64)
     flags = np.zeros(2048, np.int64)
     for i, pid in enumerate(ids):
-        r = O.trace_paths(sc, sp, int(pid), 1)
+        r = O.trace_paths(sc, sp, int(pid), 1, cdf=cdf)
         c_ref[i], b_ref[i], flags[i] = r["contrib"][0], r["bin"][0], r["flags"][0]
     assert np.array_equal(pb.cpu().numpy(), b_ref)
     gc = pc.cpu().numpy().astype(np.float64)
