@@ -205,6 +205,42 @@ darts_status darts_get_stats(darts_ctx* ctx, darts_stats* out);
 darts_status darts_set_kernel_timing(darts_ctx* ctx, int enable);
 darts_status darts_last_kernel_ms(darts_ctx* ctx, float* ms);
 
+/* ---- rendering without allocating ----------------------------------------- */
+
+/* darts_render without a context and without any device allocation, for
+ * callers that must not call cudaMalloc (for example a plug-in inside a host
+ * application that reserves all device memory in its own pool, or a pipeline
+ * that may not allocate after start-up; darts_create allocates, so such
+ * callers cannot hold a context).  The paper has no counterpart: this is
+ * plumbing around the same kernels.
+ *
+ * Runs on the calling thread's current device, ordered on cuda_stream
+ * (cudaStream_t, NULL = legacy default stream).  The caller passes the
+ * outputs, exactly as for darts_render: hist_dev[n_bins] (overwritten) and
+ * optional sumsq_dev[n_bins].  No per-path probe, no statistics, no table
+ * cache: the direction table is rebuilt on every call.
+ *
+ * Scratch: one file-scope device array of 4 MiB, present on every GPU that
+ * loads the library until the process exits.  It holds the path counter and
+ * statistics (256 B), the direction table (at most 256 KiB:
+ * table_n_rho * table_n_s * darts_table_row_stride(table_n_mu) <= 65536
+ * floats) and the block partials (number of SMs * 2 * n_bins doubles, at most
+ * 4 MiB - 256 KiB - 256 B, i.e. n_bins <= 1616 on a 152-SM GB300).  Larger
+ * requests return DARTS_ERR_UNSUPPORTED before anything is launched.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Every call shares the one array and clears the parts that
+ * must start at zero; calls whose work overlaps on the GPU (other streams,
+ * other threads, concurrent graphs) race on it and must be serialised by the
+ * caller.  Device-side non-finite contributions are zeroed as in
+ * darts_render but are not reported (there is no context to sync).
+ * Returns DARTS_ERR_INVALID_ARG for invalid scenes or a NULL hist_dev,
+ * DARTS_ERR_CUDA when a launch or the set-up fails. */
+darts_status darts_render_static(const darts_scene* scene, const darts_sampling* sampling,
+                                 double* hist_dev, double* sumsq_dev, uint64_t path_offset,
+                                 void* cuda_stream);
+
 /* ---- checking ------------------------------------------------------------ */
 
 /* Trace paths first .. first+count-1 one per thread-slot of the render kernel

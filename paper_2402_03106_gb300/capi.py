@@ -31,7 +31,8 @@ STATUS_NAMES = {0: "DARTS_OK", 1: "DARTS_ERR_INVALID_ARG", 2: "DARTS_ERR_CUDA", 
 EXPORTED = ("darts_create", "darts_destroy", "darts_set_stream", "darts_status_string",
             "darts_last_error", "darts_sync", "darts_build_table", "darts_table_row_stride",
             "darts_render", "darts_render_host", "darts_get_stats", "darts_debug_paths",
-            "darts_debug_philox", "darts_set_kernel_timing", "darts_last_kernel_ms")
+            "darts_debug_philox", "darts_set_kernel_timing", "darts_last_kernel_ms",
+            "darts_render_static")
 
 
 class DartsError(RuntimeError):
@@ -118,6 +119,7 @@ def load(path: str = LIB_PATH):
         lib.darts_debug_philox.argtypes = [vp, vp, C.c_uint64, C.c_uint32, vp]
         lib.darts_set_kernel_timing.argtypes = [vp, C.c_int]
         lib.darts_last_kernel_ms.argtypes = [vp, C.POINTER(C.c_float)]
+        lib.darts_render_static.argtypes = [sc_p, sp_p, vp, vp, C.c_uint64, vp]
         for name in EXPORTED:
             if name not in ("darts_status_string", "darts_table_row_stride"):
                 getattr(lib, name).restype = st
@@ -246,6 +248,20 @@ def darts_last_kernel_ms(h) -> float:
     ms = C.c_float()
     _check(h, load().darts_last_kernel_ms(h, C.byref(ms)))
     return float(ms.value)
+
+
+def darts_render_static(scene, sampling, hist: torch.Tensor, sumsq: Optional[torch.Tensor] = None,
+                        path_offset: int = 0, stream=None):
+    """darts_render_static: render without a context and without allocating
+    device memory (for callers that may not call cudaMalloc); scratch comes
+    from the library's fixed 4 MiB device array.  `stream` is a torch stream
+    (default: the current stream of hist's device)."""
+    cs, keep = to_c_scene(scene)
+    if stream is None:
+        stream = torch.cuda.current_stream(hist.device)
+    _check(None, load().darts_render_static(C.byref(cs), C.byref(to_c_sampling(sampling)), _ptr(hist),
+                                            _ptr(sumsq), int(path_offset),
+                                            C.c_void_p(stream.cuda_stream)))
 
 
 # ----------------------------------------------------------------------------

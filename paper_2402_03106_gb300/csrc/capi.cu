@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "darts.h"
@@ -544,3 +545,128 @@ darts_status darts_debug_philox(darts_ctx* ctx, const uint32_t* ctr_dev, uint64_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free rendering.
+//
+// Some callers cannot call cudaMalloc: plug-ins hosted by an application that
+// reserves all device memory up front in its own pool and forbids libraries
+// from allocating behind its back, or pipelines that must not allocate after
+// start-up.  darts_create() allocates the context's scratch, so those callers
+// cannot use darts_render().  darts_render_static() takes its scratch (path
+// counter, statistics, direction table, block partials) from one file-scope
+// device array instead; the caller passes only the histogram buffers.
+//
+// The array lives in every GPU that loads this library until the process
+// exits.  In host code its name is only a host-side stand-in for the device
+// variable, so the device address is looked up with cudaGetSymbolAddress()
+// once per device (with that device current) on the first call there, and
+// that address is what the kernels receive.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchBytes = 4u << 20;   // 4 MiB per device
+constexpr size_t kStaticHeaderBytes = 256;         // counter, ticket, status, statistics
+constexpr size_t kStaticTableBytes = 256u << 10;   // direction table, up to 65536 floats
+constexpr size_t kStaticPartialBytes = kStaticScratchBytes - kStaticHeaderBytes - kStaticTableBytes;
+constexpr int kStaticMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+struct StaticDevice {
+  bool ready = false;
+  unsigned char* base = nullptr;  // device address of g_static_scratch
+  int sm_count = 0;
+  int smem_optin = 0;
+};
+StaticDevice g_static_dev[kStaticMaxDevices];
+std::mutex g_static_mutex;
+
+// Per-device set-up: device address of the scratch array and launch limits.
+cudaError_t static_setup(int dev, StaticDevice** out) {
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  StaticDevice& d = g_static_dev[dev];
+  if (!d.ready) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    d.smem_optin -= 1024;
+    d.base = static_cast<unsigned char*>(p);
+    d.ready = true;
+  }
+  *out = &d;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" darts_status darts_render_static(const darts_scene* scene, const darts_sampling* sampling,
+                                            double* hist_dev, double* sumsq_dev, uint64_t path_offset,
+                                            void* cuda_stream) {
+  darts_ctx tmp;  // stack only: carries the launch settings, owns nothing
+  darts_ctx* ctx = &tmp;
+  darts_status s = validate(ctx, scene, sampling);
+  if (s != DARTS_OK) return s;
+  if (!hist_dev) return DARTS_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return DARTS_ERR_CUDA;
+  if (dev < 0 || dev >= kStaticMaxDevices) return DARTS_ERR_UNSUPPORTED;
+  StaticDevice* sd = nullptr;
+  if (static_setup(dev, &sd) != cudaSuccess) return DARTS_ERR_CUDA;
+  const cudaStream_t stream = (cudaStream_t)cuda_stream;
+  const int B = scene->gate.n_bins;
+  const size_t hb = (size_t)B * sizeof(double);
+  unsigned long long* header = reinterpret_cast<unsigned long long*>(sd->base);
+  float* table = reinterpret_cast<float*>(sd->base + kStaticHeaderBytes);
+  double* partials = reinterpret_cast<double*>(sd->base + kStaticHeaderBytes + kStaticTableBytes);
+
+  // sizes beyond the static maximum are rejected before anything is launched
+  const size_t table_bytes = (size_t)sampling->table_n_rho * sampling->table_n_s *
+                             row_stride_of(sampling->table_n_mu) * sizeof(float);
+  const size_t partial_bytes = (size_t)sd->sm_count * 2 * hb;
+  if (table_bytes > kStaticTableBytes || partial_bytes > kStaticPartialBytes) return DARTS_ERR_UNSUPPORTED;
+
+  tmp.device = dev;
+  tmp.stream = stream;
+  tmp.sm_count = sd->sm_count;
+  tmp.smem_optin = sd->smem_optin;
+  tmp.scratch = header;
+  tmp.table = table;
+
+  // the array keeps the previous call's contents: reset counter, ticket, status, statistics
+  if (cudaMemsetAsync(header, 0, kStaticHeaderBytes, stream) != cudaSuccess) return DARTS_ERR_CUDA;
+  if (sampling->paths_per_element == 0) {
+    if (cudaMemsetAsync(hist_dev, 0, hb, stream) != cudaSuccess) return DARTS_ERR_CUDA;
+    if (sumsq_dev && cudaMemsetAsync(sumsq_dev, 0, hb, stream) != cudaSuccess) return DARTS_ERR_CUDA;
+    return DARTS_OK;
+  }
+  if (sampling->method == DARTS_METHOD_DARTS) {
+    TableParams tp;
+    make_table_params(scene, sampling, &tp);
+    tp.cdf = table;
+    if (launch_table(tp, stream) != cudaSuccess) return DARTS_ERR_CUDA;
+  }
+  TraceParams P;
+  make_trace_params(ctx, scene, sampling, &P);
+  P.N = sampling->paths_per_element;
+  P.path_offset = path_offset;
+  P.hist = hist_dev;
+  P.sumsq = sumsq_dev;
+  P.partials = partials;
+  bool tile = true;
+  size_t smem = trace_smem_bytes(sampling->method, P, tmp.block, tile);
+  if (smem > (size_t)tmp.smem_optin) {
+    tile = false;
+    smem = trace_smem_bytes(sampling->method, P, tmp.block, tile);
+    P.acc = partials;  // 2 * B doubles, zeroed below
+    if (cudaMemsetAsync(partials, 0, 2 * hb, stream) != cudaSuccess) return DARTS_ERR_CUDA;
+  }
+  if (smem > (size_t)tmp.smem_optin) return DARTS_ERR_UNSUPPORTED;
+  if (launch_trace(sampling->method, P, tmp.sm_count, tmp.block, false, tile, smem, stream) != cudaSuccess)
+    return DARTS_ERR_CUDA;
+  return DARTS_OK;
+}
