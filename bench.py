@@ -271,13 +271,12 @@ def main():
     B = sc.gate.n_bins
     hist = torch.zeros(B, dtype=torch.float64, device="cuda")
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MiB > L2
-    offset = rank * N
+    from paper_2402_03106_gb300 import sharding
+    offset = sharding.path_offset(rank, N)
 
     def step():
         ctx.render(sc, sp, out=hist, path_offset=offset)
-        if pg is not None:
-            pg.all_reduce(hist)
-            hist.div_(ws)
+        sharding.combine(hist, ws)
 
     for _ in range(args.warmup):
         step()
