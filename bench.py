@@ -278,6 +278,7 @@ def main():
         ctx.render(sc, sp, out=hist, path_offset=offset)
         sharding.combine(hist, ws)
 
+    tuned_block = ctx.autotune(sc, sp)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -345,7 +346,8 @@ def main():
     if args.only_timed:
         print(json.dumps({"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws,
                           "steps": K, "warmup": args.warmup, "ms_per_step": t_step,
-                          "roofline": roof, "note": "timed steps only"}), flush=True)
+                          "roofline": roof, "block": tuned_block, "note": "timed steps only"}),
+              flush=True)
         ctx.close()
         return 0
 
@@ -389,6 +391,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "paths_per_gpu_per_step": N,
+                       "block": tuned_block, "grid": "one CTA per SM (persistent)",
                        "l2": "256 MiB buffer written between timed steps (flush)",
                        "parallelism": f"path-id shards x{ws}, FP64 histogram all-reduce" if ws > 1
                        else "single GPU"},

@@ -205,6 +205,21 @@ darts_status darts_get_stats(darts_ctx* ctx, darts_stats* out);
 darts_status darts_set_kernel_timing(darts_ctx* ctx, int enable);
 darts_status darts_last_kernel_ms(darts_ctx* ctx, float* ms);
 
+/* ---- launch shape ---------------------------------------------------------- */
+
+/* Block size of the persistent path kernel (one CTA per SM): 512, 640 or 768
+ * threads, or 0 for the default (the largest whose shared memory fits).
+ * Other values return DARTS_ERR_INVALID_ARG. */
+darts_status darts_set_launch(darts_ctx* ctx, int block);
+
+/* Autotuner: times darts_render of (scene, sampling) with every supported
+ * block size (3 timed renders each, after one warm-up; CUDA events on the
+ * context's stream), keeps the fastest on the context and returns it in
+ * *block_out (may be NULL).  Synchronises the stream.  The renders write the
+ * context's scratch histogram, not a caller buffer. */
+darts_status darts_autotune(darts_ctx* ctx, const darts_scene* scene,
+                            const darts_sampling* sampling, int* block_out);
+
 /* ---- rendering without allocating ----------------------------------------- */
 
 /* darts_render without a context and without any device allocation, for

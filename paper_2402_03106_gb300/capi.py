@@ -32,7 +32,7 @@ EXPORTED = ("darts_create", "darts_destroy", "darts_set_stream", "darts_status_s
             "darts_last_error", "darts_sync", "darts_build_table", "darts_table_row_stride",
             "darts_render", "darts_render_host", "darts_get_stats", "darts_debug_paths",
             "darts_debug_philox", "darts_set_kernel_timing", "darts_last_kernel_ms",
-            "darts_render_static")
+            "darts_render_static", "darts_set_launch", "darts_autotune")
 
 
 class DartsError(RuntimeError):
@@ -120,6 +120,8 @@ def load(path: str = LIB_PATH):
         lib.darts_set_kernel_timing.argtypes = [vp, C.c_int]
         lib.darts_last_kernel_ms.argtypes = [vp, C.POINTER(C.c_float)]
         lib.darts_render_static.argtypes = [sc_p, sp_p, vp, vp, C.c_uint64, vp]
+        lib.darts_set_launch.argtypes = [vp, C.c_int]
+        lib.darts_autotune.argtypes = [vp, sc_p, sp_p, C.POINTER(C.c_int)]
         for name in EXPORTED:
             if name not in ("darts_status_string", "darts_table_row_stride"):
                 getattr(lib, name).restype = st
@@ -250,6 +252,17 @@ def darts_last_kernel_ms(h) -> float:
     return float(ms.value)
 
 
+def darts_set_launch(h, block: int):
+    _check(h, load().darts_set_launch(h, int(block)))
+
+
+def darts_autotune(h, scene, sampling) -> int:
+    cs, keep = to_c_scene(scene)
+    b = C.c_int()
+    _check(h, load().darts_autotune(h, C.byref(cs), C.byref(to_c_sampling(sampling)), C.byref(b)))
+    return int(b.value)
+
+
 def darts_render_static(scene, sampling, hist: torch.Tensor, sumsq: Optional[torch.Tensor] = None,
                         path_offset: int = 0, stream=None):
     """darts_render_static: render without a context and without allocating
@@ -317,6 +330,12 @@ class Context:
         cdf = torch.empty(rows, stride, dtype=torch.float32, device=self._dev())
         darts_build_table(self.h, scene, sampling, cdf)
         return cdf
+
+    def set_launch(self, block: int):
+        darts_set_launch(self.h, block)
+
+    def autotune(self, scene, sampling) -> int:
+        return darts_autotune(self.h, scene, sampling)
 
     def set_kernel_timing(self, enable: bool):
         darts_set_kernel_timing(self.h, enable)

@@ -34,8 +34,9 @@ struct darts_ctx {
   size_t table_bytes = 0;
   bool table_valid = false;
   double table_key[9] = {0};
-  // launch shape
-  int block = 512;
+  // launch shape: requested block size of the path kernel (0 = largest that fits)
+  int block = 0;
+  int last_block = 0;
   unsigned long long last_paths = 0;  // paths of the last render
   // kernel timing
   bool timing = false;
@@ -208,6 +209,7 @@ void make_trace_params(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
   const double D = 1.0 / (3.0 * (m.sigma_a + m.sigma_s * (1.0 - m.g)));
   P->sigma_s = (float)m.sigma_s;
   P->sigma_t = (float)st;
+  P->inv_st = (float)(1.0 / st);
   P->albedo = (float)(m.sigma_s / st);
   P->sa_v = (float)(m.sigma_a * m.v);
   P->v = (float)m.v;
@@ -266,16 +268,33 @@ void make_trace_params(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
 }
 
 // Common launch of the path kernel for render and debug.
+// Launch shape: the requested (or largest) block size whose shared memory
+// fits, falling back to global FP64 accumulation when no tile fits.
+void choose_launch(const darts_ctx* ctx, const darts_sampling* sp, const TraceParams& P, bool debug,
+                   int* block, bool* tile, size_t* smem) {
+  const int want = ctx->block ? ctx->block : 768;
+  *tile = true;
+  *block = trace_block_for(want, debug, true, sp->method, sp->ris_m);
+  *smem = trace_smem_bytes(sp->method, P, *block, true);
+  while (*smem > (size_t)ctx->smem_optin && *block > 512) {
+    *block = *block == 768 ? 640 : 512;
+    *smem = trace_smem_bytes(sp->method, P, *block, true);
+  }
+  if (*smem > (size_t)ctx->smem_optin) {
+    *tile = false;
+    *block = 512;
+    *smem = trace_smem_bytes(sp->method, P, *block, false);
+  }
+}
+
 darts_status run_trace(darts_ctx* ctx, const darts_scene* sc, const darts_sampling* sp,
                        TraceParams& P, bool debug) {
-  const int block = ctx->block;
   const int grid = ctx->sm_count;
-  bool tile = true;
-  size_t smem = trace_smem_bytes(sp->method, P, block, tile);
-  if (smem > (size_t)ctx->smem_optin) {
-    tile = false;
-    smem = trace_smem_bytes(sp->method, P, block, tile);
-  }
+  int block;
+  bool tile;
+  size_t smem;
+  choose_launch(ctx, sp, P, debug, &block, &tile, &smem);
+  ctx->last_block = block;
   if (smem > (size_t)ctx->smem_optin)
     return fail(ctx, DARTS_ERR_UNSUPPORTED, "direction table of %zu bytes exceeds shared memory", smem);
   const size_t pbytes = (size_t)grid * 2 * P.n_bins * sizeof(double);
@@ -409,6 +428,58 @@ darts_status darts_last_kernel_ms(darts_ctx* ctx, float* ms) {
   CK(cudaEventSynchronize(ctx->ev_stop), "event synchronize");
   CK(cudaEventElapsedTime(ms, ctx->ev_start, ctx->ev_stop), "event elapsed time");
   return DARTS_OK;
+}
+
+darts_status darts_set_launch(darts_ctx* ctx, int block) {
+  if (!ctx) return DARTS_ERR_INVALID_ARG;
+  if (block != 0 && block != 512 && block != 640 && block != 768)
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "block must be 0, 512, 640 or 768");
+  ctx->block = block;
+  return DARTS_OK;
+}
+
+darts_status darts_autotune(darts_ctx* ctx, const darts_scene* scene, const darts_sampling* sampling,
+                            int* block_out) {
+  if (!ctx) return DARTS_ERR_INVALID_ARG;
+  darts_status s = validate(ctx, scene, sampling);
+  if (s != DARTS_OK) return s;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const size_t hb = (size_t)scene->gate.n_bins * sizeof(double);
+  CK(ensure((void**)&ctx->host_hist, &ctx->host_hist_bytes, 2 * hb), "histogram allocation");
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "event create");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(ctx, DARTS_ERR_CUDA, "event create");
+  }
+  const int saved = ctx->block;
+  const int cand[3] = {512, 640, 768};
+  int best = 0;
+  float best_ms = 0.0f;
+  s = DARTS_OK;
+  for (int c = 0; c < 3 && s == DARTS_OK; ++c) {
+    ctx->block = cand[c];
+    float tot = 0.0f;
+    for (int it = 0; it < 4 && s == DARTS_OK; ++it) {
+      if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) s = fail(ctx, DARTS_ERR_CUDA, "event record");
+      if (s == DARTS_OK) s = darts_render(ctx, scene, sampling, ctx->host_hist, nullptr, 0, nullptr);
+      if (s == DARTS_OK && cudaEventRecord(e1, ctx->stream) != cudaSuccess) s = fail(ctx, DARTS_ERR_CUDA, "event record");
+      float ms = 0.0f;
+      if (s == DARTS_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        s = fail(ctx, DARTS_ERR_CUDA, "event timing");
+      if (it > 0) tot += ms;
+    }
+    // a block size whose shared memory does not fit falls back to a smaller one
+    if (s == DARTS_OK && ctx->last_block == cand[c] && (best == 0 || tot < best_ms)) {
+      best = cand[c];
+      best_ms = tot;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->block = (s == DARTS_OK && best) ? best : saved;
+  if (block_out) *block_out = ctx->block;
+  return s;
 }
 
 int32_t darts_table_row_stride(int32_t table_n_mu) { return row_stride_of(table_n_mu); }
@@ -657,16 +728,16 @@ extern "C" darts_status darts_render_static(const darts_scene* scene, const dart
   P.hist = hist_dev;
   P.sumsq = sumsq_dev;
   P.partials = partials;
-  bool tile = true;
-  size_t smem = trace_smem_bytes(sampling->method, P, tmp.block, tile);
-  if (smem > (size_t)tmp.smem_optin) {
-    tile = false;
-    smem = trace_smem_bytes(sampling->method, P, tmp.block, tile);
-    P.acc = partials;  // 2 * B doubles, zeroed below
+  int block;
+  bool tile;
+  size_t smem;
+  choose_launch(&tmp, sampling, P, false, &block, &tile, &smem);
+  if (!tile) {
+    P.acc = partials;  // 2 * B doubles, zeroed here
     if (cudaMemsetAsync(partials, 0, 2 * hb, stream) != cudaSuccess) return DARTS_ERR_CUDA;
   }
   if (smem > (size_t)tmp.smem_optin) return DARTS_ERR_UNSUPPORTED;
-  if (launch_trace(sampling->method, P, tmp.sm_count, tmp.block, false, tile, smem, stream) != cudaSuccess)
+  if (launch_trace(sampling->method, P, tmp.sm_count, block, false, tile, smem, stream) != cudaSuccess)
     return DARTS_ERR_CUDA;
   return DARTS_OK;
 }

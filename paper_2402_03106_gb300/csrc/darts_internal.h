@@ -28,7 +28,7 @@ struct TableParams {
 // Path kernels.  Everything the step functions read, in FP32 unless noted.
 struct TraceParams {
   // medium
-  float sigma_s, sigma_t, albedo, sa_v, v, inv_v;
+  float sigma_s, sigma_t, inv_st, albedo, sa_v, v, inv_v;
   float phi_k0, phi_invk;          // Eq. 9 in log form, see TableParams
   float hg_a, hg_b, hg_c, g;       // HG constants (hg_eval) and g
   double phi_k0_d, phi_invk_d, sa_v_d, inv_v_d;  // the same, FP64 (small-t' branch)
@@ -52,6 +52,7 @@ struct TraceParams {
   int K, M;
   uint32_t key0, key1, stream;
   uint32_t o_e;                    // bin offset of the sensor element
+  unsigned long long bin_base;     // (path_offset + o_e) mod n_bins: bin of local path 0
   unsigned long long N;            // paths in this launch (local index 0..N-1)
   unsigned long long path_offset;  // global id = path_offset + local index
   float wb;                        // weight per path contribution (DARTS n_bins/N_e, else 1/N_e)
@@ -83,6 +84,8 @@ cudaError_t launch_trace(int method, const TraceParams& p, int grid, int block, 
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t n,
                           uint32_t* out, cudaStream_t s);
 size_t trace_smem_bytes(int method, const TraceParams& p, int block, bool tile);
+// Block size actually launched for a request (non-production variants use 512).
+int trace_block_for(int block, bool debug, bool tile, int method, int M);
 int trace_max_m();
 
 }  // namespace darts

@@ -54,8 +54,18 @@ struct Path {
   unsigned long long j;  // local path index
 };
 
+// Event counting.  Common events set a bit for the current vertex step; the
+// warp turns the bits into counts with ballots once per step (no per-lane
+// counter registers).  Rare FP64 events go straight to block counters in
+// shared memory.
+__shared__ unsigned long long s_rare[2];
+
 struct Counters {
-  unsigned v[kStatCount];
+  unsigned bits;
+  __device__ __forceinline__ void add(int slot) { bits |= 1u << slot; }
+  __device__ __forceinline__ void add_rare(int slot) {
+    atomicAdd(&s_rare[slot - ST_FP64E], 1ull);
+  }
 };
 
 __device__ __forceinline__ U4 rng(const TraceParams& P, unsigned long long id, uint32_t vertex,
@@ -85,13 +95,26 @@ __device__ __forceinline__ float box_exit(const TraceParams& P, float x, float y
   return fmaxf(d, 0.0f);
 }
 
+// Near-degenerate ellipse (S - C < 2^-12 C): the solve of Eq. 18 in FP64,
+// kept out of line so that none of its conversions enter the common path.
+__device__ __noinline__ void ellipse_fp64(float delta, float C, float S_lo, float dS, float q,
+                                          float* r1, float* den, float* cos_s) {
+  const double dd = (double)delta, Cd = (double)C, Sd = (double)S_lo + (double)dS, qd = (double)q;
+  const double dend = dd + Cd * qd;  // S - C mu
+  const double r1d = (dd * dd + 2.0 * Sd * Cd * qd) / (2.0 * dend);
+  const double td = dd * (Sd + Cd) / (2.0 * dend);
+  *cos_s = (float)((Cd * (1.0 - qd) - td) / r1d);
+  *r1 = (float)r1d;
+  *den = (float)dend;
+}
+
 // Control vertex on the ray (x, w) with S in [S_lo, S_hi) (Eq. 18, 21, 22).
 // uniform_S selects the uniform temporal density of the baseline.  Returns
-// the contribution divided by beta (0 when the range is empty) and S.
-__device__ __forceinline__ float connect(const TraceParams& P, float x, float y, float z, float wx,
-                                         float wy, float wz, float C, float ax, float ay, float az,
-                                         float S_lo, float S_hi, float u, bool uniform_S,
-                                         float* S_out, Counters& cnt) {
+// the contribution divided by beta and writes S.
+__device__ __forceinline__ float connect(const TraceParams& P, float wx, float wy, float wz,
+                                         float C, float ax, float ay, float az, float S_lo,
+                                         float S_hi, float u, bool uniform_S, float* S_out,
+                                         Counters& cnt) {
   const float W = S_hi - S_lo;
   float dS, conn_w;  // conn_w = exp(-sigma_t S) / p(S)
   if (!uniform_S) {
@@ -109,19 +132,12 @@ __device__ __forceinline__ float connect(const TraceParams& P, float x, float y,
   const float q = 0.5f * fmaf(qx, qx, fmaf(qy, qy, qz * qz));  // 1 - mu
   float r1, den, cos_s;
   if (delta < C * (1.0f / 4096.0f)) {
-    // near-degenerate ellipse: solve in FP64
-    const double dd = (double)delta, Cd = (double)C, Sd = (double)S_lo + (double)dS, qd = (double)q;
-    const double dend = dd + Cd * qd;  // S - C mu
-    const double r1d = (dd * dd + 2.0 * Sd * Cd * qd) / (2.0 * dend);
-    const double td = dd * (Sd + Cd) / (2.0 * dend);
-    cos_s = (float)((Cd * (1.0 - qd) - td) / r1d);
-    r1 = (float)r1d;
-    den = (float)dend;
-    cnt.v[ST_FP64E] += 1;
+    ellipse_fp64(delta, C, S_lo, dS, q, &r1, &den, &cos_s);
+    cnt.add_rare(ST_FP64E);
   } else {
-    den = fmaf(C, q, delta);                                   // S - C mu
-    r1 = __fdividef(fmaf(delta, delta, 2.0f * S * C * q), 2.0f * den);  // S - t
-    const float t = __fdividef(delta * (S + C), 2.0f * den);   // Eq. 18
+    den = fmaf(C, q, delta);                                             // S - C mu
+    r1 = __fdividef(fmaf(delta, delta, 2.0f * S * C * q), 2.0f * den);   // S - t
+    const float t = __fdividef(delta * (S + C), 2.0f * den);             // Eq. 18
     cos_s = __fdividef(fmaf(C, 1.0f - q, -t), r1);
   }
   *S_out = S;
@@ -130,22 +146,55 @@ __device__ __forceinline__ float connect(const TraceParams& P, float x, float y,
   return P.sigma_s * conn_w * f * P.Ie / (r1 * den);
 }
 
-// log Phi(r, t') of Eq. 9 with s = v t' (length units), FP32 or FP64 for small s.
-__device__ __forceinline__ float log_phi(const TraceParams& P, float r2, float s, double s_d,
-                                         bool small, Counters& cnt) {
-  if (!small) {
-    const float tp = s * P.inv_v;
-    return P.phi_k0 - 1.5f * __logf(tp) - __fdividef(r2 * P.phi_invk, tp) - P.sa_v * tp;
-  }
-  cnt.v[ST_FP64P] += 1;
-  const double tp = s_d * P.inv_v_d;
+// One distance step of a DARTS vertex, as handed to the RIS evaluation:
+// r^2 of a candidate at distance d is (d + b)^2 + h2 with b = <w, x - x_e>
+// and h2 the squared distance of x_e from the ray; S_M as a float pair.
+struct RisTask {
+  float b, h2, SM, SMlo;
+  float pm, u3;
+  uint32_t e0row;  // eps0 (24 bits) | radical-inverse row << 24
+  uint32_t nonempty;  // decision-trace bit of this vertex's control vertex
+};
+struct RisResult {
+  float factor, dsel;
+  int sel, ok;
+};
+
+// log Phi (Eq. 9) for a candidate with remaining length s = S_M - d, in FP64
+// (small t'), kept out of line.
+__device__ __noinline__ float log_phi_fp64(const TraceParams& P, float r2, float SM, float SMlo,
+                                           float d) {
+  const double s = ((double)SM + (double)SMlo) - (double)d;
+  const double tp = s * P.inv_v_d;
   return (float)(P.phi_k0_d - 1.5 * log(tp) - (double)r2 * P.phi_invk_d / tp - P.sa_v_d * tp);
+}
+
+// Candidate j of a RIS task: distance (Eq. 13-14, sign fixed) and log target
+// weight (Eq. 10, -FLT_MAX when non-causal).
+__device__ __forceinline__ float ris_candidate(const TraceParams& P, const RisTask& T, int j,
+                                               bool act, float* d_out, Counters& cnt) {
+  const uint32_t srow = T.e0row >> 24, e0 = T.e0row & 0xFFFFFFu;
+  const uint32_t idx = (8u * srow + (uint32_t)j) & 255u;
+  const uint32_t ri24 = __brev(idx) >> 8;
+  const float eps = u01(((ri24 + e0) & 0xFFFFFFu) << 8);
+  const float d = -log1m(T.pm * eps) * P.inv_st;
+  const float e = d + T.b;
+  const float r2 = fmaf(e, e, T.h2);
+  const float s = T.SM - d;  // remaining length budget
+  *d_out = d;
+  if (!(s > 0.0f && r2 < s * s)) return -FLT_MAX;
+  if (act && s < P.tiny_s) {
+    cnt.add_rare(ST_FP64P);
+    return log_phi_fp64(P, r2, T.SM, T.SMlo, d);
+  }
+  const float tp = s * P.inv_v;
+  return P.phi_k0 - 1.5f * __logf(tp) - __fdividef(r2 * P.phi_invk, tp) - P.sa_v * tp;
 }
 
 template <int METHOD, int MAXM, bool DEBUG>
 struct Stepper {
   // Initialise a path with local index j.
-  __device__ static void init(const TraceParams& P, Path& p, unsigned long long j) {
+  __device__ static void init(const TraceParams& P, Path& p, unsigned long long j, int bin) {
     p.x = P.xs[0];
     p.y = P.xs[1];
     p.z = P.xs[2];
@@ -158,8 +207,7 @@ struct Stepper {
     p.wy = 0.0f;
     p.wz = 1.0f;
     if (METHOD == kDarts) {
-      const unsigned long long gid = P.path_offset + j;
-      p.bin = (int)((gid + P.o_e) % (unsigned long long)P.n_bins);
+      p.bin = bin;
       p.Sm0 = fmaf((float)p.bin, P.S_bin, P.S_gate_lo);
       p.SM0 = fmaf((float)(p.bin + 1), P.S_bin, P.S_gate_lo);
       p.beta = 1.0f;
@@ -177,10 +225,13 @@ struct Stepper {
     if (DEBUG && p.j < P.N && p.k < P.K) P.dbg_dec[(p.j * P.K + p.k) * 4 + slot] = val;
   }
 
-  // One vertex of a DARTS path; returns true when the path ended.
-  __device__ static bool step_darts(const TraceParams& P, Path& p, const float* tab,
-                                    Counters& cnt) {
-    cnt.v[ST_VERT] += 1;
+  // Vertex step of a DARTS path up to the distance step: early exit,
+  // direction (MIS of the EDA table and the base strategy), control vertex,
+  // max-depth test and the Bernoulli medium event.  Returns true when the
+  // path ended; otherwise fills the RIS task of its distance step.
+  __device__ static bool vertex_darts(const TraceParams& P, Path& p, const float* tab,
+                                      Counters& cnt, RisTask& task) {
+    cnt.add(ST_VERT);
     const float ex = P.xe[0] - p.x, ey = P.xe[1] - p.y, ez = P.xe[2] - p.z;
     const float C2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
     const float C = sqrtf(C2);
@@ -188,7 +239,7 @@ struct Stepper {
     const float ax = ex * invC, ay = ey * invC, az = ez * invC;
     const float SM = p.SM0 - p.L, Sm = p.Sm0 - p.L;
     if (!(SM > C)) {  // Sec. 5.2 early exit
-      cnt.v[ST_EARLY] += 1;
+      cnt.add(ST_EARLY);
       record(P, p, 0, EV_EARLY);
       return true;
     }
@@ -199,7 +250,7 @@ struct Stepper {
     int i_s = (int)floorf((__log2f(SM * P.inv_smax) + 8.0f) * P.n_s_over_8);
     i_s = min(max(i_s, 0), P.n_s - 1);
     const float* row = tab + (i_rho * P.n_s + i_s) * P.row_stride;
-    float gamma = rho / (rho + P.mis_alpha);
+    float gamma = __fdividef(rho, rho + P.mis_alpha);
     const bool sensor = p.k == 0;
     if (sensor && P.uniform_sensor) gamma = 0.0f;
     const float gb = sensor ? 0.0f : P.g;
@@ -208,158 +259,146 @@ struct Stepper {
     const float v0 = u01(u1.x), v1 = u01(u1.y);
     float sphi, cphi;
     sincos_2pi(u01(u1.z), &sphi, &cphi);
-    float wx, wy, wz, pE, mu_b;
-    int mu_bin;
     const bool eda = v0 < gamma;
-    if (eda) {
-      // inverse CDF: first bin whose upper edge exceeds v1
-      int lo = 0, n = P.n_mu;
-      while (n > 1) {
-        const int half = n >> 1;
-        const bool right = !(row[lo + half] > v1);
-        lo = right ? lo + half : lo;
-        n -= half;
-      }
-      const float c_lo = row[lo], c_hi = row[lo + 1];
-      const float frac = __fdividef(v1 - c_lo, c_hi - c_lo);
-      const float mu = fmaf((float)lo + frac, 1.0f / P.mu_scale, -1.0f);
-      frame_dir(ax, ay, az, mu, sphi, cphi, &wx, &wy, &wz);
-      pE = (c_hi - c_lo) * P.mu_scale * (1.0f / kTwoPi);
-      mu_b = fmaf(wx, bx, fmaf(wy, by, wz * bz));
-      mu_bin = lo;
-    } else {
-      mu_b = hg_sample(gb, v1);
-      frame_dir(bx, by, bz, mu_b, sphi, cphi, &wx, &wy, &wz);
-      const float mua = fmaf(wx, ax, fmaf(wy, ay, wz * az));
-      int i = (int)floorf((mua + 1.0f) * P.mu_scale);
-      i = min(max(i, 0), P.n_mu - 1);
-      pE = (row[i + 1] - row[i]) * P.mu_scale * (1.0f / kTwoPi);
-      mu_bin = i;
+    // inverse CDF of the row: first bin whose upper edge exceeds v1
+    int lo = 0, n = P.n_mu;
+    while (n > 1) {
+      const int half = n >> 1;
+      lo = (row[lo + half] > v1) ? lo : lo + half;
+      n -= half;
     }
+    const float c_lo = row[lo], c_hi = row[lo + 1];
+    const float mu_eda = fmaf((float)lo + __fdividef(v1 - c_lo, c_hi - c_lo), 1.0f / P.mu_scale, -1.0f);
+    const float mu_hg = hg_sample(gb, v1);
+    float wx, wy, wz;
+    frame_dir(eda ? ax : bx, eda ? ay : by, eda ? az : bz, eda ? mu_eda : mu_hg, sphi, cphi, &wx, &wy,
+              &wz);
+    const float mu_b = eda ? fmaf(wx, bx, fmaf(wy, by, wz * bz)) : mu_hg;
+    int bin = lo;
+    if (!eda) {
+      const float mua = fmaf(wx, ax, fmaf(wy, ay, wz * az));
+      bin = min(max((int)floorf((mua + 1.0f) * P.mu_scale), 0), P.n_mu - 1);
+    }
+    const float pE = (eda ? c_hi - c_lo : row[bin + 1] - row[bin]) * P.mu_scale * (1.0f / kTwoPi);
     const float gb2 = gb * gb;
     const float pB = hg_eval(mu_b, (1.0f - gb2) * kInv4Pi, 1.0f + gb2, 2.0f * gb);
     const float f = sensor ? 1.0f : hg_eval(mu_b, P.hg_a, P.hg_b, P.hg_c);
     p.beta *= __fdividef(f, fmaf(gamma, pE - pB, pB));
     if (DEBUG) {
       record(P, p, 2, eda ? 1 : 0);
-      record(P, p, 3, (uint8_t)(mu_bin & 0xFF));
+      record(P, p, 3, (uint8_t)(bin & 0xFF));
     }
     // ---- control vertex (Eq. 18, 21, 22), medium boundary as the cap
     const float dm = box_exit(P, p.x, p.y, p.z, wx, wy, wz);
-    const float mx = fmaf(wx, dm, p.x) - P.xe[0], my = fmaf(wy, dm, p.y) - P.xe[1],
-                mz = fmaf(wz, dm, p.z) - P.xe[2];
+    const float mx = fmaf(wx, dm, -ex), my = fmaf(wy, dm, -ey), mz = fmaf(wz, dm, -ez);
     const float S_dm = dm + sqrtf(fmaf(mx, mx, fmaf(my, my, mz * mz)));
     const float S_hi = fminf(SM, S_dm), S_lo = fmaxf(Sm, C);
     const bool ok = S_hi > S_lo;
     if (ok) {
       float S;
-      const float cc = connect(P, p.x, p.y, p.z, wx, wy, wz, C, ax, ay, az, S_lo, S_hi,
-                               u01(u1.w), false, &S, cnt);
+      const float cc = connect(P, wx, wy, wz, C, ax, ay, az, S_lo, S_hi, u01(u1.w), false, &S, cnt);
       p.c = fmaf(p.beta, cc, p.c);
-      cnt.v[ST_CONN] += 1;
+      cnt.add(ST_CONN);
     }
     const uint8_t nonempty = ok ? 0x10 : 0;
+    p.wx = wx;  // the walk continues along the connection direction (Eq. 20)
+    p.wy = wy;
+    p.wz = wz;
     if (p.k + 1 == P.K) {
       record(P, p, 0, EV_MAXDEPTH | nonempty);
       return true;
     }
-    // ---- distance: Bernoulli medium event (Eq. 12) + DA-RIS (Eq. 13-15)
+    // ---- Bernoulli medium event (Eq. 12)
     const U4 u0 = rng(P, p.j, (uint32_t)p.k, 0);
-    const float em = expm1_neg(-P.sigma_t * dm);
-    const float pm = -em;
+    const float pm = -expm1_neg(-P.sigma_t * dm);
     if (!(u01(u0.x) < pm)) {
-      cnt.v[ST_ESCAPE] += 1;
+      cnt.add(ST_ESCAPE);
       record(P, p, 0, EV_ESCAPE | nonempty);
       return true;
     }
-    cnt.v[ST_DIST] += 1;
-    const uint32_t srow = u0.y >> 27;  // floor(32 u)
-    const uint32_t e0 = u0.z >> 8;     // eps0 as a 24-bit fraction
-    const float inv_st = 1.0f / P.sigma_t;
-    float dj[MAXM], lw[MAXM];
-    float lmax = -FLT_MAX;
-    const int M = MAXM == 8 ? 8 : P.M;
-#pragma unroll
-    for (int j = 0; j < MAXM; ++j) {
-      if (j < M) {
-        const uint32_t idx = (8u * srow + (uint32_t)j) & 255u;
-        const uint32_t ri24 = __brev(idx) >> 8;
-        const float eps = u01(((ri24 + e0) & 0xFFFFFFu) << 8);
-        const float d = -log1m(pm * eps) * inv_st;  // Eq. 14 (sign fixed)
-        const float cx = fmaf(wx, d, p.x) - P.xe[0], cy = fmaf(wy, d, p.y) - P.xe[1],
-                    cz = fmaf(wz, d, p.z) - P.xe[2];
-        const float r2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-        const float s = SM - d;  // remaining length budget
-        const bool valid = s > 0.0f && r2 < s * s;
-        float l = -FLT_MAX;
-        if (valid) {
-          const bool small = s < P.tiny_s;
-          double s_d = 0.0;
-          if (small) s_d = ((double)p.SM0 - (double)p.L + (double)p.Lc) - (double)d;
-          l = log_phi(P, r2, s, s_d, small, cnt);
-        }
-        dj[j] = d;
-        lw[j] = l;
-        lmax = fmaxf(lmax, l);
-      }
-    }
-    if (lmax == -FLT_MAX) {
-      cnt.v[ST_INVALID] += 1;
-      record(P, p, 0, EV_INVALID | nonempty);
+    cnt.add(ST_DIST);
+    // ---- RIS task of the distance step (Eq. 13-15)
+    task.b = -fmaf(wx, ex, fmaf(wy, ey, wz * ez));
+    const float hx = fmaf(wy, ez, -wz * ey), hy = fmaf(wz, ex, -wx * ez), hz = fmaf(wx, ey, -wy * ex);
+    task.h2 = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
+    task.SM = SM;
+    task.SMlo = ((p.SM0 - SM) - p.L) + p.Lc;  // S_M = SM + SMlo incl. the Kahan term
+    task.pm = pm;
+    task.u3 = u01(u0.w);
+    task.e0row = (u0.z >> 8) | ((u0.y >> 27) << 24);
+    task.nonempty = nonempty;
+    return false;
+  }
+
+  // Apply a RIS selection: throughput (Eq. 15) and vertex advance.
+  __device__ static bool finish_ris(const TraceParams& P, Path& p, const RisResult& r,
+                                    uint32_t nonempty, Counters& cnt) {
+    if (!r.ok) {
+      cnt.add(ST_INVALID);
+      record(P, p, 0, (uint8_t)(EV_INVALID | nonempty));
       return true;
     }
+    record(P, p, 0, (uint8_t)(EV_SCATTER | nonempty));
+    record(P, p, 1, (uint8_t)r.sel);
+    p.beta *= r.factor;
+    p.x = fmaf(p.wx, r.dsel, p.x);
+    p.y = fmaf(p.wy, r.dsel, p.y);
+    p.z = fmaf(p.wz, r.dsel, p.z);
+    kahan_add(p.L, p.Lc, r.dsel);
+    p.k += 1;
+    return false;
+  }
+
+  // RIS of one lane's task, candidate by candidate (any M <= MAXM).
+  __device__ static RisResult ris_lane(const TraceParams& P, const RisTask& T, Counters& cnt) {
+    float dj[MAXM], lw[MAXM];
+    float lmax = -FLT_MAX;
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) {
+      if (j < P.M) {
+        lw[j] = ris_candidate(P, T, j, true, &dj[j], cnt);
+        lmax = fmaxf(lmax, lw[j]);
+      }
+    }
+    RisResult r{0.0f, 0.0f, -1, 0};
+    if (lmax == -FLT_MAX) return r;
     float wsum = 0.0f;
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) {
-      if (j < M) {
-        const float w = lw[j] == -FLT_MAX ? 0.0f : __expf(lw[j] - lmax);
-        lw[j] = w;
-        wsum += w;
+      if (j < P.M) {
+        lw[j] = lw[j] == -FLT_MAX ? 0.0f : __expf(lw[j] - lmax);
+        wsum += lw[j];
       }
     }
-    const float target = u01(u0.w) * wsum;
-    float prefix = 0.0f, dsel = 0.0f, wsel = 0.0f;
-    int sel = -1, last_valid = 0;
+    const float target = T.u3 * wsum;
+    float prefix = 0.0f;
+    int last_valid = 0;
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) {
-      if (j < M) {
+      if (j < P.M) {
         prefix += lw[j];
         if (lw[j] > 0.0f) last_valid = j;
-        if (sel < 0 && prefix > target) {
-          sel = j;
-          dsel = dj[j];
-          wsel = lw[j];
-        }
+        if (r.sel < 0 && prefix > target) r.sel = j;
       }
     }
-    if (sel < 0) {  // rounding at the top end
+    if (r.sel < 0) r.sel = last_valid;
+    float wsel = 0.0f;
 #pragma unroll
-      for (int j = 0; j < MAXM; ++j)
-        if (j == last_valid) {
-          sel = j;
-          dsel = dj[j];
-          wsel = lw[j];
-        }
-    }
-    p.beta *= P.albedo * __fdividef(wsum, wsel * (float)M);
-    record(P, p, 1, (uint8_t)sel);
-    record(P, p, 0, EV_SCATTER | nonempty);
-    p.x = fmaf(wx, dsel, p.x);
-    p.y = fmaf(wy, dsel, p.y);
-    p.z = fmaf(wz, dsel, p.z);
-    kahan_add(p.L, p.Lc, dsel);
-    p.wx = wx;
-    p.wy = wy;
-    p.wz = wz;
-    p.k += 1;
-    return false;
+    for (int j = 0; j < MAXM; ++j)
+      if (j == r.sel) {
+        wsel = lw[j];
+        r.dsel = dj[j];
+      }
+    r.factor = P.albedo * __fdividef(wsum, wsel * (float)P.M);
+    r.ok = 1;
+    return r;
   }
 
   // One vertex of a baseline path.  `out_bin`/`out_c` receive a contribution
   // to commit this step (out_bin < 0: none).  Returns true when the path ended.
   __device__ static bool step_base(const TraceParams& P, Path& p, Counters& cnt, int* out_bin,
                                    float* out_c) {
-    cnt.v[ST_VERT] += 1;
+    cnt.add(ST_VERT);
     *out_bin = -1;
     if (METHOD == kPlain) {
       const float ex = P.xe[0] - p.x, ey = P.xe[1] - p.y, ez = P.xe[2] - p.z;
@@ -367,7 +406,7 @@ struct Stepper {
       const float invC = 1.0f / C;
       const float SM = P.S_gate_hi - p.L, Sm = P.S_gate_lo - p.L;
       if (!(SM > C)) {
-        cnt.v[ST_EARLY] += 1;
+        cnt.add(ST_EARLY);
         record(P, p, 0, EV_EARLY);
         return true;
       }
@@ -379,9 +418,9 @@ struct Stepper {
       const U4 u1 = rng(P, p.j, (uint32_t)p.k, 1);
       if (S_hi > S_lo) {
         float S;
-        const float cc = connect(P, p.x, p.y, p.z, p.wx, p.wy, p.wz, C, ex * invC, ey * invC,
-                                 ez * invC, S_lo, S_hi, u01(u1.w), true, &S, cnt);
-        cnt.v[ST_CONN] += 1;
+        const float cc = connect(P, p.wx, p.wy, p.wz, C, ex * invC, ey * invC, ez * invC, S_lo,
+                                 S_hi, u01(u1.w), true, &S, cnt);
+        cnt.add(ST_CONN);
         const float y = ((p.L + S) - P.S_gate_lo) * P.inv_S_bin;
         int b = (int)floorf(y);
         b = min(max(b, 0), P.n_bins - 1);
@@ -396,7 +435,7 @@ struct Stepper {
       const U4 u0 = rng(P, p.j, (uint32_t)p.k, 0);
       const float d = -log1m(u01(u0.x)) / P.sigma_t;
       if (!(d < dm)) {
-        cnt.v[ST_ESCAPE] += 1;
+        cnt.add(ST_ESCAPE);
         record(P, p, 0, EV_ESCAPE);
         return true;
       }
@@ -411,7 +450,7 @@ struct Stepper {
       const U4 u0 = rng(P, p.j, (uint32_t)p.k, 0);
       const float d = -log1m(u01(u0.x)) / P.sigma_t;
       if (!(d < dm)) {
-        cnt.v[ST_ESCAPE] += 1;
+        cnt.add(ST_ESCAPE);
         record(P, p, 0, EV_ESCAPE);
         return true;
       }
@@ -426,14 +465,14 @@ struct Stepper {
       const float cos_s = -(ex * p.wx + ey * p.wy + ez * p.wz) / C;
       const float y = ((p.L + C) - P.S_gate_lo) * P.inv_S_bin;
       if (y >= 0.0f && y < (float)P.n_bins) {
-        cnt.v[ST_CONN] += 1;
+        cnt.add(ST_CONN);
         *out_bin = min((int)y, P.n_bins - 1);
         *out_c = p.beta * hg_eval(cos_s, P.hg_a, P.hg_b, P.hg_c) * __expf(-P.sigma_t * C) * P.Ie /
                  C2;
         p.c += *out_c;
       }
       if (!(p.L + C < P.S_gate_hi)) {
-        cnt.v[ST_EARLY] += 1;
+        cnt.add(ST_EARLY);
         record(P, p, 0, EV_EARLY);
         return true;
       }
@@ -485,38 +524,105 @@ __device__ __forceinline__ void warp_commit(bool has, int bin, float val, float*
   }
 }
 
-template <int METHOD, int MAXM, bool DEBUG, bool TILE>
-__global__ void __launch_bounds__(512, 1) trace_kernel(const TraceParams P) {
+// Cooperative RIS of a warp (M = 8): every lane that passed the medium event
+// publishes its task; each round the 32 lanes evaluate 4 tasks x 8 candidates,
+// one candidate per lane, and the 8-lane segments reduce (max), weight
+// (exp), scan (prefix sums) and select by ballot.  All lanes must call this.
+__device__ __forceinline__ void ris_warp(const TraceParams& P, bool need, const RisTask& task,
+                                         RisTask* tasks, RisResult* results, RisResult& mine,
+                                         Counters& cnt) {
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(kFull, need);
+  if (!m) return;
+  const int n = __popc(m);
+  const int slot = __popc(m & ((1u << lane) - 1u));
+  if (need) tasks[slot] = task;
+  __syncwarp();
+  const int seg = lane & 24, j = lane & 7;
+  for (int base = 0; base < n; base += 4) {
+    const int t = base + (lane >> 3);
+    const bool act = t < n;
+    const RisTask T = tasks[act ? t : 0];
+    float d;
+    const float lw = ris_candidate(P, T, j, act, &d, cnt);
+    const bool valid = act && lw != -FLT_MAX;
+    float mx = lw;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o, 8));
+    const float w = valid ? __expf(lw - mx) : 0.0f;
+    float pre = w;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const float y = __shfl_up_sync(kFull, pre, o, 8);
+      if (j >= o) pre += y;
+    }
+    const float tot = __shfl_sync(kFull, pre, 7, 8);
+    const unsigned gt = __ballot_sync(kFull, act && pre > T.u3 * tot);
+    const unsigned vb = __ballot_sync(kFull, valid);
+    const unsigned gbits = (gt >> seg) & 0xFFu, vbits = (vb >> seg) & 0xFFu;
+    const int sel = gbits ? __ffs(gbits) - 1 : (vbits ? 31 - __clz(vbits) : 0);
+    const float wsel = __shfl_sync(kFull, w, sel, 8);
+    const float dsel = __shfl_sync(kFull, d, sel, 8);
+    if (act && j == 0) {
+      RisResult r;
+      r.ok = vbits != 0;
+      r.sel = sel;
+      r.dsel = dsel;
+      r.factor = P.albedo * __fdividef(tot, wsel * 8.0f);
+      results[t] = r;
+    }
+  }
+  __syncwarp();
+  if (need) mine = results[slot];
+  __syncwarp();
+}
+
+// (a + r) mod B for 0 <= a < B and 0 <= r < 64 without a division when B >= 64.
+__device__ __forceinline__ int add_mod(int a, int r, int B) {
+  const int v = a + r;
+  return v < B ? v : (B >= 64 ? v - B : v % B);
+}
+
+template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   const int tab_floats = METHOD == kDarts ? P.rows * P.row_stride : 0;
   float* tab = smem;
-  const int nwarps = blockDim.x >> 5;
+  constexpr int nwarps = BLOCK / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int B = P.n_bins;
-  float* tiles = smem + tab_floats;
-  float* wsum = tiles + (size_t)warp * 3 * B;
+  const bool do_sq = P.sumsq != nullptr;
+  const int tile_stride = (do_sq ? 3 : 2) * B;
+  constexpr bool kCoop = METHOD == kDarts && MAXM == 8;
+  RisTask* ris_tasks = reinterpret_cast<RisTask*>(smem + tab_floats);
+  RisResult* ris_results = reinterpret_cast<RisResult*>(ris_tasks + (kCoop ? nwarps * 32 : 0));
+  RisTask* wtasks = ris_tasks + warp * 32;
+  RisResult* wresults = ris_results + warp * 32;
+  float* tiles = reinterpret_cast<float*>(ris_results + (kCoop ? nwarps * 32 : 0));
+  float* wsum = tiles + (size_t)warp * tile_stride;
   float* wcomp = wsum + B;
   float* wsq = wcomp + B;
   __shared__ unsigned long long blk_stats[kStatCount];
+  __shared__ unsigned warp_events[nwarps][8];
 
   // stage the direction table (row stride is a multiple of 4 floats)
   if (METHOD == kDarts) {
     const float4* src = reinterpret_cast<const float4*>(P.table);
-    for (int i = threadIdx.x; i < tab_floats / 4; i += blockDim.x) smem4[i] = __ldg(src + i);
+    for (int i = threadIdx.x; i < tab_floats / 4; i += BLOCK) smem4[i] = __ldg(src + i);
   }
   if (TILE)
-    for (int i = threadIdx.x; i < nwarps * 3 * B; i += blockDim.x) tiles[i] = 0.0f;
+    for (int i = threadIdx.x; i < nwarps * tile_stride; i += BLOCK) tiles[i] = 0.0f;
   if (threadIdx.x < kStatCount) blk_stats[threadIdx.x] = 0;
+  if (threadIdx.x < 2) s_rare[threadIdx.x] = 0;
+  if (lane < 8) warp_events[warp][lane] = 0;
   __syncthreads();
 
-  const bool do_sq = P.sumsq != nullptr;
   Counters cnt;
-#pragma unroll
-  for (int i = 0; i < kStatCount; ++i) cnt.v[i] = 0;
   Path p;
   bool alive = false;
   unsigned long long pool_next = 0, pool_end = 0;
+  int pool_bin = 0;  // DARTS bin of path pool_next
   bool drained = false;
 
   for (;;) {
@@ -527,7 +633,7 @@ __global__ void __launch_bounds__(512, 1) trace_kernel(const TraceParams P) {
       const int n_dead = __popc(dead);
       const unsigned long long avail = pool_end - pool_next;
       if (!alive && (unsigned long long)rank < avail) {
-        Stepper<METHOD, MAXM, DEBUG>::init(P, p, pool_next + rank);
+        Stepper<METHOD, MAXM, DEBUG>::init(P, p, pool_next + rank, add_mod(pool_bin, rank, B));
         alive = true;
       }
       if ((unsigned long long)n_dead > avail) {
@@ -539,42 +645,58 @@ __global__ void __launch_bounds__(512, 1) trace_kernel(const TraceParams P) {
           pool_next = pool_end = 0;
         } else {
           const unsigned long long end = min(base + (unsigned long long)kPathChunk, P.N);
+          const int base_bin = (int)((P.bin_base + base) % (unsigned long long)B);
           const long long r2 = (long long)rank - (long long)avail;
           if (!alive && r2 >= 0 && (unsigned long long)r2 < end - base) {
-            Stepper<METHOD, MAXM, DEBUG>::init(P, p, base + (unsigned long long)r2);
+            Stepper<METHOD, MAXM, DEBUG>::init(P, p, base + (unsigned long long)r2,
+                                               add_mod(base_bin, (int)r2, B));
             alive = true;
           }
-          pool_next = base + min((unsigned long long)n_dead - avail, end - base);
+          const int used = (int)min((unsigned long long)n_dead - avail, end - base);
+          pool_next = base + used;
           pool_end = end;
+          pool_bin = add_mod(base_bin, used, B);
         }
       } else {
         pool_next += (unsigned long long)n_dead;
+        pool_bin = add_mod(pool_bin, n_dead, B);
       }
     }
     if (!__any_sync(kFull, alive)) break;
 
     // ---- one vertex step
+    cnt.bits = 0;
     bool fin = false;
     int cbin = -1;
     float cval = 0.0f;
-    if (alive) {
-      if (METHOD == kDarts) {
-        fin = Stepper<METHOD, MAXM, DEBUG>::step_darts(P, p, tab, cnt);
-        if (fin) {
-          cbin = p.bin;
-          cval = P.wb * p.c;
-        }
-      } else {
-        fin = Stepper<METHOD, MAXM, DEBUG>::step_base(P, p, cnt, &cbin, &cval);
-        cval *= P.wb;
+    if (METHOD == kDarts) {
+      RisTask task;
+      bool need = false;
+      if (alive) {
+        fin = Stepper<METHOD, MAXM, DEBUG>::vertex_darts(P, p, tab, cnt, task);
+        need = !fin;
       }
-      if (cbin >= 0 && !isfinite(cval)) {
-        atomicOr(P.status, 1u);
-        cval = 0.0f;
+      RisResult r;
+      if (kCoop) {
+        ris_warp(P, need, task, wtasks, wresults, r, cnt);
+      } else if (need) {
+        r = Stepper<METHOD, MAXM, DEBUG>::ris_lane(P, task, cnt);
       }
+      if (need) fin = Stepper<METHOD, MAXM, DEBUG>::finish_ris(P, p, r, task.nonempty, cnt);
+      if (alive && fin) {
+        cbin = p.bin;
+        cval = P.wb * p.c;
+      }
+    } else if (alive) {
+      fin = Stepper<METHOD, MAXM, DEBUG>::step_base(P, p, cnt, &cbin, &cval);
+      cval *= P.wb;
     }
-    const bool has = cbin >= 0;
-    if (fin) {
+    if (cbin >= 0 && !isfinite(cval)) {
+      atomicOr(P.status, 1u);
+      cval = 0.0f;
+    }
+    const bool has = alive && cbin >= 0;
+    if (alive && fin) {
       if (P.probe_stride && p.j >= P.probe_first && (p.j - P.probe_first) % P.probe_stride == 0) {
         const unsigned long long slot = (p.j - P.probe_first) / P.probe_stride;
         if (slot < P.probe_count) {
@@ -590,29 +712,39 @@ __global__ void __launch_bounds__(512, 1) trace_kernel(const TraceParams P) {
     }
     warp_commit(has, cbin, cval, wsum, wcomp, wsq, TILE, P, do_sq);
     if (fin) alive = false;
+    // ---- event counts of this step (lane i keeps counter i of its warp)
+    {
+      unsigned mine = 0;
+#pragma unroll
+      for (int e = 0; e < ST_FP64E; ++e) {
+        const unsigned c = __popc(__ballot_sync(kFull, (cnt.bits >> e) & 1u));
+        mine = lane == e ? c : mine;
+      }
+      if (lane < ST_FP64E) warp_events[warp][lane] += mine;
+    }
   }
 
   // ---- statistics
-#pragma unroll
-  for (int i = 0; i < kStatCount; ++i) {
-    unsigned v = cnt.v[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    if (lane == 0 && v) atomicAdd(&blk_stats[i], (unsigned long long)v);
-  }
   __syncthreads();
-  if (threadIdx.x < kStatCount && blk_stats[threadIdx.x])
-    atomicAdd(&P.stats[threadIdx.x], blk_stats[threadIdx.x]);
+  if (threadIdx.x < kStatCount) {
+    unsigned long long v = 0;
+    if (threadIdx.x < ST_FP64E) {
+      for (int w = 0; w < nwarps; ++w) v += warp_events[w][threadIdx.x];
+    } else if (threadIdx.x < ST_FP64E + 2) {
+      v = s_rare[threadIdx.x - ST_FP64E];
+    }
+    if (v) atomicAdd(&P.stats[threadIdx.x], v);
+  }
 
   // ---- flush: FP64 reduction of the warp tiles into this block's partials
   double* part = P.partials + (size_t)blockIdx.x * 2 * B;
   if (TILE) {
-    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    for (int b = threadIdx.x; b < B; b += BLOCK) {
       double s = 0.0, q = 0.0;
       for (int w = 0; w < nwarps; ++w) {
-        const float* t = tiles + (size_t)w * 3 * B;
+        const float* t = tiles + (size_t)w * tile_stride;
         s += (double)t[b] - (double)t[B + b];
-        q += (double)t[2 * B + b];
+        if (do_sq) q += (double)t[2 * B + b];
       }
       part[b] = s;
       part[B + b] = q;
@@ -626,7 +758,7 @@ __global__ void __launch_bounds__(512, 1) trace_kernel(const TraceParams P) {
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+  for (int b = threadIdx.x; b < B; b += BLOCK) {
     double s = 0.0, q = 0.0;
     if (TILE) {
       for (unsigned g = 0; g < gridDim.x; ++g) {
@@ -655,42 +787,57 @@ __global__ void philox_kernel(const uint32_t* ctr, uint32_t k0, uint32_t k1, uin
   out[4 * i + 3] = r.w;
 }
 
-template <int METHOD, int MAXM, bool DEBUG, bool TILE>
-cudaError_t launch_one(const TraceParams& p, int grid, int block, size_t smem, cudaStream_t s) {
-  auto kern = trace_kernel<METHOD, MAXM, DEBUG, TILE>;
+template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK>
+cudaError_t launch_one(const TraceParams& p, int grid, size_t smem, cudaStream_t s) {
+  auto kern = trace_kernel<METHOD, MAXM, DEBUG, TILE, BLOCK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, block, smem, s>>>(p);
+  kern<<<grid, BLOCK, smem, s>>>(p);
   return cudaGetLastError();
 }
 
-template <int METHOD, bool DEBUG, bool TILE>
-cudaError_t launch_m(const TraceParams& p, int grid, int block, size_t smem, cudaStream_t s) {
-  if (METHOD == kDarts && p.M != 8) return launch_one<METHOD, kMaxM, DEBUG, TILE>(p, grid, block, smem, s);
-  return launch_one<METHOD, 8, DEBUG, TILE>(p, grid, block, smem, s);
-}
-
+// Block sizes: the production variant (no debug, shared-memory tile, M = 8)
+// is built for 512, 640 and 768 threads; the others for 512.
 template <int METHOD>
 cudaError_t launch_method(const TraceParams& p, int grid, int block, bool debug, bool tile,
                           size_t smem, cudaStream_t s) {
-  if (debug) return tile ? launch_m<METHOD, true, true>(p, grid, block, smem, s)
-                         : launch_m<METHOD, true, false>(p, grid, block, smem, s);
-  return tile ? launch_m<METHOD, false, true>(p, grid, block, smem, s)
-              : launch_m<METHOD, false, false>(p, grid, block, smem, s);
+  const bool m8 = METHOD != kDarts || p.M == 8;
+  if (debug) {
+    if (!m8) return tile ? launch_one<METHOD, kMaxM, true, true, 512>(p, grid, smem, s)
+                         : launch_one<METHOD, kMaxM, true, false, 512>(p, grid, smem, s);
+    return tile ? launch_one<METHOD, 8, true, true, 512>(p, grid, smem, s)
+                : launch_one<METHOD, 8, true, false, 512>(p, grid, smem, s);
+  }
+  if (!m8) return tile ? launch_one<METHOD, kMaxM, false, true, 512>(p, grid, smem, s)
+                       : launch_one<METHOD, kMaxM, false, false, 512>(p, grid, smem, s);
+  if (!tile) return launch_one<METHOD, 8, false, false, 512>(p, grid, smem, s);
+  switch (block) {
+    case 640: return launch_one<METHOD, 8, false, true, 640>(p, grid, smem, s);
+    case 768: return launch_one<METHOD, 8, false, true, 768>(p, grid, smem, s);
+    default: return launch_one<METHOD, 8, false, true, 512>(p, grid, smem, s);
+  }
 }
 
 }  // namespace
 
 size_t trace_smem_bytes(int method, const TraceParams& p, int block, bool tile) {
   size_t b = method == kDarts ? (size_t)p.rows * p.row_stride * sizeof(float) : 0;
-  if (tile) b += (size_t)(block / 32) * 3 * p.n_bins * sizeof(float);
+  if (method == kDarts && p.M == 8) b += (size_t)(block / 32) * 32 * (sizeof(RisTask) + sizeof(RisResult));
+  if (tile) b += (size_t)(block / 32) * (p.sumsq ? 3 : 2) * p.n_bins * sizeof(float);
   return b;
 }
 
 int trace_max_m() { return kMaxM; }
 
-cudaError_t launch_trace(int method, const TraceParams& p, int grid, int block, bool debug,
+int trace_block_for(int block, bool debug, bool tile, int method, int M) {
+  if (debug || !tile || (method == kDarts && M != 8)) return 512;
+  return (block == 640 || block == 768) ? block : 512;
+}
+
+cudaError_t launch_trace(int method, const TraceParams& p0, int grid, int block, bool debug,
                          bool tile, size_t smem, cudaStream_t s) {
+  TraceParams p = p0;
+  p.bin_base = (p0.path_offset + p0.o_e) % (unsigned long long)p0.n_bins;
   switch (method) {
     case kDarts: return launch_method<kDarts>(p, grid, block, debug, tile, smem, s);
     case kPlain: return launch_method<kPlain>(p, grid, block, debug, tile, smem, s);

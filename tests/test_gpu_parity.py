@@ -198,6 +198,29 @@ def test_stats_match_oracle_counts(ctx):
     assert abs(st["escapes"] - ost["escapes"]) <= 0.002 * ost["escapes"] + 5
 
 
+@pytest.mark.parametrize("method", [S.DARTS, S.PLAIN_UNIFORM_T])
+def test_block_sizes_agree_and_autotune(ctx, method):
+    """Every block size of the path kernel renders the same histogram (paths
+    are assigned to blocks dynamically: equal up to FP64 summation order)."""
+    sc, sp = S.cube_workload(paths=1 << 18, seed=21)
+    sp.method = method
+    outs = []
+    for block in (512, 640, 768):
+        ctx.set_launch(block)
+        outs.append(ctx.render(sc, sp).cpu())
+    ctx.set_launch(0)
+    for o in outs[1:]:
+        torch.testing.assert_close(o, outs[0], rtol=1e-6, atol=1e-15)
+    href, _, _ = O.render(sc, sp, method)
+    assert np.linalg.norm(outs[0].numpy() - href) <= 1e-3 * np.linalg.norm(href)
+    best = ctx.autotune(sc, sp)
+    assert best in (512, 640, 768)
+    ctx.set_launch(0)
+    from paper_2402_03106_gb300 import capi
+    with pytest.raises(capi.DartsError):
+        ctx.set_launch(100)
+
+
 # ---------------------------------------------------------------------------
 # Edge cases
 # ---------------------------------------------------------------------------
