@@ -246,6 +246,7 @@ void make_trace_params(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
   P->inv_smax = (float)(1.0 / (m.v * (G.t_max - e.t0)));
   P->n_s_over_8 = (float)(sp->table_n_s / 8.0);
   P->mu_scale = (float)(sp->table_n_mu / 2.0);
+  P->inv_mu_scale = (float)(2.0 / sp->table_n_mu);
   P->mis_alpha = (float)sp->mis_alpha;
   P->uniform_sensor = (sp->flags & DARTS_FLAG_SENSOR_UNIFORM_ONLY) ? 1 : 0;
   P->table = ctx->table;

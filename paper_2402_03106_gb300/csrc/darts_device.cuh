@@ -117,7 +117,7 @@ __device__ __forceinline__ void sincos_2pi(float u, float* s, float* c) {
 __device__ __forceinline__ void frame_dir(float nx, float ny, float nz, float mu, float sphi,
                                           float cphi, float* ox, float* oy, float* oz) {
   const float sign = nz >= 0.0f ? 1.0f : -1.0f;
-  const float a = -1.0f / (sign + nz);
+  const float a = -__fdividef(1.0f, sign + nz);  // |sign + nz| >= 1
   const float b = nx * ny * a;
   const float b1x = fmaf(sign * nx * nx, a, 1.0f), b1y = sign * b, b1z = -sign * nx;
   const float b2x = b, b2y = fmaf(ny * ny, a, sign), b2z = -ny;

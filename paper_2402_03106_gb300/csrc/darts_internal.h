@@ -44,7 +44,7 @@ struct TraceParams {
   int n_bins;
   // direction table
   int n_rho, n_s, n_mu, row_stride, rows;
-  float inv_smax, n_s_over_8, mu_scale;  // 1/S_max, n_s / 8, n_mu / 2
+  float inv_smax, n_s_over_8, mu_scale, inv_mu_scale;  // 1/S_max, n_s / 8, n_mu / 2, 2 / n_mu
   float mis_alpha;
   int uniform_sensor;
   const float* table;              // [rows][row_stride]

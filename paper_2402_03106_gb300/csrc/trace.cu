@@ -100,11 +100,10 @@ __device__ __forceinline__ float box_exit(const TraceParams& P, float x, float y
 __device__ __noinline__ void ellipse_fp64(float delta, float C, float S_lo, float dS, float q,
                                           float* r1, float* den, float* cos_s) {
   const double dd = (double)delta, Cd = (double)C, Sd = (double)S_lo + (double)dS, qd = (double)q;
-  const double dend = dd + Cd * qd;  // S - C mu
-  const double r1d = (dd * dd + 2.0 * Sd * Cd * qd) / (2.0 * dend);
-  const double td = dd * (Sd + Cd) / (2.0 * dend);
-  *cos_s = (float)((Cd * (1.0 - qd) - td) / r1d);
-  *r1 = (float)r1d;
+  const double dend = dd + Cd * qd;                 // S - C mu
+  const double nr = dd * dd + 2.0 * Sd * Cd * qd;    // 2 (S - C mu) r1
+  *cos_s = (float)((2.0 * Cd * Cd * qd * (1.0 - qd) - dd * dd - 2.0 * Cd * qd * dd) / nr);
+  *r1 = (float)(nr / (2.0 * dend));
   *den = (float)dend;
 }
 
@@ -119,9 +118,9 @@ __device__ __forceinline__ float connect(const TraceParams& P, float wx, float w
   float dS, conn_w;  // conn_w = exp(-sigma_t S) / p(S)
   if (!uniform_S) {
     const float em = expm1_neg(-P.sigma_t * W);  // -(1 - e^{-st W})
-    dS = -log1m(-em * u) / P.sigma_t;
+    dS = -log1m(-em * u) * P.inv_st;
     // e^{-st S} / p_S = e^{-st S_lo} (1 - e^{-st W}) / st
-    conn_w = __expf(-P.sigma_t * S_lo) * (-em) / P.sigma_t;
+    conn_w = __expf(-P.sigma_t * S_lo) * (-em) * P.inv_st;
   } else {
     dS = u * W;
     conn_w = __expf(-P.sigma_t * (S_lo + dS)) * W;
@@ -135,15 +134,19 @@ __device__ __forceinline__ float connect(const TraceParams& P, float wx, float w
     ellipse_fp64(delta, C, S_lo, dS, q, &r1, &den, &cos_s);
     cnt.add_rare(ST_FP64E);
   } else {
-    den = fmaf(C, q, delta);                                             // S - C mu
-    r1 = __fdividef(fmaf(delta, delta, 2.0f * S * C * q), 2.0f * den);   // S - t
-    const float t = __fdividef(delta * (S + C), 2.0f * den);             // Eq. 18
-    cos_s = __fdividef(fmaf(C, 1.0f - q, -t), r1);
+    // with t from Eq. 18: S - C mu = delta + C q, r1 = S - t = (delta^2 + 2 S C q) / (2 (S - C mu)),
+    // and the scattering cosine at the control vertex (C mu - t) / r1 written
+    // without the cancellation of C mu - t near the emitter
+    den = fmaf(C, q, delta);
+    const float nr = fmaf(delta, delta, 2.0f * S * C * q);
+    r1 = __fdividef(nr, 2.0f * den);
+    const float cq = C * q;
+    cos_s = __fdividef(fmaf(2.0f * C * cq, 1.0f - q, -delta * fmaf(2.0f, cq, delta)), nr);
   }
   *S_out = S;
   const float f = hg_eval(cos_s, P.hg_a, P.hg_b, P.hg_c);
   // sigma_s e^{-st S} f I_e / r1^2 / p(t),  p(t) = p(S) (S - C mu) / r1
-  return P.sigma_s * conn_w * f * P.Ie / (r1 * den);
+  return __fdividef(P.sigma_s * conn_w * f * P.Ie, r1 * den);
 }
 
 // One distance step of a DARTS vertex, as handed to the RIS evaluation:
@@ -235,7 +238,7 @@ struct Stepper {
     const float ex = P.xe[0] - p.x, ey = P.xe[1] - p.y, ez = P.xe[2] - p.z;
     const float C2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
     const float C = sqrtf(C2);
-    const float invC = 1.0f / C;
+    const float invC = __frcp_rn(C);
     const float ax = ex * invC, ay = ey * invC, az = ez * invC;
     const float SM = p.SM0 - p.L, Sm = p.Sm0 - p.L;
     if (!(SM > C)) {  // Sec. 5.2 early exit
@@ -244,7 +247,7 @@ struct Stepper {
       return true;
     }
     // ---- direction: MIS of the EDA table and HG / uniform (Eq. 19)
-    const float rho = C / SM;
+    const float rho = __fdividef(C, SM);
     int i_rho = (int)(rho * (float)P.n_rho);
     i_rho = min(max(i_rho, 0), P.n_rho - 1);
     int i_s = (int)floorf((__log2f(SM * P.inv_smax) + 8.0f) * P.n_s_over_8);
@@ -268,7 +271,7 @@ struct Stepper {
       n -= half;
     }
     const float c_lo = row[lo], c_hi = row[lo + 1];
-    const float mu_eda = fmaf((float)lo + __fdividef(v1 - c_lo, c_hi - c_lo), 1.0f / P.mu_scale, -1.0f);
+    const float mu_eda = fmaf((float)lo + __fdividef(v1 - c_lo, c_hi - c_lo), P.inv_mu_scale, -1.0f);
     const float mu_hg = hg_sample(gb, v1);
     float wx, wy, wz;
     frame_dir(eda ? ax : bx, eda ? ay : by, eda ? az : bz, eda ? mu_eda : mu_hg, sphi, cphi, &wx, &wy,
@@ -280,9 +283,11 @@ struct Stepper {
       bin = min(max((int)floorf((mua + 1.0f) * P.mu_scale), 0), P.n_mu - 1);
     }
     const float pE = (eda ? c_hi - c_lo : row[bin + 1] - row[bin]) * P.mu_scale * (1.0f / kTwoPi);
-    const float gb2 = gb * gb;
-    const float pB = hg_eval(mu_b, (1.0f - gb2) * kInv4Pi, 1.0f + gb2, 2.0f * gb);
-    const float f = sensor ? 1.0f : hg_eval(mu_b, P.hg_a, P.hg_b, P.hg_c);
+    // base density: HG(g) about the previous direction (= the phase function
+    // f itself), or the uniform sphere at the sensor where f = 1
+    const float hg = hg_eval(mu_b, P.hg_a, P.hg_b, P.hg_c);
+    const float pB = sensor ? kInv4Pi : hg;
+    const float f = sensor ? 1.0f : hg;
     p.beta *= __fdividef(f, fmaf(gamma, pE - pB, pB));
     if (DEBUG) {
       record(P, p, 2, eda ? 1 : 0);
@@ -433,7 +438,7 @@ struct Stepper {
         return true;
       }
       const U4 u0 = rng(P, p.j, (uint32_t)p.k, 0);
-      const float d = -log1m(u01(u0.x)) / P.sigma_t;
+      const float d = -log1m(u01(u0.x)) * P.inv_st;
       if (!(d < dm)) {
         cnt.add(ST_ESCAPE);
         record(P, p, 0, EV_ESCAPE);
@@ -448,7 +453,7 @@ struct Stepper {
     } else {  // vanilla: free flight, then a direct connection from the new vertex
       const float dm = box_exit(P, p.x, p.y, p.z, p.wx, p.wy, p.wz);
       const U4 u0 = rng(P, p.j, (uint32_t)p.k, 0);
-      const float d = -log1m(u01(u0.x)) / P.sigma_t;
+      const float d = -log1m(u01(u0.x)) * P.inv_st;
       if (!(d < dm)) {
         cnt.add(ST_ESCAPE);
         record(P, p, 0, EV_ESCAPE);
@@ -462,7 +467,7 @@ struct Stepper {
       const float ex = p.x - P.xe[0], ey = p.y - P.xe[1], ez = p.z - P.xe[2];
       const float C2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
       const float C = sqrtf(C2);
-      const float cos_s = -(ex * p.wx + ey * p.wy + ez * p.wz) / C;
+      const float cos_s = -__fdividef(ex * p.wx + ey * p.wy + ez * p.wz, C);
       const float y = ((p.L + C) - P.S_gate_lo) * P.inv_S_bin;
       if (y >= 0.0f && y < (float)P.n_bins) {
         cnt.add(ST_CONN);
