@@ -194,6 +194,23 @@ darts_status darts_render_host(darts_ctx* ctx, const darts_scene* scene,
                                const darts_sampling* sampling, double* hist_host,
                                double* sumsq_host, uint64_t path_offset);
 
+/* Path-replay adjoint of the DARTS estimator (not in the paper; its Sec. 7
+ * lists differentiable transient rendering as future work).  Traces the paths
+ * path_offset .. +N-1 of `sampling` (use a seed independent of the forward
+ * render) and accumulates, per path, dL/dh[b] * (n_bins / N) * sum over its
+ * connections v of c_v * s_v, where s_v is the derivative of log f_v w.r.t.
+ * (sigma_s, sigma_a, g) with every sampling density held fixed:
+ *   d/dsigma_s = n_v / sigma_s - l_v,  d/dsigma_a = -l_v,
+ *   d/dg = sum over the scattering vertices of d log HG / dg,
+ * n_v the number of scattering vertices and l_v the length of the path.
+ * dLdh_dev: double [n_bins] (input); grad3_dev: double [3] (overwritten);
+ * grad3_sq_dev: optional double [3], sum over paths of the squared per-path
+ * terms (for standard errors).  method must be DARTS
+ * (DARTS_ERR_UNSUPPORTED otherwise). */
+darts_status darts_adjoint(darts_ctx* ctx, const darts_scene* scene,
+                           const darts_sampling* sampling, const double* dLdh_dev,
+                           double* grad3_dev, double* grad3_sq_dev, uint64_t path_offset);
+
 /* Counters of the last render on this context (synchronises the stream). */
 darts_status darts_get_stats(darts_ctx* ctx, darts_stats* out);
 

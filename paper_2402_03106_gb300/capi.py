@@ -32,7 +32,7 @@ EXPORTED = ("darts_create", "darts_destroy", "darts_set_stream", "darts_status_s
             "darts_last_error", "darts_sync", "darts_build_table", "darts_table_row_stride",
             "darts_render", "darts_render_host", "darts_get_stats", "darts_debug_paths",
             "darts_debug_philox", "darts_set_kernel_timing", "darts_last_kernel_ms",
-            "darts_render_static", "darts_set_launch", "darts_autotune")
+            "darts_render_static", "darts_set_launch", "darts_autotune", "darts_adjoint")
 
 
 class DartsError(RuntimeError):
@@ -121,6 +121,7 @@ def load(path: str = LIB_PATH):
         lib.darts_last_kernel_ms.argtypes = [vp, C.POINTER(C.c_float)]
         lib.darts_render_static.argtypes = [sc_p, sp_p, vp, vp, C.c_uint64, vp]
         lib.darts_set_launch.argtypes = [vp, C.c_int]
+        lib.darts_adjoint.argtypes = [vp, sc_p, sp_p, vp, vp, vp, C.c_uint64]
         lib.darts_autotune.argtypes = [vp, sc_p, sp_p, C.POINTER(C.c_int)]
         for name in EXPORTED:
             if name not in ("darts_status_string", "darts_table_row_stride"):
@@ -252,6 +253,13 @@ def darts_last_kernel_ms(h) -> float:
     return float(ms.value)
 
 
+def darts_adjoint(h, scene, sampling, dLdh: torch.Tensor, grad3: torch.Tensor,
+                  grad3_sq: Optional[torch.Tensor] = None, path_offset: int = 0):
+    cs, keep = to_c_scene(scene)
+    _check(h, load().darts_adjoint(h, C.byref(cs), C.byref(to_c_sampling(sampling)), _ptr(dLdh),
+                                   _ptr(grad3), _ptr(grad3_sq), int(path_offset)))
+
+
 def darts_set_launch(h, block: int):
     _check(h, load().darts_set_launch(h, int(block)))
 
@@ -330,6 +338,14 @@ class Context:
         cdf = torch.empty(rows, stride, dtype=torch.float32, device=self._dev())
         darts_build_table(self.h, scene, sampling, cdf)
         return cdf
+
+    def adjoint(self, scene, sampling, dLdh: torch.Tensor, sumsq: bool = False, path_offset: int = 0):
+        """Gradient of sum_b dLdh[b] h_b w.r.t. (sigma_s, sigma_a, g) by path replay."""
+        d = dLdh.to(device=self._dev(), dtype=torch.float64).contiguous()
+        g3 = torch.empty(3, dtype=torch.float64, device=self._dev())
+        q3 = torch.empty(3, dtype=torch.float64, device=self._dev()) if sumsq else None
+        darts_adjoint(self.h, scene, sampling, d, g3, q3, path_offset)
+        return (g3, q3) if sumsq else g3
 
     def set_launch(self, block: int):
         darts_set_launch(self.h, block)

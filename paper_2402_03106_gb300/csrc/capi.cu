@@ -224,6 +224,8 @@ void make_trace_params(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
   P->hg_a = (float)((1.0 - m.g * m.g) / (4.0 * M_PI));
   P->hg_b = (float)(1.0 + m.g * m.g);
   P->hg_c = (float)(2.0 * m.g);
+  P->hg_dlog_a = (float)(-2.0 * m.g / (1.0 - m.g * m.g));
+  P->inv_sigma_s = m.sigma_s > 0.0 ? (float)(1.0 / m.sigma_s) : 0.0f;
   for (int i = 0; i < 3; ++i) {
     P->lo[i] = (float)sc->geom.lo[i];
     P->hi[i] = (float)sc->geom.hi[i];
@@ -574,6 +576,43 @@ darts_status darts_get_stats(darts_ctx* ctx, darts_stats* out) {
   out->escapes = s[5];
   out->fp64_ellipse = s[6];
   out->fp64_phi = s[7];
+  return DARTS_OK;
+}
+
+darts_status darts_adjoint(darts_ctx* ctx, const darts_scene* scene, const darts_sampling* sampling,
+                           const double* dLdh_dev, double* grad3_dev, double* grad3_sq_dev,
+                           uint64_t path_offset) {
+  if (!ctx) return DARTS_ERR_INVALID_ARG;
+  darts_status s = validate(ctx, scene, sampling);
+  if (s != DARTS_OK) return s;
+  if (!dLdh_dev || !grad3_dev) return fail(ctx, DARTS_ERR_INVALID_ARG, "dLdh_dev and grad3_dev must not be NULL");
+  if (sampling->method != DARTS_METHOD_DARTS)
+    return fail(ctx, DARTS_ERR_UNSUPPORTED, "the adjoint is implemented for the DARTS method");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (sampling->paths_per_element == 0) {
+    CK(cudaMemsetAsync(grad3_dev, 0, 3 * sizeof(double), ctx->stream), "memset");
+    if (grad3_sq_dev) CK(cudaMemsetAsync(grad3_sq_dev, 0, 3 * sizeof(double), ctx->stream), "memset");
+    return DARTS_OK;
+  }
+  s = ensure_table(ctx, scene, sampling);
+  if (s != DARTS_OK) return s;
+  TraceParams P;
+  make_trace_params(ctx, scene, sampling, &P);
+  P.N = sampling->paths_per_element;
+  P.path_offset = path_offset;
+  P.dLdh = dLdh_dev;
+  P.grad3 = grad3_dev;
+  P.grad3_sq = grad3_sq_dev;
+  const int grid = ctx->sm_count;
+  const size_t smem = adjoint_smem_bytes(P);
+  if (smem > (size_t)ctx->smem_optin)
+    return fail(ctx, DARTS_ERR_UNSUPPORTED, "direction table of %zu bytes exceeds shared memory", smem);
+  CK(ensure((void**)&ctx->partials, &ctx->partials_bytes, (size_t)grid * 6 * sizeof(double)), "partials allocation");
+  P.partials = ctx->partials;
+  CK(cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), ctx->stream), "memset");
+  CK(cudaMemsetAsync(ctx->scratch + 2, 0, kStatCount * sizeof(unsigned long long), ctx->stream), "memset");
+  ctx->last_paths = P.N;
+  CK(launch_adjoint(P, grid, smem, ctx->stream), "adjoint kernel launch");
   return DARTS_OK;
 }
 

@@ -31,6 +31,8 @@ struct TraceParams {
   float sigma_s, sigma_t, inv_st, albedo, sa_v, v, inv_v;
   float phi_k0, phi_invk;          // Eq. 9 in log form, see TableParams
   float hg_a, hg_b, hg_c, g;       // HG constants (hg_eval) and g
+  float hg_dlog_a;                 // -2 g / (1 - g^2)
+  float inv_sigma_s;               // 1 / sigma_s (0 when sigma_s = 0)
   double phi_k0_d, phi_invk_d, sa_v_d, inv_v_d;  // the same, FP64 (small-t' branch)
   // geometry
   float lo[3], hi[3], xe[3], xs[3];
@@ -65,6 +67,10 @@ struct TraceParams {
   unsigned int* ticket;            // last-block ticket
   unsigned int* status;            // device status word (bit 0: non-finite)
   unsigned long long* stats;       // [kStatCount]
+  // path-replay adjoint
+  const double* dLdh;              // [n_bins]
+  double* grad3;                   // [3]
+  double* grad3_sq;                // [3] or null
   // per-path probe (sampled paths of a full launch)
   unsigned long long probe_first, probe_stride;
   unsigned int probe_count;
@@ -81,6 +87,8 @@ struct TraceParams {
 cudaError_t launch_table(const TableParams& p, cudaStream_t s);
 cudaError_t launch_trace(int method, const TraceParams& p, int grid, int block, bool debug,
                          bool tile, size_t smem, cudaStream_t s);
+cudaError_t launch_adjoint(const TraceParams& p, int grid, size_t smem, cudaStream_t s);
+size_t adjoint_smem_bytes(const TraceParams& p);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t n,
                           uint32_t* out, cudaStream_t s);
 size_t trace_smem_bytes(int method, const TraceParams& p, int block, bool tile);

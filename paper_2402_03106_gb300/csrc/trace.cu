@@ -52,6 +52,9 @@ struct Path {
   int k;             // vertex index
   int bin;           // DARTS bin
   unsigned long long j;  // local path index
+  // path-replay adjoint: sum over the path's connections of c_v * s_v, and
+  // the running sum of d log HG / dg over the walk vertices
+  float a0, a1, a2, gsum;
 };
 
 // Event counting.  Common events set a bit for the current vertex step; the
@@ -113,7 +116,7 @@ __device__ __noinline__ void ellipse_fp64(float delta, float C, float S_lo, floa
 __device__ __forceinline__ float connect(const TraceParams& P, float wx, float wy, float wz,
                                          float C, float ax, float ay, float az, float S_lo,
                                          float S_hi, float u, bool uniform_S, float* S_out,
-                                         Counters& cnt) {
+                                         Counters& cnt, float* cos_out = nullptr) {
   const float W = S_hi - S_lo;
   float dS, conn_w;  // conn_w = exp(-sigma_t S) / p(S)
   if (!uniform_S) {
@@ -144,6 +147,7 @@ __device__ __forceinline__ float connect(const TraceParams& P, float wx, float w
     cos_s = __fdividef(fmaf(2.0f * C * cq, 1.0f - q, -delta * fmaf(2.0f, cq, delta)), nr);
   }
   *S_out = S;
+  if (cos_out) *cos_out = cos_s;
   const float f = hg_eval(cos_s, P.hg_a, P.hg_b, P.hg_c);
   // sigma_s e^{-st S} f I_e / r1^2 / p(t),  p(t) = p(S) (S - C mu) / r1
   return __fdividef(P.sigma_s * conn_w * f * P.Ie, r1 * den);
@@ -194,7 +198,12 @@ __device__ __forceinline__ float ris_candidate(const TraceParams& P, const RisTa
   return P.phi_k0 - 1.5f * __logf(tp) - __fdividef(r2 * P.phi_invk, tp) - P.sa_v * tp;
 }
 
-template <int METHOD, int MAXM, bool DEBUG>
+// d log HG(mu; g) / dg = -2g/(1 - g^2) - 3 (g - mu) / (1 + g^2 - 2 g mu)
+__device__ __forceinline__ float hg_dlog_dg(const TraceParams& P, float mu) {
+  return fmaf(-3.0f * (P.g - mu), __frcp_rn(fmaf(-P.hg_c, mu, P.hg_b)), P.hg_dlog_a);
+}
+
+template <int METHOD, int MAXM, bool DEBUG, bool ADJ = false>
 struct Stepper {
   // Initialise a path with local index j.
   __device__ static void init(const TraceParams& P, Path& p, unsigned long long j, int bin) {
@@ -206,6 +215,7 @@ struct Stepper {
     p.c = 0.0f;
     p.k = 0;
     p.j = j;
+    p.a0 = p.a1 = p.a2 = p.gsum = 0.0f;
     p.wx = 0.0f;
     p.wy = 0.0f;
     p.wz = 1.0f;
@@ -289,6 +299,7 @@ struct Stepper {
     const float pB = sensor ? kInv4Pi : hg;
     const float f = sensor ? 1.0f : hg;
     p.beta *= __fdividef(f, fmaf(gamma, pE - pB, pB));
+    if (ADJ && !sensor) p.gsum += hg_dlog_dg(P, mu_b);
     if (DEBUG) {
       record(P, p, 2, eda ? 1 : 0);
       record(P, p, 3, (uint8_t)(bin & 0xFF));
@@ -300,10 +311,19 @@ struct Stepper {
     const float S_hi = fminf(SM, S_dm), S_lo = fmaxf(Sm, C);
     const bool ok = S_hi > S_lo;
     if (ok) {
-      float S;
-      const float cc = connect(P, wx, wy, wz, C, ax, ay, az, S_lo, S_hi, u01(u1.w), false, &S, cnt);
+      float S, cos_s;
+      const float cc = connect(P, wx, wy, wz, C, ax, ay, az, S_lo, S_hi, u01(u1.w), false, &S, cnt,
+                               ADJ ? &cos_s : nullptr);
       p.c = fmaf(p.beta, cc, p.c);
       cnt.add(ST_CONN);
+      if (ADJ) {
+        // score of log f: k walk vertices + the control vertex scatter (sigma_s),
+        // total length L + S attenuates (sigma_t), HG at every scattering vertex (g)
+        const float cv = p.beta * cc, ell = p.L + S;
+        p.a0 = fmaf(cv, fmaf((float)(p.k + 1), P.inv_sigma_s, -ell), p.a0);
+        p.a1 = fmaf(-cv, ell, p.a1);
+        p.a2 = fmaf(cv, p.gsum + hg_dlog_dg(P, cos_s), p.a2);
+      }
     }
     const uint8_t nonempty = ok ? 0x10 : 0;
     p.wx = wx;  // the walk continues along the connection direction (Eq. 20)
@@ -588,7 +608,7 @@ __device__ __forceinline__ int add_mod(int a, int r, int B) {
   return v < B ? v : (B >= 64 ? v - B : v % B);
 }
 
-template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK>
+template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK, bool ADJ = false>
 __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
@@ -625,6 +645,8 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
 
   Counters cnt;
   Path p;
+  // adjoint: per-lane Kahan sums of the weighted path scores and their squares
+  float g_s[3] = {0.0f, 0.0f, 0.0f}, g_c[3] = {0.0f, 0.0f, 0.0f}, g_q[3] = {0.0f, 0.0f, 0.0f};
   bool alive = false;
   unsigned long long pool_next = 0, pool_end = 0;
   int pool_bin = 0;  // DARTS bin of path pool_next
@@ -638,7 +660,7 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
       const int n_dead = __popc(dead);
       const unsigned long long avail = pool_end - pool_next;
       if (!alive && (unsigned long long)rank < avail) {
-        Stepper<METHOD, MAXM, DEBUG>::init(P, p, pool_next + rank, add_mod(pool_bin, rank, B));
+        Stepper<METHOD, MAXM, DEBUG, ADJ>::init(P, p, pool_next + rank, add_mod(pool_bin, rank, B));
         alive = true;
       }
       if ((unsigned long long)n_dead > avail) {
@@ -653,7 +675,7 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
           const int base_bin = (int)((P.bin_base + base) % (unsigned long long)B);
           const long long r2 = (long long)rank - (long long)avail;
           if (!alive && r2 >= 0 && (unsigned long long)r2 < end - base) {
-            Stepper<METHOD, MAXM, DEBUG>::init(P, p, base + (unsigned long long)r2,
+            Stepper<METHOD, MAXM, DEBUG, ADJ>::init(P, p, base + (unsigned long long)r2,
                                                add_mod(base_bin, (int)r2, B));
             alive = true;
           }
@@ -678,22 +700,22 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
       RisTask task;
       bool need = false;
       if (alive) {
-        fin = Stepper<METHOD, MAXM, DEBUG>::vertex_darts(P, p, tab, cnt, task);
+        fin = Stepper<METHOD, MAXM, DEBUG, ADJ>::vertex_darts(P, p, tab, cnt, task);
         need = !fin;
       }
       RisResult r;
       if (kCoop) {
         ris_warp(P, need, task, wtasks, wresults, r, cnt);
       } else if (need) {
-        r = Stepper<METHOD, MAXM, DEBUG>::ris_lane(P, task, cnt);
+        r = Stepper<METHOD, MAXM, DEBUG, ADJ>::ris_lane(P, task, cnt);
       }
-      if (need) fin = Stepper<METHOD, MAXM, DEBUG>::finish_ris(P, p, r, task.nonempty, cnt);
+      if (need) fin = Stepper<METHOD, MAXM, DEBUG, ADJ>::finish_ris(P, p, r, task.nonempty, cnt);
       if (alive && fin) {
         cbin = p.bin;
         cval = P.wb * p.c;
       }
     } else if (alive) {
-      fin = Stepper<METHOD, MAXM, DEBUG>::step_base(P, p, cnt, &cbin, &cval);
+      fin = Stepper<METHOD, MAXM, DEBUG, ADJ>::step_base(P, p, cnt, &cbin, &cval);
       cval *= P.wb;
     }
     if (cbin >= 0 && !isfinite(cval)) {
@@ -715,7 +737,19 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
         P.dbg_n[p.j] = p.k + 1;
       }
     }
-    warp_commit(has, cbin, cval, wsum, wcomp, wsq, TILE, P, do_sq);
+    if (ADJ) {
+      if (alive && fin) {
+        const float wgt = (float)P.dLdh[p.bin] * P.wb;
+        const float gv[3] = {wgt * p.a0, wgt * p.a1, wgt * p.a2};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          kahan_add(g_s[i], g_c[i], gv[i]);
+          g_q[i] = fmaf(gv[i], gv[i], g_q[i]);
+        }
+      }
+    } else {
+      warp_commit(has, cbin, cval, wsum, wcomp, wsq, TILE, P, do_sq);
+    }
     if (fin) alive = false;
     // ---- event counts of this step (lane i keeps counter i of its warp)
     {
@@ -739,6 +773,44 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
       v = s_rare[threadIdx.x - ST_FP64E];
     }
     if (v) atomicAdd(&P.stats[threadIdx.x], v);
+  }
+
+  // ---- adjoint: FP64 reduction of the per-lane gradient sums into block partials
+  if (ADJ) {
+    __shared__ double adj_w[nwarps][6];
+    double v[6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      v[i] = (double)g_s[i] - (double)g_c[i];
+      v[3 + i] = (double)g_q[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(kFull, v[i], o);
+      if (lane == 0) adj_w[warp][i] = v[i];
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+      double t = 0.0;
+      for (int w = 0; w < nwarps; ++w) t += adj_w[w][threadIdx.x];
+      P.partials[(size_t)blockIdx.x * 6 + threadIdx.x] = t;
+    }
+    __threadfence();
+    __shared__ unsigned last_adj;
+    __syncthreads();
+    if (threadIdx.x == 0) last_adj = (atomicAdd(P.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!last_adj) return;
+    __threadfence();
+    if (threadIdx.x < 6) {
+      double t = 0.0;
+      for (unsigned g = 0; g < gridDim.x; ++g) t += __ldcg(P.partials + (size_t)g * 6 + threadIdx.x);
+      if (threadIdx.x < 3) P.grad3[threadIdx.x] = t;
+      else if (P.grad3_sq) P.grad3_sq[threadIdx.x - 3] = t;
+    }
+    if (threadIdx.x == 0) *P.ticket = 0u;
+    return;
   }
 
   // ---- flush: FP64 reduction of the warp tiles into this block's partials
@@ -824,6 +896,29 @@ cudaError_t launch_method(const TraceParams& p, int grid, int block, bool debug,
 }
 
 }  // namespace
+
+size_t adjoint_smem_bytes(const TraceParams& p) {
+  size_t b = (size_t)p.rows * p.row_stride * sizeof(float);
+  if (p.M == 8) b += (size_t)(512 / 32) * 32 * (sizeof(RisTask) + sizeof(RisResult));
+  return b;
+}
+
+cudaError_t launch_adjoint(const TraceParams& p0, int grid, size_t smem, cudaStream_t s) {
+  TraceParams p = p0;
+  p.bin_base = (p0.path_offset + p0.o_e) % (unsigned long long)p0.n_bins;
+  if (p.M == 8) {
+    auto kern = trace_kernel<kDarts, 8, false, false, 512, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 512, smem, s>>>(p);
+  } else {
+    auto kern = trace_kernel<kDarts, kMaxM, false, false, 512, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 512, smem, s>>>(p);
+  }
+  return cudaGetLastError();
+}
 
 size_t trace_smem_bytes(int method, const TraceParams& p, int block, bool tile) {
   size_t b = method == kDarts ? (size_t)p.rows * p.row_stride * sizeof(float) : 0;
