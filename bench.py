@@ -248,6 +248,43 @@ def mse_time(ctx, S, torch, n_paths=1 << 16, seeds=8, ref_paths=1 << 26):
     return out
 
 
+def batched_compare(ctx, S, torch, reps=5):
+    """256 independent slab media with uneven budgets (2^U[12,20] paths,
+    128 bins): one graph-captured persistent launch vs one launch per medium."""
+    media = S.batched_media(n_media=256, seed=0)
+    scenes = [m[0] for m in media]
+    samplings = [m[1] for m in media]
+    total = sum(sp.paths_per_element for sp in samplings)
+    outs = ctx.render_batch(scenes, samplings)
+    ctx.render_batch(scenes, samplings, outs=outs)
+    torch.cuda.synchronize()
+
+    def timed(fn, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    t_batch = timed(lambda: ctx.render_batch(scenes, samplings, outs=outs), reps)
+    singles = [torch.empty(sc.gate.n_bins, dtype=torch.float64, device="cuda") for sc in scenes]
+
+    def loop():
+        for sc, sp, o in zip(scenes, samplings, singles):
+            ctx.render(sc, sp, out=o)
+
+    loop()
+    t_loop = timed(loop, 2)
+    return {"media": len(scenes), "paths": total, "ms_batched_graph": t_batch,
+            "ms_one_launch_per_medium": t_loop, "paths_per_s_batched": total / (t_batch * 1e-3),
+            "paths_per_s_per_medium_launches": total / (t_loop * 1e-3),
+            "speedup": t_loop / t_batch,
+            "workload": "256 slab media: sigma_s log-uniform [0.1,10], albedo U[0.5,0.999], "
+                        "g U[-0.3,0.9], side U[0.5,4], budgets 2^U[12,20], 128 bins, K=50, M=8"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -385,6 +422,7 @@ def main():
                    "histogram copied back to pinned host memory, stream synchronised per step"}
 
     mse = None if args.no_mse else mse_time(ctx, S, torch)
+    batched = batched_compare(ctx, S, torch)
     cpu = cpu_baseline() if ws == 1 else None
 
     line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws, "steps": K,
@@ -398,7 +436,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 2 * K,
             "clocks": clk, "wall_s_timed_region": wall,
-            "as_configured_2e16": as_conf, "mse_time": mse}
+            "as_configured_2e16": as_conf, "mse_time": mse, "batched": batched}
     print(json.dumps(line), flush=True)
     ctx.close()
     if pg is not None:

@@ -211,6 +211,21 @@ darts_status darts_adjoint(darts_ctx* ctx, const darts_scene* scene,
                            const darts_sampling* sampling, const double* dLdh_dev,
                            double* grad3_dev, double* grad3_sq_dev, uint64_t path_offset);
 
+/* Render n independent media in one persistent launch (captured once in a
+ * CUDA graph and replayed while the arguments stay the same): the direction
+ * tables of all media are built by one kernel launch, then every CTA of the
+ * path kernel pops work items of at most 2^16 paths of one medium, staging
+ * that medium's table in shared memory when it changes.  hist_dev[i]
+ * (double [scenes[i].gate.n_bins], overwritten) receives medium i's
+ * histogram, exactly as darts_render(scenes[i], samplings[i], path_offset 0)
+ * would (up to FP64 summation order).  All media must use method DARTS,
+ * ris_m 8 and one table shape.  flags: DARTS_BATCH_NO_GRAPH launches the
+ * kernels directly.  Synchronises the stream once to upload the work list. */
+#define DARTS_BATCH_NO_GRAPH (1u << 0)
+darts_status darts_render_batch(darts_ctx* ctx, int n, const darts_scene* scenes,
+                                const darts_sampling* samplings, double* const* hist_dev,
+                                uint32_t flags);
+
 /* Counters of the last render on this context (synchronises the stream). */
 darts_status darts_get_stats(darts_ctx* ctx, darts_stats* out);
 

@@ -32,7 +32,9 @@ EXPORTED = ("darts_create", "darts_destroy", "darts_set_stream", "darts_status_s
             "darts_last_error", "darts_sync", "darts_build_table", "darts_table_row_stride",
             "darts_render", "darts_render_host", "darts_get_stats", "darts_debug_paths",
             "darts_debug_philox", "darts_set_kernel_timing", "darts_last_kernel_ms",
-            "darts_render_static", "darts_set_launch", "darts_autotune", "darts_adjoint")
+            "darts_render_static", "darts_set_launch", "darts_autotune", "darts_adjoint",
+            "darts_render_batch")
+BATCH_NO_GRAPH = 1
 
 
 class DartsError(RuntimeError):
@@ -122,6 +124,7 @@ def load(path: str = LIB_PATH):
         lib.darts_render_static.argtypes = [sc_p, sp_p, vp, vp, C.c_uint64, vp]
         lib.darts_set_launch.argtypes = [vp, C.c_int]
         lib.darts_adjoint.argtypes = [vp, sc_p, sp_p, vp, vp, vp, C.c_uint64]
+        lib.darts_render_batch.argtypes = [vp, C.c_int, sc_p, sp_p, C.POINTER(C.c_void_p), C.c_uint32]
         lib.darts_autotune.argtypes = [vp, sc_p, sp_p, C.POINTER(C.c_int)]
         for name in EXPORTED:
             if name not in ("darts_status_string", "darts_table_row_stride"):
@@ -260,6 +263,19 @@ def darts_adjoint(h, scene, sampling, dLdh: torch.Tensor, grad3: torch.Tensor,
                                    _ptr(grad3), _ptr(grad3_sq), int(path_offset)))
 
 
+def darts_render_batch(h, scenes, samplings, hists, flags: int = 0):
+    n = len(scenes)
+    cs_arr = (darts_scene * n)()
+    keep = []
+    for i, sc in enumerate(scenes):
+        cs, k = to_c_scene(sc)
+        cs_arr[i] = cs
+        keep.append(k)
+    sp_arr = (darts_sampling * n)(*[to_c_sampling(sp) for sp in samplings])
+    ptrs = (C.c_void_p * n)(*[t.data_ptr() for t in hists])
+    _check(h, load().darts_render_batch(h, n, cs_arr, sp_arr, ptrs, int(flags)))
+
+
 def darts_set_launch(h, block: int):
     _check(h, load().darts_set_launch(h, int(block)))
 
@@ -346,6 +362,13 @@ class Context:
         q3 = torch.empty(3, dtype=torch.float64, device=self._dev()) if sumsq else None
         darts_adjoint(self.h, scene, sampling, d, g3, q3, path_offset)
         return (g3, q3) if sumsq else g3
+
+    def render_batch(self, scenes, samplings, graph: bool = True, outs=None):
+        """Histograms of many media from one persistent launch (CUDA graph)."""
+        if outs is None:
+            outs = [torch.empty(sc.gate.n_bins, dtype=torch.float64, device=self._dev()) for sc in scenes]
+        darts_render_batch(self.h, scenes, samplings, outs, 0 if graph else BATCH_NO_GRAPH)
+        return outs
 
     def set_launch(self, block: int):
         darts_set_launch(self.h, block)

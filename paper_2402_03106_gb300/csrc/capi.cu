@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -42,6 +43,15 @@ struct darts_ctx {
   bool timing = false;
   bool timed = false;
   cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+  // batched rendering: per-medium tables and parameters, work items, graph
+  float* batch_tables = nullptr;
+  size_t batch_tables_bytes = 0;
+  void* batch_buf = nullptr;   // TableParams[n] | TraceParams[n] | BatchItem[m] | item counter
+  size_t batch_buf_bytes = 0;
+  cudaStream_t capture_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  uint64_t graph_key = 0;
   char err[512] = {0};
 };
 
@@ -380,6 +390,11 @@ darts_status darts_destroy(darts_ctx* ctx) {
   cudaFree(ctx->acc);
   cudaFree(ctx->table);
   cudaFree(ctx->host_hist);
+  cudaFree(ctx->batch_tables);
+  cudaFree(ctx->batch_buf);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
   if (ctx->ev_stop) cudaEventDestroy(ctx->ev_stop);
   delete ctx;
@@ -576,6 +591,136 @@ darts_status darts_get_stats(darts_ctx* ctx, darts_stats* out) {
   out->escapes = s[5];
   out->fp64_ellipse = s[6];
   out->fp64_phi = s[7];
+  return DARTS_OK;
+}
+
+// FNV-1a over bytes (graph cache key).
+static uint64_t fnv1a(const void* data, size_t n, uint64_t h) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < n; ++i) h = (h ^ p[i]) * 1099511628211ull;
+  return h;
+}
+
+darts_status darts_render_batch(darts_ctx* ctx, int n, const darts_scene* scenes,
+                                const darts_sampling* samplings, double* const* hist_dev,
+                                uint32_t flags) {
+  if (!ctx) return DARTS_ERR_INVALID_ARG;
+  if (n < 1 || !scenes || !samplings || !hist_dev)
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "need n >= 1 media, scenes, samplings and outputs");
+  const darts_sampling& s0 = samplings[0];
+  int max_bins = 1;
+  for (int i = 0; i < n; ++i) {
+    darts_status st = validate(ctx, &scenes[i], &samplings[i]);
+    if (st != DARTS_OK) return st;
+    if (!hist_dev[i]) return fail(ctx, DARTS_ERR_INVALID_ARG, "hist_dev[%d] is NULL", i);
+    const darts_sampling& si = samplings[i];
+    if (si.method != DARTS_METHOD_DARTS || si.ris_m != 8 || si.table_n_rho != s0.table_n_rho ||
+        si.table_n_s != s0.table_n_s || si.table_n_mu != s0.table_n_mu)
+      return fail(ctx, DARTS_ERR_UNSUPPORTED,
+                  "a batch needs method DARTS, ris_m 8 and one table shape for all media");
+    max_bins = std::max(max_bins, scenes[i].gate.n_bins);
+  }
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const int rows = s0.table_n_rho * s0.table_n_s, stride = row_stride_of(s0.table_n_mu);
+  const size_t tab_floats = (size_t)rows * stride;
+  CK(ensure((void**)&ctx->batch_tables, &ctx->batch_tables_bytes, (size_t)n * tab_floats * sizeof(float)),
+     "batch table allocation");
+
+  // host-side parameter blocks and work items (chunks of at most 2^16 paths)
+  const uint64_t chunk = 1ull << 16;
+  size_t n_items = 0;
+  for (int i = 0; i < n; ++i) n_items += (samplings[i].paths_per_element + chunk - 1) / chunk;
+  const size_t off_tp = 0, off_trp = ((size_t)n * sizeof(TableParams) + 255) / 256 * 256;
+  const size_t off_items = off_trp + ((size_t)n * sizeof(TraceParams) + 255) / 256 * 256;
+  const size_t off_cnt = off_items + (n_items * sizeof(BatchItem) + 255) / 256 * 256;
+  const size_t total = off_cnt + 256;
+  unsigned char* host = static_cast<unsigned char*>(std::malloc(total));
+  if (!host) return fail(ctx, DARTS_ERR_OOM, "host staging buffer");
+  std::memset(host, 0, total);
+  CK(ensure(&ctx->batch_buf, &ctx->batch_buf_bytes, total), "batch buffer allocation");
+  unsigned char* dev = static_cast<unsigned char*>(ctx->batch_buf);
+  TableParams* tps = reinterpret_cast<TableParams*>(host + off_tp);
+  TraceParams* trps = reinterpret_cast<TraceParams*>(host + off_trp);
+  BatchItem* items = reinterpret_cast<BatchItem*>(host + off_items);
+  size_t k = 0;
+  uint64_t total_paths = 0;
+  for (int i = 0; i < n; ++i) {
+    make_table_params(&scenes[i], &samplings[i], &tps[i]);
+    tps[i].cdf = ctx->batch_tables + (size_t)i * tab_floats;
+    make_trace_params(ctx, &scenes[i], &samplings[i], &trps[i]);
+    trps[i].table = ctx->batch_tables + (size_t)i * tab_floats;
+    trps[i].N = samplings[i].paths_per_element;
+    trps[i].path_offset = 0;
+    trps[i].bin_base = trps[i].o_e % (unsigned long long)scenes[i].gate.n_bins;
+    trps[i].hist = hist_dev[i];
+    for (uint64_t f = 0; f < samplings[i].paths_per_element; f += chunk) {
+      items[k].medium = (unsigned)i;
+      items[k].first = f;
+      items[k].count = std::min<uint64_t>(chunk, samplings[i].paths_per_element - f);
+      ++k;
+    }
+    total_paths += samplings[i].paths_per_element;
+  }
+  BatchParams bp;
+  bp.params = reinterpret_cast<const TraceParams*>(dev + off_trp);
+  bp.items = reinterpret_cast<const BatchItem*>(dev + off_items);
+  bp.n_items = (int)n_items;
+  bp.n_media = n;
+  bp.item_counter = reinterpret_cast<unsigned int*>(dev + off_cnt);
+  bp.max_bins = max_bins;
+  bp.rows = rows;
+  bp.row_stride = stride;
+  bp.stats = ctx->scratch + 2;
+  int block = ctx->block ? ctx->block : 512;
+  size_t smem = batch_smem_bytes(bp, block);
+  while (smem > (size_t)ctx->smem_optin && block > 512) {
+    block = block == 768 ? 640 : 512;
+    smem = batch_smem_bytes(bp, block);
+  }
+  if (smem > (size_t)ctx->smem_optin) {
+    std::free(host);
+    return fail(ctx, DARTS_ERR_UNSUPPORTED, "batch shared memory of %zu bytes does not fit", smem);
+  }
+  uint64_t key = fnv1a(host, total, 1469598103934665603ull);
+  key = fnv1a(&bp, sizeof(bp), key);
+  key = fnv1a(&block, sizeof(block), key);
+  // upload (outside any capture), then run the captured graph
+  cudaError_t e = cudaMemcpyAsync(dev, host, off_cnt, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // host buffer is freed next
+  std::free(host);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "batch upload");
+  ctx->last_paths = total_paths;
+  const bool use_graph = !(flags & DARTS_BATCH_NO_GRAPH);
+  auto enqueue = [&](cudaStream_t st) -> cudaError_t {
+    cudaError_t r = cudaMemsetAsync(dev + off_cnt, 0, 256, st);
+    if (r == cudaSuccess) r = cudaMemsetAsync(ctx->scratch, 0, (2 + kStatCount) * sizeof(unsigned long long), st);
+    if (r == cudaSuccess) r = launch_table_batch(reinterpret_cast<const TableParams*>(dev + off_tp), n, rows, st);
+    if (r == cudaSuccess) r = launch_batch(bp, ctx->sm_count, block, smem, st);
+    return r;
+  };
+  if (!use_graph) {
+    CK(enqueue(ctx->stream), "batch launch");
+    return DARTS_OK;
+  }
+  if (!ctx->graph_exec || ctx->graph_key != key) {
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->graph_exec = nullptr;
+    ctx->graph = nullptr;
+    if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking), "stream create");
+    CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t r = enqueue(ctx->capture_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t r2 = cudaStreamEndCapture(ctx->capture_stream, &g);
+    if (r != cudaSuccess || r2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(ctx, r != cudaSuccess ? r : r2, "batch graph capture");
+    }
+    ctx->graph = g;
+    CK(cudaGraphInstantiate(&ctx->graph_exec, g, 0), "graph instantiate");
+    ctx->graph_key = key;
+  }
+  CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream), "graph launch");
   return DARTS_OK;
 }
 

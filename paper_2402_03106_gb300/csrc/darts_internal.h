@@ -83,10 +83,29 @@ struct TraceParams {
   uint8_t* dbg_dec;                // [N][K][4]
 };
 
+// Batched rendering: one work item = a range of one medium's paths.
+struct BatchItem {
+  unsigned int medium;
+  unsigned int pad;
+  unsigned long long first, count;
+};
+struct BatchParams {
+  const TraceParams* params;   // [n_media], device
+  const BatchItem* items;      // [n_items], device, grouped by medium
+  int n_items, n_media;
+  unsigned int* item_counter;  // zeroed before the launch
+  int max_bins;                // tile sizing
+  int rows, row_stride;        // direction-table shape (common to the batch)
+  unsigned long long* stats;   // [kStatCount]
+};
+
 // Launchers (stream-ordered; return the launch's cudaError_t).
 cudaError_t launch_table(const TableParams& p, cudaStream_t s);
 cudaError_t launch_trace(int method, const TraceParams& p, int grid, int block, bool debug,
                          bool tile, size_t smem, cudaStream_t s);
+cudaError_t launch_table_batch(const TableParams* ps_dev, int n_media, int rows, cudaStream_t s);
+cudaError_t launch_batch(const BatchParams& bp, int grid, int block, size_t smem, cudaStream_t s);
+size_t batch_smem_bytes(const BatchParams& bp, int block);
 cudaError_t launch_adjoint(const TraceParams& p, int grid, size_t smem, cudaStream_t s);
 size_t adjoint_smem_bytes(const TraceParams& p);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t n,

@@ -29,11 +29,10 @@ __device__ __forceinline__ float warp_incl_scan(float v, int lane) {
   return v;
 }
 
-__global__ void __launch_bounds__(kTableThreads) eda_table_kernel(const TableParams P) {
+__device__ __forceinline__ void table_row(const TableParams& P, const int row) {
   __shared__ float logF[kMaxMu];
   __shared__ float wsum[kTableThreads / 32];
   __shared__ float wmax[kTableThreads / 32];
-  const int row = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i_rho = row / P.n_s, i_s = row - i_rho * P.n_s;
   const float rho = (i_rho + 0.5f) / P.n_rho;
@@ -117,7 +116,23 @@ __global__ void __launch_bounds__(kTableThreads) eda_table_kernel(const TablePar
   for (int j = P.n_mu + 1 + tid; j < P.row_stride; j += kTableThreads) out[j] = 1.0f;
 }
 
+__global__ void __launch_bounds__(kTableThreads) eda_table_kernel(const TableParams P) {
+  table_row(P, blockIdx.x);
+}
+
+// All media of a batch in one launch: blockIdx.y selects the medium.
+__global__ void __launch_bounds__(kTableThreads) eda_table_batch_kernel(const TableParams* Ps) {
+  const TableParams& P = Ps[blockIdx.y];
+  if ((int)blockIdx.x < P.n_rho * P.n_s) table_row(P, blockIdx.x);
+}
+
 }  // namespace
+
+cudaError_t launch_table_batch(const TableParams* ps_dev, int n_media, int rows, cudaStream_t s) {
+  if (n_media <= 0) return cudaSuccess;
+  eda_table_batch_kernel<<<dim3(rows, n_media), kTableThreads, 0, s>>>(ps_dev);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_table(const TableParams& p, cudaStream_t s) {
   if (p.n_mu > kMaxMu || p.n_mu > 4 * kTableThreads) return cudaErrorInvalidValue;

@@ -608,45 +608,21 @@ __device__ __forceinline__ int add_mod(int a, int r, int B) {
   return v < B ? v : (B >= 64 ? v - B : v % B);
 }
 
-template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK, bool ADJ = false>
-__global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
-  extern __shared__ float4 smem4[];
-  float* smem = reinterpret_cast<float*>(smem4);
-  const int tab_floats = METHOD == kDarts ? P.rows * P.row_stride : 0;
-  float* tab = smem;
-  constexpr int nwarps = BLOCK / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// The per-warp path loop shared by the single-scene and the batched kernels:
+// warps claim path ids [*counter, N) in chunks of kPathChunk, refill lanes
+// whose path ended, run one vertex step per iteration and commit finished
+// paths into the warp tile (or the adjoint sums).
+template <int METHOD, int MAXM, bool DEBUG, bool TILE, bool ADJ>
+__device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab,
+                                          unsigned long long* counter, unsigned long long N,
+                                          float* wsum, float* wcomp, float* wsq, RisTask* wtasks,
+                                          RisResult* wresults, unsigned* wev, bool do_sq,
+                                          float (&g_s)[3], float (&g_c)[3], float (&g_q)[3]) {
+  const int lane = threadIdx.x & 31;
   const int B = P.n_bins;
-  const bool do_sq = P.sumsq != nullptr;
-  const int tile_stride = (do_sq ? 3 : 2) * B;
   constexpr bool kCoop = METHOD == kDarts && MAXM == 8;
-  RisTask* ris_tasks = reinterpret_cast<RisTask*>(smem + tab_floats);
-  RisResult* ris_results = reinterpret_cast<RisResult*>(ris_tasks + (kCoop ? nwarps * 32 : 0));
-  RisTask* wtasks = ris_tasks + warp * 32;
-  RisResult* wresults = ris_results + warp * 32;
-  float* tiles = reinterpret_cast<float*>(ris_results + (kCoop ? nwarps * 32 : 0));
-  float* wsum = tiles + (size_t)warp * tile_stride;
-  float* wcomp = wsum + B;
-  float* wsq = wcomp + B;
-  __shared__ unsigned long long blk_stats[kStatCount];
-  __shared__ unsigned warp_events[nwarps][8];
-
-  // stage the direction table (row stride is a multiple of 4 floats)
-  if (METHOD == kDarts) {
-    const float4* src = reinterpret_cast<const float4*>(P.table);
-    for (int i = threadIdx.x; i < tab_floats / 4; i += BLOCK) smem4[i] = __ldg(src + i);
-  }
-  if (TILE)
-    for (int i = threadIdx.x; i < nwarps * tile_stride; i += BLOCK) tiles[i] = 0.0f;
-  if (threadIdx.x < kStatCount) blk_stats[threadIdx.x] = 0;
-  if (threadIdx.x < 2) s_rare[threadIdx.x] = 0;
-  if (lane < 8) warp_events[warp][lane] = 0;
-  __syncthreads();
-
   Counters cnt;
   Path p;
-  // adjoint: per-lane Kahan sums of the weighted path scores and their squares
-  float g_s[3] = {0.0f, 0.0f, 0.0f}, g_c[3] = {0.0f, 0.0f, 0.0f}, g_q[3] = {0.0f, 0.0f, 0.0f};
   bool alive = false;
   unsigned long long pool_next = 0, pool_end = 0;
   int pool_bin = 0;  // DARTS bin of path pool_next
@@ -665,13 +641,13 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
       }
       if ((unsigned long long)n_dead > avail) {
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(P.counter, (unsigned long long)kPathChunk);
+        if (lane == 0) base = atomicAdd(counter, (unsigned long long)kPathChunk);
         base = __shfl_sync(kFull, base, 0);
-        if (base >= P.N) {
+        if (base >= N) {
           drained = true;
           pool_next = pool_end = 0;
         } else {
-          const unsigned long long end = min(base + (unsigned long long)kPathChunk, P.N);
+          const unsigned long long end = min(base + (unsigned long long)kPathChunk, N);
           const int base_bin = (int)((P.bin_base + base) % (unsigned long long)B);
           const long long r2 = (long long)rank - (long long)avail;
           if (!alive && r2 >= 0 && (unsigned long long)r2 < end - base) {
@@ -759,9 +735,51 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
         const unsigned c = __popc(__ballot_sync(kFull, (cnt.bits >> e) & 1u));
         mine = lane == e ? c : mine;
       }
-      if (lane < ST_FP64E) warp_events[warp][lane] += mine;
+      if (lane < ST_FP64E) wev[lane] += mine;
     }
   }
+
+}
+
+template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK, bool ADJ = false>
+__global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  const int tab_floats = METHOD == kDarts ? P.rows * P.row_stride : 0;
+  float* tab = smem;
+  constexpr int nwarps = BLOCK / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int B = P.n_bins;
+  const bool do_sq = P.sumsq != nullptr;
+  const int tile_stride = (do_sq ? 3 : 2) * B;
+  constexpr bool kCoop = METHOD == kDarts && MAXM == 8;
+  RisTask* ris_tasks = reinterpret_cast<RisTask*>(smem + tab_floats);
+  RisResult* ris_results = reinterpret_cast<RisResult*>(ris_tasks + (kCoop ? nwarps * 32 : 0));
+  RisTask* wtasks = ris_tasks + warp * 32;
+  RisResult* wresults = ris_results + warp * 32;
+  float* tiles = reinterpret_cast<float*>(ris_results + (kCoop ? nwarps * 32 : 0));
+  float* wsum = tiles + (size_t)warp * tile_stride;
+  float* wcomp = wsum + B;
+  float* wsq = wcomp + B;
+  __shared__ unsigned long long blk_stats[kStatCount];
+  __shared__ unsigned warp_events[nwarps][8];
+
+  // stage the direction table (row stride is a multiple of 4 floats)
+  if (METHOD == kDarts) {
+    const float4* src = reinterpret_cast<const float4*>(P.table);
+    for (int i = threadIdx.x; i < tab_floats / 4; i += BLOCK) smem4[i] = __ldg(src + i);
+  }
+  if (TILE)
+    for (int i = threadIdx.x; i < nwarps * tile_stride; i += BLOCK) tiles[i] = 0.0f;
+  if (threadIdx.x < kStatCount) blk_stats[threadIdx.x] = 0;
+  if (threadIdx.x < 2) s_rare[threadIdx.x] = 0;
+  if (lane < 8) warp_events[warp][lane] = 0;
+  __syncthreads();
+
+  // adjoint: per-lane Kahan sums of the weighted path scores and their squares
+  float g_s[3] = {0.0f, 0.0f, 0.0f}, g_c[3] = {0.0f, 0.0f, 0.0f}, g_q[3] = {0.0f, 0.0f, 0.0f};
+  path_loop<METHOD, MAXM, DEBUG, TILE, ADJ>(P, tab, P.counter, P.N, wsum, wcomp, wsq, wtasks, wresults,
+                                            warp_events[warp], do_sq, g_s, g_c, g_q);
 
   // ---- statistics
   __syncthreads();
@@ -853,6 +871,99 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
   if (threadIdx.x == 0) *P.ticket = 0u;
 }
 
+// ---------------------------------------------------------------------------
+// Batched rendering of many media in one persistent launch.  Each CTA pops
+// work items (a path range of one medium) from a global counter; when the
+// medium changes it flushes its tiles into the previous medium's histogram
+// (FP64 atomics), copies the new medium's parameters into shared memory and
+// stages its direction table.
+// ---------------------------------------------------------------------------
+__global__ void zero_hists_kernel(const TraceParams* Ps) {
+  const TraceParams& P = Ps[blockIdx.x];
+  for (int b = threadIdx.x; b < P.n_bins; b += blockDim.x) P.hist[b] = 0.0;
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1) trace_batch_kernel(const BatchParams BP) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  __shared__ TraceParams Ps;
+  __shared__ int s_item;
+  __shared__ unsigned long long s_counter;
+  __shared__ unsigned warp_events[BLOCK / 32][8];
+  constexpr int nwarps = BLOCK / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tab_floats = BP.rows * BP.row_stride;
+  float* tab = smem;
+  RisTask* ris_tasks = reinterpret_cast<RisTask*>(smem + tab_floats);
+  RisResult* ris_results = reinterpret_cast<RisResult*>(ris_tasks + nwarps * 32);
+  float* tiles = reinterpret_cast<float*>(ris_results + nwarps * 32);
+  const int tile_stride = 2 * BP.max_bins;
+  float* wsum = tiles + (size_t)warp * tile_stride;
+  for (int i = threadIdx.x; i < nwarps * tile_stride; i += BLOCK) tiles[i] = 0.0f;
+  if (threadIdx.x < 2) s_rare[threadIdx.x] = 0;
+  if (lane < 8) warp_events[warp][lane] = 0;
+  float g_s[3] = {0.0f, 0.0f, 0.0f}, g_c[3] = {0.0f, 0.0f, 0.0f}, g_q[3] = {0.0f, 0.0f, 0.0f};
+  int cur = -1;
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(BP.item_counter, 1u);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= BP.n_items) break;
+    const BatchItem item = BP.items[it];
+    if ((int)item.medium != cur) {
+      if (cur >= 0) {
+        for (int b = threadIdx.x; b < Ps.n_bins; b += BLOCK) {
+          double v = 0.0;
+          for (int w = 0; w < nwarps; ++w) {
+            float* t = tiles + (size_t)w * tile_stride;
+            v += (double)t[b] - (double)t[Ps.n_bins + b];
+            t[b] = 0.0f;
+            t[Ps.n_bins + b] = 0.0f;
+          }
+          if (v != 0.0) atomicAdd(&Ps.hist[b], v);
+        }
+      }
+      __syncthreads();
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(BP.params + item.medium);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&Ps);
+      for (int i = threadIdx.x; i < (int)(sizeof(TraceParams) / 4); i += BLOCK) dst[i] = src[i];
+      __syncthreads();
+      const float4* tsrc = reinterpret_cast<const float4*>(Ps.table);
+      for (int i = threadIdx.x; i < tab_floats / 4; i += BLOCK) smem4[i] = __ldg(tsrc + i);
+      cur = (int)item.medium;
+    }
+    if (threadIdx.x == 0) s_counter = item.first;
+    __syncthreads();
+    path_loop<kDarts, 8, false, true, false>(Ps, tab, &s_counter, item.first + item.count, wsum,
+                                             wsum + Ps.n_bins, nullptr, ris_tasks + warp * 32,
+                                             ris_results + warp * 32, warp_events[warp], false, g_s,
+                                             g_c, g_q);
+    __syncthreads();
+  }
+  if (cur >= 0) {
+    for (int b = threadIdx.x; b < Ps.n_bins; b += BLOCK) {
+      double v = 0.0;
+      for (int w = 0; w < nwarps; ++w) {
+        const float* t = tiles + (size_t)w * tile_stride;
+        v += (double)t[b] - (double)t[Ps.n_bins + b];
+      }
+      if (v != 0.0) atomicAdd(&Ps.hist[b], v);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < kStatCount) {
+    unsigned long long v = 0;
+    if (threadIdx.x < ST_FP64E) {
+      for (int w = 0; w < nwarps; ++w) v += warp_events[w][threadIdx.x];
+    } else if (threadIdx.x < ST_FP64E + 2) {
+      v = s_rare[threadIdx.x - ST_FP64E];
+    }
+    if (v) atomicAdd(&BP.stats[threadIdx.x], v);
+  }
+}
+
 __global__ void philox_kernel(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t n,
                               uint32_t* out) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -896,6 +1007,39 @@ cudaError_t launch_method(const TraceParams& p, int grid, int block, bool debug,
 }
 
 }  // namespace
+
+size_t batch_smem_bytes(const BatchParams& bp, int block) {
+  return (size_t)bp.rows * bp.row_stride * sizeof(float) +
+         (size_t)(block / 32) * 32 * (sizeof(RisTask) + sizeof(RisResult)) +
+         (size_t)(block / 32) * 2 * bp.max_bins * sizeof(float);
+}
+
+cudaError_t launch_batch(const BatchParams& bp, int grid, int block, size_t smem, cudaStream_t s) {
+  zero_hists_kernel<<<bp.n_media, 128, 0, s>>>(bp.params);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  switch (block) {
+    case 768: {
+      auto k = trace_batch_kernel<768>;
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) k<<<grid, 768, smem, s>>>(bp);
+      break;
+    }
+    case 640: {
+      auto k = trace_batch_kernel<640>;
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) k<<<grid, 640, smem, s>>>(bp);
+      break;
+    }
+    default: {
+      auto k = trace_batch_kernel<512>;
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) k<<<grid, 512, smem, s>>>(bp);
+    }
+  }
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
 
 size_t adjoint_smem_bytes(const TraceParams& p) {
   size_t b = (size_t)p.rows * p.row_stride * sizeof(float);
