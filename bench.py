@@ -205,46 +205,50 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
-def mse_time(ctx, S, torch, n_paths=1 << 16, seeds=8, ref_paths=1 << 26):
-    """MSE x time of DARTS against the plain uniform-temporal path tracer on
-    the benchmark scene at the configured 2^16 paths per render."""
-    sc, _ = S.cube_workload()
-    B = sc.gate.n_bins
-    ref = torch.zeros(B, dtype=torch.float64, device="cuda")
-    for m, seed in ((S.DARTS, 1000), (S.PLAIN_UNIFORM_T, 2000)):
-        for r in range(4):
-            sp = S.Sampling(seed=seed + r, paths_per_element=ref_paths, method=m)
-            ref += ctx.render(sc, sp)
-    ref /= 8
-    out = {}
-    for name, m in (("darts", S.DARTS), ("plain_uniform_t", S.PLAIN_UNIFORM_T),
-                    ("vanilla_direct", S.VANILLA_DIRECT)):
-        mses, mses_nb0, times = [], [], []
-        for s in range(seeds):
-            sp = S.Sampling(seed=7 + s, paths_per_element=n_paths, method=m,
-                            flags=S.FLAG_REBUILD_TABLE if m == S.DARTS else 0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            h = ctx.render(sc, sp)
-            e1.record()
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1) * 1e-3)
-            d = (h - ref).double()
-            mses.append(float((d * d).mean()))
-            mses_nb0.append(float((d[1:] * d[1:]).mean()))
-        out[name] = {"mse_mean": statistics.fmean(mses), "mse_median": statistics.median(mses),
-                     "mse_mean_excl_bin0": statistics.fmean(mses_nb0),
-                     "mse_median_excl_bin0": statistics.median(mses_nb0),
-                     "seconds_per_render": statistics.median(times)}
-    d = out["darts"]
-    for base in ("plain_uniform_t", "vanilla_direct"):
-        b = out[base]
-        out[f"ratio_mse_time_{base}_over_darts"] = {
-            k: (b[k] * b["seconds_per_render"]) / max(d[k] * d["seconds_per_render"], 1e-300)
-            for k in ("mse_mean", "mse_median", "mse_mean_excl_bin0", "mse_median_excl_bin0")}
-    out["paths_per_render"] = n_paths
-    out["seeds"] = seeds
-    out["reference"] = f"mean of 4 DARTS + 4 plain renders of {ref_paths} paths each"
+def mse_time(ctx, S, torch, n_paths=1 << 20, seeds=8, ref_paths=1 << 26):
+    """MSE x time of DARTS against the plain uniform-temporal path tracer (and
+    the vanilla direct-connection tracer) at equal path counts, on the
+    benchmark's unit cube and on a paper-shaped dense variant (sigma_s = 13.5:
+    about 3.2 transport mean free paths between emitter and sensor).  MSE is
+    the mean over bins of (h - h_ref)^2, h_ref the mean of 4 DARTS and 4 plain
+    renders of ref_paths paths; time is the render time (table build + trace)
+    from CUDA events."""
+    out = {"paths_per_render": n_paths, "seeds": seeds,
+           "reference": f"mean of 4 DARTS + 4 plain renders of {ref_paths} paths each"}
+    for label, sc in (("unit_cube", S.slab_scene()), ("unit_cube_sigma_s_13.5", S.slab_scene(sigma_s=13.5))):
+        B = sc.gate.n_bins
+        ref = torch.zeros(B, dtype=torch.float64, device="cuda")
+        for m, seed in ((S.DARTS, 1000), (S.PLAIN_UNIFORM_T, 2000)):
+            for r in range(4):
+                ref += ctx.render(sc, S.Sampling(seed=seed + r, paths_per_element=ref_paths, method=m))
+        ref /= 8
+        res = {}
+        for name, m in (("darts", S.DARTS), ("plain_uniform_t", S.PLAIN_UNIFORM_T),
+                        ("vanilla_direct", S.VANILLA_DIRECT)):
+            mses, mses_nb0, times = [], [], []
+            for s_ in range(seeds):
+                sp = S.Sampling(seed=7 + s_, paths_per_element=n_paths, method=m,
+                                flags=S.FLAG_REBUILD_TABLE if m == S.DARTS else 0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                h = ctx.render(sc, sp)
+                e1.record()
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1) * 1e-3)
+                d = (h - ref).double()
+                mses.append(float((d * d).mean()))
+                mses_nb0.append(float((d[1:] * d[1:]).mean()))
+            res[name] = {"mse_mean": statistics.fmean(mses), "mse_median": statistics.median(mses),
+                         "mse_mean_excl_bin0": statistics.fmean(mses_nb0),
+                         "mse_median_excl_bin0": statistics.median(mses_nb0),
+                         "seconds_per_render": statistics.median(times)}
+        d = res["darts"]
+        for base in ("plain_uniform_t", "vanilla_direct"):
+            b = res[base]
+            res[f"ratio_mse_time_{base}_over_darts"] = {
+                k: (b[k] * b["seconds_per_render"]) / max(d[k] * d["seconds_per_render"], 1e-300)
+                for k in ("mse_mean", "mse_median", "mse_mean_excl_bin0", "mse_median_excl_bin0")}
+        out[label] = res
     return out
 
 

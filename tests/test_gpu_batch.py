@@ -34,11 +34,11 @@ def test_batch_equals_single_renders(ctx):
     samplings = [m[1] for m in media]
     outs = ctx.render_batch(scenes, samplings)
     ctx.sync()
+    st = ctx.stats()
+    assert st["paths"] == sum(sp.paths_per_element for sp in samplings)
     for sc, sp, h in zip(scenes, samplings, outs):
         ref = ctx.render(sc, sp)
         torch.testing.assert_close(h, ref, rtol=1e-5, atol=1e-14 * float(ref.abs().max()) + 1e-300)
-    st = ctx.stats()
-    assert st["paths"] == sum(sp.paths_per_element for sp in samplings)
 
 
 def test_batch_matches_oracle(ctx):
