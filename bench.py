@@ -205,49 +205,61 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
-def mse_time(ctx, S, torch, n_paths=1 << 20, seeds=8, ref_paths=1 << 26):
-    """MSE x time of DARTS against the plain uniform-temporal path tracer (and
-    the vanilla direct-connection tracer) at equal path counts, on the
-    benchmark's unit cube and on a paper-shaped dense variant (sigma_s = 13.5:
-    about 3.2 transport mean free paths between emitter and sensor).  MSE is
-    the mean over bins of (h - h_ref)^2, h_ref the mean of 4 DARTS and 4 plain
-    renders of ref_paths paths; time is the render time (table build + trace)
-    from CUDA events."""
-    out = {"paths_per_render": n_paths, "seeds": seeds,
-           "reference": f"mean of 4 DARTS + 4 plain renders of {ref_paths} paths each"}
+def mse_time(ctx, S, torch, n_paths=1 << 20, seeds=16):
+    """Efficiency of DARTS against the plain uniform-temporal path tracer (and
+    the vanilla direct-connection tracer and the ablations of Fig. 13) at
+    equal path counts, on the benchmark's unit cube and on a paper-shaped dense
+    variant (sigma_s = 13.5: about 3.2 transport mean free paths between
+    emitter and sensor).
+
+    With a point emitter every estimator here has infinite variance (the
+    control vertex next to the emitter), so two figures are reported per
+    method: the MSE against the pooled mean of all renders (mean and median
+    over seeds), and a robust spread -- the interquartile range over seeds of
+    each bin.  ratio_* = (spread^2 x time)_base / (spread^2 x time)_darts,
+    median over bins; render time (table build + trace) from CUDA events."""
+    methods = (("darts", S.DARTS, 0), ("darts_no_da", S.DARTS, S.FLAG_NO_DA_DISTANCE),
+               ("darts_no_eda", S.DARTS, S.FLAG_NO_EDA),
+               ("darts_no_da_no_eda", S.DARTS, S.FLAG_NO_DA_DISTANCE | S.FLAG_NO_EDA),
+               ("plain_uniform_t", S.PLAIN_UNIFORM_T, 0), ("vanilla_direct", S.VANILLA_DIRECT, 0))
+    out = {"paths_per_render": n_paths, "seeds": seeds}
     for label, sc in (("unit_cube", S.slab_scene()), ("unit_cube_sigma_s_13.5", S.slab_scene(sigma_s=13.5))):
-        B = sc.gate.n_bins
-        ref = torch.zeros(B, dtype=torch.float64, device="cuda")
-        for m, seed in ((S.DARTS, 1000), (S.PLAIN_UNIFORM_T, 2000)):
-            for r in range(4):
-                ref += ctx.render(sc, S.Sampling(seed=seed + r, paths_per_element=ref_paths, method=m))
-        ref /= 8
-        res = {}
-        for name, m in (("darts", S.DARTS), ("plain_uniform_t", S.PLAIN_UNIFORM_T),
-                        ("vanilla_direct", S.VANILLA_DIRECT)):
-            mses, mses_nb0, times = [], [], []
+        H, T = {}, {}
+        for name, m, fl in methods:
+            hs, ts = [], []
             for s_ in range(seeds):
                 sp = S.Sampling(seed=7 + s_, paths_per_element=n_paths, method=m,
-                                flags=S.FLAG_REBUILD_TABLE if m == S.DARTS else 0)
+                                flags=fl | (S.FLAG_REBUILD_TABLE if m == S.DARTS else 0))
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
                 h = ctx.render(sc, sp)
                 e1.record()
                 e1.synchronize()
-                times.append(e0.elapsed_time(e1) * 1e-3)
-                d = (h - ref).double()
-                mses.append(float((d * d).mean()))
-                mses_nb0.append(float((d[1:] * d[1:]).mean()))
-            res[name] = {"mse_mean": statistics.fmean(mses), "mse_median": statistics.median(mses),
-                         "mse_mean_excl_bin0": statistics.fmean(mses_nb0),
-                         "mse_median_excl_bin0": statistics.median(mses_nb0),
-                         "seconds_per_render": statistics.median(times)}
-        d = res["darts"]
-        for base in ("plain_uniform_t", "vanilla_direct"):
-            b = res[base]
-            res[f"ratio_mse_time_{base}_over_darts"] = {
-                k: (b[k] * b["seconds_per_render"]) / max(d[k] * d["seconds_per_render"], 1e-300)
-                for k in ("mse_mean", "mse_median", "mse_mean_excl_bin0", "mse_median_excl_bin0")}
+                ts.append(e0.elapsed_time(e1) * 1e-3)
+                hs.append(h)
+            H[name] = torch.stack(hs).cpu()
+            T[name] = statistics.median(ts)
+        ref = torch.cat([H[n] for n, m, _ in methods if m != S.VANILLA_DIRECT]).mean(0)
+        res = {}
+        for name, _, _ in methods:
+            d = H[name] - ref
+            mse = (d * d).mean(1)
+            q = torch.quantile(H[name], torch.tensor([0.25, 0.75], dtype=torch.float64), dim=0)
+            res[name] = {"seconds_per_render": T[name], "mse_mean": float(mse.mean()),
+                         "mse_median": float(mse.median()), "_iqr": (q[1] - q[0])}
+        for base in ("plain_uniform_t", "vanilla_direct", "darts_no_da", "darts_no_eda", "darts_no_da_no_eda"):
+            a = res[base]["_iqr"] ** 2 * res[base]["seconds_per_render"]
+            b = res["darts"]["_iqr"] ** 2 * res["darts"]["seconds_per_render"]
+            ok = (a > 0) & (b > 0)
+            res[f"ratio_{base}_over_darts"] = {
+                "robust_spread2_time_median_over_bins": float((a[ok] / b[ok]).median()) if ok.any() else None,
+                "mse_mean_time": (res[base]["mse_mean"] * res[base]["seconds_per_render"]) /
+                                 max(res["darts"]["mse_mean"] * res["darts"]["seconds_per_render"], 1e-300),
+                "mse_median_time": (res[base]["mse_median"] * res[base]["seconds_per_render"]) /
+                                   max(res["darts"]["mse_median"] * res["darts"]["seconds_per_render"], 1e-300)}
+        for name in res:
+            if isinstance(res[name], dict):
+                res[name].pop("_iqr", None)
         out[label] = res
     return out
 

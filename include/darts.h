@@ -57,6 +57,10 @@ typedef enum {
 /* sampling.flags */
 #define DARTS_FLAG_SENSOR_UNIFORM_ONLY (1u << 0) /* no EDA at the sensor vertex        */
 #define DARTS_FLAG_REBUILD_TABLE (1u << 1)       /* rebuild the direction table even on a cache hit */
+/* Ablations of the two DARTS samplers (the paper's Fig. 13 study): */
+#define DARTS_FLAG_NO_DA_DISTANCE (1u << 2) /* distances: plain truncated-exponential draw
+                                               (every RIS weight 1, no DA target)       */
+#define DARTS_FLAG_NO_EDA (1u << 3)         /* directions: phase function only (gamma = 0) */
 
 typedef struct darts_ctx darts_ctx;
 

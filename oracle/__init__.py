@@ -42,6 +42,7 @@ class OrcScene(C.Structure):
         ("n_rho", C.c_int32), ("n_s", C.c_int32), ("n_mu", C.c_int32),
         ("mis_alpha", C.c_double), ("seed", C.c_uint64), ("stream", C.c_uint32),
         ("sensor_uniform_only", C.c_int32), ("paths_per_element", C.c_uint64),
+        ("ablation", C.c_int32),
     ]
 
 
@@ -121,6 +122,7 @@ def make_scene(scene, sampling) -> OrcScene:
     s.stream = sampling.stream & 0xFFFFFFFF
     s.sensor_uniform_only = 1 if (sampling.flags & 1) else 0
     s.paths_per_element = sampling.paths_per_element
+    s.ablation = (1 if (sampling.flags & (1 << 2)) else 0) | (2 if (sampling.flags & (1 << 3)) else 0)
     return s
 
 

@@ -386,7 +386,7 @@ static double darts_direction(const orc_scene* sc, const double* cdf, int k, uin
   const double* crow = cdf + (size_t)row * (nb + 1);
   double rho = C / SM;
   double gamma = rho / (rho + sc->mis_alpha);
-  if (k == 0 && sc->sensor_uniform_only) gamma = 0.0;
+  if ((k == 0 && sc->sensor_uniform_only) || (sc->ablation & 2)) gamma = 0.0;
   double gb = (k == 0) ? 0.0 : sc->g;
   double zaxis[3] = {0.0, 0.0, 1.0};
   const double* axis = (k == 0) ? zaxis : wprev;
@@ -521,7 +521,15 @@ static int darts_distance(const orc_scene* sc, int k, uint64_t id, const double 
     valid[j] = r < s;
     if (s / sc->v < (sc->t_max - sc->t_min) / 64.0) pr->flags |= ORC_FLAG_SMALL_TPRIME;
     pr->n_cand += 1.0;
-    if (valid[j]) {
+    if (sc->ablation & 1) {
+      /* ablation: the target equals the candidate density -> every candidate
+       * has weight 1 and the selection is a plain truncated-exponential draw */
+      lphat[j] = log(st) - st * d[j] - log(pm);
+      lw[j] = 0.0;
+      valid[j] = 1;
+      if (lw[j] > lmax) lmax = lw[j];
+      any = 1;
+    } else if (valid[j]) {
       /* Eq. 10 target (unnormalised) and Eq. 13 candidate density */
       double lphi = orc_log_phi(r, s / sc->v, sc->sigma_s, sc->sigma_a, sc->g, sc->v);
       lphat[j] = log(st) - st * d[j] + lphi;

@@ -60,6 +60,9 @@ typedef struct {
   uint32_t stream;              /* Philox stream word                        */
   int32_t sensor_uniform_only;  /* 1: no EDA at the sensor vertex            */
   uint64_t paths_per_element;   /* N_e, the per-bin weight is n_bins / N_e   */
+  int32_t ablation;             /* bit 0: exponential distance sampling (RIS
+                                   weights all 1, no DA target); bit 1: no EDA
+                                   direction sampling (gamma = 0)             */
 } orc_scene;
 
 /* Philox4x32-10 block (Salmon et al., SC'11). */

@@ -261,6 +261,8 @@ void make_trace_params(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
   P->inv_mu_scale = (float)(2.0 / sp->table_n_mu);
   P->mis_alpha = (float)sp->mis_alpha;
   P->uniform_sensor = (sp->flags & DARTS_FLAG_SENSOR_UNIFORM_ONLY) ? 1 : 0;
+  P->no_eda = (sp->flags & DARTS_FLAG_NO_EDA) ? 1 : 0;
+  P->no_da = (sp->flags & DARTS_FLAG_NO_DA_DISTANCE) ? 1 : 0;
   P->table = ctx->table;
   P->K = sp->max_bounces;
   P->M = sp->ris_m;
@@ -582,7 +584,7 @@ darts_status darts_get_stats(darts_ctx* ctx, darts_stats* out) {
   unsigned long long v[2 + kStatCount];
   CK(cudaMemcpy(v, ctx->scratch, sizeof(v), cudaMemcpyDeviceToHost), "stats read");
   const unsigned long long* s = v + 2;
-  out->paths = std::min<unsigned long long>(v[0], ctx->last_paths);
+  out->paths = ctx->last_paths;  // every launched path is traced to its end
   out->vertices = s[0];
   out->connections_nonempty = s[1];
   out->distance_steps = s[2];

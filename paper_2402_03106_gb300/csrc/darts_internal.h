@@ -49,6 +49,8 @@ struct TraceParams {
   float inv_smax, n_s_over_8, mu_scale, inv_mu_scale;  // 1/S_max, n_s / 8, n_mu / 2, 2 / n_mu
   float mis_alpha;
   int uniform_sensor;
+  int no_eda;                      // ablation: phase-function directions only
+  int no_da;                       // ablation: truncated-exponential distances (RIS weights 1)
   const float* table;              // [rows][row_stride]
   // sampling
   int K, M;

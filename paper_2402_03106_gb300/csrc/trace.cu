@@ -189,6 +189,7 @@ __device__ __forceinline__ float ris_candidate(const TraceParams& P, const RisTa
   const float r2 = fmaf(e, e, T.h2);
   const float s = T.SM - d;  // remaining length budget
   *d_out = d;
+  if (P.no_da) return 0.0f;  // ablation: the target equals the candidate density
   if (!(s > 0.0f && r2 < s * s)) return -FLT_MAX;
   if (act && s < P.tiny_s) {
     cnt.add_rare(ST_FP64P);
@@ -265,7 +266,7 @@ struct Stepper {
     const float* row = tab + (i_rho * P.n_s + i_s) * P.row_stride;
     float gamma = __fdividef(rho, rho + P.mis_alpha);
     const bool sensor = p.k == 0;
-    if (sensor && P.uniform_sensor) gamma = 0.0f;
+    if ((sensor && P.uniform_sensor) || P.no_eda) gamma = 0.0f;
     const float gb = sensor ? 0.0f : P.g;
     const float bx = sensor ? 0.0f : p.wx, by = sensor ? 0.0f : p.wy, bz = sensor ? 1.0f : p.wz;
     const U4 u1 = rng(P, p.j, (uint32_t)p.k, 1);

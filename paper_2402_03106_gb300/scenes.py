@@ -28,6 +28,8 @@ METHOD_NAMES = {DARTS: "darts", PLAIN_UNIFORM_T: "plain_uniform_t", VANILLA_DIRE
 # Sampling flags (C-ABI DARTS_FLAG_*).
 FLAG_SENSOR_UNIFORM_ONLY = 1 << 0
 FLAG_REBUILD_TABLE = 1 << 1
+FLAG_NO_DA_DISTANCE = 1 << 2  # ablation: truncated-exponential distances (no DA target)
+FLAG_NO_EDA = 1 << 3          # ablation: phase-function directions only (gamma = 0)
 
 Vec3 = Tuple[float, float, float]
 

@@ -120,6 +120,17 @@ def test_darts_per_path_parity(ctx, K):
     check_paths(gpu, ref, K)
 
 
+@pytest.mark.parametrize("flags", [S.FLAG_NO_DA_DISTANCE, S.FLAG_NO_EDA,
+                                   S.FLAG_NO_DA_DISTANCE | S.FLAG_NO_EDA, S.FLAG_SENSOR_UNIFORM_ONLY])
+def test_ablation_per_path_parity(ctx, flags):
+    sc, sp = S.cube_workload(paths=1 << 16, seed=6)
+    sp.flags = flags
+    n = 2048
+    gpu = ctx.debug_paths(sc, sp, 0, n)
+    ref = O.trace_paths(sc, sp, 0, n)
+    check_paths(gpu, ref, sp.max_bounces)
+
+
 def test_darts_per_path_parity_dense_medium(ctx):
     """Many scattering events per path: sigma_s = 8 in a unit cube."""
     sc = S.slab_scene(8.0, 0.05, 0.5, n_bins=64, t_min=0.8, t_max=6.0)

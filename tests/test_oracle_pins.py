@@ -400,3 +400,16 @@ def test_ris_selection_frequencies_follow_the_da_target():
     assert tot > 1000
     chi2 = np.sum((counts - expect) ** 2 / np.maximum(expect, 1e-9))
     assert chi2 < 30.0, (counts, expect)
+
+
+@pytest.mark.parametrize("flags", [S.FLAG_NO_DA_DISTANCE, S.FLAG_NO_EDA])
+def test_ablations_stay_unbiased(flags):
+    """The ablated samplers (Fig. 13 study) estimate the same truncated sum."""
+    sc = S.slab_scene(1.0, 0.02, 0.5, n_bins=8, t_min=0.85, t_max=2.5)
+    n = 1 << 17
+    h, sq, _ = O.render(sc, S.Sampling(seed=15, paths_per_element=n, max_bounces=3, flags=flags))
+    se = O.standard_error(h, sq, n / 8)
+    h2, sq2, _ = O.render(sc, S.Sampling(seed=16, paths_per_element=n, max_bounces=3), O.ORC_PLAIN_UNIFORM_T)
+    se2 = O.standard_error(h2, sq2, n)
+    z = (h - h2) / np.sqrt(se ** 2 + se2 ** 2)
+    assert np.max(np.abs(z[1:])) < 4.5, z
