@@ -31,6 +31,11 @@ EV_NONE, EV_EARLY, EV_SCATTER, EV_ESCAPE, EV_INVALID, EV_MAXDEPTH = range(6)
 FLAG_NEAR_DEGENERATE, FLAG_SMALL_TPRIME = 1, 2
 
 
+class OrcEmitter(C.Structure):
+    _fields_ = [("pos", C.c_double * 3), ("t0", C.c_double), ("energy", C.c_double),
+                ("kind", C.c_int32), ("u", C.c_double * 3), ("v", C.c_double * 3)]
+
+
 class OrcScene(C.Structure):
     _fields_ = [
         ("sigma_s", C.c_double), ("sigma_a", C.c_double), ("g", C.c_double), ("v", C.c_double),
@@ -43,6 +48,11 @@ class OrcScene(C.Structure):
         ("mis_alpha", C.c_double), ("seed", C.c_uint64), ("stream", C.c_uint32),
         ("sensor_uniform_only", C.c_int32), ("paths_per_element", C.c_uint64),
         ("ablation", C.c_int32),
+        ("n_emitters", C.c_int32), ("em", OrcEmitter * 8),
+        ("sensor_kind", C.c_int32), ("look_at", C.c_double * 3), ("up", C.c_double * 3),
+        ("fov_deg", C.c_double), ("width", C.c_int32), ("height", C.c_int32),
+        ("walls", C.c_int32), ("wall_albedo", C.c_double), ("n_spheres", C.c_int32),
+        ("spheres", (C.c_double * 5) * 64),
     ]
 
 
@@ -89,6 +99,11 @@ def load():
     lib.orc_ris_step.argtypes = [sp, C.c_uint64, C.c_int, dp, dp, C.c_double, C.c_double, dp, dp,
                                  C.POINTER(C.c_int32), C.POINTER(C.c_int32), dp]
     lib.orc_ris_step.restype = C.c_int
+    lib.orc_trace_ray.argtypes = [sp, dp, dp, C.POINTER(C.c_int32), dp]
+    lib.orc_trace_ray.restype = C.c_double
+    lib.orc_camera_ray.argtypes = [sp, C.c_int32, C.c_double, C.c_double, dp, dp, dp]
+    lib.orc_camera_ray.restype = C.c_int
+    lib.orc_sample_emitter.argtypes = [sp, C.c_uint64, dp, dp]
     lib.orc_adjoint.argtypes = [sp, dp, C.c_uint64, C.c_uint64, C.c_int, dp, dp, dp]
     lib.orc_adjoint.restype = C.c_int
     _lib = lib
@@ -108,12 +123,36 @@ def make_scene(scene, sampling) -> OrcScene:
     s.sigma_s, s.sigma_a, s.g, s.v = m.sigma_s, m.sigma_a, m.g, m.v
     s.lo[:] = list(scene.geometry.lo)
     s.hi[:] = list(scene.geometry.hi)
-    if len(scene.emitters) != 1:
-        raise ValueError("the oracle models exactly one point emitter")
-    e = scene.emitters[0]
+    ems = scene.emitters
+    if not 1 <= len(ems) <= 8:
+        raise ValueError("the oracle models 1 to 8 emitters")
+    e = ems[0]
     s.xe[:] = list(e.pos)
-    s.t0, s.energy = e.t0, e.energy
-    s.xs[:] = list(scene.sensor.pos)
+    s.t0 = min(x.t0 for x in ems)
+    s.energy = e.energy
+    s.n_emitters = len(ems)
+    for i, x in enumerate(ems):
+        s.em[i].pos[:] = list(x.pos)
+        s.em[i].t0, s.em[i].energy = x.t0, x.energy
+        s.em[i].kind = getattr(x, "kind", 0)
+        s.em[i].u[:] = list(getattr(x, "u", (0.0, 0.0, 0.0)))
+        s.em[i].v[:] = list(getattr(x, "v", (0.0, 0.0, 0.0)))
+    sen = scene.sensor
+    s.xs[:] = list(sen.pos)
+    s.sensor_kind = getattr(sen, "kind", 0)
+    s.look_at[:] = list(getattr(sen, "look_at", (0.0, 0.0, 1.0)))
+    s.up[:] = list(getattr(sen, "up", (0.0, 1.0, 0.0)))
+    s.fov_deg = getattr(sen, "fov_deg", 40.0)
+    s.width, s.height = getattr(sen, "width", 1), getattr(sen, "height", 1)
+    geo = scene.geometry
+    s.walls = getattr(geo, "walls", 0)
+    s.wall_albedo = getattr(geo, "wall_albedo", 0.0)
+    sph = list(getattr(geo, "spheres", []))
+    if len(sph) > 64:
+        raise ValueError("at most 64 spheres")
+    s.n_spheres = len(sph)
+    for i, q in enumerate(sph):
+        s.spheres[i][:] = [float(v) for v in q]
     s.t_min, s.t_max, s.n_bins = scene.gate.t_min, scene.gate.t_max, scene.gate.n_bins
     s.max_bounces, s.ris_m = sampling.max_bounces, sampling.ris_m
     s.n_rho, s.n_s, s.n_mu = sampling.table_n_rho, sampling.table_n_s, sampling.table_n_mu
@@ -185,7 +224,7 @@ def build_table(scene, sampling) -> np.ndarray:
     """Direction table of the scene (cached per medium, S_max and dims: the
     table depends on nothing else).  Returns a copy."""
     s = make_scene(scene, sampling)
-    key = (s.sigma_s, s.sigma_a, s.g, s.v, s.t_max - s.t0, s.n_rho, s.n_s, s.n_mu)
+    key = (s.sigma_s, s.sigma_a, s.g, s.v, s.t_max - s.t0, s.n_rho, s.n_s, s.n_mu)  # t0 = earliest
     if key in _table_cache:
         return _table_cache[key].copy()
     rows = s.n_rho * s.n_s
@@ -248,6 +287,34 @@ def ris_step(scene, sampling, path_id, k, x, w, SM, dm):
     return dict(status=r, d=d, logw=lw, valid=valid.astype(bool), sel=sel.value, factor=fac.value)
 
 
+def trace_ray(scene, sampling, x, w):
+    """Nearest surface along a ray from inside the box: (distance, kind, normal);
+    kind 0 = open boundary, 1 = wall, 2 + i = sphere i."""
+    s = make_scene(scene, sampling)
+    k = C.c_int32()
+    n = np.zeros(3)
+    d = load().orc_trace_ray(C.byref(s), _ptr(np.ascontiguousarray(x, np.float64)),
+                             _ptr(np.ascontiguousarray(w, np.float64)), C.byref(k), _ptr(n))
+    return d, k.value, n
+
+
+def camera_ray(scene, sampling, pixel, jx, jy):
+    """(hit, entry point, direction, camera-leg length) of a pinhole ray."""
+    s = make_scene(scene, sampling)
+    x = np.zeros(3)
+    w = np.zeros(3)
+    leg = C.c_double()
+    hit = load().orc_camera_ray(C.byref(s), pixel, jx, jy, _ptr(x), _ptr(w), C.byref(leg))
+    return bool(hit), x, w, leg.value
+
+
+def sample_emitter(scene, sampling, path_id, q):
+    s = make_scene(scene, sampling)
+    out = np.zeros(8)
+    load().orc_sample_emitter(C.byref(s), path_id, _ptr(np.ascontiguousarray(q, np.float64)), _ptr(out))
+    return dict(y=out[:3], n=out[3:6], wsel=out[6], intensity=out[7])
+
+
 STAT_NAMES = ("paths", "vertices", "connections", "connections_nonempty", "ris_candidates",
               "early_exits", "all_invalid", "escapes")
 
@@ -260,8 +327,9 @@ def render(scene, sampling, method=ORC_DARTS, n_paths=None, offset=0, threads=No
     if method == ORC_DARTS and cdf is None:
         cdf = build_table(scene, sampling)
     threads = threads or (os.cpu_count() or 1)
-    hist = np.zeros(s.n_bins)
-    sumsq = np.zeros(s.n_bins)
+    elements = s.width * s.height if s.sensor_kind == 1 else 1
+    hist = np.zeros(s.n_bins * elements)
+    sumsq = np.zeros(s.n_bins * elements)
     stats = np.zeros(8)
     cdf_c = None if cdf is None else np.ascontiguousarray(cdf, dtype=np.float64)
     rc = load().orc_render(C.byref(s), method, _ptr(cdf_c), n, offset, threads, _ptr(hist),
@@ -281,7 +349,8 @@ def adjoint(scene, sampling, dLdh, n_paths=None, offset=0, threads=None, cdf=Non
     """Path-replay gradient estimate of sum_b dLdh[b] * h_b w.r.t.
     (sigma_s, sigma_a, g), with per-path squared sums for a standard error."""
     s = make_scene(scene, sampling)
-    n = sampling.paths_per_element if n_paths is None else n_paths
+    elements = s.width * s.height if s.sensor_kind == 1 else 1
+    n = sampling.paths_per_element * elements if n_paths is None else n_paths
     if cdf is None:
         cdf = build_table(scene, sampling)
     threads = threads or (os.cpu_count() or 1)

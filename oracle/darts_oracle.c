@@ -137,14 +137,136 @@ double orc_control_pdf(double pS, double S, double C, double mu, double r1) {
   return pS * (S - C * mu) / r1;
 }
 
-/* Distance from x (inside the box) to the box boundary along unit w. */
-static double box_exit(const orc_scene* sc, const double x[3], const double w[3]) {
+/* ------------------------------------------------------------------------ */
+/* Surfaces, emitters and the camera.                                        */
+/* ------------------------------------------------------------------------ */
+#define ORC_EPS 1e-5
+
+static void cross3(const double a[3], const double b[3], double o[3]) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+static void normalize3(double a[3]) {
+  double n = norm3(a);
+  for (int i = 0; i < 3; ++i) a[i] /= n;
+}
+
+/* Smallest root t > ORC_EPS of |x + w t - c| = r, or INFINITY. */
+static double ray_sphere(const double c[3], double r, const double x[3], const double w[3]) {
+  double oc[3] = {x[0] - c[0], x[1] - c[1], x[2] - c[2]};
+  double b = dot3(oc, w), cc = dot3(oc, oc) - r * r;
+  double disc = b * b - cc;
+  if (disc < 0.0) return INFINITY;
+  double sq = sqrt(disc);
+  double t0 = -b - sq, t1 = -b + sq;
+  if (t0 > ORC_EPS) return t0;
+  if (t1 > ORC_EPS) return t1;
+  return INFINITY;
+}
+
+/* Nearest surface or medium-boundary point along (x, w), x inside the box. */
+double orc_trace_ray(const orc_scene* sc, const double x[3], const double w[3], int32_t* kind,
+                     double normal[3]) {
   double d = INFINITY;
+  int face = -1;
   for (int i = 0; i < 3; ++i) {
-    if (w[i] > 0.0) d = dmin(d, (sc->hi[i] - x[i]) / w[i]);
-    else if (w[i] < 0.0) d = dmin(d, (sc->lo[i] - x[i]) / w[i]);
+    double di = INFINITY;
+    int fi = -1;
+    if (w[i] > 0.0) { di = (sc->hi[i] - x[i]) / w[i]; fi = 2 * i + 1; }
+    else if (w[i] < 0.0) { di = (sc->lo[i] - x[i]) / w[i]; fi = 2 * i; }
+    if (di < d) { d = di; face = fi; }
   }
-  return dmax(d, 0.0);
+  d = dmax(d, 0.0);
+  *kind = (face >= 0 && (sc->walls >> face) & 1) ? 1 : 0;
+  normal[0] = normal[1] = normal[2] = 0.0;
+  if (face >= 0) normal[face / 2] = (face & 1) ? -1.0 : 1.0;  /* walls face inward */
+  for (int k = 0; k < sc->n_spheres; ++k) {
+    double t = ray_sphere(sc->spheres[k], sc->spheres[k][3], x, w);
+    if (t < d) {
+      d = t;
+      *kind = 2 + k;
+      for (int i = 0; i < 3; ++i) normal[i] = (x[i] + w[i] * t - sc->spheres[k][i]) / sc->spheres[k][3];
+    }
+  }
+  return d;
+}
+
+/* 1 when no sphere blocks the open segment a -> b (the box is convex, so its
+ * walls never occlude two points inside it). */
+static int visible(const orc_scene* sc, const double a[3], const double b[3]) {
+  double w[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  double len = norm3(w);
+  for (int i = 0; i < 3; ++i) w[i] /= len;
+  for (int k = 0; k < sc->n_spheres; ++k)
+    if (ray_sphere(sc->spheres[k], sc->spheres[k][3], a, w) < len - ORC_EPS) return 0;
+  return 1;
+}
+
+/* The emitter point of a path: chosen among the emitters with probability
+ * proportional to energy, a uniform point on an area emitter (an area
+ * emitter is treated as point samples, Sec. 7). */
+typedef struct {
+  double y[3], n[3];
+  int kind;
+  double energy, t0, wsel;
+} emit_pt;
+
+static void pick_emitter(const orc_scene* sc, uint64_t id, emit_pt* e);
+
+/* Radiant intensity toward x of the sampled emitter point: E / 4 pi for an
+ * isotropic point; (E / pi) max(0, cos) for a Lambertian area point sampled
+ * with density 1 / area (L_e = E / (pi A)). */
+static double emit_intensity(const emit_pt* e, const double x[3]) {
+  if (e->kind == 0) return e->energy / (4.0 * M_PI);
+  double d[3] = {x[0] - e->y[0], x[1] - e->y[1], x[2] - e->y[2]};
+  double c = dot3(d, e->n) / norm3(d);
+  return c > 0.0 ? e->energy / M_PI * c : 0.0;
+}
+
+/* Pinhole camera: ray of pixel `pixel` through the jittered point (jx, jy) of
+ * the pixel; the path starts where the ray enters the medium box. */
+int orc_camera_ray(const orc_scene* sc, int32_t pixel, double jx, double jy, double x0[3],
+                   double w[3], double* leg) {
+  double f[3] = {sc->look_at[0] - sc->xs[0], sc->look_at[1] - sc->xs[1], sc->look_at[2] - sc->xs[2]};
+  normalize3(f);
+  double r[3], u[3];
+  cross3(f, sc->up, r);
+  normalize3(r);
+  cross3(r, f, u);
+  double th = tan(0.5 * sc->fov_deg * M_PI / 180.0);
+  double aspect = (double)sc->width / (double)sc->height;
+  int px = pixel % sc->width, py = pixel / sc->width;
+  double sx = (2.0 * (px + jx) / sc->width - 1.0) * th * aspect;
+  double sy = (1.0 - 2.0 * (py + jy) / sc->height) * th;
+  for (int i = 0; i < 3; ++i) w[i] = f[i] + sx * r[i] + sy * u[i];
+  normalize3(w);
+  int inside = 1;
+  for (int i = 0; i < 3; ++i)
+    if (!(sc->xs[i] >= sc->lo[i] && sc->xs[i] <= sc->hi[i])) inside = 0;
+  if (inside) {
+    for (int i = 0; i < 3; ++i) x0[i] = sc->xs[i];
+    *leg = 0.0;
+    return 1;
+  }
+  double tin = -INFINITY, tout = INFINITY;
+  int face = -1;
+  for (int i = 0; i < 3; ++i) {
+    if (w[i] == 0.0) {
+      if (sc->xs[i] < sc->lo[i] || sc->xs[i] > sc->hi[i]) return 0;
+      continue;
+    }
+    double t1 = (sc->lo[i] - sc->xs[i]) / w[i], t2 = (sc->hi[i] - sc->xs[i]) / w[i];
+    int f1 = 2 * i, f2 = 2 * i + 1;
+    if (t1 > t2) { double tt = t1; t1 = t2; t2 = tt; int ff = f1; f1 = f2; f2 = ff; }
+    if (t1 > tin) { tin = t1; face = f1; }
+    if (t2 < tout) tout = t2;
+  }
+  if (!(tin <= tout) || tout <= 0.0 || tin < 0.0) return 0;
+  if (face >= 0 && (sc->walls >> face) & 1) return 0; /* opaque wall seen from outside */
+  for (int i = 0; i < 3; ++i) x0[i] = sc->xs[i] + w[i] * tin;
+  *leg = tin;
+  return 1;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -188,7 +310,12 @@ double orc_radical_inverse2(uint32_t i) {
 /* log-spaced over 8 octaves below S_max = v (t_max - t0) in n_s cells.      */
 /* Each cell is integrated at its centre; mu in [-1,1] in n_mu equal bins.    */
 /* ------------------------------------------------------------------------ */
-static double table_smax(const orc_scene* sc) { return sc->v * (sc->t_max - sc->t0); }
+static double table_smax(const orc_scene* sc) {
+  /* one table per medium: S_max of the earliest emitter */
+  double t0 = sc->t0;
+  for (int i = 0; i < sc->n_emitters; ++i) t0 = dmin(t0, sc->em[i].t0);
+  return sc->v * (sc->t_max - t0);
+}
 
 static void table_cell_centre(const orc_scene* sc, int row, double* C, double* S) {
   int i_rho = row / sc->n_s, i_s = row % sc->n_s;
@@ -366,7 +493,34 @@ typedef struct {
   /* adjoint: per-connection scores */
   double score[3];
   int dec_sel;
+  /* the path's emitter point and sensor element */
+  const emit_pt* E;
+  int elem;
 } path_rec;
+
+#define ORC_VERTEX_INIT 0xFFFFFFu
+
+static void pick_emitter(const orc_scene* sc, uint64_t id, emit_pt* e) {
+  uint32_t u[4];
+  orc_rng4(sc, id, ORC_VERTEX_INIT, 2, u);
+  double tot = 0.0;
+  for (int i = 0; i < sc->n_emitters; ++i) tot += sc->em[i].energy;
+  int pick = sc->n_emitters - 1;
+  double acc = 0.0, target = orc_u01(u[0]) * tot;
+  for (int i = 0; i < sc->n_emitters; ++i) {
+    acc += sc->em[i].energy;
+    if (target < acc) { pick = i; break; }
+  }
+  const orc_emitter* m = &sc->em[pick];
+  double su = orc_u01(u[1]), sv = orc_u01(u[2]);
+  e->kind = m->kind;
+  for (int i = 0; i < 3; ++i) e->y[i] = m->pos[i] + (m->kind ? su * m->u[i] + sv * m->v[i] : 0.0);
+  cross3(m->u, m->v, e->n);
+  if (m->kind) normalize3(e->n);
+  e->energy = m->energy;
+  e->t0 = m->t0;
+  e->wsel = m->energy > 0.0 ? tot / m->energy : 0.0;
+}
 
 static void rec_margin(path_rec* pr, int k, double m) {
   if (pr->margin && m < pr->margin[k]) pr->margin[k] = m;
@@ -441,15 +595,17 @@ static double darts_direction(const orc_scene* sc, const double* cdf, int k, uin
 }
 
 /* Elliptical control vertex on the ray (x, w), Sec. 5.2 case I with the
- * medium boundary as the cap of case II: S ~ truncated exponential on
- * [max(S_m, C), min(S_M, S(d_m))), t from Eq. 18/21, p(t) from Eq. 22. */
+ * first surface or the medium boundary as the cap of case II: S ~ truncated
+ * exponential on [max(S_m, C), min(S_M, S(d_m))), t from Eq. 18/21, p(t)
+ * from Eq. 22; the segment to the emitter point must be unoccluded. */
 static double darts_connect(const orc_scene* sc, int k, double beta, const double x[3],
                             const double w[3], double C, double Sm, double SM, double dm,
                             double u3, int uniform_S, double L, path_rec* pr, int* ok,
                             double* S_out) {
+  const emit_pt* E = pr->E;
   double st = sc->sigma_s + sc->sigma_a;
   double xm[3] = {x[0] + w[0] * dm, x[1] + w[1] * dm, x[2] + w[2] * dm};
-  double S_dm = dm + dist3(xm, sc->xe);
+  double S_dm = dm + dist3(xm, E->y);
   double S_hi = dmin(SM, S_dm);
   double S_lo = dmax(Sm, C);
   *ok = 0;
@@ -465,23 +621,45 @@ static double darts_connect(const orc_scene* sc, int k, double beta, const doubl
     S = S_lo + u3 * Wd;
     pS = 1.0 / Wd;
   }
-  double a[3] = {(sc->xe[0] - x[0]) / C, (sc->xe[1] - x[1]) / C, (sc->xe[2] - x[2]) / C};
+  double a[3] = {(E->y[0] - x[0]) / C, (E->y[1] - x[1]) / C, (E->y[2] - x[2]) / C};
   double mu = dot3(w, a);
   double t, r1;
   orc_ellipse(S, C, mu, &t, &r1);
   double pt = orc_control_pdf(pS, S, C, mu, r1);
   double xell[3] = {x[0] + w[0] * t, x[1] + w[1] * t, x[2] + w[2] * t};
   double cos_s = 0.0;
-  for (int i = 0; i < 3; ++i) cos_s += (xell[i] - sc->xe[i]) / r1 * (-w[i]);
+  for (int i = 0; i < 3; ++i) cos_s += (xell[i] - E->y[i]) / r1 * (-w[i]);
   if ((S - C) / C < 1.0 / 4096.0) pr->flags |= ORC_FLAG_NEAR_DEGENERATE;
-  double Ie = sc->energy / (4.0 * M_PI);
-  double c = beta * sc->sigma_s * exp(-st * S) * orc_hg_pdf(cos_s, sc->g) * Ie / (r1 * r1) / pt;
+  double Ie = emit_intensity(E, xell);
+  double vis = (sc->n_spheres && !visible(sc, xell, E->y)) ? 0.0 : 1.0;
+  double c = beta * sc->sigma_s * exp(-st * S) * orc_hg_pdf(cos_s, sc->g) * Ie * vis / (r1 * r1) / pt;
   *ok = 1;
   *S_out = S;
-  /* score of log f for the adjoint: (k walk vertices + control vertex) */
   (void)L;
   pr->score[2] = hg_dlog_dg(cos_s, sc->g);
   return c;
+}
+
+/* Direct connection from a surface vertex xs (normal n facing the medium)
+ * to the emitter point: Lambertian BRDF albedo / pi, transmittance, the
+ * emitter's intensity toward xs, 1/r^2 and visibility.  Returns 0 when the
+ * emitter is behind the surface. */
+static double surface_connect(const orc_scene* sc, const emit_pt* E, const double xs[3],
+                              const double n[3], double albedo, double* r_out) {
+  double d[3] = {E->y[0] - xs[0], E->y[1] - xs[1], E->y[2] - xs[2]};
+  double r = norm3(d);
+  *r_out = r;
+  double cs = dot3(d, n) / r;
+  if (!(cs > 0.0)) return 0.0;
+  if (sc->n_spheres && !visible(sc, xs, E->y)) return 0.0;
+  double st = sc->sigma_s + sc->sigma_a;
+  return albedo / M_PI * cs * exp(-st * r) * emit_intensity(E, xs) / (r * r);
+}
+
+/* Cosine-weighted direction about n (Malley's method on the frame of n). */
+static void cosine_dir(const double n[3], double u1, double u2, double out[3]) {
+  double mu = sqrt(u1);
+  frame_dir(n, mu, 2.0 * M_PI * u2, out);
 }
 
 /* DA distance sampling by RIS (Sec. 4.3, Eq. 12-15).  Returns 0 = escape,
@@ -515,7 +693,7 @@ static int darts_distance(const orc_scene* sc, int k, uint64_t id, const double 
     /* Eq. 13-14: truncated exponential on [0, d_m); sign of Eq. 14 fixed */
     d[j] = -log1p(-pm * eps) / st;
     for (int i = 0; i < 3; ++i) xs[j][i] = x[i] + w[i] * d[j];
-    double r = dist3(xs[j], sc->xe);
+    double r = dist3(xs[j], pr->E->y);
     double s = SM - d[j]; /* remaining length budget to the upper gate edge */
     rec_margin(pr, k, fabs(r - s) / dmax(dmax(fabs(r), fabs(s)), 1e-300));
     valid[j] = r < s;
@@ -576,6 +754,9 @@ int orc_ris_step(const orc_scene* sc, uint64_t id, int k, const double x[3], con
                  int32_t* sel_out, double* factor_out) {
   path_rec pr;
   memset(&pr, 0, sizeof(pr));
+  emit_pt E;
+  pick_emitter(sc, id, &E);
+  pr.E = &E;
   double beta = 1.0, xn[3], dsel;
   int r = darts_distance(sc, k, id, x, w, SM, dm, &beta, xn, &dsel, &pr);
   double st = sc->sigma_s + sc->sigma_a;
@@ -590,7 +771,7 @@ int orc_ris_step(const orc_scene* sc, uint64_t id, int k, const double x[3], con
     double eps = (double)((ri24 + e0) & 0xFFFFFFu) * (1.0 / 16777216.0);
     d_out[j] = -log1p(-pm * eps) / st;
     double xs_[3] = {x[0] + w[0] * d_out[j], x[1] + w[1] * d_out[j], x[2] + w[2] * d_out[j]};
-    double rr = dist3(xs_, sc->xe), ss = SM - d_out[j];
+    double rr = dist3(xs_, E.y), ss = SM - d_out[j];
     valid_out[j] = rr < ss;
     lw_out[j] = valid_out[j] ? orc_log_phi(rr, ss / sc->v, sc->sigma_s, sc->sigma_a, sc->g, sc->v) + log(pm)
                              : -INFINITY;
@@ -600,49 +781,110 @@ int orc_ris_step(const orc_scene* sc, uint64_t id, int k, const double x[3], con
   return r;
 }
 
-/* Sensor element bookkeeping: one point sensor -> element 0.  The bin of
- * path j is (j + o_e) mod B with o_e drawn once per element (Sec. 6.2:
- * an equal number of paths per frame, each path dedicated to one frame). */
-static int darts_bin(const orc_scene* sc, uint64_t id) {
+/* Test hook: the emitter point of path `id`: out = (y[3], n[3], wsel,
+ * intensity toward q[3]). */
+void orc_sample_emitter(const orc_scene* sc, uint64_t id, const double q[3], double out[8]) {
+  emit_pt E;
+  pick_emitter(sc, id, &E);
+  for (int i = 0; i < 3; ++i) {
+    out[i] = E.y[i];
+    out[3 + i] = E.n[i];
+  }
+  out[6] = E.wsel;
+  out[7] = emit_intensity(&E, q);
+}
+
+/* Sensor elements: the point sensor is element 0 and path id j; the camera's
+ * pixel p owns ids p * N_e ... p * N_e + N_e - 1.  A DARTS path is dedicated
+ * to bin (j + o_e) mod B with o_e drawn once per element (Sec. 6.2: every
+ * frame gets the same number of paths, each path serves one frame). */
+static void path_element(const orc_scene* sc, uint64_t id, int* elem, uint64_t* j) {
+  if (sc->sensor_kind == 1) {
+    *elem = (int)(id / sc->paths_per_element);
+    *j = id % sc->paths_per_element;
+  } else {
+    *elem = 0;
+    *j = id;
+  }
+}
+
+static int darts_bin(const orc_scene* sc, int elem, uint64_t j) {
   uint32_t u[4];
-  orc_rng4(sc, 0, ORC_VERTEX_ELEMENT, 0, u);
+  orc_rng4(sc, (uint64_t)elem, ORC_VERTEX_ELEMENT, 0, u);
   uint64_t oe = (uint64_t)floor(orc_u01(u[0]) * sc->n_bins);
   if (oe >= (uint64_t)sc->n_bins) oe = sc->n_bins - 1;
-  return (int)((id + oe) % (uint64_t)sc->n_bins);
+  return (int)((j + oe) % (uint64_t)sc->n_bins);
+}
+
+/* Start of a path: the point sensor (direction sampled at vertex 0) or the
+ * camera ray, entering the medium after `leg` (direction fixed).  Returns 0
+ * when the camera ray misses the medium. */
+static int path_start(const orc_scene* sc, uint64_t id, int elem, double x[3], double w[3],
+                      double* L, int* fixed) {
+  if (sc->sensor_kind == 1) {
+    uint32_t u[4];
+    orc_rng4(sc, id, ORC_VERTEX_INIT, 3, u);
+    *fixed = 1;
+    return orc_camera_ray(sc, elem, orc_u01(u[0]), orc_u01(u[1]), x, w, L);
+  }
+  for (int i = 0; i < 3; ++i) x[i] = sc->xs[i];
+  w[0] = 0.0; w[1] = 0.0; w[2] = 1.0;
+  *L = 0.0;
+  *fixed = 0;
+  return 1;
+}
+
+static double surface_albedo(const orc_scene* sc, int kind) {
+  return kind == 1 ? sc->wall_albedo : sc->spheres[kind - 2][4];
 }
 
 static void trace_darts(const orc_scene* sc, const double* cdf, uint64_t id, path_rec* pr,
                         const double* dLdh, double grad[3]) {
   int K = sc->max_bounces, B = sc->n_bins;
   double dt = (sc->t_max - sc->t_min) / B;
-  int b = darts_bin(sc, id);
-  double Tm = sc->t_min + b * dt, TM = sc->t_min + (b + 1) * dt;
-  double x[3] = {sc->xs[0], sc->xs[1], sc->xs[2]};
-  double wprev[3] = {0.0, 0.0, 1.0};
-  double L = 0.0, beta = 1.0;
-  double st = sc->sigma_s + sc->sigma_a;
-  double gsum = 0.0; /* sum of d log HG / dg over walk vertices */
-  pr->bin = b;
+  int elem;
+  uint64_t j;
+  path_element(sc, id, &elem, &j);
+  int b = darts_bin(sc, elem, j);
+  emit_pt E;
+  pick_emitter(sc, id, &E);
+  pr->E = &E;
+  pr->elem = elem;
+  pr->bin = elem * B + b;  /* flat histogram index */
   pr->contrib = 0.0;
+  double Tm = sc->t_min + b * dt, TM = sc->t_min + (b + 1) * dt;
+  double x[3], w[3], L;
+  int fixed;
+  if (!path_start(sc, id, elem, x, w, &L, &fixed)) return;
+  double wprev[3] = {w[0], w[1], w[2]};
+  double beta = E.wsel;
+  double gsum = 0.0;  /* sum of d log HG / dg over medium walk vertices */
+  int n_med = 0;      /* medium scattering vertices of the walk */
+  double wb = (double)B / (double)sc->paths_per_element;
   for (int k = 0; k < K; ++k) {
     pr->nvert = k + 1;
     pr->n_vert += 1.0;
-    double ev[3] = {sc->xe[0] - x[0], sc->xe[1] - x[1], sc->xe[2] - x[2]};
+    double ev[3] = {E.y[0] - x[0], E.y[1] - x[1], E.y[2] - x[2]};
     double C = norm3(ev);
     double a[3] = {ev[0] / C, ev[1] / C, ev[2] / C};
     /* Eq. 5 residual bounds in length units */
-    double SM = sc->v * (TM - sc->t0) - L;
-    double Sm = sc->v * (Tm - sc->t0) - L;
+    double SM = sc->v * (TM - E.t0) - L;
+    double Sm = sc->v * (Tm - E.t0) - L;
     rec_margin(pr, k, fabs(SM - C) / dmax(SM, 1e-300));
     if (!(SM > C)) { /* Sec. 5.2: no causal continuation remains */
       if (pr->dec) pr->dec[k * 4] = ORC_EV_EARLY;
       pr->n_early += 1.0;
       return;
     }
-    double w[3], mu_b;
-    beta *= darts_direction(sc, cdf, k, id, a, C, SM, wprev, w, &mu_b, pr);
-    if (k >= 1) gsum += hg_dlog_dg(mu_b, sc->g);
-    double dm = box_exit(sc, x, w);
+    if (!fixed) {
+      double wn[3], mu_b;
+      beta *= darts_direction(sc, cdf, k, id, a, C, SM, wprev, wn, &mu_b, pr);
+      if (k >= 1) gsum += hg_dlog_dg(mu_b, sc->g);
+      for (int i = 0; i < 3; ++i) w[i] = wn[i];
+    }
+    int32_t hit;
+    double nrm[3];
+    double dm = orc_trace_ray(sc, x, w, &hit, nrm);
     uint32_t u[4];
     orc_rng4(sc, id, (uint32_t)k, 1, u);
     int ok;
@@ -653,39 +895,79 @@ static void trace_darts(const orc_scene* sc, const double* cdf, uint64_t id, pat
       pr->n_conn_nonempty += 1.0;
       pr->contrib += c;
       if (dLdh) {
-        double ell = L + S, n = k + 1.0;
-        double wb = (double)B / (double)sc->paths_per_element;
+        double ell = L + S, n = n_med + 1.0;
         double s0 = n / sc->sigma_s - ell, s1 = -ell, s2 = gsum + pr->score[2];
-        grad[0] += dLdh[b] * wb * c * s0;
-        grad[1] += dLdh[b] * wb * c * s1;
-        grad[2] += dLdh[b] * wb * c * s2;
+        grad[0] += dLdh[elem * B + b] * wb * c * s0;
+        grad[1] += dLdh[elem * B + b] * wb * c * s1;
+        grad[2] += dLdh[elem * B + b] * wb * c * s2;
       }
     }
-    uint8_t code = ORC_EV_SCATTER | (uint8_t)(ok ? 0x10 : 0);
+    uint8_t ne = (uint8_t)(ok ? 0x10 : 0);
     if (k + 1 == K) {
-      if (pr->dec) pr->dec[k * 4] = ORC_EV_MAXDEPTH | (uint8_t)(ok ? 0x10 : 0);
+      if (pr->dec) pr->dec[k * 4] = ORC_EV_MAXDEPTH | ne;
       return;
+    }
+    /* medium event (Eq. 12): DA-RIS distance; otherwise the ray reaches the
+     * first surface or leaves the medium */
+    double st = sc->sigma_s + sc->sigma_a;
+    uint32_t u0[4];
+    orc_rng4(sc, id, (uint32_t)k, 0, u0);
+    double pm = 1.0 - exp(-st * dm);
+    if (!(orc_u01(u0[0]) < pm)) {
+      rec_margin(pr, k, fabs(orc_u01(u0[0]) - pm));
+      if (hit == 0) {
+        if (pr->dec) pr->dec[k * 4] = ORC_EV_ESCAPE | ne;
+        pr->n_escape += 1.0;
+        return;
+      }
+      /* surface vertex: transmittance / probability = 1 */
+      for (int i = 0; i < 3; ++i) x[i] += w[i] * dm;
+      L += dm;
+      double alb = surface_albedo(sc, hit), r;
+      double cs = beta * surface_connect(sc, &E, x, nrm, alb, &r);
+      double Ltot = L + r;
+      double lo = sc->v * (Tm - E.t0), hi = sc->v * (TM - E.t0);
+      rec_margin(pr, k, dmin(fabs(Ltot - lo), fabs(Ltot - hi)) / hi);
+      if (cs > 0.0 && Ltot >= lo && Ltot < hi) {
+        pr->contrib += cs;
+        if (dLdh) {
+          double s0 = n_med / sc->sigma_s - Ltot, s1 = -Ltot, s2 = gsum;
+          grad[0] += dLdh[elem * B + b] * wb * cs * s0;
+          grad[1] += dLdh[elem * B + b] * wb * cs * s1;
+          grad[2] += dLdh[elem * B + b] * wb * cs * s2;
+        }
+      }
+      if (pr->dec) pr->dec[k * 4] = ORC_EV_SURFACE | ne;
+      uint32_t us[4];
+      orc_rng4(sc, id, (uint32_t)(k + 1), 1, us);
+      double wn[3];
+      cosine_dir(nrm, orc_u01(us[1]), orc_u01(us[2]), wn);
+      for (int i = 0; i < 3; ++i) w[i] = wn[i];
+      beta *= alb;
+      fixed = 1;
+      continue;
     }
     double xn[3], d;
     int r = darts_distance(sc, k, id, x, w, SM, dm, &beta, xn, &d, pr);
     if (r == 0) {
-      if (pr->dec) pr->dec[k * 4] = ORC_EV_ESCAPE | (uint8_t)(ok ? 0x10 : 0);
+      if (pr->dec) pr->dec[k * 4] = ORC_EV_ESCAPE | ne;
       pr->n_escape += 1.0;
       return;
     }
     if (r == 2) {
-      if (pr->dec) pr->dec[k * 4] = ORC_EV_INVALID | (uint8_t)(ok ? 0x10 : 0);
+      if (pr->dec) pr->dec[k * 4] = ORC_EV_INVALID | ne;
       pr->n_invalid += 1.0;
       return;
     }
-    if (pr->dec) pr->dec[k * 4] = code;
+    if (pr->dec) pr->dec[k * 4] = ORC_EV_SCATTER | ne;
     for (int i = 0; i < 3; ++i) {
       x[i] = xn[i];
       wprev[i] = w[i];
     }
     L += d;
+    n_med += 1;
+    fixed = 0;
   }
-  (void)st;
 }
 
 /* Bin of an absolute time for the binned baselines; -1 outside the gate. */
@@ -706,6 +988,46 @@ static void emit(path_rec* pr, int b, double c) {
   }
 }
 
+/* Start of a baseline path: the point sensor draws a uniform direction
+ * (weight 4 pi, the detector is isotropic); the camera ray has weight 1. */
+static int base_start(const orc_scene* sc, uint64_t id, int elem, double x[3], double w[3],
+                      double* L, double* beta) {
+  int fixed;
+  if (!path_start(sc, id, elem, x, w, L, &fixed)) return 0;
+  if (!fixed) {
+    uint32_t u[4];
+    orc_rng4(sc, id, 0, 1, u);
+    double mu = 2.0 * orc_u01(u[1]) - 1.0;
+    double zaxis[3] = {0.0, 0.0, 1.0};
+    frame_dir(zaxis, mu, 2.0 * M_PI * orc_u01(u[2]), w);
+    *beta = 4.0 * M_PI;
+  } else {
+    *beta = 1.0;
+  }
+  return 1;
+}
+
+/* A surface vertex of a baseline path: direct connection binned by time,
+ * then a cosine-weighted direction (BRDF cos / pdf = albedo). */
+static void base_surface(const orc_scene* sc, uint64_t id, int k, const emit_pt* E, double x[3],
+                         double w[3], const double nrm[3], int hit, double L, double* beta,
+                         path_rec* pr) {
+  double alb = surface_albedo(sc, hit), r;
+  double cs = *beta * surface_connect(sc, E, x, nrm, alb, &r);
+  pr->n_conn += 1.0;
+  if (cs > 0.0) {
+    int b = time_bin(sc, E->t0 + (L + r) / sc->v, pr, k);
+    if (b >= 0) {
+      pr->n_conn_nonempty += 1.0;
+      emit(pr, b, cs);
+    }
+  }
+  uint32_t us[4];
+  orc_rng4(sc, id, (uint32_t)(k + 1), 1, us);
+  cosine_dir(nrm, orc_u01(us[1]), orc_u01(us[2]), w);
+  *beta *= alb;
+}
+
 /* Baseline "plain transient PT" with Jarabo-style uniform temporal sampling:
  * exponential free flight, HG directions, and at every vertex a control
  * vertex along the walk direction with S uniform over the whole gate
@@ -713,31 +1035,33 @@ static void emit(path_rec* pr, int b, double c) {
 static void trace_plain(const orc_scene* sc, uint64_t id, path_rec* pr) {
   int K = sc->max_bounces;
   double st = sc->sigma_s + sc->sigma_a;
-  double x[3] = {sc->xs[0], sc->xs[1], sc->xs[2]};
-  double w[3];
-  double L = 0.0, beta;
-  uint32_t u[4];
-  orc_rng4(sc, id, 0, 1, u);
-  {
-    double mu = 2.0 * orc_u01(u[1]) - 1.0;
-    double zaxis[3] = {0.0, 0.0, 1.0};
-    frame_dir(zaxis, mu, 2.0 * M_PI * orc_u01(u[2]), w);
-    beta = 4.0 * M_PI; /* isotropic sensor over the uniform-sphere pdf */
-  }
+  int elem;
+  uint64_t j;
+  path_element(sc, id, &elem, &j);
+  emit_pt E;
+  pick_emitter(sc, id, &E);
+  pr->E = &E;
+  pr->elem = elem;
   pr->bin = -1;
   pr->contrib = 0.0;
-  double Smin_abs = sc->v * (sc->t_min - sc->t0), Smax_abs = sc->v * (sc->t_max - sc->t0);
+  double x[3], w[3], L, beta;
+  if (!base_start(sc, id, elem, x, w, &L, &beta)) return;
+  beta *= E.wsel;
+  double Smin_abs = sc->v * (sc->t_min - E.t0), Smax_abs = sc->v * (sc->t_max - E.t0);
   for (int k = 0; k < K; ++k) {
     pr->nvert = k + 1;
     pr->n_vert += 1.0;
-    double C = dist3(sc->xe, x);
+    double C = dist3(E.y, x);
     double SM = Smax_abs - L, Sm = Smin_abs - L;
     if (!(SM > C)) {
       if (pr->dec) pr->dec[k * 4] = ORC_EV_EARLY;
       pr->n_early += 1.0;
       return;
     }
-    double dm = box_exit(sc, x, w);
+    int32_t hit;
+    double nrm[3];
+    double dm = orc_trace_ray(sc, x, w, &hit, nrm);
+    uint32_t u[4];
     orc_rng4(sc, id, (uint32_t)k, 1, u);
     int ok;
     double S;
@@ -745,7 +1069,7 @@ static void trace_plain(const orc_scene* sc, uint64_t id, path_rec* pr) {
     pr->n_conn += 1.0;
     if (ok) {
       pr->n_conn_nonempty += 1.0;
-      int b = time_bin(sc, sc->t0 + (L + S) / sc->v, pr, k);
+      int b = time_bin(sc, E.t0 + (L + S) / sc->v, pr, k);
       if (b >= 0) emit(pr, b, c);
     }
     if (k + 1 == K) {
@@ -755,9 +1079,16 @@ static void trace_plain(const orc_scene* sc, uint64_t id, path_rec* pr) {
     orc_rng4(sc, id, (uint32_t)k, 0, u);
     double d = -log1p(-orc_u01(u[0])) / st;
     if (!(d < dm)) {
-      if (pr->dec) pr->dec[k * 4] = ORC_EV_ESCAPE;
-      pr->n_escape += 1.0;
-      return;
+      if (hit == 0) {
+        if (pr->dec) pr->dec[k * 4] = ORC_EV_ESCAPE;
+        pr->n_escape += 1.0;
+        return;
+      }
+      for (int i = 0; i < 3; ++i) x[i] += w[i] * dm;
+      L += dm;
+      if (pr->dec) pr->dec[k * 4] = ORC_EV_SURFACE;
+      base_surface(sc, id, k, &E, x, w, nrm, hit, L, &beta, pr);
+      continue;
     }
     beta *= sc->sigma_s / st; /* sigma_s e^{-st d} / (st e^{-st d}) */
     for (int i = 0; i < 3; ++i) x[i] += w[i] * d;
@@ -778,42 +1109,73 @@ static void trace_plain(const orc_scene* sc, uint64_t id, path_rec* pr) {
 static void trace_vanilla(const orc_scene* sc, uint64_t id, path_rec* pr) {
   int K = sc->max_bounces;
   double st = sc->sigma_s + sc->sigma_a;
-  double x[3] = {sc->xs[0], sc->xs[1], sc->xs[2]};
-  double w[3];
-  double L = 0.0, beta;
-  uint32_t u[4];
-  orc_rng4(sc, id, 0, 1, u);
-  {
-    double mu = 2.0 * orc_u01(u[1]) - 1.0;
-    double zaxis[3] = {0.0, 0.0, 1.0};
-    frame_dir(zaxis, mu, 2.0 * M_PI * orc_u01(u[2]), w);
-    beta = 4.0 * M_PI;
-  }
+  int elem;
+  uint64_t j;
+  path_element(sc, id, &elem, &j);
+  emit_pt E;
+  pick_emitter(sc, id, &E);
+  pr->E = &E;
+  pr->elem = elem;
   pr->bin = -1;
   pr->contrib = 0.0;
-  double Smax_abs = sc->v * (sc->t_max - sc->t0);
-  double Ie = sc->energy / (4.0 * M_PI);
+  double x[3], w[3], L, beta;
+  if (!base_start(sc, id, elem, x, w, &L, &beta)) return;
+  beta *= E.wsel;
+  double Smax_abs = sc->v * (sc->t_max - E.t0);
   for (int k = 0; k < K; ++k) {
     pr->nvert = k + 1;
     pr->n_vert += 1.0;
-    double dm = box_exit(sc, x, w);
+    int32_t hit;
+    double nrm[3];
+    double dm = orc_trace_ray(sc, x, w, &hit, nrm);
+    uint32_t u[4];
     orc_rng4(sc, id, (uint32_t)k, 0, u);
     double d = -log1p(-orc_u01(u[0])) / st;
+    double C;
     if (!(d < dm)) {
-      if (pr->dec) pr->dec[k * 4] = ORC_EV_ESCAPE;
-      pr->n_escape += 1.0;
-      return;
+      if (hit == 0) {
+        if (pr->dec) pr->dec[k * 4] = ORC_EV_ESCAPE;
+        pr->n_escape += 1.0;
+        return;
+      }
+      for (int i = 0; i < 3; ++i) x[i] += w[i] * dm;
+      L += dm;
+      C = dist3(E.y, x);
+      if (k + 1 == K) {
+        /* a surface vertex still closes a path of k + 1 scattering vertices */
+        double alb = surface_albedo(sc, hit), r;
+        double cs = beta * surface_connect(sc, &E, x, nrm, alb, &r);
+        pr->n_conn += 1.0;
+        if (cs > 0.0) {
+          int b = time_bin(sc, E.t0 + (L + r) / sc->v, pr, k);
+          if (b >= 0) {
+            pr->n_conn_nonempty += 1.0;
+            emit(pr, b, cs);
+          }
+        }
+        if (pr->dec) pr->dec[k * 4] = ORC_EV_MAXDEPTH;
+        return;
+      }
+      base_surface(sc, id, k, &E, x, w, nrm, hit, L, &beta, pr);
+      if (!(L + C < Smax_abs)) {
+        if (pr->dec) pr->dec[k * 4] = ORC_EV_EARLY;
+        pr->n_early += 1.0;
+        return;
+      }
+      if (pr->dec) pr->dec[k * 4] = ORC_EV_SURFACE;
+      continue;
     }
     beta *= sc->sigma_s / st;
     for (int i = 0; i < 3; ++i) x[i] += w[i] * d;
     L += d;
     /* direct connection from the new scattering vertex x_{k+1} */
-    double C = dist3(sc->xe, x);
+    C = dist3(E.y, x);
     double cos_s = 0.0;
-    for (int i = 0; i < 3; ++i) cos_s += (x[i] - sc->xe[i]) / C * (-w[i]);
-    double c = beta * orc_hg_pdf(cos_s, sc->g) * exp(-st * C) * Ie / (C * C);
+    for (int i = 0; i < 3; ++i) cos_s += (x[i] - E.y[i]) / C * (-w[i]);
+    double vis = (sc->n_spheres && !visible(sc, x, E.y)) ? 0.0 : 1.0;
+    double c = beta * orc_hg_pdf(cos_s, sc->g) * exp(-st * C) * emit_intensity(&E, x) * vis / (C * C);
     pr->n_conn += 1.0;
-    int b = time_bin(sc, sc->t0 + (L + C) / sc->v, pr, k);
+    int b = time_bin(sc, E.t0 + (L + C) / sc->v, pr, k);
     if (b >= 0) {
       pr->n_conn_nonempty += 1.0;
       emit(pr, b, c);
@@ -853,6 +1215,9 @@ static int scene_ok(const orc_scene* sc, int method, const double* cdf) {
   if (!(sc->mis_alpha > 0.0)) return 0;
   if (method == ORC_DARTS && !cdf) return 0;
   if (sc->paths_per_element < 1) return 0;
+  if (sc->n_emitters < 1 || sc->n_emitters > ORC_MAX_EMITTERS) return 0;
+  if (sc->n_spheres < 0 || sc->n_spheres > ORC_MAX_SPHERES) return 0;
+  if (sc->sensor_kind == 1 && (sc->width < 1 || sc->height < 1 || !(sc->fov_deg > 0.0))) return 0;
   return 1;
 }
 
@@ -927,12 +1292,13 @@ static void* render_worker(void* p) {
       wk->hist[pr->bin] += c;
       wk->sumsq[pr->bin] += c * c;
     } else {
+      size_t row = (size_t)pr->elem * B;
       for (int j = 0; j < pr->n_out; ++j) tmp[pr->out_bin[j]] += inv_n * pr->out_c[j];
       for (int j = 0; j < pr->n_out; ++j) {
         int b = pr->out_bin[j];
         if (tmp[b] != 0.0) {
-          wk->hist[b] += tmp[b];
-          wk->sumsq[b] += tmp[b] * tmp[b];
+          wk->hist[row + b] += tmp[b];
+          wk->sumsq[row + b] += tmp[b] * tmp[b];
           tmp[b] = 0.0;
         }
       }
@@ -958,6 +1324,7 @@ static int run_threads(const orc_scene* sc, int method, const double* cdf, uint6
   if (n_threads < 1) n_threads = 1;
   if ((uint64_t)n_threads > n_paths && n_paths > 0) n_threads = (int)n_paths;
   int B = sc->n_bins;
+  size_t HB = (size_t)B * (sc->sensor_kind == 1 ? (size_t)sc->width * sc->height : 1);
   work_t* wk = (work_t*)calloc((size_t)n_threads, sizeof(work_t));
   pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
   if (!wk || !th) return -2;
@@ -970,19 +1337,19 @@ static int run_threads(const orc_scene* sc, int method, const double* cdf, uint6
     wk[t].first = start;
     wk[t].count = per + ((uint64_t)t < rem ? 1 : 0);
     start += wk[t].count;
-    wk[t].hist = (double*)calloc((size_t)B, sizeof(double));
-    wk[t].sumsq = (double*)calloc((size_t)B, sizeof(double));
+    wk[t].hist = (double*)calloc(HB, sizeof(double));
+    wk[t].sumsq = (double*)calloc(HB, sizeof(double));
     wk[t].dLdh = dLdh;
     pthread_create(&th[t], NULL, render_worker, &wk[t]);
   }
   for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
-  if (hist) memset(hist, 0, sizeof(double) * B);
-  if (sumsq) memset(sumsq, 0, sizeof(double) * B);
+  if (hist) memset(hist, 0, sizeof(double) * HB);
+  if (sumsq) memset(sumsq, 0, sizeof(double) * HB);
   if (stats) memset(stats, 0, sizeof(double) * 8);
   if (grad3) memset(grad3, 0, sizeof(double) * 3);
   if (grad3_sq) memset(grad3_sq, 0, sizeof(double) * 3);
   for (int t = 0; t < n_threads; ++t) {
-    for (int b = 0; b < B; ++b) {
+    for (size_t b = 0; b < HB; ++b) {
       if (hist) hist[b] += wk[t].hist[b];
       if (sumsq) sumsq[b] += wk[t].sumsq[b];
     }

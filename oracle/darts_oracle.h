@@ -30,7 +30,8 @@ enum {
   ORC_EV_SCATTER = 2,   /* connection made (maybe empty), walk continued     */
   ORC_EV_ESCAPE = 3,    /* Bernoulli medium event failed: ray leaves medium  */
   ORC_EV_INVALID = 4,   /* every RIS candidate non-causal: path ends          */
-  ORC_EV_MAXDEPTH = 5   /* k+1 == max_bounces after the connection            */
+  ORC_EV_MAXDEPTH = 5,  /* k+1 == max_bounces after the connection            */
+  ORC_EV_SURFACE = 6    /* the ray reached a surface: the next vertex lies on it */
 };
 
 /* Path-level flags (bit mask) reported by the per-path debug routine. */
@@ -38,6 +39,18 @@ enum {
   ORC_FLAG_NEAR_DEGENERATE = 1, /* a connection had (S-C)/C < 2^-12            */
   ORC_FLAG_SMALL_TPRIME = 2     /* a RIS candidate had t' < 2^-6 (t_max-t_min) */
 };
+
+#define ORC_MAX_EMITTERS 8
+#define ORC_MAX_SPHERES 64
+
+/* Pulse emitter: kind 0 = isotropic point; kind 1 = one-sided Lambertian
+ * parallelogram pos + s u + t v (s, t in [0,1]) emitting toward u x v. */
+typedef struct {
+  double pos[3];
+  double t0, energy;
+  int32_t kind;
+  double u[3], v[3];
+} orc_emitter;
 
 typedef struct {
   /* medium (Eq. 9, Eq. 12): sigma_s, sigma_a, Henyey-Greenstein g, v = c/eta */
@@ -63,6 +76,22 @@ typedef struct {
   int32_t ablation;             /* bit 0: exponential distance sampling (RIS
                                    weights all 1, no DA target); bit 1: no EDA
                                    direction sampling (gamma = 0)             */
+  /* emitters (em[0] repeats xe/t0/energy for the single point emitter) */
+  int32_t n_emitters;
+  orc_emitter em[ORC_MAX_EMITTERS];
+  /* sensor: 0 = isotropic point fluence detector at xs; 1 = pinhole camera at
+   * xs looking at look_at, vertical field of view fov_deg, width x height
+   * pixels, each pixel an element of paths_per_element paths */
+  int32_t sensor_kind;
+  double look_at[3], up[3];
+  double fov_deg;
+  int32_t width, height;
+  /* opaque Lambertian surfaces: box faces set in `walls` (bit 2*axis + side,
+   * side 1 = hi face) with albedo wall_albedo; spheres (cx, cy, cz, r, albedo) */
+  int32_t walls;
+  double wall_albedo;
+  int32_t n_spheres;
+  double spheres[ORC_MAX_SPHERES][5];
 } orc_scene;
 
 /* Philox4x32-10 block (Salmon et al., SC'11). */
@@ -123,13 +152,27 @@ int orc_ris_step(const orc_scene* sc, uint64_t id, int k, const double x[3], con
                  int32_t* sel_out, double* factor_out);
 
 /* Full histogram render of n_paths paths starting at path id `offset`,
- * split over n_threads POSIX threads; hist/sumsq are [n_bins] and are
+ * split over n_threads POSIX threads; hist/sumsq are [elements][n_bins]
+ * (elements = 1 for the point sensor, width*height for the camera) and are
  * overwritten.  stats (optional, 8 doubles): paths, vertices, connections,
  * nonempty connections, RIS candidates, early exits, all-invalid stops,
  * escapes. */
 int orc_render(const orc_scene* sc, int method, const double* cdf,
                uint64_t n_paths, uint64_t offset, int n_threads,
                double* hist, double* sumsq, double* stats);
+
+/* Geometry test hooks: nearest surface along a ray from inside the medium
+ * box (returns the distance; *kind = 0 open boundary, 1 wall, 2 sphere;
+ * normal[3] the surface normal facing the ray's origin); pinhole ray of a
+ * pixel and jitter (returns 0 when the ray misses the medium, else writes
+ * the entry point, direction and camera-leg length). */
+double orc_trace_ray(const orc_scene* sc, const double x[3], const double w[3], int32_t* kind,
+                     double normal[3]);
+int orc_camera_ray(const orc_scene* sc, int32_t pixel, double jx, double jy, double x0[3],
+                   double w[3], double* leg);
+/* The emitter point chosen by path `id`: out = (y[3], n[3], 1/selection
+ * probability, radiant intensity toward q). */
+void orc_sample_emitter(const orc_scene* sc, uint64_t id, const double q[3], double out[8]);
 
 /* Path-replay score of the DARTS estimator (detached sampling):
  * grad[3] += sum over paths of dLdh[bin] * w_b * sum_v c_v * s_v, with s_v the

@@ -42,17 +42,39 @@ class Medium:
     v: float = 1.0
 
 
+EMITTER_POINT = 0
+EMITTER_AREA = 1
+SENSOR_POINT = 0
+SENSOR_PINHOLE = 1
+
+
 @dataclass
 class Emitter:
+    """Pulse emitter: an isotropic point (kind 0), or a one-sided Lambertian
+    parallelogram pos + s u + t v emitting toward u x v (kind 1)."""
     pos: Vec3
     t0: float = 0.0
     energy: float = 1.0
+    kind: int = EMITTER_POINT
+    u: Vec3 = (0.0, 0.0, 0.0)
+    v: Vec3 = (0.0, 0.0, 0.0)
 
 
 @dataclass
 class Sensor:
-    """Isotropic point fluence detector (one sensor element)."""
+    """Isotropic point fluence detector (kind 0, one element) or a pinhole
+    camera at pos (kind 1, width x height elements, vertical FOV)."""
     pos: Vec3
+    kind: int = SENSOR_POINT
+    look_at: Vec3 = (0.0, 0.0, 1.0)
+    up: Vec3 = (0.0, 1.0, 0.0)
+    fov_deg: float = 40.0
+    width: int = 1
+    height: int = 1
+
+    @property
+    def elements(self) -> int:
+        return self.width * self.height if self.kind == SENSOR_PINHOLE else 1
 
 
 @dataclass
@@ -62,11 +84,19 @@ class Gate:
     n_bins: int
 
 
+# Box faces that carry walls: bit 2*axis + side (side 1 = the high face).
+WALL_X_LO, WALL_X_HI, WALL_Y_LO, WALL_Y_HI, WALL_Z_LO, WALL_Z_HI = (1 << i for i in range(6))
+
+
 @dataclass
 class Geometry:
-    """Axis-aligned medium box [lo, hi]; no surfaces."""
+    """Axis-aligned medium box [lo, hi]; optional opaque Lambertian walls on
+    some faces and opaque Lambertian spheres (cx, cy, cz, r, albedo)."""
     lo: Vec3 = (0.0, 0.0, 0.0)
     hi: Vec3 = (1.0, 1.0, 1.0)
+    walls: int = 0
+    wall_albedo: float = 0.0
+    spheres: List[Tuple[float, float, float, float, float]] = field(default_factory=list)
 
 
 @dataclass
@@ -134,6 +164,71 @@ def infinite_scene(sigma_s, sigma_a, g, separation=1.0, n_bins=64, t_min=None,
     )
 
 
+def box_camera_scene(seed: int = 0, width: int = 64, height: int = 64, n_bins: int = 512,
+                     t_max: float = 16.0) -> Scene:
+    """2x2x2 box with five Lambertian walls (albedo 0.5; the front face z = 0
+    is open) filled with a medium drawn from the seed (sigma_s U[0.5, 2],
+    albedo U[0.9, 0.99], g U[0, 0.9]); a 0.3 x 0.3 Lambertian pulse emitter
+    centred on the ceiling (1, 2, 1) facing -y; a pinhole camera at
+    (1, 1, -2.5) looking +z through the open face, 40 degree FOV."""
+    rs = np.random.default_rng(np.random.SeedSequence([seed, 0xB0C5]))
+    sigma_s = float(rs.uniform(0.5, 2.0))
+    albedo = float(rs.uniform(0.9, 0.99))
+    g = float(rs.uniform(0.0, 0.9))
+    sigma_a = sigma_s * (1.0 - albedo) / albedo
+    walls = WALL_X_LO | WALL_X_HI | WALL_Y_LO | WALL_Y_HI | WALL_Z_HI
+    return Scene(
+        medium=Medium(sigma_s, sigma_a, g, 1.0),
+        geometry=Geometry((0.0, 0.0, 0.0), (2.0, 2.0, 2.0), walls, 0.5, []),
+        emitters=[Emitter((0.85, 2.0, 0.85), 0.0, 1.0, EMITTER_AREA, (0.3, 0.0, 0.0), (0.0, 0.0, 0.3))],
+        sensor=Sensor((1.0, 1.0, -2.5), SENSOR_PINHOLE, (1.0, 1.0, 0.0), (0.0, 1.0, 0.0), 40.0,
+                      width, height),
+        gate=Gate(0.0, t_max, n_bins),
+    )
+
+
+def box_camera_workload(seed: int = 0) -> Tuple[Scene, Sampling]:
+    """64 x 64 pinhole view of the walled box, 16 paths per pixel, 512 bins."""
+    return box_camera_scene(seed), Sampling(seed=seed, paths_per_element=16, max_bounces=50)
+
+
+def cube_camera_scene(width: int = 32, height: int = 32) -> Scene:
+    """The unit-cube medium seen by a 32 x 32 pinhole camera at
+    (0.5, 0.5, -1.5) looking +z (40 degree FOV); 256 bins on [0.8, 6) shifted
+    by the 1.5 camera leg."""
+    sc = slab_scene()
+    sc.sensor = Sensor((0.5, 0.5, -1.5), SENSOR_PINHOLE, (0.5, 0.5, 0.0), (0.0, 1.0, 0.0), 40.0,
+                       width, height)
+    sc.gate = Gate(0.8 + 1.5, 6.0 + 1.5, 256)
+    return sc
+
+
+def spheres_camera_scene(seed: int = 0, width: int = 512, height: int = 512, n_spheres: int = 32,
+                         n_bins: int = 1000) -> Scene:
+    """4x4x4 medium (sigma_s 0.8, sigma_a 0.005, g 0.8) with seeded opaque
+    Lambertian spheres (radius U[0.05, 0.3], albedo U[0.2, 0.8]), two point
+    pulse emitters at (1, 3.5, 1) t0 = 0 and (3, 3.5, 3) t0 = 1.5, a pinhole
+    camera inside at (2, 2, 0.05) looking +z; 1000 bins on [0, 20)."""
+    rs = np.random.default_rng(np.random.SeedSequence([seed, 0x5FE5]))
+    emitters = [Emitter((1.0, 3.5, 1.0), 0.0, 1.0), Emitter((3.0, 3.5, 3.0), 1.5, 1.0)]
+    cam = (2.0, 2.0, 0.05)
+    spheres = []
+    while len(spheres) < n_spheres:
+        r = float(rs.uniform(0.05, 0.3))
+        c = rs.uniform(r, 4.0 - r, size=3)
+        keep = all(np.linalg.norm(c - np.array(p)) > r + 1e-3 for p in [e.pos for e in emitters] + [cam])
+        alb = float(rs.uniform(0.2, 0.8))
+        if keep:
+            spheres.append((float(c[0]), float(c[1]), float(c[2]), r, alb))
+    return Scene(
+        medium=Medium(0.8, 0.005, 0.8, 1.0),
+        geometry=Geometry((0.0, 0.0, 0.0), (4.0, 4.0, 4.0), 0, 0.0, spheres),
+        emitters=emitters,
+        sensor=Sensor(cam, SENSOR_PINHOLE, (2.0, 2.0, 1.0), (0.0, 1.0, 0.0), 40.0, width, height),
+        gate=Gate(0.0, 20.0, n_bins),
+    )
+
+
 def batched_media(n_media: int = 256, seed: int = 0, n_bins: int = 128,
                   log2_budget: Tuple[float, float] = (12.0, 20.0)) -> List[Tuple[Scene, Sampling]]:
     """Independent slab media with uneven path budgets.
@@ -162,5 +257,5 @@ def with_paths(sp: Sampling, n: int) -> Sampling:
 
 
 def total_paths(sc: Scene, sp: Sampling) -> int:
-    """Number of paths one render call traces (one sensor element)."""
-    return int(sp.paths_per_element)
+    """Number of paths one render call traces (every sensor element)."""
+    return int(sp.paths_per_element) * sc.sensor.elements

@@ -413,3 +413,133 @@ def test_ablations_stay_unbiased(flags):
     se2 = O.standard_error(h2, sq2, n)
     z = (h - h2) / np.sqrt(se ** 2 + se2 ** 2)
     assert np.max(np.abs(z[1:])) < 4.5, z
+
+
+# ---------------------------------------------------------------------------
+# Surfaces, camera, area and multiple emitters
+# ---------------------------------------------------------------------------
+def test_trace_ray_matches_brute_force_marching():
+    sc = S.spheres_camera_scene(seed=2, width=4, height=4, n_spheres=12)
+    sc.geometry.walls = S.WALL_X_LO | S.WALL_Y_HI
+    sc.geometry.wall_albedo = 0.5
+    sp = S.Sampling()
+    rng = np.random.default_rng(5)
+    sph = np.array(sc.geometry.spheres)
+    lo, hi = np.array(sc.geometry.lo), np.array(sc.geometry.hi)
+
+    def inside_sphere(p):
+        return np.any(np.linalg.norm(sph[:, :3] - p, axis=1) < sph[:, 3])
+
+    n_checked = 0
+    while n_checked < 60:
+        x = rng.uniform(0.05, 3.95, 3)
+        if inside_sphere(x):
+            continue
+        w = rng.normal(size=3)
+        w /= np.linalg.norm(w)
+        d, kind, nrm = O.trace_ray(sc, sp, x, w)
+        h = 2e-4
+        t = np.arange(1, int(8.0 / h)) * h
+        pts = x + np.outer(t, w)
+        out_box = np.any((pts < lo) | (pts > hi), axis=1)
+        in_sph = np.any(np.linalg.norm(pts[:, None, :] - sph[None, :, :3], axis=2) < sph[None, :, 3], axis=1)
+        first = np.argmax(out_box | in_sph)
+        assert abs(t[first] - d) < 2 * h, (t[first], d)
+        if kind >= 2:
+            assert in_sph[first]
+            assert np.dot(nrm, w) < 0  # the normal faces the incoming ray
+        elif kind == 1:
+            face = int(np.argmax(np.abs(nrm)))
+            assert (sc.geometry.walls >> (2 * face + (1 if nrm[face] < 0 else 0))) & 1
+        n_checked += 1
+
+
+def test_camera_rays():
+    sc = S.box_camera_scene(width=8, height=6)
+    sp = S.Sampling()
+    # the image centre looks at look_at: pixel (4, 3) with zero jitter
+    hit, x0, w, leg = O.camera_ray(sc, sp, 3 * 8 + 4, 0.0, 0.0)
+    f = np.subtract(sc.sensor.look_at, sc.sensor.pos)
+    np.testing.assert_allclose(w, f / np.linalg.norm(f), atol=1e-12)
+    assert hit and abs(x0[2]) < 1e-12 and leg == pytest.approx(2.5)
+    np.testing.assert_allclose(x0, np.add(sc.sensor.pos, w * leg), atol=1e-12)
+    # 40 degree vertical field of view: the top edge of the image
+    hit, x0, w, leg = O.camera_ray(sc, sp, 0 * 8 + 4, 0.0, 0.0)
+    assert math.degrees(math.atan2(w[1], w[2])) == pytest.approx(20.0, abs=1e-9)
+    # a camera inside the medium starts at its own position
+    sc5 = S.spheres_camera_scene(width=4, height=4, n_spheres=0)
+    hit, x0, w, leg = O.camera_ray(sc5, sp, 5, 0.5, 0.5)
+    assert hit and leg == 0.0 and np.allclose(x0, sc5.sensor.pos)
+
+
+def test_area_emitter_irradiance_matches_quadrature():
+    """Point sampling of a Lambertian square (Sec. 7: area emitters as point
+    samples) reproduces the irradiance integral int L_e cos_e cos_x / r^2 dA."""
+    from scipy import integrate
+    sc = S.box_camera_scene()
+    sp = S.Sampling()
+    em = sc.emitters[0]
+    q = np.array([0.6, 0.7, 1.3])
+    nq = np.array([0.0, 1.0, 0.0])  # receiver facing the ceiling
+    A = 0.3 * 0.3
+    Le = em.energy / (math.pi * A)
+
+    def integrand(b, a):
+        y = np.array(em.pos) + a * np.array(em.u) / 0.3 + b * np.array(em.v) / 0.3
+        d = q - y
+        r2 = d @ d
+        ce = d @ np.array([0.0, -1.0, 0.0]) / math.sqrt(r2)
+        cq = -d @ nq / math.sqrt(r2)
+        return Le * ce * cq / r2
+
+    ref, _ = integrate.dblquad(integrand, 0.0, 0.3, 0.0, 0.3, epsabs=1e-13, epsrel=1e-10)
+    n = 40000
+    acc = 0.0
+    for pid in range(n):
+        e = O.sample_emitter(sc, sp, pid, q)
+        d = q - e["y"]
+        r = np.linalg.norm(d)
+        acc += e["wsel"] * e["intensity"] * max(0.0, -d @ nq / r) / (r * r)
+    assert acc / n == pytest.approx(ref, rel=0.01)
+
+
+def test_emitters_add_linearly_with_start_times():
+    """Two non-synchronised emitters (Fig. 1): the render with both equals the
+    sum of the renders with each alone (emitter choice by energy)."""
+    import copy
+    base = S.slab_scene(1.0, 0.02, 0.5, side=1.0, n_bins=16, t_min=0.3, t_max=3.0)
+    e1 = S.Emitter((0.5, 0.5, 0.1), 0.0, 1.0)
+    e2 = S.Emitter((0.3, 0.6, 0.4), 0.5, 2.0)
+    n = 1 << 16
+    hs = []
+    for ems in ([e1, e2], [e1], [e2]):
+        sc = copy.deepcopy(base)
+        sc.emitters = ems
+        h, sq, _ = O.render(sc, S.Sampling(seed=3, paths_per_element=n, max_bounces=3),
+                            O.ORC_PLAIN_UNIFORM_T)
+        hs.append((h, O.standard_error(h, sq, n)))
+    (hb, sb), (h1, s1), (h2, s2) = hs
+    z = (hb - h1 - h2) / np.sqrt(sb ** 2 + s1 ** 2 + s2 ** 2 + 1e-300)
+    assert np.max(np.abs(z)) < 4.5, z
+
+
+@pytest.mark.parametrize("scene", ["box", "spheres"])
+def test_estimators_agree_with_surfaces_and_camera(scene):
+    """DARTS, the uniform-temporal and the vanilla tracers agree on scenes with
+    walls or spheres, an area or two point emitters and a pinhole camera."""
+    if scene == "box":
+        sc = S.box_camera_scene(seed=1, width=2, height=2, n_bins=8, t_max=8.0)
+        K = 3
+    else:
+        sc = S.spheres_camera_scene(seed=1, width=2, height=2, n_spheres=10, n_bins=8)
+        sc.gate.t_min, sc.gate.t_max = 1.0, 9.0
+        K = 3
+    n = 1 << 15
+    res = []
+    for m, seed in ((O.ORC_DARTS, 11), (O.ORC_PLAIN_UNIFORM_T, 12), (O.ORC_VANILLA_DIRECT, 13)):
+        h, sq, _ = O.render(sc, S.Sampling(seed=seed, paths_per_element=n, max_bounces=K), m)
+        per_bin = n / 8 if m == O.ORC_DARTS else n
+        res.append((h.sum(), np.sqrt(np.sum(O.standard_error(h, sq, per_bin) ** 2))))
+    (hd, sd), (hp, spp), (hv, sv) = res
+    assert abs(hd - hp) < 4.5 * math.sqrt(sd ** 2 + spp ** 2), res
+    assert abs(hv - hp) < 4.5 * math.sqrt(sv ** 2 + spp ** 2), res
