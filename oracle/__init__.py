@@ -92,7 +92,7 @@ def load():
     lib.orc_table_row.restype = C.c_int
     lib.orc_trace_paths.argtypes = [sp, C.c_int, dp, C.c_uint64, C.c_uint32, dp,
                                     C.POINTER(C.c_int32), C.POINTER(C.c_uint8), dp,
-                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32), dp]
     lib.orc_trace_paths.restype = C.c_int
     lib.orc_render.argtypes = [sp, C.c_int, dp, C.c_uint64, C.c_uint64, C.c_int, dp, dp, dp]
     lib.orc_render.restype = C.c_int
@@ -260,12 +260,13 @@ def trace_paths(scene, sampling, first, count, method=ORC_DARTS, cdf=None):
         contrib=np.zeros(count), bin=np.zeros(count, np.int32),
         decisions=np.zeros((count, K, 4), np.uint8), margin=np.zeros((count, K)),
         flags=np.zeros(count, np.int32), nvert=np.zeros(count, np.int32),
+        cond=np.zeros(count),
     )
     cdf_c = None if cdf is None else np.ascontiguousarray(cdf, dtype=np.float64)
     rc = load().orc_trace_paths(
         C.byref(s), method, _ptr(cdf_c), first, count, _ptr(out["contrib"]),
         _ptr(out["bin"], C.c_int32), _ptr(out["decisions"], C.c_uint8), _ptr(out["margin"]),
-        _ptr(out["flags"], C.c_int32), _ptr(out["nvert"], C.c_int32))
+        _ptr(out["flags"], C.c_int32), _ptr(out["nvert"], C.c_int32), _ptr(out["cond"]))
     if rc != 0:
         raise ValueError(f"orc_trace_paths rejected the scene ({rc})")
     return out
@@ -320,14 +321,16 @@ STAT_NAMES = ("paths", "vertices", "connections", "connections_nonempty", "ris_c
 
 
 def render(scene, sampling, method=ORC_DARTS, n_paths=None, offset=0, threads=None, cdf=None):
-    """Histogram [n_bins] (time-integrated fluence per bin, unit energy),
-    sum of squared per-path bin contributions, and event statistics."""
+    """Histogram [elements * n_bins] (time-integrated fluence per bin, unit
+    energy; one row of n_bins per camera pixel), sum of squared per-path bin
+    contributions, and event statistics.  n_paths defaults to every path of
+    every element."""
     s = make_scene(scene, sampling)
-    n = sampling.paths_per_element if n_paths is None else n_paths
+    elements = s.width * s.height if s.sensor_kind == 1 else 1
+    n = sampling.paths_per_element * elements if n_paths is None else n_paths
     if method == ORC_DARTS and cdf is None:
         cdf = build_table(scene, sampling)
     threads = threads or (os.cpu_count() or 1)
-    elements = s.width * s.height if s.sensor_kind == 1 else 1
     hist = np.zeros(s.n_bins * elements)
     sumsq = np.zeros(s.n_bins * elements)
     stats = np.zeros(8)

@@ -493,6 +493,8 @@ typedef struct {
   /* adjoint: per-connection scores */
   double score[3];
   int dec_sel;
+  /* largest (L + S_hi) / (S_hi - S_lo) over the connections */
+  double cond;
   /* the path's emitter point and sensor element */
   const emit_pt* E;
   int elem;
@@ -579,7 +581,7 @@ static double darts_direction(const orc_scene* sc, const double* cdf, int k, uin
     int i = (int)floor(y);
     if (i < 0) i = 0;
     if (i > nb - 1) i = nb - 1;
-    if (gamma > 0.0) rec_margin(pr, k, near_int(y) / (nb / 2.0));
+    rec_margin(pr, k, near_int(y) / (nb / 2.0)); /* the bin is recorded even when gamma = 0 */
     pE = (crow[i + 1] - crow[i]) * (nb / 2.0) / (2.0 * M_PI);
     mis_choice = 0;
     mu_bin = i;
@@ -612,6 +614,7 @@ static double darts_connect(const orc_scene* sc, int k, double beta, const doubl
   rec_margin(pr, k, fabs(S_hi - S_lo) / dmax(S_hi, 1e-300));
   if (!(S_hi > S_lo)) return 0.0;
   double Wd = S_hi - S_lo;
+  if ((L + S_hi) / Wd > pr->cond) pr->cond = (L + S_hi) / Wd;
   double S, pS;
   if (!uniform_S) {
     double dS = -log1p(-(1.0 - exp(-st * Wd)) * u3) / st;
@@ -635,7 +638,6 @@ static double darts_connect(const orc_scene* sc, int k, double beta, const doubl
   double c = beta * sc->sigma_s * exp(-st * S) * orc_hg_pdf(cos_s, sc->g) * Ie * vis / (r1 * r1) / pt;
   *ok = 1;
   *S_out = S;
-  (void)L;
   pr->score[2] = hg_dlog_dg(cos_s, sc->g);
   return c;
 }
@@ -795,12 +797,15 @@ void orc_sample_emitter(const orc_scene* sc, uint64_t id, const double q[3], dou
 }
 
 /* Sensor elements: the point sensor is element 0 and path id j; the camera's
- * pixel p owns ids p * N_e ... p * N_e + N_e - 1.  A DARTS path is dedicated
- * to bin (j + o_e) mod B with o_e drawn once per element (Sec. 6.2: every
- * frame gets the same number of paths, each path serves one frame). */
+ * pixel p owns ids p * N_e ... p * N_e + N_e - 1 (ids beyond the last pixel wrap
+ * around to pixel 0, so shards of a larger render keep the layout).  A DARTS
+ * path is dedicated to bin (j + o_e) mod B with o_e drawn once per element
+ * (Sec. 6.2: every frame gets the same number of paths, each path serves one
+ * frame). */
 static void path_element(const orc_scene* sc, uint64_t id, int* elem, uint64_t* j) {
   if (sc->sensor_kind == 1) {
-    *elem = (int)(id / sc->paths_per_element);
+    uint64_t e = id / sc->paths_per_element;
+    *elem = (int)(e % ((uint64_t)sc->width * (uint64_t)sc->height));
     *j = id % sc->paths_per_element;
   } else {
     *elem = 0;
@@ -1223,7 +1228,7 @@ static int scene_ok(const orc_scene* sc, int method, const double* cdf) {
 
 int orc_trace_paths(const orc_scene* sc, int method, const double* cdf, uint64_t first,
                     uint32_t count, double* contrib, int32_t* bin, uint8_t* decisions,
-                    double* margin, int32_t* flags, int32_t* nbounce) {
+                    double* margin, int32_t* flags, int32_t* nbounce, double* cond) {
   if (!scene_ok(sc, method, cdf)) return -1;
   int K = sc->max_bounces;
   path_rec* pr = (path_rec*)malloc(sizeof(path_rec));
@@ -1248,6 +1253,7 @@ int orc_trace_paths(const orc_scene* sc, int method, const double* cdf, uint64_t
     if (bin) bin[i] = pr->bin;
     if (flags) flags[i] = pr->flags;
     if (nbounce) nbounce[i] = pr->nvert;
+    if (cond) cond[i] = pr->cond;
   }
   free(pr);
   return 0;

@@ -136,12 +136,16 @@ int orc_table_row(const orc_scene* sc, double C, double SM, double* margin);
  * decisions[i*K*4 + k*4 + j] (optional): per-vertex decision bytes;
  * margin[i*K + k] (optional): smallest relative distance to a decision
  * threshold met at vertex k; flags[i] (optional): ORC_FLAG_* bits;
- * nbounce[i] (optional): vertices visited.  cdf may be NULL for methods
- * other than DARTS.  Returns 0 on success. */
+ * nbounce[i] (optional): vertices visited; cond[i] (optional): the largest
+ * (L + S_hi) / (S_hi - S_lo) over the path's control-vertex connections
+ * (0 when it has none) -- how strongly an absolute error in the path length
+ * L or in the window bounds [S_lo, S_hi) of Eq. 21 is magnified in the
+ * contribution, a conditioning number for reduced-precision comparisons.
+ * cdf may be NULL for methods other than DARTS.  Returns 0 on success. */
 int orc_trace_paths(const orc_scene* sc, int method, const double* cdf,
                     uint64_t first, uint32_t count, double* contrib,
                     int32_t* bin, uint8_t* decisions, double* margin,
-                    int32_t* flags, int32_t* nbounce);
+                    int32_t* flags, int32_t* nbounce, double* cond);
 
 /* Distance step (Eq. 12-15) of vertex k from an explicit state, for tests:
  * candidate distances, validity, log RIS weights, selected index (-1 when
