@@ -70,16 +70,39 @@ typedef struct {
   double sigma_s, sigma_a, g, v;
 } darts_medium;
 
-/* Isotropic point pulse emitter (Eq. 1: L_e with start time t_e). */
+/* Pulse emitter (Eq. 1: L_e with start time t_e).  kind DARTS_EMITTER_POINT:
+ * isotropic point at pos, radiant intensity energy / (4 pi).
+ * kind DARTS_EMITTER_AREA: one-sided Lambertian parallelogram pos + s u + t v
+ * (s, t in [0, 1]) emitting toward u x v with radiance energy / (pi area);
+ * every path draws one uniform point on it and treats it as a point
+ * emitter with intensity (energy / pi) cos (Sec. 7 of the paper).  With
+ * several emitters every path picks one with probability proportional to
+ * its energy; each has its own pulse start time t0 (Fig. 1). */
+#define DARTS_EMITTER_POINT 0
+#define DARTS_EMITTER_AREA 1
 typedef struct {
   double pos[3];
   double t0;     /* start time of the pulse */
-  double energy; /* emitted energy; radiant intensity energy / (4 pi) */
+  double energy; /* emitted energy */
+  int32_t kind;
+  double u[3], v[3];
 } darts_emitter;
 
-/* Isotropic point fluence sensor (one sensor element). */
+/* Sensor.  kind DARTS_SENSOR_POINT: isotropic point fluence detector at pos
+ * (one element; histogram [n_bins]).  kind DARTS_SENSOR_PINHOLE: pinhole
+ * camera at pos looking at look_at with the given up vector and vertical
+ * field of view, width x height pixels (elements; histogram
+ * [height][width][n_bins]); a pixel records radiance averaged over its
+ * area, and the camera leg outside the medium counts toward the path time.
+ * paths_per_element paths are traced per element. */
+#define DARTS_SENSOR_POINT 0
+#define DARTS_SENSOR_PINHOLE 1
 typedef struct {
   double pos[3];
+  int32_t kind;
+  double look_at[3], up[3];
+  double fov_deg;
+  int32_t width, height;
 } darts_sensor;
 
 /* Time gate [t_min, t_max) in n_bins equal bins. */
@@ -88,15 +111,27 @@ typedef struct {
   int32_t n_bins;
 } darts_gate;
 
-/* The medium fills the axis-aligned box [lo, hi]; there are no surfaces. */
+/* The medium fills the axis-aligned box [lo, hi].  Faces whose bit
+ * (2 * axis + 1 for the high face) is set in `walls` are opaque Lambertian
+ * walls of albedo wall_albedo; the others are open (paths leave the scene).
+ * spheres: host array [n_spheres][5] = centre, radius, albedo of opaque
+ * Lambertian spheres inside the box (at most 64).  A path reaching a
+ * surface connects from it directly to its emitter point (accepted only when
+ * the total length falls in the path's bin) and continues with a
+ * cosine-distributed direction; control vertices stay in the medium, capped
+ * at the first surface along the ray (case II of Sec. 5.2). */
 typedef struct {
   double lo[3], hi[3];
+  int32_t walls;
+  double wall_albedo;
+  int32_t n_spheres;
+  const double* spheres;
 } darts_geometry;
 
 typedef struct {
   darts_medium medium;
   darts_geometry geom;
-  const darts_emitter* emitters; /* host array; this build supports n_emitters == 1 */
+  const darts_emitter* emitters; /* host array of 1..8 emitters */
   int32_t n_emitters;
   darts_sensor sensor;
   darts_gate gate;
@@ -179,8 +214,10 @@ darts_status darts_build_table(darts_ctx* ctx, const darts_scene* scene,
 /* Row stride (floats) of the table written by darts_build_table. */
 int32_t darts_table_row_stride(int32_t table_n_mu);
 
-/* Render sampling->paths_per_element paths with ids path_offset .. +N-1 and
- * write the histogram estimate hist_dev[n_bins] (double, overwritten):
+/* Render sampling->paths_per_element paths per sensor element (N paths in
+ * all, ids path_offset .. +N-1; the camera's pixel p owns ids
+ * p * paths_per_element onwards) and write the histogram estimate
+ * hist_dev[elements][n_bins] (double, overwritten):
  * DARTS dedicates each path to one bin (Sec. 6.2) and weights it by
  * n_bins / N; the baselines bin each contribution by its time and weight it
  * by 1 / N.  sumsq_dev (optional, [n_bins]) receives the sum over paths of

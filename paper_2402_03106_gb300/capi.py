@@ -48,11 +48,14 @@ class darts_medium(C.Structure):
 
 
 class darts_emitter(C.Structure):
-    _fields_ = [("pos", C.c_double * 3), ("t0", C.c_double), ("energy", C.c_double)]
+    _fields_ = [("pos", C.c_double * 3), ("t0", C.c_double), ("energy", C.c_double),
+                ("kind", C.c_int32), ("u", C.c_double * 3), ("v", C.c_double * 3)]
 
 
 class darts_sensor(C.Structure):
-    _fields_ = [("pos", C.c_double * 3)]
+    _fields_ = [("pos", C.c_double * 3), ("kind", C.c_int32), ("look_at", C.c_double * 3),
+                ("up", C.c_double * 3), ("fov_deg", C.c_double), ("width", C.c_int32),
+                ("height", C.c_int32)]
 
 
 class darts_gate(C.Structure):
@@ -60,7 +63,9 @@ class darts_gate(C.Structure):
 
 
 class darts_geometry(C.Structure):
-    _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3)]
+    _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3), ("walls", C.c_int32),
+                ("wall_albedo", C.c_double), ("n_spheres", C.c_int32),
+                ("spheres", C.POINTER(C.c_double))]
 
 
 class darts_scene(C.Structure):
@@ -144,16 +149,34 @@ def to_c_scene(scene: S.Scene):
         arr[i].pos[:] = [float(x) for x in e.pos]
         arr[i].t0 = float(e.t0)
         arr[i].energy = float(e.energy)
+        arr[i].kind = int(e.kind)
+        arr[i].u[:] = [float(x) for x in e.u]
+        arr[i].v[:] = [float(x) for x in e.v]
     cs = darts_scene()
     m = scene.medium
     cs.medium = darts_medium(float(m.sigma_s), float(m.sigma_a), float(m.g), float(m.v))
-    cs.geom.lo[:] = [float(x) for x in scene.geometry.lo]
-    cs.geom.hi[:] = [float(x) for x in scene.geometry.hi]
+    geo = scene.geometry
+    cs.geom.lo[:] = [float(x) for x in geo.lo]
+    cs.geom.hi[:] = [float(x) for x in geo.hi]
+    cs.geom.walls = int(geo.walls)
+    cs.geom.wall_albedo = float(geo.wall_albedo)
+    sph = (C.c_double * max(5 * len(geo.spheres), 1))()
+    for k, q in enumerate(geo.spheres):
+        sph[5 * k:5 * k + 5] = [float(x) for x in q]
+    cs.geom.n_spheres = len(geo.spheres)
+    cs.geom.spheres = C.cast(sph, C.POINTER(C.c_double))
     cs.emitters = C.cast(arr, C.POINTER(darts_emitter))
     cs.n_emitters = n
-    cs.sensor.pos[:] = [float(x) for x in scene.sensor.pos]
+    sen = scene.sensor
+    cs.sensor.pos[:] = [float(x) for x in sen.pos]
+    cs.sensor.kind = int(sen.kind)
+    cs.sensor.look_at[:] = [float(x) for x in sen.look_at]
+    cs.sensor.up[:] = [float(x) for x in sen.up]
+    cs.sensor.fov_deg = float(sen.fov_deg)
+    cs.sensor.width = int(sen.width)
+    cs.sensor.height = int(sen.height)
     cs.gate = darts_gate(float(scene.gate.t_min), float(scene.gate.t_max), int(scene.gate.n_bins))
-    return cs, arr
+    return cs, (arr, sph)
 
 
 def to_c_sampling(sp: S.Sampling) -> darts_sampling:
@@ -337,9 +360,9 @@ class Context:
 
     def render(self, scene, sampling, sumsq: bool = False, path_offset: int = 0,
                out: Optional[torch.Tensor] = None, probe: Optional[darts_probe] = None):
-        B = scene.gate.n_bins
-        hist = out if out is not None else torch.empty(B, dtype=torch.float64, device=self._dev())
-        sq = torch.empty(B, dtype=torch.float64, device=self._dev()) if sumsq else None
+        shape = S.histogram_shape(scene)
+        hist = out if out is not None else torch.empty(shape, dtype=torch.float64, device=self._dev())
+        sq = torch.empty(shape, dtype=torch.float64, device=self._dev()) if sumsq else None
         darts_render(self.h, scene, sampling, hist, sq, path_offset, probe)
         return (hist, sq) if sumsq else hist
 

@@ -26,8 +26,6 @@ struct darts_ctx {
   unsigned long long* scratch = nullptr;
   double* partials = nullptr;  // block partials, grown on demand
   size_t partials_bytes = 0;
-  double* acc = nullptr;       // global accumulator (no-tile mode)
-  size_t acc_bytes = 0;
   double* host_hist = nullptr; // device histogram for darts_render_host
   size_t host_hist_bytes = 0;
   // direction-table cache
@@ -113,6 +111,25 @@ void gauss_legendre(int n, double* x, double* w) {
 
 int row_stride_of(int n_mu) { return ((n_mu + 1) + 3) / 4 * 4; }
 
+// Earliest pulse start: one direction table per medium uses S_max of it.
+double earliest_t0(const darts_scene* sc) {
+  double t0 = sc->emitters[0].t0;
+  for (int k = 1; k < sc->n_emitters; ++k) t0 = std::min(t0, sc->emitters[k].t0);
+  return t0;
+}
+
+// Sensor elements (pixels of a camera, 1 for the point sensor).
+uint64_t elements_of(const darts_scene* sc) {
+  return sc->sensor.kind == DARTS_SENSOR_PINHOLE ? (uint64_t)sc->sensor.width * sc->sensor.height : 1;
+}
+
+// Scenes beyond one point emitter seen by a point sensor in an open box run
+// the general variant of the path kernel.
+bool general_scene(const darts_scene* sc) {
+  if (sc->n_emitters != 1 || sc->emitters[0].kind != DARTS_EMITTER_POINT) return true;
+  return sc->sensor.kind != DARTS_SENSOR_POINT || sc->geom.walls != 0 || sc->geom.n_spheres > 0;
+}
+
 darts_status validate(darts_ctx* ctx, const darts_scene* sc, const darts_sampling* sp) {
   if (!sc || !sp) return fail(ctx, DARTS_ERR_INVALID_ARG, "scene and sampling must not be NULL");
   const darts_medium& m = sc->medium;
@@ -125,21 +142,62 @@ darts_status validate(darts_ctx* ctx, const darts_scene* sc, const darts_samplin
   for (int i = 0; i < 3; ++i)
     if (!(sc->geom.hi[i] > sc->geom.lo[i])) return fail(ctx, DARTS_ERR_INVALID_ARG, "empty medium box");
   if (sc->n_emitters < 1 || !sc->emitters) return fail(ctx, DARTS_ERR_INVALID_ARG, "need an emitter");
-  if (sc->n_emitters != 1) return fail(ctx, DARTS_ERR_UNSUPPORTED, "this build supports one emitter");
-  const darts_emitter& e = sc->emitters[0];
-  if (!(e.energy >= 0.0) || !std::isfinite(e.t0)) return fail(ctx, DARTS_ERR_INVALID_ARG, "bad emitter");
-  for (int i = 0; i < 3; ++i) {
-    if (!(e.pos[i] >= sc->geom.lo[i] && e.pos[i] <= sc->geom.hi[i]))
-      return fail(ctx, DARTS_ERR_INVALID_ARG, "emitter outside the medium box");
-    if (!(sc->sensor.pos[i] >= sc->geom.lo[i] && sc->sensor.pos[i] <= sc->geom.hi[i]))
-      return fail(ctx, DARTS_ERR_INVALID_ARG, "sensor outside the medium box");
+  if (sc->n_emitters > kMaxEmitters)
+    return fail(ctx, DARTS_ERR_UNSUPPORTED, "at most %d emitters", kMaxEmitters);
+  double e_tot = 0.0;
+  for (int k = 0; k < sc->n_emitters; ++k) {
+    const darts_emitter& e = sc->emitters[k];
+    if (!(e.energy >= 0.0) || !std::isfinite(e.t0) || !std::isfinite(e.energy))
+      return fail(ctx, DARTS_ERR_INVALID_ARG, "bad emitter %d", k);
+    if (e.kind != DARTS_EMITTER_POINT && e.kind != DARTS_EMITTER_AREA)
+      return fail(ctx, DARTS_ERR_INVALID_ARG, "emitter %d: unknown kind", k);
+    for (int i = 0; i < 3; ++i)
+      if (!(e.pos[i] >= sc->geom.lo[i] && e.pos[i] <= sc->geom.hi[i]))
+        return fail(ctx, DARTS_ERR_INVALID_ARG, "emitter %d outside the medium box", k);
+    if (e.kind == DARTS_EMITTER_AREA) {
+      const double cx = e.u[1] * e.v[2] - e.u[2] * e.v[1], cy = e.u[2] * e.v[0] - e.u[0] * e.v[2],
+                   cz = e.u[0] * e.v[1] - e.u[1] * e.v[0];
+      if (!(cx * cx + cy * cy + cz * cz > 0.0)) return fail(ctx, DARTS_ERR_INVALID_ARG, "emitter %d: zero area", k);
+      for (int i = 0; i < 3; ++i) {
+        const double far = e.pos[i] + e.u[i] + e.v[i];
+        if (!(far >= sc->geom.lo[i] && far <= sc->geom.hi[i]))
+          return fail(ctx, DARTS_ERR_INVALID_ARG, "emitter %d extends outside the medium box", k);
+      }
+    }
+    if (!(sc->gate.t_max > e.t0)) return fail(ctx, DARTS_ERR_INVALID_ARG, "gate ends before emitter %d's pulse", k);
+    e_tot += e.energy;
   }
-  if (!(sc->gate.t_max > e.t0)) return fail(ctx, DARTS_ERR_INVALID_ARG, "gate ends before the pulse");
-  {
-    double d2 = 0.0;
-    for (int i = 0; i < 3; ++i) d2 += (sc->sensor.pos[i] - e.pos[i]) * (sc->sensor.pos[i] - e.pos[i]);
-    if (!(d2 > 0.0)) return fail(ctx, DARTS_ERR_INVALID_ARG, "sensor coincides with the emitter");
+  if (!(e_tot > 0.0)) return fail(ctx, DARTS_ERR_INVALID_ARG, "total emitted energy must be > 0");
+  const darts_sensor& sen = sc->sensor;
+  if (sen.kind == DARTS_SENSOR_POINT) {
+    for (int i = 0; i < 3; ++i)
+      if (!(sen.pos[i] >= sc->geom.lo[i] && sen.pos[i] <= sc->geom.hi[i]))
+        return fail(ctx, DARTS_ERR_INVALID_ARG, "sensor outside the medium box");
+    for (int k = 0; k < sc->n_emitters; ++k) {
+      const darts_emitter& e = sc->emitters[k];
+      double d2 = 0.0;
+      for (int i = 0; i < 3; ++i) d2 += (sen.pos[i] - e.pos[i]) * (sen.pos[i] - e.pos[i]);
+      if (e.kind == DARTS_EMITTER_POINT && !(d2 > 0.0))
+        return fail(ctx, DARTS_ERR_INVALID_ARG, "sensor coincides with emitter %d", k);
+    }
+  } else if (sen.kind == DARTS_SENSOR_PINHOLE) {
+    if (sen.width < 1 || sen.height < 1 || !(sen.fov_deg > 0.0 && sen.fov_deg < 180.0))
+      return fail(ctx, DARTS_ERR_INVALID_ARG, "camera needs width, height >= 1 and 0 < fov < 180");
+    double f2 = 0.0;
+    for (int i = 0; i < 3; ++i) f2 += (sen.look_at[i] - sen.pos[i]) * (sen.look_at[i] - sen.pos[i]);
+    if (!(f2 > 0.0)) return fail(ctx, DARTS_ERR_INVALID_ARG, "camera look_at equals its position");
+  } else {
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "unknown sensor kind %d", sen.kind);
   }
+  if (sc->geom.n_spheres < 0 || sc->geom.n_spheres > kMaxSpheres || (sc->geom.n_spheres && !sc->geom.spheres))
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "0..%d spheres with a host array", kMaxSpheres);
+  for (int k = 0; k < sc->geom.n_spheres; ++k) {
+    const double* q = sc->geom.spheres + 5 * k;
+    if (!(q[3] > 0.0) || !(q[4] >= 0.0 && q[4] <= 1.0))
+      return fail(ctx, DARTS_ERR_INVALID_ARG, "sphere %d needs radius > 0 and albedo in [0, 1]", k);
+  }
+  if (sc->geom.walls < 0 || sc->geom.walls >= 64 || !(sc->geom.wall_albedo >= 0.0 && sc->geom.wall_albedo <= 1.0))
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "walls is a 6-bit face mask and wall_albedo in [0, 1]");
   if (sp->max_bounces < 1 || sp->max_bounces > 1024)
     return fail(ctx, DARTS_ERR_INVALID_ARG, "max_bounces must be in 1..1024");
   if (sp->ris_m < 1 || sp->ris_m > trace_max_m())
@@ -162,7 +220,7 @@ void make_table_params(const darts_scene* sc, const darts_sampling* sp, TablePar
   tp->phi_k0 = (float)(std::log(m.v) - 1.5 * std::log(4.0 * M_PI * m.v * D));
   tp->phi_invk = (float)(1.0 / (4.0 * m.v * D));
   tp->sa_v = (float)(m.sigma_a * m.v);
-  tp->smax = (float)(m.v * (sc->gate.t_max - sc->emitters[0].t0));
+  tp->smax = (float)(m.v * (sc->gate.t_max - earliest_t0(sc)));
   tp->n_rho = sp->table_n_rho;
   tp->n_s = sp->table_n_s;
   tp->n_mu = sp->table_n_mu;
@@ -185,7 +243,7 @@ void table_key(const darts_scene* sc, const darts_sampling* sp, double key[9]) {
   key[1] = sc->medium.sigma_a;
   key[2] = sc->medium.g;
   key[3] = sc->medium.v;
-  key[4] = sc->gate.t_max - sc->emitters[0].t0;
+  key[4] = sc->gate.t_max - earliest_t0(sc);
   key[5] = sp->table_n_rho;
   key[6] = sp->table_n_s;
   key[7] = sp->table_n_mu;
@@ -255,7 +313,7 @@ void make_trace_params(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
   P->n_mu = sp->table_n_mu;
   P->row_stride = row_stride_of(sp->table_n_mu);
   P->rows = sp->table_n_rho * sp->table_n_s;
-  P->inv_smax = (float)(1.0 / (m.v * (G.t_max - e.t0)));
+  P->inv_smax = (float)(1.0 / (m.v * (G.t_max - earliest_t0(sc))));
   P->n_s_over_8 = (float)(sp->table_n_s / 8.0);
   P->mu_scale = (float)(sp->table_n_mu / 2.0);
   P->inv_mu_scale = (float)(2.0 / sp->table_n_mu);
@@ -276,6 +334,73 @@ void make_trace_params(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
   P->o_e = (uint32_t)oe;
   const double ne = (double)std::max<uint64_t>(sp->paths_per_element, 1);
   P->wb = (float)(sp->method == DARTS_METHOD_DARTS ? G.n_bins / ne : 1.0 / ne);
+  P->spp = std::max<uint64_t>(sp->paths_per_element, 1);
+  // general scenes: emitters, surfaces, camera
+  P->general = general_scene(sc) ? 1 : 0;
+  double e_tot = 0.0;
+  for (int k = 0; k < sc->n_emitters; ++k) e_tot += sc->emitters[k].energy;
+  double acc = 0.0;
+  P->n_emitters = sc->n_emitters;
+  for (int k = 0; k < sc->n_emitters; ++k) {
+    const darts_emitter& q = sc->emitters[k];
+    EmitterParams& E = P->em[k];
+    acc += q.energy;
+    E.cdf = (float)(acc / e_tot);
+    E.wsel = q.energy > 0.0 ? (float)(e_tot / q.energy) : 0.0f;
+    E.kind = q.kind;
+    E.ie = (float)(q.kind == DARTS_EMITTER_AREA ? q.energy / M_PI : q.energy / (4.0 * M_PI));
+    E.s_lo = (float)(m.v * (G.t_min - q.t0));
+    E.s_hi = (float)(m.v * (G.t_max - q.t0));
+    double nx = q.u[1] * q.v[2] - q.u[2] * q.v[1], ny = q.u[2] * q.v[0] - q.u[0] * q.v[2],
+           nz = q.u[0] * q.v[1] - q.u[1] * q.v[0];
+    const double nn = std::sqrt(nx * nx + ny * ny + nz * nz);
+    for (int i = 0; i < 3; ++i) {
+      E.pos[i] = (float)q.pos[i];
+      E.u[i] = (float)(q.kind == DARTS_EMITTER_AREA ? q.u[i] : 0.0);
+      E.v[i] = (float)(q.kind == DARTS_EMITTER_AREA ? q.v[i] : 0.0);
+    }
+    E.n[0] = q.kind == DARTS_EMITTER_AREA ? (float)(nx / nn) : 0.0f;
+    E.n[1] = q.kind == DARTS_EMITTER_AREA ? (float)(ny / nn) : 0.0f;
+    E.n[2] = q.kind == DARTS_EMITTER_AREA ? (float)(nz / nn) : 0.0f;
+  }
+  P->em[sc->n_emitters - 1].cdf = 1.0f;
+  P->n_spheres = sc->geom.n_spheres;
+  for (int k = 0; k < sc->geom.n_spheres; ++k) {
+    const double* q = sc->geom.spheres + 5 * k;
+    P->sph[k] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
+    P->sph_albedo[k] = (float)q[4];
+  }
+  P->walls = sc->geom.walls;
+  P->wall_albedo = (float)sc->geom.wall_albedo;
+  const darts_sensor& sen = sc->sensor;
+  P->camera = sen.kind == DARTS_SENSOR_PINHOLE ? 1 : 0;
+  if (P->camera) {
+    double f[3], r[3], u[3];
+    for (int i = 0; i < 3; ++i) f[i] = sen.look_at[i] - sen.pos[i];
+    double fn = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    for (int i = 0; i < 3; ++i) f[i] /= fn;
+    r[0] = f[1] * sen.up[2] - f[2] * sen.up[1];
+    r[1] = f[2] * sen.up[0] - f[0] * sen.up[2];
+    r[2] = f[0] * sen.up[1] - f[1] * sen.up[0];
+    double rn = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    for (int i = 0; i < 3; ++i) r[i] /= rn;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    bool inside = true;
+    for (int i = 0; i < 3; ++i) {
+      P->cam_pos[i] = (float)sen.pos[i];
+      P->cam_f[i] = (float)f[i];
+      P->cam_r[i] = (float)r[i];
+      P->cam_u[i] = (float)u[i];
+      if (!(sen.pos[i] >= sc->geom.lo[i] && sen.pos[i] <= sc->geom.hi[i])) inside = false;
+    }
+    P->cam_inside = inside ? 1 : 0;
+    P->cam_th = (float)std::tan(0.5 * sen.fov_deg * M_PI / 180.0);
+    P->cam_aspect = (float)((double)sen.width / (double)sen.height);
+    P->width = sen.width;
+    P->height = sen.height;
+  }
   P->stats = ctx->scratch + 2;
   P->counter = ctx->scratch;
   P->ticket = reinterpret_cast<unsigned int*>(ctx->scratch + 1);
@@ -284,12 +409,19 @@ void make_trace_params(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
 
 // Common launch of the path kernel for render and debug.
 // Launch shape: the requested (or largest) block size whose shared memory
-// fits, falling back to global FP64 accumulation when no tile fits.
+// fits, falling back to FP64 atomics straight into the outputs when no tile
+// fits (and always for a camera, whose output has one row per pixel).
 void choose_launch(const darts_ctx* ctx, const darts_sampling* sp, const TraceParams& P, bool debug,
                    int* block, bool* tile, size_t* smem) {
   const int want = ctx->block ? ctx->block : 768;
+  if (P.camera) {  // one histogram row per pixel: FP64 atomics straight into the output
+    *tile = false;
+    *block = 512;
+    *smem = trace_smem_bytes(sp->method, P, *block, false);
+    return;
+  }
   *tile = true;
-  *block = trace_block_for(want, debug, true, sp->method, sp->ris_m);
+  *block = trace_block_for(want, debug, true, sp->method, sp->ris_m, P.general != 0);
   *smem = trace_smem_bytes(sp->method, P, *block, true);
   while (*smem > (size_t)ctx->smem_optin && *block > 512) {
     *block = *block == 768 ? 640 : 512;
@@ -315,15 +447,14 @@ darts_status run_trace(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
   const size_t pbytes = (size_t)grid * 2 * P.n_bins * sizeof(double);
   CK(ensure((void**)&ctx->partials, &ctx->partials_bytes, pbytes), "partials allocation");
   P.partials = ctx->partials;
-  if (!tile) {
-    CK(ensure((void**)&ctx->acc, &ctx->acc_bytes, 2 * P.n_bins * sizeof(double)), "accumulator");
-    CK(cudaMemsetAsync(ctx->acc, 0, 2 * P.n_bins * sizeof(double), ctx->stream), "memset");
-    P.acc = ctx->acc;
+  if (!tile) {  // contributions go straight into the (zeroed) outputs
+    const size_t ob = elements_of(sc) * (size_t)P.n_bins * sizeof(double);
+    CK(cudaMemsetAsync(P.hist, 0, ob, ctx->stream), "memset");
+    if (P.sumsq) CK(cudaMemsetAsync(P.sumsq, 0, ob, ctx->stream), "memset");
   }
   // zero the path counter and the statistics (ticket and status persist)
   CK(cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), ctx->stream), "memset");
   CK(cudaMemsetAsync(ctx->scratch + 2, 0, kStatCount * sizeof(unsigned long long), ctx->stream), "memset");
-  (void)sc;
   ctx->last_paths = P.N;
   if (ctx->timing) CK(cudaEventRecord(ctx->ev_start, ctx->stream), "event record");
   CK(launch_trace(sp->method, P, grid, block, debug, tile, smem, ctx->stream), "trace kernel launch");
@@ -389,7 +520,6 @@ darts_status darts_destroy(darts_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   cudaFree(ctx->scratch);
   cudaFree(ctx->partials);
-  cudaFree(ctx->acc);
   cudaFree(ctx->table);
   cudaFree(ctx->host_hist);
   cudaFree(ctx->batch_tables);
@@ -464,7 +594,7 @@ darts_status darts_autotune(darts_ctx* ctx, const darts_scene* scene, const dart
   darts_status s = validate(ctx, scene, sampling);
   if (s != DARTS_OK) return s;
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-  const size_t hb = (size_t)scene->gate.n_bins * sizeof(double);
+  const size_t hb = elements_of(scene) * (size_t)scene->gate.n_bins * sizeof(double);
   CK(ensure((void**)&ctx->host_hist, &ctx->host_hist_bytes, 2 * hb), "histogram allocation");
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0), "event create");
@@ -528,7 +658,7 @@ darts_status darts_render(darts_ctx* ctx, const darts_scene* scene, const darts_
   if (probe && (probe->stride == 0 || (probe->count && (!probe->contrib_dev || !probe->bin_dev))))
     return fail(ctx, DARTS_ERR_INVALID_ARG, "probe needs stride >= 1 and output buffers");
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-  const size_t hb = (size_t)scene->gate.n_bins * sizeof(double);
+  const size_t hb = elements_of(scene) * (size_t)scene->gate.n_bins * sizeof(double);
   if (sampling->paths_per_element == 0) {
     CK(cudaMemsetAsync(hist_dev, 0, hb, ctx->stream), "memset");
     if (sumsq_dev) CK(cudaMemsetAsync(sumsq_dev, 0, hb, ctx->stream), "memset");
@@ -543,7 +673,7 @@ darts_status darts_render(darts_ctx* ctx, const darts_scene* scene, const darts_
   }
   TraceParams P;
   make_trace_params(ctx, scene, sampling, &P);
-  P.N = sampling->paths_per_element;
+  P.N = sampling->paths_per_element * elements_of(scene);
   P.path_offset = path_offset;
   P.hist = hist_dev;
   P.sumsq = sumsq_dev;
@@ -565,15 +695,15 @@ darts_status darts_render_host(darts_ctx* ctx, const darts_scene* scene,
   darts_status s = validate(ctx, scene, sampling);
   if (s != DARTS_OK) return s;
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-  const size_t hb = (size_t)scene->gate.n_bins * sizeof(double);
+  const size_t nh = elements_of(scene) * (size_t)scene->gate.n_bins;
+  const size_t hb = nh * sizeof(double);
   CK(ensure((void**)&ctx->host_hist, &ctx->host_hist_bytes, 2 * hb), "histogram allocation");
-  s = darts_render(ctx, scene, sampling, ctx->host_hist, sumsq_host ? ctx->host_hist + scene->gate.n_bins : nullptr,
-                   path_offset, nullptr);
+  s = darts_render(ctx, scene, sampling, ctx->host_hist, sumsq_host ? ctx->host_hist + nh : nullptr, path_offset,
+                   nullptr);
   if (s != DARTS_OK) return s;
   CK(cudaMemcpyAsync(hist_host, ctx->host_hist, hb, cudaMemcpyDeviceToHost, ctx->stream), "histogram copy");
   if (sumsq_host)
-    CK(cudaMemcpyAsync(sumsq_host, ctx->host_hist + scene->gate.n_bins, hb, cudaMemcpyDeviceToHost, ctx->stream),
-       "histogram copy");
+    CK(cudaMemcpyAsync(sumsq_host, ctx->host_hist + nh, hb, cudaMemcpyDeviceToHost, ctx->stream), "histogram copy");
   return darts_sync(ctx);
 }
 
@@ -616,6 +746,8 @@ darts_status darts_render_batch(darts_ctx* ctx, int n, const darts_scene* scenes
     if (st != DARTS_OK) return st;
     if (!hist_dev[i]) return fail(ctx, DARTS_ERR_INVALID_ARG, "hist_dev[%d] is NULL", i);
     const darts_sampling& si = samplings[i];
+    if (general_scene(&scenes[i]))
+      return fail(ctx, DARTS_ERR_UNSUPPORTED, "a batch renders point-emitter, point-sensor media without surfaces");
     if (si.method != DARTS_METHOD_DARTS || si.ris_m != 8 || si.table_n_rho != s0.table_n_rho ||
         si.table_n_s != s0.table_n_s || si.table_n_mu != s0.table_n_mu)
       return fail(ctx, DARTS_ERR_UNSUPPORTED,
@@ -745,7 +877,7 @@ darts_status darts_adjoint(darts_ctx* ctx, const darts_scene* scene, const darts
   if (s != DARTS_OK) return s;
   TraceParams P;
   make_trace_params(ctx, scene, sampling, &P);
-  P.N = sampling->paths_per_element;
+  P.N = sampling->paths_per_element * elements_of(scene);
   P.path_offset = path_offset;
   P.dLdh = dLdh_dev;
   P.grad3 = grad3_dev;
@@ -782,7 +914,8 @@ darts_status darts_debug_paths(darts_ctx* ctx, const darts_scene* scene,
   make_trace_params(ctx, scene, sampling, &P);
   P.N = count;
   P.path_offset = first;
-  CK(ensure((void**)&ctx->host_hist, &ctx->host_hist_bytes, 2 * (size_t)scene->gate.n_bins * sizeof(double)),
+  CK(ensure((void**)&ctx->host_hist, &ctx->host_hist_bytes,
+            2 * elements_of(scene) * (size_t)scene->gate.n_bins * sizeof(double)),
      "histogram allocation");
   P.hist = ctx->host_hist;
   P.sumsq = nullptr;
@@ -877,7 +1010,7 @@ extern "C" darts_status darts_render_static(const darts_scene* scene, const dart
   if (static_setup(dev, &sd) != cudaSuccess) return DARTS_ERR_CUDA;
   const cudaStream_t stream = (cudaStream_t)cuda_stream;
   const int B = scene->gate.n_bins;
-  const size_t hb = (size_t)B * sizeof(double);
+  const size_t hb = elements_of(scene) * (size_t)B * sizeof(double);
   unsigned long long* header = reinterpret_cast<unsigned long long*>(sd->base);
   float* table = reinterpret_cast<float*>(sd->base + kStaticHeaderBytes);
   double* partials = reinterpret_cast<double*>(sd->base + kStaticHeaderBytes + kStaticTableBytes);
@@ -885,7 +1018,7 @@ extern "C" darts_status darts_render_static(const darts_scene* scene, const dart
   // sizes beyond the static maximum are rejected before anything is launched
   const size_t table_bytes = (size_t)sampling->table_n_rho * sampling->table_n_s *
                              row_stride_of(sampling->table_n_mu) * sizeof(float);
-  const size_t partial_bytes = (size_t)sd->sm_count * 2 * hb;
+  const size_t partial_bytes = (size_t)sd->sm_count * 2 * (size_t)B * sizeof(double);
   if (table_bytes > kStaticTableBytes || partial_bytes > kStaticPartialBytes) return DARTS_ERR_UNSUPPORTED;
 
   tmp.device = dev;
@@ -910,7 +1043,7 @@ extern "C" darts_status darts_render_static(const darts_scene* scene, const dart
   }
   TraceParams P;
   make_trace_params(ctx, scene, sampling, &P);
-  P.N = sampling->paths_per_element;
+  P.N = sampling->paths_per_element * elements_of(scene);
   P.path_offset = path_offset;
   P.hist = hist_dev;
   P.sumsq = sumsq_dev;
@@ -919,9 +1052,9 @@ extern "C" darts_status darts_render_static(const darts_scene* scene, const dart
   bool tile;
   size_t smem;
   choose_launch(&tmp, sampling, P, false, &block, &tile, &smem);
-  if (!tile) {
-    P.acc = partials;  // 2 * B doubles, zeroed here
-    if (cudaMemsetAsync(partials, 0, 2 * hb, stream) != cudaSuccess) return DARTS_ERR_CUDA;
+  if (!tile) {  // contributions go straight into the (zeroed) outputs
+    if (cudaMemsetAsync(hist_dev, 0, hb, stream) != cudaSuccess) return DARTS_ERR_CUDA;
+    if (sumsq_dev && cudaMemsetAsync(sumsq_dev, 0, hb, stream) != cudaSuccess) return DARTS_ERR_CUDA;
   }
   if (smem > (size_t)tmp.smem_optin) return DARTS_ERR_UNSUPPORTED;
   if (launch_trace(sampling->method, P, tmp.sm_count, block, false, tile, smem, stream) != cudaSuccess)

@@ -105,6 +105,19 @@ __device__ __forceinline__ float hg_sample(float g, float xi) {
   return fminf(1.0f, fmaxf(-1.0f, mu));
 }
 
+// sin(theta) of the HG sample of the same xi, free of the cancellation of
+// sqrt(1 - mu^2) near mu = +-1 (strongly forward or backward g): with
+// e = 1 - g + 2 g xi,
+//   1 - mu = 2 (1 - g)^2 (1 - xi) (1 + g xi) / e^2,
+//   1 + mu = 2 (1 + g)^2 xi (1 - g + g xi) / e^2,
+// so sin = 2 (1 - g^2) sqrt(xi (1 - xi) (1 + g xi) (1 - g + g xi)) / e^2,
+// a product of positive factors.
+__device__ __forceinline__ float hg_sin(float g, float xi) {
+  const float e = fmaf(2.0f * g, xi, 1.0f - g);
+  const float q = xi * (1.0f - xi) * fmaf(g, xi, 1.0f) * fmaf(g, xi, 1.0f - g);
+  return fminf(1.0f, __fdividef(2.0f * (1.0f - g * g) * sqrtf(q), e * e));
+}
+
 // cos/sin of 2 pi u for u in [0, 1), with the argument kept in [-pi, pi).
 __device__ __forceinline__ void sincos_2pi(float u, float* s, float* c) {
   float ss, cc;
@@ -113,16 +126,16 @@ __device__ __forceinline__ void sincos_2pi(float u, float* s, float* c) {
   *c = -cc;
 }
 
-// dir = mu n + sqrt(1 - mu^2) (cos phi b1 + sin phi b2), frame of Duff et al.
-__device__ __forceinline__ void frame_dir(float nx, float ny, float nz, float mu, float sphi,
-                                          float cphi, float* ox, float* oy, float* oz) {
+// dir = mu n + sin_t (cos phi b1 + sin phi b2), frame of Duff et al.; the
+// caller passes sin_t = sqrt(1 - mu^2) in a form accurate near mu = +-1.
+__device__ __forceinline__ void frame_dir(float nx, float ny, float nz, float mu, float sin_t,
+                                          float sphi, float cphi, float* ox, float* oy, float* oz) {
   const float sign = nz >= 0.0f ? 1.0f : -1.0f;
   const float a = -__fdividef(1.0f, sign + nz);  // |sign + nz| >= 1
   const float b = nx * ny * a;
   const float b1x = fmaf(sign * nx * nx, a, 1.0f), b1y = sign * b, b1z = -sign * nx;
   const float b2x = b, b2y = fmaf(ny * ny, a, sign), b2z = -ny;
-  const float s = sqrtf(fmaxf(0.0f, fmaf(-mu, mu, 1.0f)));
-  const float p = s * cphi, q = s * sphi;
+  const float p = sin_t * cphi, q = sin_t * sphi;
   *ox = fmaf(mu, nx, fmaf(p, b1x, q * b2x));
   *oy = fmaf(mu, ny, fmaf(p, b1y, q * b2y));
   *oz = fmaf(mu, nz, fmaf(p, b1z, q * b2z));

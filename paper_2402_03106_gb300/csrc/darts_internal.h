@@ -11,6 +11,19 @@ constexpr int kMaxTabMuNodes = 4;   // Gauss-Legendre nodes per cos-theta bin
 constexpr int kMaxTabTNodes = 32;   // Gauss-Legendre nodes per t-panel (two panels)
 constexpr int kStatCount = 9;       // darts_stats fields after `paths`
 constexpr int kPathChunk = 64;      // paths a warp claims from the global counter
+constexpr int kMaxEmitters = 8;
+constexpr int kMaxSpheres = 64;
+
+// One pulse emitter: an isotropic point (kind 0) or a one-sided Lambertian
+// parallelogram pos + s u + t v emitting toward n = u x v / |u x v| (kind 1).
+struct EmitterParams {
+  float pos[3], u[3], v[3], n[3];
+  float ie;          // radiant intensity scale: E / (4 pi) (point), E / pi (area)
+  float cdf;         // cumulative energy fraction up to and including this emitter
+  float wsel;        // total energy / this emitter's energy (1 / selection probability)
+  float s_lo, s_hi;  // v (t_min - t0), v (t_max - t0)
+  int kind;
+};
 
 // Elliptical DA table build (Sec. 5.1, Eq. 16-18).
 struct TableParams {
@@ -44,6 +57,21 @@ struct TraceParams {
   float S_gate_hi;                 // v (t_max - t0)
   float tiny_s;                    // 2^-6 v (t_max - t_min): small-t' threshold
   int n_bins;
+  // general scenes: several / area emitters, surfaces, a pinhole camera
+  int general;                     // run the general variant of the path kernel
+  int n_emitters;
+  EmitterParams em[kMaxEmitters];
+  int n_spheres;
+  float4 sph[kMaxSpheres];         // centre, radius
+  float sph_albedo[kMaxSpheres];
+  int walls;                       // box faces with walls: bit 2 * axis + (1: hi face)
+  float wall_albedo;
+  int camera;                      // 0: point sensor at xs; 1: pinhole camera
+  int cam_inside;                  // camera inside the medium box
+  float cam_pos[3], cam_f[3], cam_r[3], cam_u[3];
+  float cam_th, cam_aspect;
+  int width, height;
+  unsigned long long spp;          // paths per sensor element
   // direction table
   int n_rho, n_s, n_mu, row_stride, rows;
   float inv_smax, n_s_over_8, mu_scale, inv_mu_scale;  // 1/S_max, n_s / 8, n_mu / 2, 2 / n_mu
@@ -61,10 +89,9 @@ struct TraceParams {
   unsigned long long path_offset;  // global id = path_offset + local index
   float wb;                        // weight per path contribution (DARTS n_bins/N_e, else 1/N_e)
   // outputs and scratch
-  double* hist;                    // [n_bins]
-  double* sumsq;                   // [n_bins] or null
+  double* hist;                    // [elements][n_bins]; zeroed before a launch without tiles
+  double* sumsq;                   // [elements][n_bins] or null
   double* partials;                // [grid][2][n_bins]
-  double* acc;                     // [2][n_bins] global accumulator (no-tile mode)
   unsigned long long* counter;     // path counter
   unsigned int* ticket;            // last-block ticket
   unsigned int* status;            // device status word (bit 0: non-finite)
@@ -114,7 +141,7 @@ cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_
                           uint32_t* out, cudaStream_t s);
 size_t trace_smem_bytes(int method, const TraceParams& p, int block, bool tile);
 // Block size actually launched for a request (non-production variants use 512).
-int trace_block_for(int block, bool debug, bool tile, int method, int M);
+int trace_block_for(int block, bool debug, bool tile, int method, int M, bool general);
 int trace_max_m();
 
 }  // namespace darts

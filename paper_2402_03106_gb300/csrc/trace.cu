@@ -37,7 +37,8 @@ constexpr int kMaxM = 32;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 enum : int { kDarts = 0, kPlain = 1, kVanilla = 2 };
-enum : int { EV_NONE = 0, EV_EARLY = 1, EV_SCATTER = 2, EV_ESCAPE = 3, EV_INVALID = 4, EV_MAXDEPTH = 5 };
+enum : int { EV_NONE = 0, EV_EARLY = 1, EV_SCATTER = 2, EV_ESCAPE = 3, EV_INVALID = 4, EV_MAXDEPTH = 5,
+             EV_SURFACE = 6 };
 // stats slots (after `paths`)
 enum : int { ST_VERT = 0, ST_CONN = 1, ST_DIST = 2, ST_EARLY = 3, ST_INVALID = 4, ST_ESCAPE = 5,
              ST_FP64E = 6, ST_FP64P = 7, ST_SPARE = 8 };
@@ -55,6 +56,14 @@ struct Path {
   // path-replay adjoint: sum over the path's connections of c_v * s_v, and
   // the running sum of d log HG / dg over the walk vertices
   float a0, a1, a2, gsum;
+  // general scenes: the path's emitter point and normal (0 for a point
+  // emitter), its intensity scale and gate bounds, the sensor element, the
+  // medium scattering vertices so far, and whether the direction of the
+  // current vertex is already fixed (camera ray, surface bounce)
+  float ey0, ey1, ey2, en0, en1, en2, ie, s_hi_e;
+  int elem, nmed;
+  int surf;          // sphere the current vertex lies on, -1 otherwise
+  bool fixed, miss;
 };
 
 // Event counting.  Common events set a bit for the current vertex step; the
@@ -116,7 +125,8 @@ __device__ __noinline__ void ellipse_fp64(float delta, float C, float S_lo, floa
 __device__ __forceinline__ float connect(const TraceParams& P, float wx, float wy, float wz,
                                          float C, float ax, float ay, float az, float S_lo,
                                          float S_hi, float u, bool uniform_S, float* S_out,
-                                         Counters& cnt, float* cos_out = nullptr) {
+                                         Counters& cnt, float* cos_out = nullptr,
+                                         float* t_out = nullptr, float Ie = -1.0f) {
   const float W = S_hi - S_lo;
   float dS, conn_w;  // conn_w = exp(-sigma_t S) / p(S)
   if (!uniform_S) {
@@ -136,6 +146,7 @@ __device__ __forceinline__ float connect(const TraceParams& P, float wx, float w
   if (delta < C * (1.0f / 4096.0f)) {
     ellipse_fp64(delta, C, S_lo, dS, q, &r1, &den, &cos_s);
     cnt.add_rare(ST_FP64E);
+    if (t_out) *t_out = S - r1;
   } else {
     // with t from Eq. 18: S - C mu = delta + C q, r1 = S - t = (delta^2 + 2 S C q) / (2 (S - C mu)),
     // and the scattering cosine at the control vertex (C mu - t) / r1 written
@@ -143,6 +154,7 @@ __device__ __forceinline__ float connect(const TraceParams& P, float wx, float w
     den = fmaf(C, q, delta);
     const float nr = fmaf(delta, delta, 2.0f * S * C * q);
     r1 = __fdividef(nr, 2.0f * den);
+    if (t_out) *t_out = __fdividef(delta * (S + C), 2.0f * den);  // Eq. 18
     const float cq = C * q;
     cos_s = __fdividef(fmaf(2.0f * C * cq, 1.0f - q, -delta * fmaf(2.0f, cq, delta)), nr);
   }
@@ -150,7 +162,7 @@ __device__ __forceinline__ float connect(const TraceParams& P, float wx, float w
   if (cos_out) *cos_out = cos_s;
   const float f = hg_eval(cos_s, P.hg_a, P.hg_b, P.hg_c);
   // sigma_s e^{-st S} f I_e / r1^2 / p(t),  p(t) = p(S) (S - C mu) / r1
-  return __fdividef(P.sigma_s * conn_w * f * P.Ie, r1 * den);
+  return __fdividef(P.sigma_s * conn_w * f * (Ie < 0.0f ? P.Ie : Ie), r1 * den);
 }
 
 // One distance step of a DARTS vertex, as handed to the RIS evaluation:
@@ -199,12 +211,105 @@ __device__ __forceinline__ float ris_candidate(const TraceParams& P, const RisTa
   return P.phi_k0 - 1.5f * __logf(tp) - __fdividef(r2 * P.phi_invk, tp) - P.sa_v * tp;
 }
 
+// ---- general scenes: surfaces, emitter points, camera -----------------------
+constexpr float kGeomEps = 1e-5f;
+
+// Smallest root t > kGeomEps of |x + w t - c| = r, or FLT_MAX.
+// The discriminant is r^2 - |o - b w|^2 (the squared distance of the centre
+// from the line), not b^2 - (|o|^2 - r^2): for a far sphere the latter
+// cancels two large terms and loses most FP32 digits of the hit distance.
+// The near root comes from the product of the roots (|o|^2 - r^2) divided
+// by the root of larger magnitude, which has no cancellation either.
+__device__ __forceinline__ float ray_sphere(const float4 c, float x, float y, float z, float wx,
+                                            float wy, float wz) {
+  const float ox = x - c.x, oy = y - c.y, oz = z - c.z;
+  const float b = fmaf(ox, wx, fmaf(oy, wy, oz * wz));
+  const float lx = fmaf(-b, wx, ox), ly = fmaf(-b, wy, oy), lz = fmaf(-b, wz, oz);
+  const float disc = fmaf(c.w, c.w, -fmaf(lx, lx, fmaf(ly, ly, lz * lz)));
+  if (disc < 0.0f) return FLT_MAX;
+  const float q = -b - copysignf(sqrtf(disc), b);
+  if (q == 0.0f) return FLT_MAX;
+  const float cc = fmaf(ox, ox, fmaf(oy, oy, fmaf(oz, oz, -c.w * c.w)));
+  const float ta = q, tb = cc / q;
+  const float t0 = fminf(ta, tb), t1 = fmaxf(ta, tb);
+  return t0 > kGeomEps ? t0 : (t1 > kGeomEps ? t1 : FLT_MAX);
+}
+
+// Nearest wall, sphere or open face along (x, w) from inside the box.
+// hit: 0 open face, 1 wall, 2 + i sphere i; n: the surface normal facing the
+// ray.  Sphere `skip` is the one the ray leaves (outward): being convex it
+// cannot be met again, and skipping it keeps FP32 rounding of the start point
+// from producing a spurious second hit.
+__device__ __forceinline__ float cast_ray(const TraceParams& P, float x, float y, float z, float wx,
+                                          float wy, float wz, int skip, int* hit, float* nx, float* ny,
+                                          float* nz) {
+  float d = FLT_MAX;
+  int face = -1;
+  const float px[3] = {x, y, z}, pw[3] = {wx, wy, wz};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float di = FLT_MAX;
+    int fi = -1;
+    if (pw[i] > 0.0f) { di = __fdividef(P.hi[i] - px[i], pw[i]); fi = 2 * i + 1; }
+    else if (pw[i] < 0.0f) { di = __fdividef(P.lo[i] - px[i], pw[i]); fi = 2 * i; }
+    if (di < d) { d = di; face = fi; }
+  }
+  d = fmaxf(d, 0.0f);
+  *hit = (face >= 0 && ((P.walls >> face) & 1)) ? 1 : 0;
+  *nx = face / 2 == 0 ? ((face & 1) ? -1.0f : 1.0f) : 0.0f;
+  *ny = face / 2 == 1 ? ((face & 1) ? -1.0f : 1.0f) : 0.0f;
+  *nz = face / 2 == 2 ? ((face & 1) ? -1.0f : 1.0f) : 0.0f;
+  int hs = -1;
+  for (int k = 0; k < P.n_spheres; ++k) {
+    if (k == skip) continue;
+    const float t = ray_sphere(P.sph[k], x, y, z, wx, wy, wz);
+    if (t < d) {
+      d = t;
+      hs = k;
+    }
+  }
+  if (hs >= 0) {
+    const float4 c = P.sph[hs];
+    const float ir = 1.0f / c.w;
+    *hit = 2 + hs;
+    *nx = (fmaf(wx, d, x) - c.x) * ir;
+    *ny = (fmaf(wy, d, y) - c.y) * ir;
+    *nz = (fmaf(wz, d, z) - c.z) * ir;
+  }
+  return d;
+}
+
+// No sphere blocks the open segment a -> b (the box is convex: its walls
+// never occlude two points inside it).  Sphere `skip` carries a (the segment
+// leaves it outward, or the caller's contribution is zero anyway).
+__device__ __forceinline__ bool visible(const TraceParams& P, float ax, float ay, float az, float bx,
+                                        float by, float bz, int skip) {
+  if (P.n_spheres == 0) return true;
+  float wx = bx - ax, wy = by - ay, wz = bz - az;
+  const float len = sqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz)));
+  const float il = 1.0f / len;
+  wx *= il;
+  wy *= il;
+  wz *= il;
+  for (int k = 0; k < P.n_spheres; ++k)
+    if (k != skip && ray_sphere(P.sph[k], ax, ay, az, wx, wy, wz) < len - kGeomEps) return false;
+  return true;
+}
+
+// Radiant intensity of the path's emitter point toward x.
+__device__ __forceinline__ float emit_intensity(const Path& p, float x, float y, float z) {
+  if (p.en0 == 0.0f && p.en1 == 0.0f && p.en2 == 0.0f) return p.ie;
+  const float dx = x - p.ey0, dy = y - p.ey1, dz = z - p.ey2;
+  const float c = fmaf(dx, p.en0, fmaf(dy, p.en1, dz * p.en2)) * rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+  return c > 0.0f ? p.ie * c : 0.0f;
+}
+
 // d log HG(mu; g) / dg = -2g/(1 - g^2) - 3 (g - mu) / (1 + g^2 - 2 g mu)
 __device__ __forceinline__ float hg_dlog_dg(const TraceParams& P, float mu) {
   return fmaf(-3.0f * (P.g - mu), __frcp_rn(fmaf(-P.hg_c, mu, P.hg_b)), P.hg_dlog_a);
 }
 
-template <int METHOD, int MAXM, bool DEBUG, bool ADJ = false>
+template <int METHOD, int MAXM, bool DEBUG, bool ADJ = false, bool GEN = false>
 struct Stepper {
   // Initialise a path with local index j.
   __device__ static void init(const TraceParams& P, Path& p, unsigned long long j, int bin) {
@@ -230,9 +335,462 @@ struct Stepper {
       const U4 u = rng(P, j, 0, 1);
       float s, c;
       sincos_2pi(u01(u.z), &s, &c);
-      frame_dir(0.0f, 0.0f, 1.0f, fmaf(2.0f, u01(u.y), -1.0f), s, c, &p.wx, &p.wy, &p.wz);
+      const float uy = u01(u.y);
+      frame_dir(0.0f, 0.0f, 1.0f, fmaf(2.0f, uy, -1.0f), 2.0f * sqrtf(uy * (1.0f - uy)), s, c, &p.wx, &p.wy,
+                &p.wz);
       p.beta = 4.0f * kPi;
     }
+  }
+
+  // ---- general scenes -------------------------------------------------------
+  // Path start: sensor element and (DARTS) bin, the emitter point (chosen by
+  // energy, a uniform point on an area emitter), then the point sensor or
+  // the camera ray entering the medium (p.miss when it never does).
+  __device__ static void init_gen(const TraceParams& P, Path& p, unsigned long long j) {
+    const unsigned long long gid = P.path_offset + j;
+    const int B = P.n_bins;
+    unsigned long long s = gid;
+    p.elem = 0;
+    if (P.camera) {
+      const unsigned long long e = gid / P.spp;
+      s = gid - e * P.spp;
+      p.elem = (int)(e % (unsigned long long)(P.width * P.height));
+    }
+    p.j = j;
+    p.L = p.Lc = p.c = 0.0f;
+    p.k = 0;
+    p.nmed = 0;
+    p.a0 = p.a1 = p.a2 = p.gsum = 0.0f;
+    p.miss = false;
+    p.surf = -1;
+    // emitter point
+    const U4 ue = rng(P, j, 0xFFFFFFu, 2);
+    const float target = u01(ue.x);
+    int pick = P.n_emitters - 1;
+    for (int k = P.n_emitters - 1; k >= 0; --k)
+      if (target < P.em[k].cdf) pick = k;
+    const EmitterParams& E = P.em[pick];
+    const float su = u01(ue.y), sv = u01(ue.z);
+    p.ey0 = fmaf(su, E.u[0], fmaf(sv, E.v[0], E.pos[0]));
+    p.ey1 = fmaf(su, E.u[1], fmaf(sv, E.v[1], E.pos[1]));
+    p.ey2 = fmaf(su, E.u[2], fmaf(sv, E.v[2], E.pos[2]));
+    p.en0 = E.n[0];
+    p.en1 = E.n[1];
+    p.en2 = E.n[2];
+    p.ie = E.ie;
+    p.s_hi_e = E.s_hi;
+    p.beta = E.wsel;
+    if (METHOD == kDarts) {
+      const U4 uo = philox4x32_10((uint32_t)p.elem, 0u, P.stream, (kVertexElement << 8) | 0u, P.key0, P.key1);
+      const unsigned oe = (unsigned)(((unsigned long long)(uo.x >> 8) * (unsigned)B) >> 24);
+      const int b = (int)((s % (unsigned long long)B + oe) % (unsigned)B);
+      p.bin = p.elem * B + b;
+      p.Sm0 = fmaf((float)b, P.S_bin, E.s_lo);
+      p.SM0 = fmaf((float)(b + 1), P.S_bin, E.s_lo);
+    } else {  // the baselines bin each contribution by its time (row p.elem)
+      p.bin = -1;
+      p.Sm0 = E.s_lo;
+      p.SM0 = E.s_hi;
+    }
+    if (P.camera) {
+      const U4 uc = rng(P, j, 0xFFFFFFu, 3);
+      const int px = p.elem % P.width, py = p.elem / P.width;
+      const float sx = (2.0f * ((float)px + u01(uc.x)) / (float)P.width - 1.0f) * P.cam_th * P.cam_aspect;
+      const float sy = (1.0f - 2.0f * ((float)py + u01(uc.y)) / (float)P.height) * P.cam_th;
+      float wx = P.cam_f[0] + sx * P.cam_r[0] + sy * P.cam_u[0];
+      float wy = P.cam_f[1] + sx * P.cam_r[1] + sy * P.cam_u[1];
+      float wz = P.cam_f[2] + sx * P.cam_r[2] + sy * P.cam_u[2];
+      const float iw = rsqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz)));
+      p.wx = wx * iw;
+      p.wy = wy * iw;
+      p.wz = wz * iw;
+      p.fixed = true;
+      if (P.cam_inside) {
+        p.x = P.cam_pos[0];
+        p.y = P.cam_pos[1];
+        p.z = P.cam_pos[2];
+      } else {
+        const float o[3] = {P.cam_pos[0], P.cam_pos[1], P.cam_pos[2]}, w[3] = {p.wx, p.wy, p.wz};
+        float tin = -FLT_MAX, tout = FLT_MAX;
+        int face = -1;
+        bool miss = false;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          if (w[i] == 0.0f) {
+            if (o[i] < P.lo[i] || o[i] > P.hi[i]) miss = true;
+            continue;
+          }
+          float t1 = (P.lo[i] - o[i]) / w[i], t2 = (P.hi[i] - o[i]) / w[i];
+          int f1 = 2 * i, f2 = 2 * i + 1;
+          if (t1 > t2) {
+            const float tt = t1; t1 = t2; t2 = tt;
+            const int ff = f1; f1 = f2; f2 = ff;
+          }
+          if (t1 > tin) { tin = t1; face = f1; }
+          if (t2 < tout) tout = t2;
+        }
+        if (miss || !(tin <= tout) || tout <= 0.0f || tin < 0.0f) p.miss = true;
+        if (face >= 0 && ((P.walls >> face) & 1)) p.miss = true;
+        p.x = fmaf(p.wx, tin, o[0]);
+        p.y = fmaf(p.wy, tin, o[1]);
+        p.z = fmaf(p.wz, tin, o[2]);
+        p.L = p.miss ? 0.0f : tin;
+      }
+    } else {
+      p.x = P.xs[0];
+      p.y = P.xs[1];
+      p.z = P.xs[2];
+      p.wx = 0.0f;
+      p.wy = 0.0f;
+      p.wz = 1.0f;
+      p.fixed = false;
+      if (METHOD != kDarts) {  // the baselines draw the uniform direction here
+        const U4 u = rng(P, j, 0, 1);
+        float sn, cs;
+        sincos_2pi(u01(u.z), &sn, &cs);
+        const float uy = u01(u.y);
+        frame_dir(0.0f, 0.0f, 1.0f, fmaf(2.0f, uy, -1.0f), 2.0f * sqrtf(uy * (1.0f - uy)), sn, cs, &p.wx,
+                  &p.wy, &p.wz);
+        p.beta *= 4.0f * kPi;
+        p.fixed = true;
+      }
+    }
+  }
+
+  // Direct connection from a surface vertex (normal n facing the medium) to
+  // the path's emitter point: BRDF albedo / pi, transmittance, intensity,
+  // 1 / r^2 and visibility.  Writes r.
+  __device__ static float surface_connect(const TraceParams& P, const Path& p, float nx, float ny,
+                                          float nz, float albedo, float* r_out) {
+    const float dx = p.ey0 - p.x, dy = p.ey1 - p.y, dz = p.ey2 - p.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float ir = rsqrtf(r2);
+    const float r = r2 * ir;
+    *r_out = r;
+    const float cs = fmaf(dx, nx, fmaf(dy, ny, dz * nz)) * ir;
+    if (!(cs > 0.0f)) return 0.0f;
+    if (!visible(P, p.x, p.y, p.z, p.ey0, p.ey1, p.ey2, p.surf)) return 0.0f;
+    return albedo * (1.0f / kPi) * cs * __expf(-P.sigma_t * r) * emit_intensity(p, p.x, p.y, p.z) / r2;
+  }
+
+  // Surface vertex: move onto the surface, connect, then a cosine-weighted
+  // direction (Lambertian: BRDF cos / pdf = albedo) from group 1 of vertex k+1.
+  __device__ static float surface_bounce(const TraceParams& P, Path& p, float dm, int hit, float nx,
+                                         float ny, float nz, float* r_out) {
+    p.x = fmaf(p.wx, dm, p.x);
+    p.y = fmaf(p.wy, dm, p.y);
+    p.z = fmaf(p.wz, dm, p.z);
+    kahan_add(p.L, p.Lc, dm);
+    p.surf = hit >= 2 ? hit - 2 : -1;
+    const float alb = hit == 1 ? P.wall_albedo : P.sph_albedo[hit - 2];
+    const float c = p.beta * surface_connect(P, p, nx, ny, nz, alb, r_out);
+    const U4 us = rng(P, p.j, (uint32_t)(p.k + 1), 1);
+    float sn, cs;
+    sincos_2pi(u01(us.z), &sn, &cs);
+    const float uc = u01(us.y);
+    frame_dir(nx, ny, nz, sqrtf(uc), sqrtf(1.0f - uc), sn, cs, &p.wx, &p.wy, &p.wz);
+    p.beta *= alb;
+    p.fixed = true;
+    return c;
+  }
+
+  // DARTS vertex in a general scene.  Returns 1 when the path ended, 0 when
+  // the RIS task of the distance step was filled, 2 when the path moved to a
+  // surface vertex (no distance step).
+  __device__ static int vertex_gen(const TraceParams& P, Path& p, const float* tab, Counters& cnt,
+                                   RisTask& task) {
+    if (p.miss) return 1;  // camera ray that never enters the medium
+    cnt.add(ST_VERT);
+    const float ex = p.ey0 - p.x, ey = p.ey1 - p.y, ez = p.ey2 - p.z;
+    const float C2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+    const float C = sqrtf(C2);
+    const float invC = __frcp_rn(C);
+    const float ax = ex * invC, ay = ey * invC, az = ez * invC;
+    const float SM = p.SM0 - p.L, Sm = p.Sm0 - p.L;
+    if (!(SM > C)) {
+      cnt.add(ST_EARLY);
+      record(P, p, 0, EV_EARLY);
+      return 1;
+    }
+    float wx = p.wx, wy = p.wy, wz = p.wz;
+    const U4 u1 = rng(P, p.j, (uint32_t)p.k, 1);
+    if (!p.fixed) {
+      // MIS of the EDA table and HG (uniform sphere at the point sensor), Eq. 19
+      const float rho = __fdividef(C, SM);
+      int i_rho = min(max((int)(rho * (float)P.n_rho), 0), P.n_rho - 1);
+      int i_s = (int)floorf((__log2f(SM * P.inv_smax) + 8.0f) * P.n_s_over_8);
+      i_s = min(max(i_s, 0), P.n_s - 1);
+      const float* row = tab + (i_rho * P.n_s + i_s) * P.row_stride;
+      float gamma = __fdividef(rho, rho + P.mis_alpha);
+      const bool sensor = p.k == 0;
+      if ((sensor && P.uniform_sensor) || P.no_eda) gamma = 0.0f;
+      const float gb = sensor ? 0.0f : P.g;
+      const float bx = sensor ? 0.0f : p.wx, by = sensor ? 0.0f : p.wy, bz = sensor ? 1.0f : p.wz;
+      const float v0 = u01(u1.x), v1 = u01(u1.y);
+      float sphi, cphi;
+      sincos_2pi(u01(u1.z), &sphi, &cphi);
+      const bool eda = v0 < gamma;
+      int lo = 0, n = P.n_mu;
+      while (n > 1) {
+        const int half = n >> 1;
+        lo = (row[lo + half] > v1) ? lo : lo + half;
+        n -= half;
+      }
+      const float c_lo = row[lo], c_hi = row[lo + 1];
+      const float fr = __fdividef(v1 - c_lo, c_hi - c_lo);
+      const float mu_eda = fmaf((float)lo + fr, P.inv_mu_scale, -1.0f);
+      // 1 -+ mu of the table sample from the bin index: no cancellation near +-1
+      const float st_eda = sqrtf(fmaxf(0.0f, ((float)(P.n_mu - lo) - fr) * P.inv_mu_scale *
+                                                 (((float)lo + fr) * P.inv_mu_scale)));
+      const float mu_hg = hg_sample(gb, v1);
+      const float st_hg = hg_sin(gb, v1);
+      frame_dir(eda ? ax : bx, eda ? ay : by, eda ? az : bz, eda ? mu_eda : mu_hg, eda ? st_eda : st_hg, sphi,
+                cphi, &wx, &wy, &wz);
+      const float mu_b = eda ? fmaf(wx, bx, fmaf(wy, by, wz * bz)) : mu_hg;
+      int bin = lo;
+      if (!eda) {
+        const float mua = fmaf(wx, ax, fmaf(wy, ay, wz * az));
+        bin = min(max((int)floorf((mua + 1.0f) * P.mu_scale), 0), P.n_mu - 1);
+      }
+      const float pE = (eda ? c_hi - c_lo : row[bin + 1] - row[bin]) * P.mu_scale * (1.0f / kTwoPi);
+      const float hg = hg_eval(mu_b, P.hg_a, P.hg_b, P.hg_c);
+      const float pB = sensor ? kInv4Pi : hg;
+      const float f = sensor ? 1.0f : hg;
+      p.beta *= __fdividef(f, fmaf(gamma, pE - pB, pB));
+      if (ADJ && !sensor) p.gsum += hg_dlog_dg(P, mu_b);
+      if (DEBUG) {
+        record(P, p, 2, eda ? 1 : 0);
+        record(P, p, 3, (uint8_t)(bin & 0xFF));
+      }
+    }
+    // control vertex, capped at the first surface (case II of Sec. 5.2)
+    int hit;
+    float nx, ny, nz;
+    const float dm = cast_ray(P, p.x, p.y, p.z, wx, wy, wz, p.surf, &hit, &nx, &ny, &nz);
+    const float mx = fmaf(wx, dm, -ex), my = fmaf(wy, dm, -ey), mz = fmaf(wz, dm, -ez);
+    const float S_dm = dm + sqrtf(fmaf(mx, mx, fmaf(my, my, mz * mz)));
+    const float S_hi = fminf(SM, S_dm), S_lo = fmaxf(Sm, C);
+    const bool ok = S_hi > S_lo;
+    if (ok) {
+      float S, cos_s, tctl;
+      float cc = connect(P, wx, wy, wz, C, ax, ay, az, S_lo, S_hi, u01(u1.w), false, &S, cnt, &cos_s,
+                         &tctl, 1.0f);
+      const float qx = fmaf(wx, tctl, p.x), qy = fmaf(wy, tctl, p.y), qz = fmaf(wz, tctl, p.z);
+      cc *= emit_intensity(p, qx, qy, qz);
+      if (!visible(P, qx, qy, qz, p.ey0, p.ey1, p.ey2, -1)) cc = 0.0f;
+      p.c = fmaf(p.beta, cc, p.c);
+      cnt.add(ST_CONN);
+      if (ADJ) {
+        const float cv = p.beta * cc, ell = p.L + S;
+        p.a0 = fmaf(cv, fmaf((float)(p.nmed + 1), P.inv_sigma_s, -ell), p.a0);
+        p.a1 = fmaf(-cv, ell, p.a1);
+        p.a2 = fmaf(cv, p.gsum + hg_dlog_dg(P, cos_s), p.a2);
+      }
+    }
+    const uint8_t nonempty = ok ? 0x10 : 0;
+    p.wx = wx;
+    p.wy = wy;
+    p.wz = wz;
+    if (p.k + 1 == P.K) {
+      record(P, p, 0, EV_MAXDEPTH | nonempty);
+      return 1;
+    }
+    const U4 u0 = rng(P, p.j, (uint32_t)p.k, 0);
+    const float pm = -expm1_neg(-P.sigma_t * dm);
+    if (!(u01(u0.x) < pm)) {
+      if (hit == 0) {
+        cnt.add(ST_ESCAPE);
+        record(P, p, 0, EV_ESCAPE | nonempty);
+        return 1;
+      }
+      record(P, p, 0, EV_SURFACE | nonempty);
+      float r;
+      const float cs = surface_bounce(P, p, dm, hit, nx, ny, nz, &r);
+      const float Lt = p.L + r;
+      if (cs > 0.0f && Lt >= p.Sm0 && Lt < p.SM0) {
+        p.c += cs;
+        if (ADJ) {
+          p.a0 = fmaf(cs, fmaf((float)p.nmed, P.inv_sigma_s, -Lt), p.a0);
+          p.a1 = fmaf(-cs, Lt, p.a1);
+          p.a2 = fmaf(cs, p.gsum, p.a2);
+        }
+      }
+      p.k += 1;
+      return 2;
+    }
+    cnt.add(ST_DIST);
+    task.b = -fmaf(wx, ex, fmaf(wy, ey, wz * ez));
+    const float hx = fmaf(wy, ez, -wz * ey), hy = fmaf(wz, ex, -wx * ez), hz = fmaf(wx, ey, -wy * ex);
+    task.h2 = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
+    task.SM = SM;
+    task.SMlo = ((p.SM0 - SM) - p.L) + p.Lc;
+    task.pm = pm;
+    task.u3 = u01(u0.w);
+    task.e0row = (u0.z >> 8) | ((u0.y >> 27) << 24);
+    task.nonempty = nonempty;
+    return 0;
+  }
+
+  // Baseline vertex in a general scene.
+  __device__ static bool step_base_gen(const TraceParams& P, Path& p, Counters& cnt, int* out_bin,
+                                       float* out_c, int* out_bin2, float* out_c2) {
+    *out_bin = -1;
+    *out_bin2 = -1;
+    if (p.miss) return true;
+    cnt.add(ST_VERT);
+    const int row = p.elem * P.n_bins;
+    int hit;
+    float nx, ny, nz;
+    const float dm = cast_ray(P, p.x, p.y, p.z, p.wx, p.wy, p.wz, p.surf, &hit, &nx, &ny, &nz);
+    if (METHOD == kPlain) {
+      const float ex = p.ey0 - p.x, ey = p.ey1 - p.y, ez = p.ey2 - p.z;
+      const float C = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+      const float invC = __frcp_rn(C);
+      const float SM = p.SM0 - p.L, Sm = p.Sm0 - p.L;
+      if (!(SM > C)) {
+        cnt.add(ST_EARLY);
+        record(P, p, 0, EV_EARLY);
+        return true;
+      }
+      const float mx = fmaf(p.wx, dm, -ex), my = fmaf(p.wy, dm, -ey), mz = fmaf(p.wz, dm, -ez);
+      const float S_dm = dm + sqrtf(fmaf(mx, mx, fmaf(my, my, mz * mz)));
+      const float S_hi = fminf(SM, S_dm), S_lo = fmaxf(Sm, C);
+      const U4 u1 = rng(P, p.j, (uint32_t)p.k, 1);
+      if (S_hi > S_lo) {
+        float S, cos_s, tctl;
+        float cc = connect(P, p.wx, p.wy, p.wz, C, ex * invC, ey * invC, ez * invC, S_lo, S_hi,
+                           u01(u1.w), true, &S, cnt, &cos_s, &tctl, 1.0f);
+        const float qx = fmaf(p.wx, tctl, p.x), qy = fmaf(p.wy, tctl, p.y), qz = fmaf(p.wz, tctl, p.z);
+        cc *= emit_intensity(p, qx, qy, qz);
+        if (!visible(P, qx, qy, qz, p.ey0, p.ey1, p.ey2, -1)) cc = 0.0f;
+        cnt.add(ST_CONN);
+        const float y = ((p.L + S) - p.Sm0) * P.inv_S_bin;
+        *out_bin = row + min(max((int)floorf(y), 0), P.n_bins - 1);
+        *out_c = p.beta * cc;
+        p.c += *out_c;
+      }
+      if (p.k + 1 == P.K) {
+        record(P, p, 0, EV_MAXDEPTH);
+        return true;
+      }
+      const U4 u0 = rng(P, p.j, (uint32_t)p.k, 0);
+      const float d = -log1m(u01(u0.x)) * P.inv_st;
+      if (!(d < dm)) {
+        if (hit == 0) {
+          cnt.add(ST_ESCAPE);
+          record(P, p, 0, EV_ESCAPE);
+          return true;
+        }
+        record(P, p, 0, EV_SURFACE);
+        float r;
+        const float cs = surface_bounce(P, p, dm, hit, nx, ny, nz, &r);
+        if (cs > 0.0f) {
+          const float y = ((p.L + r) - p.Sm0) * P.inv_S_bin;
+          if (y >= 0.0f && y < (float)P.n_bins) {
+            *out_bin2 = row + min((int)y, P.n_bins - 1);
+            *out_c2 = cs;
+            p.c += cs;
+          }
+        }
+        p.k += 1;
+        return false;
+      }
+      p.beta *= P.albedo;
+      p.x = fmaf(p.wx, d, p.x);
+      p.y = fmaf(p.wy, d, p.y);
+      p.z = fmaf(p.wz, d, p.z);
+      kahan_add(p.L, p.Lc, d);
+      p.surf = -1;
+      record(P, p, 0, EV_SCATTER);
+    } else {  // vanilla
+      const U4 u0 = rng(P, p.j, (uint32_t)p.k, 0);
+      const float d = -log1m(u01(u0.x)) * P.inv_st;
+      if (!(d < dm)) {
+        if (hit == 0) {
+          cnt.add(ST_ESCAPE);
+          record(P, p, 0, EV_ESCAPE);
+          return true;
+        }
+        float r;
+        const bool last = p.k + 1 == P.K;
+        float cs;
+        if (last) {  // connect only: the path ends at this surface vertex
+          p.x = fmaf(p.wx, dm, p.x);
+          p.y = fmaf(p.wy, dm, p.y);
+          p.z = fmaf(p.wz, dm, p.z);
+          kahan_add(p.L, p.Lc, dm);
+          p.surf = hit >= 2 ? hit - 2 : -1;
+          const float alb = hit == 1 ? P.wall_albedo : P.sph_albedo[hit - 2];
+          cs = p.beta * surface_connect(P, p, nx, ny, nz, alb, &r);
+        } else {
+          cs = surface_bounce(P, p, dm, hit, nx, ny, nz, &r);
+        }
+        if (cs > 0.0f) {
+          cnt.add(ST_CONN);
+          const float y = ((p.L + r) - p.Sm0) * P.inv_S_bin;
+          if (y >= 0.0f && y < (float)P.n_bins) {
+            *out_bin = row + min((int)y, P.n_bins - 1);
+            *out_c = cs;
+            p.c += cs;
+          }
+        }
+        if (last) {
+          record(P, p, 0, EV_MAXDEPTH);
+          return true;
+        }
+        const float ex = p.x - p.ey0, ey = p.y - p.ey1, ez = p.z - p.ey2;
+        const float C = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+        if (!(p.L + C < p.s_hi_e)) {
+          cnt.add(ST_EARLY);
+          record(P, p, 0, EV_EARLY);
+          return true;
+        }
+        record(P, p, 0, EV_SURFACE);
+        p.k += 1;
+        return false;
+      }
+      p.beta *= P.albedo;
+      p.x = fmaf(p.wx, d, p.x);
+      p.y = fmaf(p.wy, d, p.y);
+      p.z = fmaf(p.wz, d, p.z);
+      kahan_add(p.L, p.Lc, d);
+      p.surf = -1;
+      const float ex = p.x - p.ey0, ey = p.y - p.ey1, ez = p.z - p.ey2;
+      const float C2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+      const float C = sqrtf(C2);
+      const float cos_s = -__fdividef(ex * p.wx + ey * p.wy + ez * p.wz, C);
+      const float y = ((p.L + C) - p.Sm0) * P.inv_S_bin;
+      if (y >= 0.0f && y < (float)P.n_bins) {
+        cnt.add(ST_CONN);
+        float c = p.beta * hg_eval(cos_s, P.hg_a, P.hg_b, P.hg_c) * __expf(-P.sigma_t * C) *
+                  emit_intensity(p, p.x, p.y, p.z) / C2;
+        if (!visible(P, p.x, p.y, p.z, p.ey0, p.ey1, p.ey2, -1)) c = 0.0f;
+        *out_bin = row + min((int)y, P.n_bins - 1);
+        *out_c = c;
+        p.c += c;
+      }
+      if (!(p.L + C < p.s_hi_e)) {
+        cnt.add(ST_EARLY);
+        record(P, p, 0, EV_EARLY);
+        return true;
+      }
+      if (p.k + 1 == P.K) {
+        record(P, p, 0, EV_MAXDEPTH);
+        return true;
+      }
+      record(P, p, 0, EV_SCATTER);
+    }
+    const U4 u1 = rng(P, p.j, (uint32_t)(p.k + 1), 1);
+    float sphi, cphi;
+    sincos_2pi(u01(u1.z), &sphi, &cphi);
+    float wx, wy, wz;
+    const float xh = u01(u1.y);
+    frame_dir(p.wx, p.wy, p.wz, hg_sample(P.g, xh), hg_sin(P.g, xh), sphi, cphi, &wx, &wy, &wz);
+    p.wx = wx;
+    p.wy = wy;
+    p.wz = wz;
+    p.k += 1;
+    return false;
   }
 
   __device__ static void record(const TraceParams& P, const Path& p, int slot, uint8_t val) {
@@ -282,11 +840,16 @@ struct Stepper {
       n -= half;
     }
     const float c_lo = row[lo], c_hi = row[lo + 1];
-    const float mu_eda = fmaf((float)lo + __fdividef(v1 - c_lo, c_hi - c_lo), P.inv_mu_scale, -1.0f);
+    const float fr = __fdividef(v1 - c_lo, c_hi - c_lo);
+    const float mu_eda = fmaf((float)lo + fr, P.inv_mu_scale, -1.0f);
+    // 1 -+ mu of the table sample from the bin index: no cancellation near +-1
+    const float st_eda = sqrtf(fmaxf(0.0f, ((float)(P.n_mu - lo) - fr) * P.inv_mu_scale *
+                                               (((float)lo + fr) * P.inv_mu_scale)));
     const float mu_hg = hg_sample(gb, v1);
+    const float st_hg = hg_sin(gb, v1);
     float wx, wy, wz;
-    frame_dir(eda ? ax : bx, eda ? ay : by, eda ? az : bz, eda ? mu_eda : mu_hg, sphi, cphi, &wx, &wy,
-              &wz);
+    frame_dir(eda ? ax : bx, eda ? ay : by, eda ? az : bz, eda ? mu_eda : mu_hg, eda ? st_eda : st_hg, sphi,
+              cphi, &wx, &wy, &wz);
     const float mu_b = eda ? fmaf(wx, bx, fmaf(wy, by, wz * bz)) : mu_hg;
     int bin = lo;
     if (!eda) {
@@ -366,6 +929,9 @@ struct Stepper {
     }
     record(P, p, 0, (uint8_t)(EV_SCATTER | nonempty));
     record(P, p, 1, (uint8_t)r.sel);
+    p.fixed = false;
+    p.nmed += 1;
+    p.surf = -1;
     p.beta *= r.factor;
     p.x = fmaf(p.wx, r.dsel, p.x);
     p.y = fmaf(p.wy, r.dsel, p.y);
@@ -513,7 +1079,8 @@ struct Stepper {
     float sphi, cphi;
     sincos_2pi(u01(u1.z), &sphi, &cphi);
     float wx, wy, wz;
-    frame_dir(p.wx, p.wy, p.wz, hg_sample(P.g, u01(u1.y)), sphi, cphi, &wx, &wy, &wz);
+    const float xh = u01(u1.y);
+    frame_dir(p.wx, p.wy, p.wz, hg_sample(P.g, xh), hg_sin(P.g, xh), sphi, cphi, &wx, &wy, &wz);
     p.wx = wx;
     p.wy = wy;
     p.wz = wz;
@@ -527,10 +1094,10 @@ struct Stepper {
 __device__ __forceinline__ void warp_commit(bool has, int bin, float val, float* wsum, float* wcomp,
                                             float* wsq, bool tile, const TraceParams& P,
                                             bool do_sq) {
-  if (!tile) {
+  if (!tile) {  // outputs zeroed before the launch
     if (has) {
-      atomicAdd(&P.acc[bin], (double)val);
-      if (do_sq) atomicAdd(&P.acc[P.n_bins + bin], (double)val * (double)val);
+      atomicAdd(&P.hist[bin], (double)val);
+      if (do_sq) atomicAdd(&P.sumsq[bin], (double)val * (double)val);
     }
     return;
   }
@@ -613,7 +1180,7 @@ __device__ __forceinline__ int add_mod(int a, int r, int B) {
 // warps claim path ids [*counter, N) in chunks of kPathChunk, refill lanes
 // whose path ended, run one vertex step per iteration and commit finished
 // paths into the warp tile (or the adjoint sums).
-template <int METHOD, int MAXM, bool DEBUG, bool TILE, bool ADJ>
+template <int METHOD, int MAXM, bool DEBUG, bool TILE, bool ADJ, bool GEN = false>
 __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab,
                                           unsigned long long* counter, unsigned long long N,
                                           float* wsum, float* wcomp, float* wsq, RisTask* wtasks,
@@ -637,7 +1204,8 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
       const int n_dead = __popc(dead);
       const unsigned long long avail = pool_end - pool_next;
       if (!alive && (unsigned long long)rank < avail) {
-        Stepper<METHOD, MAXM, DEBUG, ADJ>::init(P, p, pool_next + rank, add_mod(pool_bin, rank, B));
+        if constexpr (GEN) Stepper<METHOD, MAXM, DEBUG, ADJ, GEN>::init_gen(P, p, pool_next + rank);
+        else Stepper<METHOD, MAXM, DEBUG, ADJ, GEN>::init(P, p, pool_next + rank, add_mod(pool_bin, rank, B));
         alive = true;
       }
       if ((unsigned long long)n_dead > avail) {
@@ -652,8 +1220,9 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
           const int base_bin = (int)((P.bin_base + base) % (unsigned long long)B);
           const long long r2 = (long long)rank - (long long)avail;
           if (!alive && r2 >= 0 && (unsigned long long)r2 < end - base) {
-            Stepper<METHOD, MAXM, DEBUG, ADJ>::init(P, p, base + (unsigned long long)r2,
-                                               add_mod(base_bin, (int)r2, B));
+            if constexpr (GEN) Stepper<METHOD, MAXM, DEBUG, ADJ, GEN>::init_gen(P, p, base + (unsigned long long)r2);
+            else Stepper<METHOD, MAXM, DEBUG, ADJ, GEN>::init(P, p, base + (unsigned long long)r2,
+                                                         add_mod(base_bin, (int)r2, B));
             alive = true;
           }
           const int used = (int)min((unsigned long long)n_dead - avail, end - base);
@@ -671,28 +1240,39 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
     // ---- one vertex step
     cnt.bits = 0;
     bool fin = false;
-    int cbin = -1;
-    float cval = 0.0f;
+    int cbin = -1, cbin2 = -1;
+    float cval = 0.0f, cval2 = 0.0f;
     if (METHOD == kDarts) {
       RisTask task;
       bool need = false;
       if (alive) {
-        fin = Stepper<METHOD, MAXM, DEBUG, ADJ>::vertex_darts(P, p, tab, cnt, task);
-        need = !fin;
+        if constexpr (GEN) {
+          const int st = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN>::vertex_gen(P, p, tab, cnt, task);
+          fin = st == 1;
+          need = st == 0;
+        } else {
+          fin = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN>::vertex_darts(P, p, tab, cnt, task);
+          need = !fin;
+        }
       }
       RisResult r;
       if (kCoop) {
         ris_warp(P, need, task, wtasks, wresults, r, cnt);
       } else if (need) {
-        r = Stepper<METHOD, MAXM, DEBUG, ADJ>::ris_lane(P, task, cnt);
+        r = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN>::ris_lane(P, task, cnt);
       }
-      if (need) fin = Stepper<METHOD, MAXM, DEBUG, ADJ>::finish_ris(P, p, r, task.nonempty, cnt);
+      if (need) fin = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN>::finish_ris(P, p, r, task.nonempty, cnt);
       if (alive && fin) {
         cbin = p.bin;
         cval = P.wb * p.c;
       }
     } else if (alive) {
-      fin = Stepper<METHOD, MAXM, DEBUG, ADJ>::step_base(P, p, cnt, &cbin, &cval);
+      if constexpr (GEN) {
+        fin = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN>::step_base_gen(P, p, cnt, &cbin, &cval, &cbin2, &cval2);
+        cval2 *= P.wb;
+      } else {
+        fin = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN>::step_base(P, p, cnt, &cbin, &cval);
+      }
       cval *= P.wb;
     }
     if (cbin >= 0 && !isfinite(cval)) {
@@ -711,7 +1291,7 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
       if (DEBUG && p.j < P.N) {
         P.dbg_c[p.j] = p.c;
         P.dbg_b[p.j] = p.bin;
-        P.dbg_n[p.j] = p.k + 1;
+        P.dbg_n[p.j] = (GEN && p.miss) ? 0 : p.k + 1;
       }
     }
     if (ADJ) {
@@ -726,6 +1306,13 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
       }
     } else {
       warp_commit(has, cbin, cval, wsum, wcomp, wsq, TILE, P, do_sq);
+      if constexpr (GEN && METHOD == kPlain) {
+        if (cbin2 >= 0 && !isfinite(cval2)) {
+          atomicOr(P.status, 1u);
+          cval2 = 0.0f;
+        }
+        warp_commit(alive && cbin2 >= 0, cbin2, cval2, wsum, wcomp, wsq, TILE, P, do_sq);
+      }
     }
     if (fin) alive = false;
     // ---- event counts of this step (lane i keeps counter i of its warp)
@@ -742,7 +1329,7 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
 
 }
 
-template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK, bool ADJ = false>
+template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK, bool ADJ = false, bool GEN = false>
 __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
@@ -779,8 +1366,8 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
 
   // adjoint: per-lane Kahan sums of the weighted path scores and their squares
   float g_s[3] = {0.0f, 0.0f, 0.0f}, g_c[3] = {0.0f, 0.0f, 0.0f}, g_q[3] = {0.0f, 0.0f, 0.0f};
-  path_loop<METHOD, MAXM, DEBUG, TILE, ADJ>(P, tab, P.counter, P.N, wsum, wcomp, wsq, wtasks, wresults,
-                                            warp_events[warp], do_sq, g_s, g_c, g_q);
+  path_loop<METHOD, MAXM, DEBUG, TILE, ADJ, GEN>(P, tab, P.counter, P.N, wsum, wcomp, wsq, wtasks,
+                                                 wresults, warp_events[warp], do_sq, g_s, g_c, g_q);
 
   // ---- statistics
   __syncthreads();
@@ -854,20 +1441,17 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int b = threadIdx.x; b < B; b += BLOCK) {
-    double s = 0.0, q = 0.0;
-    if (TILE) {
+  if (TILE) {
+    for (int b = threadIdx.x; b < B; b += BLOCK) {
+      double s = 0.0, q = 0.0;
       for (unsigned g = 0; g < gridDim.x; ++g) {
         const double* pg = P.partials + (size_t)g * 2 * B;
         s += __ldcg(pg + b);
         q += __ldcg(pg + B + b);
       }
-    } else {
-      s = __ldcg(P.acc + b);
-      q = __ldcg(P.acc + B + b);
+      P.hist[b] = s;
+      if (P.sumsq) P.sumsq[b] = q;
     }
-    P.hist[b] = s;
-    if (P.sumsq) P.sumsq[b] = q;
   }
   if (threadIdx.x == 0) *P.ticket = 0u;
 }
@@ -976,9 +1560,9 @@ __global__ void philox_kernel(const uint32_t* ctr, uint32_t k0, uint32_t k1, uin
   out[4 * i + 3] = r.w;
 }
 
-template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK>
+template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK, bool GEN = false>
 cudaError_t launch_one(const TraceParams& p, int grid, size_t smem, cudaStream_t s) {
-  auto kern = trace_kernel<METHOD, MAXM, DEBUG, TILE, BLOCK>;
+  auto kern = trace_kernel<METHOD, MAXM, DEBUG, TILE, BLOCK, false, GEN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, BLOCK, smem, s>>>(p);
@@ -990,6 +1574,12 @@ cudaError_t launch_one(const TraceParams& p, int grid, size_t smem, cudaStream_t
 template <int METHOD>
 cudaError_t launch_method(const TraceParams& p, int grid, int block, bool debug, bool tile,
                           size_t smem, cudaStream_t s) {
+  if (p.general) {  // general scenes: 512 threads, M = 8
+    if (debug) return tile ? launch_one<METHOD, 8, true, true, 512, true>(p, grid, smem, s)
+                           : launch_one<METHOD, 8, true, false, 512, true>(p, grid, smem, s);
+    return tile ? launch_one<METHOD, 8, false, true, 512, true>(p, grid, smem, s)
+                : launch_one<METHOD, 8, false, false, 512, true>(p, grid, smem, s);
+  }
   const bool m8 = METHOD != kDarts || p.M == 8;
   if (debug) {
     if (!m8) return tile ? launch_one<METHOD, kMaxM, true, true, 512>(p, grid, smem, s)
@@ -1051,7 +1641,12 @@ size_t adjoint_smem_bytes(const TraceParams& p) {
 cudaError_t launch_adjoint(const TraceParams& p0, int grid, size_t smem, cudaStream_t s) {
   TraceParams p = p0;
   p.bin_base = (p0.path_offset + p0.o_e) % (unsigned long long)p0.n_bins;
-  if (p.M == 8) {
+  if (p.general) {
+    auto kern = trace_kernel<kDarts, 8, false, false, 512, true, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 512, smem, s>>>(p);
+  } else if (p.M == 8) {
     auto kern = trace_kernel<kDarts, 8, false, false, 512, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1074,8 +1669,8 @@ size_t trace_smem_bytes(int method, const TraceParams& p, int block, bool tile) 
 
 int trace_max_m() { return kMaxM; }
 
-int trace_block_for(int block, bool debug, bool tile, int method, int M) {
-  if (debug || !tile || (method == kDarts && M != 8)) return 512;
+int trace_block_for(int block, bool debug, bool tile, int method, int M, bool general) {
+  if (general || debug || !tile || (method == kDarts && M != 8)) return 512;
   return (block == 640 || block == 768) ? block : 512;
 }
 

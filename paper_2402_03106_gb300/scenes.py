@@ -259,3 +259,11 @@ def with_paths(sp: Sampling, n: int) -> Sampling:
 def total_paths(sc: Scene, sp: Sampling) -> int:
     """Number of paths one render call traces (every sensor element)."""
     return int(sp.paths_per_element) * sc.sensor.elements
+
+
+def histogram_shape(sc: Scene) -> Tuple[int, ...]:
+    """Shape of a render's output: [n_bins] for a point sensor,
+    [height, width, n_bins] for a pinhole camera."""
+    if sc.sensor.kind == SENSOR_PINHOLE:
+        return (int(sc.sensor.height), int(sc.sensor.width), int(sc.gate.n_bins))
+    return (int(sc.gate.n_bins),)

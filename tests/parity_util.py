@@ -1,0 +1,81 @@
+"""Per-path comparison of GPU decision traces with the oracle's (shared by the
+GPU parity tests)."""
+import numpy as np
+
+import oracle as O
+
+NEAR_TIE = 1e-3
+REL_PATH = 1e-4
+# FP32 relative error of path lengths and window bounds (about seven units
+# of 2^-24): a connection whose window S_hi - S_lo is narrow compared with
+# the length L + S_hi it is measured against carries that error magnified by
+# cond = (L + S_hi) / (S_hi - S_lo), the oracle's per-path conditioning number.
+COND_EPS = 4e-7
+
+
+def compare_paths(gpu, ref, K):
+    """Return (same_trace mask, rel error array, report dict)."""
+    gb = gpu["bin"].cpu().numpy()
+    gn = gpu["nvert"].cpu().numpy()
+    gd = gpu["decisions"].cpu().numpy()
+    gc = gpu["contrib"].cpu().numpy().astype(np.float64)
+    n = len(gb)
+    assert np.array_equal(gb, ref["bin"]), "bin assignment differs"
+    same = np.zeros(n, bool)
+    first_diff = np.full(n, -1)
+    for i in range(n):
+        nv = ref["nvert"][i]
+        if gn[i] == nv and np.array_equal(gd[i, :nv], ref["decisions"][i, :nv]):
+            same[i] = True
+        else:
+            m = min(gn[i], nv)
+            diff = np.nonzero(np.any(gd[i, :m] != ref["decisions"][i, :m], axis=1))[0]
+            first_diff[i] = diff[0] if len(diff) else m - 1
+    rc = ref["contrib"]
+    rel = np.abs(gc - rc) / np.maximum(np.abs(rc), 1e-300)
+    rel[(rc == 0) & (gc == 0)] = 0.0
+    flips = np.nonzero(~same)[0]
+    margins = np.array([ref["margin"][i, : first_diff[i] + 1].min() for i in flips]) if len(flips) else np.array([])
+    return same, rel, dict(flips=flips, margins=margins, first_diff=first_diff)
+
+
+def displaced_sensitivity(sc, sp, first, n, method, ref, shift=1e-6):
+    """Relative change of each path's FP64 contribution when the sensor (or
+    camera) and its look-at point move by `shift` (length units).
+
+    Paths that meet surfaces at grazing angles magnify any error of their
+    start point (each hit divides it by the cosine of incidence); FP32
+    arithmetic injects such errors at every vertex (a few units of 2^-24 of
+    the coordinates, i.e. of order 1e-6 over a path), so a path whose FP64
+    contribution moves by s under this displacement can differ by about s in
+    FP32 as well.  Returns s per path (0 where both are zero)."""
+    import copy
+    sc2 = copy.deepcopy(sc)
+    d = np.array([1.0, -0.7, 0.4]) * shift
+    sc2.sensor.pos = tuple(np.asarray(sc.sensor.pos, float) + d)
+    sc2.sensor.look_at = tuple(np.asarray(sc.sensor.look_at, float) + d)
+    r2 = O.trace_paths(sc2, sp, first, n, method=method)
+    c, c2 = ref["contrib"], r2["contrib"]
+    s = np.abs(c2 - c) / np.maximum(np.abs(c), 1e-300)
+    s[(c == 0) & (c2 == 0)] = 0.0
+    return s
+
+
+def check_paths(gpu, ref, K, rel_tol=REL_PATH, max_flip_frac=0.01, extra_tol=None):
+    same, rel, rep = compare_paths(gpu, ref, K)
+    n = len(same)
+    assert (~same).sum() <= max(2, max_flip_frac * n), f"{(~same).sum()} of {n} traces differ"
+    if len(rep["margins"]):
+        assert rep["margins"].max() < NEAR_TIE, f"trace flip away from a tie: {rep['margins']}"
+    nd = (ref["flags"] & O.FLAG_NEAR_DEGENERATE) != 0
+    ok = same & ~nd
+    tol = np.maximum(rel_tol, COND_EPS * ref["cond"])
+    if extra_tol is not None:
+        tol = np.maximum(tol, extra_tol)
+    bad = np.nonzero(ok & (rel > tol))[0]
+    assert len(bad) == 0, (f"{len(bad)} paths beyond their tolerance: rel {rel[bad][:5]}, "
+                           f"tol {tol[bad][:5]}, cond {ref['cond'][bad][:5]}")
+    # near-degenerate ellipses (S - C < 2^-12 C) depend on FP32 path state; bound them loosely
+    if np.any(same & nd):
+        assert rel[same & nd].max() < 1e-2
+    return same, rel
