@@ -1,18 +1,25 @@
 #!/usr/bin/env python3
 """Throughput benchmark of the DARTS hot path on GB300.
 
-One step = one pass of the whole path: the elliptical DA direction table is
-rebuilt on the GPU, then every path of the step is traced (DA-RIS distance
-sampling, EDA/MIS directions, elliptical control vertices) and accumulated
-into the time-bin histogram.  The workload is the unit-cube medium
-(sigma_s = 1, sigma_a = 0.01, g = 0.7; point emitter at (.5,.5,.1), point
-sensor at (.5,.5,.9); 256 bins on [0.8, 6); 50 bounces, 8 RIS candidates,
-16x8x256 table) with 2^24 paths per GPU per step.
+One step = one pass of the whole path over one frame of the workload: the
+elliptical DA direction table is rebuilt on the GPU, then every path of the
+frame is traced (DA-RIS distance sampling, EDA/MIS directions, elliptical
+control vertices, surface bounces) and accumulated into per-pixel time-bin
+histograms.
+
+Default workload (``--workload box_camera``): a 64x64 pinhole camera (40 deg
+FOV) views a 2x2x2 box with five Lambertian walls (albedo 0.5, the front
+face open) filled with a medium drawn from seed 0 (sigma_s U[0.5, 2], albedo
+U[0.9, 0.99], g U[0, 0.9]) and lit by a 0.3 x 0.3 Lambertian area pulse
+emitter on the ceiling; 512 bins on [0, 16); 16 paths per pixel (65536 per
+frame), 50 bounces, 8 RIS candidates, 16x8x256 direction table.
+``--workload cube`` is the unit-cube medium with point emitter and sensor at
+2^24 paths per step (the GPU saturated); the default run reports it too.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
 Under torchrun every rank traces its own path-id range (weak scaling) and the
-per-rank histograms are summed with one FP64 all-reduce per step.  The
+per-rank histograms are combined with one FP64 all-reduce per step.  The
 ``--impl reference`` arm times the FP64 CPU oracle on this host's cores on a
 bounded sample of the same workload.
 """
@@ -34,18 +41,29 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DARTS transient path samples/s on 1 GB300; MSE×time vs plain transient PT"
-PATHS_PER_GPU = 1 << 24
-WORKLOAD = ("unit-cube medium sigma_s=1 sigma_a=0.01 g=0.7 v=1; isotropic point pulse emitter "
-            "(0.5,0.5,0.1) t0=0; point fluence sensor (0.5,0.5,0.9); 256 bins on [0.8,6.0); "
-            "K=50 bounces, N_RIS=8, table 16x8x256; 2^24 paths per GPU per step")
+WORKLOADS = {
+    "box_camera": ("64x64 pinhole camera (FOV 40 deg) at (1,1,-2.5) viewing a 2x2x2 box, five Lambertian "
+                   "walls albedo 0.5 (front face open); medium from seed 0: sigma_s U[0.5,2], albedo "
+                   "U[0.9,0.99], g U[0,0.9]; 0.3x0.3 Lambertian area pulse emitter on the ceiling, t0=0; "
+                   "512 bins on [0,16); 16 spp (65536 paths per frame), K=50, N_RIS=8, table 16x8x256; "
+                   "one frame per GPU per step"),
+    "cube": ("unit-cube medium sigma_s=1 sigma_a=0.01 g=0.7 v=1; isotropic point pulse emitter "
+             "(0.5,0.5,0.1) t0=0; point fluence sensor (0.5,0.5,0.9); 256 bins on [0.8,6.0); "
+             "K=50 bounces, N_RIS=8, table 16x8x256; 2^24 paths per GPU per step"),
+}
 
 # Algorithmic FP32 work of the DARTS step (counted from the equations of the
 # stable formulation; add/sub/mul/compare/convert = 1, FMA = 2; special
-# functions counted separately as MUFU operations).
+# functions counted separately as MUFU operations).  The general kernel
+# (surfaces, camera, area emitters) adds the box slab test and the
+# medium/surface branch to every vertex and the control-vertex point and the
+# emitter cosine to every connection.
 FLOPS_PER_VERTEX = 120
 FLOPS_PER_CONNECTION = 80
 FLOPS_PER_CANDIDATE = 52
 FLOPS_PER_DISTANCE_STEP = 30
+FLOPS_PER_VERTEX_GEN = 150
+FLOPS_PER_CONNECTION_GEN = 95
 MUFU_PER_VERTEX = 10
 MUFU_PER_CONNECTION = 6
 MUFU_PER_CANDIDATE = 5
@@ -57,14 +75,28 @@ MUFU_PER_SM_CLK = 16
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 2000 camera frames, about 1 s; 60 cube steps)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--paths", type=int, default=PATHS_PER_GPU)
-    ap.add_argument("--no-mse", action="store_true", help="skip the MSE x time comparison")
+    ap.add_argument("--workload", default="box_camera", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-mse", action="store_true", help="skip the MSE x time comparisons")
     ap.add_argument("--only-timed", action="store_true",
                     help="run only the timed steps (for profiler launch lists)")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = 2000 if a.workload == "box_camera" else 60
+    return a
+
+
+def make_workload(name, S):
+    """(scene, sampling, paths per step) of a named workload."""
+    if name == "box_camera":
+        sc, sp = S.box_camera_workload(seed=0)
+    else:
+        sc, sp = S.cube_workload(paths=1 << 24, seed=0)
+    sp.flags |= S.FLAG_REBUILD_TABLE
+    return sc, sp, S.total_paths(sc, sp)
 
 
 # ----------------------------------------------------------------------------
@@ -93,7 +125,7 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
             time.sleep(0.3)
         except Exception:
@@ -138,10 +170,12 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(paths_per_launch: int):
-    """DRAM bytes per launch from the committed ncu summary of the trace
-    kernel, scaled to this launch, when it was taken on the current source."""
-    path = os.path.join(ROOT, "profiles", "darts_trace_kernel_cube.md")
+def profiled_traffic(workload: str, paths_per_launch: int):
+    """DRAM bytes per launch of the trace kernel from the committed ncu
+    summary of this workload, when it was taken on the current source; a
+    capture of a smaller launch is scaled by the paths when the summary says
+    its traffic grows with them."""
+    path = os.path.join(ROOT, "profiles", f"darts_trace_kernel_{workload}.md")
     try:
         text = open(path).read()
     except OSError:
@@ -149,26 +183,37 @@ def profiled_traffic(paths_per_launch: int):
     m_hash = re.search(r"source_hash:\s*([0-9a-f]+)", text)
     m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+-]+)", text)
     m_paths = re.search(r"paths_per_launch:\s*([0-9]+)", text)
+    m_scale = re.search(r"traffic_scales_with_paths:\s*(yes|no)", text)
     if not (m_hash and m_bytes and m_paths) or m_hash.group(1) != kernel_source_hash():
         return None
-    # the DRAM traffic is the fixed table staging and block partials: it does
-    # not grow with the number of paths, so it is reported as captured
-    return float(m_bytes.group(1))
+    v = float(m_bytes.group(1))
+    if m_scale and m_scale.group(1) == "yes":
+        v *= paths_per_launch / float(m_paths.group(1))
+    return v
 
 
 # ----------------------------------------------------------------------------
-def cpu_baseline(paths: int = 1 << 23):
+def cpu_baseline(workload: str, budget_s: float = 12.0):
+    """The FP64 oracle, as it stands, on this host's cores: whole frames (or
+    2^22-path batches of the cube) of the benchmark workload until about
+    budget_s of CPU time has passed."""
     import oracle as O
     from paper_2402_03106_gb300 import scenes as S
-    sc, sp = S.cube_workload(paths=paths, seed=0)
+    sc, sp, n = make_workload(workload, S)
+    if workload == "cube":
+        n = 1 << 22
     cores = os.cpu_count() or 1
     cdf = O.build_table(sc, sp)
-    t0 = time.perf_counter()
-    O.render(sc, sp, O.ORC_DARTS, cdf=cdf, threads=cores)
-    dt = time.perf_counter() - t0
-    return {"value": paths / dt, "unit": "paths/s", "cores": cores, "kind": "oracle",
-            "sample": f"{paths} paths of the benchmark workload (table prebuilt), FP64 C oracle, "
-                      f"{cores} POSIX threads, {dt:.2f} s wall"}
+    done, t_tot = 0, 0.0
+    while t_tot < budget_s and done < 64:
+        t0 = time.perf_counter()
+        O.render(sc, sp, O.ORC_DARTS, n_paths=n, offset=done * n, cdf=cdf, threads=cores)
+        t_tot += time.perf_counter() - t0
+        done += 1
+    unit = "frames" if workload == "box_camera" else f"batches of {n} paths"
+    return {"value": done * n / t_tot, "unit": "paths/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} {unit} of the benchmark workload ({done * n} paths, table prebuilt), "
+                      f"FP64 C oracle, {cores} POSIX threads, {t_tot:.2f} s wall"}
 
 
 def run_reference(args):
@@ -178,27 +223,27 @@ def run_reference(args):
     import oracle as O
     from paper_2402_03106_gb300 import scenes as S
     cores = os.cpu_count() or 1
-    sample = 1 << 18
-    sc, sp = S.cube_workload(paths=sample, seed=0)
+    sc, sp, n = make_workload(args.workload, S)
+    sample = n // 16 if args.workload == "box_camera" else 1 << 18
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         cdf = O.build_table(sc, sp)
-        O.render(sc, sp, O.ORC_DARTS, cdf=cdf, threads=cores, offset=i * sample)
+        O.render(sc, sp, O.ORC_DARTS, n_paths=sample, cdf=cdf, threads=cores, offset=i * sample)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
     tot = sum(times)
     value = sample * len(times) / tot
+    what = (f"{sample} paths per step (1/16 of a frame: 256 pixels x 16 spp, bounded CPU sample)"
+            if args.workload == "box_camera" else f"{sample} paths per step (bounded CPU sample)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "paths/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD.replace("2^24 paths per GPU per step",
-                                                    f"{sample} paths per step (bounded CPU sample)")},
+            "config": {"workload": WORKLOADS[args.workload], "reference_sample": what},
             "cpu_baseline": {"value": value, "unit": "paths/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{sample} paths per step incl. the table build, "
-                                       f"{cores} POSIX threads"},
+                             "sample": f"{what} incl. the table build, {cores} POSIX threads"},
             "e2e": {"value": value, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -264,6 +309,50 @@ def mse_time(ctx, S, torch, n_paths=1 << 20, seeds=16):
     return out
 
 
+def mse_time_camera(ctx, S, torch, seeds=16, spps=(16, 64)):
+    """Config-2 comparison: the walled box seen by the 64x64 camera (512 bins),
+    DARTS against the plain uniform-temporal tracer and the vanilla
+    direct-connection tracer, 16 seeds per method and sample count.  MSE per
+    render against the pooled mean of every DARTS and plain render (all
+    pixels and bins); ratio = (MSE x time)_base / (MSE x time)_darts with the
+    median render time (table build + trace, CUDA events)."""
+    sc = S.box_camera_scene(seed=0)
+    methods = (("darts", S.DARTS), ("plain_uniform_t", S.PLAIN_UNIFORM_T), ("vanilla_direct", S.VANILLA_DIRECT))
+    out = {"workload": "box camera of the benchmark, 64x64, 512 bins, K=50", "seeds": seeds}
+    for spp in spps:
+        H, T = {}, {}
+        for name, m in methods:
+            acc, ts = [], []
+            for s_ in range(seeds):
+                sp = S.Sampling(seed=101 + s_, paths_per_element=spp, max_bounces=50, method=m,
+                                flags=S.FLAG_REBUILD_TABLE if m == S.DARTS else 0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                h = ctx.render(sc, sp)
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1) * 1e-3)
+                acc.append(h.reshape(-1).float())
+            H[name] = torch.stack(acc)
+            T[name] = statistics.median(ts)
+        ref = torch.cat([H["darts"], H["plain_uniform_t"]]).double().mean(0).float()
+        res = {}
+        for name, _ in methods:
+            d = H[name] - ref
+            mse = (d * d).double().mean(1)
+            res[name] = {"seconds_per_render": T[name], "mse_mean": float(mse.mean()),
+                         "mse_median": float(mse.median())}
+        for base in ("plain_uniform_t", "vanilla_direct"):
+            res[f"ratio_{base}_over_darts"] = {
+                "mse_mean_time": (res[base]["mse_mean"] * res[base]["seconds_per_render"]) /
+                                 max(res["darts"]["mse_mean"] * res["darts"]["seconds_per_render"], 1e-300),
+                "mse_median_time": (res[base]["mse_median"] * res[base]["seconds_per_render"]) /
+                                   max(res["darts"]["mse_median"] * res["darts"]["seconds_per_render"], 1e-300)}
+        out[f"spp_{spp}"] = res
+        del H
+    return out
+
+
 def batched_compare(ctx, S, torch, reps=5):
     """256 independent slab media with uneven budgets (2^U[12,20] paths,
     128 bins): one graph-captured persistent launch vs one launch per medium."""
@@ -301,6 +390,48 @@ def batched_compare(ctx, S, torch, reps=5):
                         "g U[-0.3,0.9], side U[0.5,4], budgets 2^U[12,20], 128 bins, K=50, M=8"}
 
 
+def time_steps(ctx, torch, step, steps, flush, kernel_timing=True):
+    """CUDA-event time of each step (L2 flushed before each), the path
+    kernel's own time and the summed event counts."""
+    step_ms, kern_ms, stats_acc = [], [], {}
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        if kernel_timing:
+            kern_ms.append(ctx.last_kernel_ms())
+        for k, v in ctx.stats().items():
+            stats_acc[k] = stats_acc.get(k, 0) + v
+    return step_ms, kern_ms, {k: v / steps for k, v in stats_acc.items()}
+
+
+def roofline(per, kms, general, workload, paths):
+    """Algorithmic FP32 work of one launch of the path kernel over its
+    measured duration, against the FP32 pipe peak derived from the SM count,
+    lanes and the measured maximum clock."""
+    fv = FLOPS_PER_VERTEX_GEN if general else FLOPS_PER_VERTEX
+    fc = FLOPS_PER_CONNECTION_GEN if general else FLOPS_PER_CONNECTION
+    flops = (fv * per["vertices"] + fc * per["connections_nonempty"]
+             + (FLOPS_PER_DISTANCE_STEP + 8 * FLOPS_PER_CANDIDATE) * per["distance_steps"])
+    mufu = (MUFU_PER_VERTEX * per["vertices"] + MUFU_PER_CONNECTION * per["connections_nonempty"]
+            + 8 * MUFU_PER_CANDIDATE * per["distance_steps"])
+    clock_mhz = measured_peaks().get("sm_max_mhz", 2070.0)
+    peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
+    peak_mufu = SM_COUNT * MUFU_PER_SM_CLK * clock_mhz * 1e6 / 1e12
+    achieved = flops / (kms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+            "frac": achieved / peak_fp32, "traffic": profiled_traffic(workload, paths),
+            "kernel": "trace_kernel<DARTS%s> (persistent path kernel)" % (", general" if general else ""),
+            "kernel_ms": kms, "flops_per_launch": flops,
+            "peak_note": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clock_mhz:.0f} MHz",
+            "mufu_achieved_tops": mufu / (kms * 1e-3) / 1e12, "mufu_peak_tops": peak_mufu,
+            "mufu_frac": mufu / (kms * 1e-3) / 1e12 / peak_mufu, "events_per_launch": per}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -309,7 +440,7 @@ def main():
     import torch
     import __graft_entry__ as g
     g.build()
-    from paper_2402_03106_gb300 import capi, scenes as S
+    from paper_2402_03106_gb300 import capi, scenes as S, sharding
 
     torch.cuda.set_device(local)
     pg = None
@@ -318,13 +449,10 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
     ctx = capi.Context(local)
-    sc, _ = S.cube_workload()
-    N = args.paths
-    sp = S.Sampling(seed=0, paths_per_element=N, flags=S.FLAG_REBUILD_TABLE)
-    B = sc.gate.n_bins
-    hist = torch.zeros(B, dtype=torch.float64, device="cuda")
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MiB > L2
-    from paper_2402_03106_gb300 import sharding
+    sc, sp, N = make_workload(args.workload, S)
+    general = args.workload == "box_camera"
+    hist = torch.zeros(S.histogram_shape(sc), dtype=torch.float64, device="cuda")
     offset = sharding.path_offset(rank, N)
 
     def step():
@@ -341,20 +469,8 @@ def main():
     if pg is not None:
         pg.barrier()
     torch.cuda.synchronize()
-    step_ms, kern_ms = [], []
-    stats_acc = {}
     wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        step()
-        e1.record()
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        kern_ms.append(ctx.last_kernel_ms())
-        for k, v in ctx.stats().items():
-            stats_acc[k] = stats_acc.get(k, 0) + v
+    step_ms, kern_ms, per = time_steps(ctx, torch, step, args.steps, flush)
     torch.cuda.synchronize()
     if pg is not None:
         pg.barrier()
@@ -373,56 +489,19 @@ def main():
         if pg is not None:
             pg.destroy_process_group()
         return 0
-
-    # ---- roofline of the dominant kernel (the persistent path kernel)
     K = args.steps
-    per = {k: v / K for k, v in stats_acc.items()}
-    flops = (FLOPS_PER_VERTEX * per["vertices"] + FLOPS_PER_CONNECTION * per["connections_nonempty"]
-             + (FLOPS_PER_DISTANCE_STEP + 8 * FLOPS_PER_CANDIDATE) * per["distance_steps"])
-    mufu = (MUFU_PER_VERTEX * per["vertices"] + MUFU_PER_CONNECTION * per["connections_nonempty"]
-            + 8 * MUFU_PER_CANDIDATE * per["distance_steps"])
     kms = statistics.fmean(kern_ms)
-    clock_mhz = measured_peaks().get("sm_max_mhz", 2070.0)
-    peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
-    peak_mufu = SM_COUNT * MUFU_PER_SM_CLK * clock_mhz * 1e6 / 1e12
-    achieved = flops / (kms * 1e-3) / 1e12
-    traffic = profiled_traffic(N)
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-            "frac": achieved / peak_fp32, "traffic": traffic,
-            "kernel": "trace_kernel<DARTS> (persistent path kernel)",
-            "kernel_ms": kms, "flops_per_launch": flops,
-            "peak_note": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clock_mhz:.0f} MHz",
-            "mufu_achieved_tops": mufu / (kms * 1e-3) / 1e12, "mufu_peak_tops": peak_mufu,
-            "mufu_frac": mufu / (kms * 1e-3) / 1e12 / peak_mufu,
-            "events_per_launch": per}
-
+    roof = roofline(per, kms, general, args.workload, N)
     if args.only_timed:
         print(json.dumps({"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws,
                           "steps": K, "warmup": args.warmup, "ms_per_step": t_step,
-                          "roofline": roof, "block": tuned_block, "note": "timed steps only"}),
-              flush=True)
+                          "workload": args.workload, "roofline": roof, "block": tuned_block,
+                          "note": "timed steps only"}), flush=True)
         ctx.close()
         return 0
 
-    # ---- as configured: 2^16 paths per render (latency-bound)
-    sp16 = S.Sampling(seed=0, paths_per_element=1 << 16, flags=S.FLAG_REBUILD_TABLE)
-    for _ in range(3):
-        ctx.render(sc, sp16)
-    torch.cuda.synchronize()
-    t16 = []
-    for _ in range(20):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        ctx.render(sc, sp16)
-        e1.record()
-        e1.synchronize()
-        t16.append(e0.elapsed_time(e1))
-    as_conf = {"paths": 1 << 16, "ms_per_render": statistics.median(t16),
-               "paths_per_s": (1 << 16) / (statistics.median(t16) * 1e-3)}
-
     # ---- end to end through the C ABI with host buffers
-    hh = torch.zeros(B, dtype=torch.float64).pin_memory()
+    hh = torch.zeros(S.histogram_shape(sc), dtype=torch.float64).pin_memory()
     ne = max(3, min(args.steps, 20))
     ctx.render_host(sc, sp, hh)
     te = time.perf_counter()
@@ -431,28 +510,59 @@ def main():
     te = time.perf_counter() - te
     cs, keep = capi.to_c_scene(sc)
     import ctypes
-    h2d = ctypes.sizeof(cs) + ctypes.sizeof(capi.darts_sampling) + ctypes.sizeof(capi.darts_emitter)
+    h2d = (ctypes.sizeof(cs) + ctypes.sizeof(capi.darts_sampling)
+           + len(sc.emitters) * ctypes.sizeof(capi.darts_emitter) + 40 * len(sc.geometry.spheres))
     e2e = {"value": N * ne / te, "unit": "paths/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": B * 8,
+           "d2h_bytes_per_step": hh.numel() * 8,
            "note": "darts_render_host: scene/sampling structs marshalled into the launches, "
-                   "histogram copied back to pinned host memory, stream synchronised per step"}
+                   "histograms copied back to pinned host memory, stream synchronised per step"}
 
-    mse = None if args.no_mse else mse_time(ctx, S, torch)
-    batched = batched_compare(ctx, S, torch)
-    cpu = cpu_baseline() if ws == 1 else None
+    extra = {}
+    # ---- the other workload: the saturated cube (2^24 paths) or the camera frame
+    other = "cube" if args.workload == "box_camera" else "box_camera"
+    sc2, sp2, N2 = make_workload(other, S)
+    h2 = torch.zeros(S.histogram_shape(sc2), dtype=torch.float64, device="cuda")
+    ctx.autotune(sc2, sp2)
+    for _ in range(3):
+        ctx.render(sc2, sp2, out=h2)
+    torch.cuda.synchronize()
+    ctx.set_kernel_timing(True)
+    s2, k2, per2 = time_steps(ctx, torch, lambda: ctx.render(sc2, sp2, out=h2), 20, flush)
+    ctx.set_kernel_timing(False)
+    t2 = statistics.fmean(s2)
+    extra[other] = {"workload": WORKLOADS[other], "paths_per_step": N2, "ms_per_step": t2,
+                    "paths_per_s": N2 / (t2 * 1e-3),
+                    "roofline": roofline(per2, statistics.fmean(k2), other == "box_camera", other, N2)}
+
+    # ---- the cube as configured: 2^16 paths per render (latency-bound)
+    sc16, sp16 = S.cube_workload(paths=1 << 16, seed=0)
+    sp16.flags |= S.FLAG_REBUILD_TABLE
+    for _ in range(3):
+        ctx.render(sc16, sp16)
+    torch.cuda.synchronize()
+    t16, _, _ = time_steps(ctx, torch, lambda: ctx.render(sc16, sp16), 20, flush, kernel_timing=False)
+    extra["cube_as_configured_2e16"] = {"paths": 1 << 16, "ms_per_render": statistics.median(t16),
+                                        "paths_per_s": (1 << 16) / (statistics.median(t16) * 1e-3)}
+    ctx.set_launch(0)
+
+    if not args.no_mse:
+        extra["mse_time_box_camera"] = mse_time_camera(ctx, S, torch)
+        extra["mse_time_cube"] = mse_time(ctx, S, torch)
+    extra["batched"] = batched_compare(ctx, S, torch)
+    cpu = cpu_baseline(args.workload) if ws == 1 else None
 
     line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws, "steps": K,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "paths_per_gpu_per_step": N,
+            "config": {"workload": WORKLOADS[args.workload], "paths_per_gpu_per_step": N,
                        "block": tuned_block, "grid": "one CTA per SM (persistent)",
                        "l2": "256 MiB buffer written between timed steps (flush)",
                        "parallelism": f"path-id shards x{ws}, FP64 histogram all-reduce" if ws > 1
                        else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 2 * K,
-            "clocks": clk, "wall_s_timed_region": wall,
-            "as_configured_2e16": as_conf, "mse_time": mse, "batched": batched}
+            "clocks": clk, "wall_s_timed_region": wall}
+    line.update(extra)
     print(json.dumps(line), flush=True)
     ctx.close()
     if pg is not None:

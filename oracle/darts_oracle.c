@@ -797,16 +797,18 @@ void orc_sample_emitter(const orc_scene* sc, uint64_t id, const double q[3], dou
 }
 
 /* Sensor elements: the point sensor is element 0 and path id j; the camera's
- * pixel p owns ids p * N_e ... p * N_e + N_e - 1 (ids beyond the last pixel wrap
- * around to pixel 0, so shards of a larger render keep the layout).  A DARTS
- * path is dedicated to bin (j + o_e) mod B with o_e drawn once per element
- * (Sec. 6.2: every frame gets the same number of paths, each path serves one
- * frame). */
+ * pixel p owns ids p * N_e ... p * N_e + N_e - 1 with sample indices j = 0 ..
+ * N_e - 1; ids beyond the last pixel wrap around to pixel 0 with j
+ * continuing (N_e, N_e + 1, ...), so the shards of a larger render keep the
+ * layout and cover further bins.  A DARTS path is dedicated to bin
+ * (j + o_e) mod B with o_e drawn once per element (Sec. 6.2: every frame gets
+ * the same number of paths, each path serves one frame). */
 static void path_element(const orc_scene* sc, uint64_t id, int* elem, uint64_t* j) {
   if (sc->sensor_kind == 1) {
     uint64_t e = id / sc->paths_per_element;
-    *elem = (int)(e % ((uint64_t)sc->width * (uint64_t)sc->height));
-    *j = id % sc->paths_per_element;
+    uint64_t pixels = (uint64_t)sc->width * (uint64_t)sc->height;
+    *elem = (int)(e % pixels);
+    *j = (e / pixels) * sc->paths_per_element + id % sc->paths_per_element;
   } else {
     *elem = 0;
     *j = id;

@@ -87,6 +87,7 @@ struct TraceParams {
   unsigned long long bin_base;     // (path_offset + o_e) mod n_bins: bin of local path 0
   unsigned long long N;            // paths in this launch (local index 0..N-1)
   unsigned long long path_offset;  // global id = path_offset + local index
+  unsigned int chunk;              // paths a warp claims per counter update (0: kPathChunk)
   float wb;                        // weight per path contribution (DARTS n_bins/N_e, else 1/N_e)
   // outputs and scratch
   double* hist;                    // [elements][n_bins]; zeroed before a launch without tiles

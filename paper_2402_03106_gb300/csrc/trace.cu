@@ -25,6 +25,7 @@
 // its end, into a warp-private Kahan tile in shared memory; baseline paths
 // commit each contribution to the bin of its time.  Tiles are reduced in FP64
 // per block; the last block to finish sums the block partials in fixed order.
+#include <algorithm>
 #include <cfloat>
 
 #include "darts_device.cuh"
@@ -351,10 +352,12 @@ struct Stepper {
     const int B = P.n_bins;
     unsigned long long s = gid;
     p.elem = 0;
-    if (P.camera) {
+    if (P.camera) {  // sample s of pixel elem; ids past the last pixel wrap with s continuing
       const unsigned long long e = gid / P.spp;
-      s = gid - e * P.spp;
-      p.elem = (int)(e % (unsigned long long)(P.width * P.height));
+      const unsigned long long pixels = (unsigned long long)(P.width * P.height);
+      const unsigned long long wrap = e / pixels;
+      s = wrap * P.spp + (gid - e * P.spp);
+      p.elem = (int)(e - wrap * pixels);
     }
     p.j = j;
     p.L = p.Lc = p.c = 0.0f;
@@ -1189,6 +1192,7 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
   const int lane = threadIdx.x & 31;
   const int B = P.n_bins;
   constexpr bool kCoop = METHOD == kDarts && MAXM == 8;
+  const unsigned long long chunk = P.chunk ? P.chunk : (unsigned long long)kPathChunk;
   Counters cnt;
   Path p;
   bool alive = false;
@@ -1210,13 +1214,13 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
       }
       if ((unsigned long long)n_dead > avail) {
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(counter, (unsigned long long)kPathChunk);
+        if (lane == 0) base = atomicAdd(counter, chunk);
         base = __shfl_sync(kFull, base, 0);
         if (base >= N) {
           drained = true;
           pool_next = pool_end = 0;
         } else {
-          const unsigned long long end = min(base + (unsigned long long)kPathChunk, N);
+          const unsigned long long end = min(base + chunk, N);
           const int base_bin = (int)((P.bin_base + base) % (unsigned long long)B);
           const long long r2 = (long long)rank - (long long)avail;
           if (!alive && r2 >= 0 && (unsigned long long)r2 < end - base) {
@@ -1560,11 +1564,23 @@ __global__ void philox_kernel(const uint32_t* ctr, uint32_t k0, uint32_t k1, uin
   out[4 * i + 3] = r.w;
 }
 
+// Paths a warp claims at a time: kPathChunk, or fewer when the launch has
+// fewer than kPathChunk paths per resident warp, so that a small launch
+// (one camera frame) spreads over every warp instead of giving some lanes
+// two paths in a row while other warps idle.
+unsigned int chunk_for(unsigned long long N, int grid, int block) {
+  const unsigned long long warps = (unsigned long long)grid * (block / 32);
+  const unsigned long long per = warps ? (N + warps - 1) / warps : kPathChunk;
+  return (unsigned int)std::max<unsigned long long>(1, std::min<unsigned long long>(per, kPathChunk));
+}
+
 template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK, bool GEN = false>
-cudaError_t launch_one(const TraceParams& p, int grid, size_t smem, cudaStream_t s) {
+cudaError_t launch_one(const TraceParams& p0, int grid, size_t smem, cudaStream_t s) {
   auto kern = trace_kernel<METHOD, MAXM, DEBUG, TILE, BLOCK, false, GEN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  TraceParams p = p0;
+  p.chunk = chunk_for(p.N, grid, BLOCK);
   kern<<<grid, BLOCK, smem, s>>>(p);
   return cudaGetLastError();
 }
@@ -1641,6 +1657,7 @@ size_t adjoint_smem_bytes(const TraceParams& p) {
 cudaError_t launch_adjoint(const TraceParams& p0, int grid, size_t smem, cudaStream_t s) {
   TraceParams p = p0;
   p.bin_base = (p0.path_offset + p0.o_e) % (unsigned long long)p0.n_bins;
+  p.chunk = chunk_for(p.N, grid, 512);
   if (p.general) {
     auto kern = trace_kernel<kDarts, 8, false, false, 512, true, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

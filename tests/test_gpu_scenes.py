@@ -174,3 +174,16 @@ def test_invalid_general_scenes_are_rejected(ctx):
     for b in bad:
         with pytest.raises(capi.DartsError):
             ctx.render(b, S.Sampling(paths_per_element=4))
+
+
+def test_camera_shards_continue_the_sample_index(ctx):
+    """A render at path offset N (one whole frame further) is the oracle's
+    second frame: pixel layout kept, sample indices (and DARTS bins) continued."""
+    sc = S.box_camera_scene(seed=2, width=8, height=8, n_bins=64)
+    sp = S.Sampling(seed=4, paths_per_element=8, max_bounces=10)
+    n = 8 * 64
+    h = ctx.render(sc, sp, path_offset=n).cpu().numpy().reshape(-1)
+    ref, _, _ = O.render(sc, sp, O.ORC_DARTS, n_paths=n, offset=n)
+    assert np.linalg.norm(h - ref) <= 1e-3 * np.linalg.norm(ref)
+    h0 = ctx.render(sc, sp).cpu().numpy().reshape(-1)
+    assert not np.allclose(h0, h)

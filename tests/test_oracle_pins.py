@@ -543,3 +543,16 @@ def test_estimators_agree_with_surfaces_and_camera(scene):
     (hd, sd), (hp, spp), (hv, sv) = res
     assert abs(hd - hp) < 4.5 * math.sqrt(sd ** 2 + spp ** 2), res
     assert abs(hv - hp) < 4.5 * math.sqrt(sv ** 2 + spp ** 2), res
+
+
+def test_camera_ids_wrap_with_continuing_sample_index():
+    """Ids one frame apart fall on the same pixel with DARTS bins N_e apart
+    (mod B): shards of a camera render cover further bins, not the same ones."""
+    sc = S.box_camera_scene(seed=0, width=4, height=2, n_bins=32)
+    sp = S.Sampling(seed=3, paths_per_element=5, max_bounces=2)
+    n = 5 * 8
+    a = O.trace_paths(sc, sp, 0, n)
+    b = O.trace_paths(sc, sp, n, n)
+    B = 32
+    assert np.array_equal(a["bin"] // B, b["bin"] // B)          # same pixels
+    assert np.array_equal((a["bin"] % B + 5) % B, b["bin"] % B)  # bins shifted by N_e
