@@ -353,6 +353,50 @@ def mse_time_camera(ctx, S, torch, seeds=16, spps=(16, 64)):
     return out
 
 
+def mse_time_gated(ctx, S, torch, seeds=16, spp=64):
+    """Time-gated rendering (one gate, one bin), the regime of the paper's
+    time-gated experiments: the walled box seen by the 64x64 camera, gates of
+    width w centred at t, DARTS against the uniform-temporal and vanilla
+    tracers.  MSE per render against the pooled mean of the DARTS and
+    uniform-temporal renders; ratio = (MSE x time)_base / (MSE x time)_darts."""
+    out = {"workload": "box camera of the benchmark, 64x64, one gate bin, K=100", "seeds": seeds, "spp": spp}
+    methods = (("darts", S.DARTS), ("plain_uniform_t", S.PLAIN_UNIFORM_T), ("vanilla_direct", S.VANILLA_DIRECT))
+    cases = [(6.125, 0.25), (10.125, 0.25), (8.0, 0.0625), (8.0, 1.0), (8.0, 4.0)]
+    for centre, width in cases:
+        sc = S.box_camera_scene(seed=0, n_bins=1, t_max=centre + width / 2)
+        sc.gate.t_min = centre - width / 2
+        H, T = {}, {}
+        for name, m in methods:
+            acc, ts = [], []
+            for s_ in range(seeds):
+                sp = S.Sampling(seed=301 + s_, paths_per_element=spp, max_bounces=100, method=m,
+                                flags=S.FLAG_REBUILD_TABLE if m == S.DARTS else 0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                h = ctx.render(sc, sp)
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1) * 1e-3)
+                acc.append(h.reshape(-1))
+            H[name] = torch.stack(acc)
+            T[name] = statistics.median(ts)
+        ref = torch.cat([H["darts"], H["plain_uniform_t"]]).mean(0)
+        res = {"gate": [centre - width / 2, centre + width / 2], "mean_signal": float(ref.mean())}
+        for name, _ in methods:
+            d = H[name] - ref
+            mse = (d * d).mean(1)
+            res[name] = {"seconds_per_render": T[name], "mse_mean": float(mse.mean()),
+                         "mse_median": float(mse.median())}
+        for base in ("plain_uniform_t", "vanilla_direct"):
+            res[f"ratio_{base}_over_darts"] = {
+                "mse_mean_time": (res[base]["mse_mean"] * res[base]["seconds_per_render"]) /
+                                 max(res["darts"]["mse_mean"] * res["darts"]["seconds_per_render"], 1e-300),
+                "mse_median_time": (res[base]["mse_median"] * res[base]["seconds_per_render"]) /
+                                   max(res["darts"]["mse_median"] * res["darts"]["seconds_per_render"], 1e-300)}
+        out[f"gate_{centre - width / 2:g}_{centre + width / 2:g}"] = res
+    return out
+
+
 def batched_compare(ctx, S, torch, reps=5):
     """256 independent slab media with uneven budgets (2^U[12,20] paths,
     128 bins): one graph-captured persistent launch vs one launch per medium."""
@@ -547,6 +591,7 @@ def main():
 
     if not args.no_mse:
         extra["mse_time_box_camera"] = mse_time_camera(ctx, S, torch)
+        extra["mse_time_gated"] = mse_time_gated(ctx, S, torch)
         extra["mse_time_cube"] = mse_time(ctx, S, torch)
     extra["batched"] = batched_compare(ctx, S, torch)
     cpu = cpu_baseline(args.workload) if ws == 1 else None

@@ -26,7 +26,7 @@ import numpy as np
 
 from . import build as _build
 
-ORC_DARTS, ORC_PLAIN_UNIFORM_T, ORC_VANILLA_DIRECT = 0, 1, 2
+ORC_DARTS, ORC_PLAIN_UNIFORM_T, ORC_VANILLA_DIRECT, ORC_DARTS_FULL_GATE = 0, 1, 2, 3
 EV_NONE, EV_EARLY, EV_SCATTER, EV_ESCAPE, EV_INVALID, EV_MAXDEPTH = range(6)
 FLAG_NEAR_DEGENERATE, FLAG_SMALL_TPRIME = 1, 2
 
@@ -253,7 +253,7 @@ def table_row(scene, sampling, Cd, SM):
 def trace_paths(scene, sampling, first, count, method=ORC_DARTS, cdf=None):
     """Per-path records for path ids first..first+count-1."""
     s = make_scene(scene, sampling)
-    if method == ORC_DARTS and cdf is None:
+    if method in (ORC_DARTS, ORC_DARTS_FULL_GATE) and cdf is None:
         cdf = build_table(scene, sampling)
     K = s.max_bounces
     out = dict(
@@ -328,7 +328,7 @@ def render(scene, sampling, method=ORC_DARTS, n_paths=None, offset=0, threads=No
     s = make_scene(scene, sampling)
     elements = s.width * s.height if s.sensor_kind == 1 else 1
     n = sampling.paths_per_element * elements if n_paths is None else n_paths
-    if method == ORC_DARTS and cdf is None:
+    if method in (ORC_DARTS, ORC_DARTS_FULL_GATE) and cdf is None:
         cdf = build_table(scene, sampling)
     threads = threads or (os.cpu_count() or 1)
     hist = np.zeros(s.n_bins * elements)

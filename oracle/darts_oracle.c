@@ -845,21 +845,31 @@ static double surface_albedo(const orc_scene* sc, int kind) {
   return kind == 1 ? sc->wall_albedo : sc->spheres[kind - 2][4];
 }
 
+static int time_bin(const orc_scene* sc, double T, path_rec* pr, int k);
+static void emit(path_rec* pr, int b, double c);
+
+/* A DARTS path (Sec. 4-5).  With full = 0 the path is dedicated to one time
+ * bin [T_m, T_M) of its sensor element (Sec. 6.2) and adds its summed
+ * contribution there.  With full = 1 ("full-gate" variant) the same samplers
+ * target the whole gate [t_min, t_max): every control vertex and surface
+ * connection lands in the bin of its own time, like the uniform-temporal
+ * tracer, with weight 1/N_e instead of B/N_e. */
 static void trace_darts(const orc_scene* sc, const double* cdf, uint64_t id, path_rec* pr,
-                        const double* dLdh, double grad[3]) {
+                        const double* dLdh, double grad[3], int full) {
   int K = sc->max_bounces, B = sc->n_bins;
   double dt = (sc->t_max - sc->t_min) / B;
   int elem;
   uint64_t j;
   path_element(sc, id, &elem, &j);
-  int b = darts_bin(sc, elem, j);
+  int b = full ? 0 : darts_bin(sc, elem, j);
   emit_pt E;
   pick_emitter(sc, id, &E);
   pr->E = &E;
   pr->elem = elem;
-  pr->bin = elem * B + b;  /* flat histogram index */
+  pr->bin = full ? -1 : elem * B + b;  /* flat histogram index */
   pr->contrib = 0.0;
-  double Tm = sc->t_min + b * dt, TM = sc->t_min + (b + 1) * dt;
+  double Tm = full ? sc->t_min : sc->t_min + b * dt;
+  double TM = full ? sc->t_max : sc->t_min + (b + 1) * dt;
   double x[3], w[3], L;
   int fixed;
   if (!path_start(sc, id, elem, x, w, &L, &fixed)) return;
@@ -898,7 +908,11 @@ static void trace_darts(const orc_scene* sc, const double* cdf, uint64_t id, pat
     double S;
     double c = darts_connect(sc, k, beta, x, w, C, Sm, SM, dm, orc_u01(u[3]), 0, L, pr, &ok, &S);
     pr->n_conn += 1.0;
-    if (ok) {
+    if (ok && full) {
+      pr->n_conn_nonempty += 1.0;
+      int bt = time_bin(sc, E.t0 + (L + S) / sc->v, pr, k);
+      if (bt >= 0) emit(pr, bt, c);
+    } else if (ok) {
       pr->n_conn_nonempty += 1.0;
       pr->contrib += c;
       if (dLdh) {
@@ -934,8 +948,15 @@ static void trace_darts(const orc_scene* sc, const double* cdf, uint64_t id, pat
       double cs = beta * surface_connect(sc, &E, x, nrm, alb, &r);
       double Ltot = L + r;
       double lo = sc->v * (Tm - E.t0), hi = sc->v * (TM - E.t0);
-      rec_margin(pr, k, dmin(fabs(Ltot - lo), fabs(Ltot - hi)) / hi);
-      if (cs > 0.0 && Ltot >= lo && Ltot < hi) {
+      if (full) {
+        if (cs > 0.0) {
+          int bt = time_bin(sc, E.t0 + Ltot / sc->v, pr, k);
+          if (bt >= 0) emit(pr, bt, cs);
+        }
+      } else {
+        rec_margin(pr, k, dmin(fabs(Ltot - lo), fabs(Ltot - hi)) / hi);
+      }
+      if (!full && cs > 0.0 && Ltot >= lo && Ltot < hi) {
         pr->contrib += cs;
         if (dLdh) {
           double s0 = n_med / sc->sigma_s - Ltot, s1 = -Ltot, s2 = gsum;
@@ -1207,7 +1228,8 @@ static void trace_vanilla(const orc_scene* sc, uint64_t id, path_rec* pr) {
 
 static void trace_one(const orc_scene* sc, int method, const double* cdf, uint64_t id,
                       path_rec* pr, const double* dLdh, double grad[3]) {
-  if (method == ORC_DARTS) trace_darts(sc, cdf, id, pr, dLdh, grad);
+  if (method == ORC_DARTS) trace_darts(sc, cdf, id, pr, dLdh, grad, 0);
+  else if (method == ORC_DARTS_FULL_GATE) trace_darts(sc, cdf, id, pr, NULL, NULL, 1);
   else if (method == ORC_PLAIN_UNIFORM_T) trace_plain(sc, id, pr);
   else trace_vanilla(sc, id, pr);
 }
@@ -1220,7 +1242,8 @@ static int scene_ok(const orc_scene* sc, int method, const double* cdf) {
   if (sc->ris_m < 1 || sc->ris_m > 32) return 0;
   if (sc->n_rho < 1 || sc->n_s < 1 || sc->n_mu < 2) return 0;
   if (!(sc->mis_alpha > 0.0)) return 0;
-  if (method == ORC_DARTS && !cdf) return 0;
+  if ((method == ORC_DARTS || method == ORC_DARTS_FULL_GATE) && !cdf) return 0;
+  if (method < ORC_DARTS || method > ORC_DARTS_FULL_GATE) return 0;
   if (sc->paths_per_element < 1) return 0;
   if (sc->n_emitters < 1 || sc->n_emitters > ORC_MAX_EMITTERS) return 0;
   if (sc->n_spheres < 0 || sc->n_spheres > ORC_MAX_SPHERES) return 0;

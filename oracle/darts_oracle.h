@@ -21,7 +21,7 @@ extern "C" {
 #endif
 
 /* Rendering methods. */
-enum { ORC_DARTS = 0, ORC_PLAIN_UNIFORM_T = 1, ORC_VANILLA_DIRECT = 2 };
+enum { ORC_DARTS = 0, ORC_PLAIN_UNIFORM_T = 1, ORC_VANILLA_DIRECT = 2, ORC_DARTS_FULL_GATE = 3 };
 
 /* Per-path event codes written to decisions[k*4+0] (low nibble). */
 enum {

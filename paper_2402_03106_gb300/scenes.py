@@ -23,7 +23,9 @@ import numpy as np
 DARTS = 0
 PLAIN_UNIFORM_T = 1
 VANILLA_DIRECT = 2
-METHOD_NAMES = {DARTS: "darts", PLAIN_UNIFORM_T: "plain_uniform_t", VANILLA_DIRECT: "vanilla_direct"}
+DARTS_FULL_GATE = 3  # DARTS samplers over the whole gate, each connection binned by its time
+METHOD_NAMES = {DARTS: "darts", PLAIN_UNIFORM_T: "plain_uniform_t", VANILLA_DIRECT: "vanilla_direct",
+                DARTS_FULL_GATE: "darts_full_gate"}
 
 # Sampling flags (C-ABI DARTS_FLAG_*).
 FLAG_SENSOR_UNIFORM_ONLY = 1 << 0

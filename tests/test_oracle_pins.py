@@ -556,3 +556,59 @@ def test_camera_ids_wrap_with_continuing_sample_index():
     B = 32
     assert np.array_equal(a["bin"] // B, b["bin"] // B)          # same pixels
     assert np.array_equal((a["bin"] % B + 5) % B, b["bin"] % B)  # bins shifted by N_e
+
+
+# ---------------------------------------------------------------------------
+# Full-gate DARTS (the samplers of Sec. 4-5 over the whole gate, connections
+# binned by their time like the uniform-temporal tracer)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("g", [0.0, 0.7])
+def test_full_gate_single_scatter_closed_form(g):
+    sc = S.infinite_scene(1.0, 0.01, g, separation=1.0, n_bins=12, t_min=1.02, t_max=3.0)
+    ref = O.single_scatter_bins(sc)
+    n = 1 << 16
+    sp = S.Sampling(seed=21, paths_per_element=n, max_bounces=1)
+    h, sq, _ = O.render(sc, sp, O.ORC_DARTS_FULL_GATE)
+    se = O.standard_error(h, sq, n)
+    assert np.max(np.abs(_z(h, se, ref))) < 4.5
+    # the bins of one path are correlated: bound the total by the summed SEs
+    assert abs(np.sum(h) - np.sum(ref)) < 4.5 * np.sum(se)
+
+
+@pytest.mark.parametrize("K,where", [(3, "cube"), (4, "inf")])
+def test_full_gate_agrees_with_plain_pt(K, where):
+    if where == "inf":
+        sc = S.infinite_scene(1.0, 0.01, 0.3, separation=1.0, n_bins=8, t_min=1.05, t_max=3.0)
+    else:
+        sc = S.slab_scene(1.0, 0.02, 0.5, n_bins=8, t_min=0.85, t_max=2.5)
+    n = 1 << 17
+    h, sq, _ = O.render(sc, S.Sampling(seed=25, paths_per_element=n, max_bounces=K), O.ORC_DARTS_FULL_GATE)
+    se = O.standard_error(h, sq, n)
+    h2, sq2, _ = O.render(sc, S.Sampling(seed=26, paths_per_element=n, max_bounces=K), O.ORC_PLAIN_UNIFORM_T)
+    se2 = O.standard_error(h2, sq2, n)
+    z = (h - h2) / np.sqrt(se ** 2 + se2 ** 2)
+    assert np.max(np.abs(z[1:])) < 4.5, z
+    assert abs(z[0]) < 6.0
+
+
+def test_full_gate_with_surfaces_and_camera():
+    sc = S.box_camera_scene(seed=1, width=2, height=2, n_bins=8, t_max=8.0)
+    n = 1 << 15
+    res = []
+    for m, seed in ((O.ORC_DARTS_FULL_GATE, 31), (O.ORC_PLAIN_UNIFORM_T, 32)):
+        h, sq, _ = O.render(sc, S.Sampling(seed=seed, paths_per_element=n, max_bounces=3), m)
+        res.append((h.sum(), np.sqrt(np.sum(O.standard_error(h, sq, n) ** 2))))
+    (a, sa), (b, sb) = res
+    assert abs(a - b) < 4.5 * math.sqrt(sa ** 2 + sb ** 2), res
+
+
+def test_full_gate_paths_follow_the_darts_decisions():
+    """With a one-bin gate the full-gate path is the DARTS path of that bin:
+    same decisions, same contribution (the weights differ by B/N_e vs 1/N_e)."""
+    sc = S.slab_scene(n_bins=1, t_min=1.0, t_max=2.2)
+    sp = S.Sampling(seed=2, paths_per_element=1024, max_bounces=12)
+    a = O.trace_paths(sc, sp, 0, 256)
+    b = O.trace_paths(sc, sp, 0, 256, method=O.ORC_DARTS_FULL_GATE)
+    assert np.array_equal(a["decisions"][..., :2], b["decisions"][..., :2])
+    np.testing.assert_allclose(a["contrib"], b["contrib"], rtol=1e-12)
+    assert np.all(b["bin"] == -1)
