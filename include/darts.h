@@ -51,7 +51,12 @@ typedef enum {
   DARTS_METHOD_DARTS = 0,           /* Sec. 4-5: DA-RIS distance, EDA+MIS direction, ellipse */
   DARTS_METHOD_PLAIN_UNIFORM_T = 1, /* Eq. 21 with uniform P (Jarabo et al.): uniform
                                        temporal control vertex, free flight, HG      */
-  DARTS_METHOD_VANILLA_DIRECT = 2   /* Sec. 5.2 "vanilla": direct shadow connections  */
+  DARTS_METHOD_VANILLA_DIRECT = 2,  /* Sec. 5.2 "vanilla": direct shadow connections  */
+  DARTS_METHOD_DARTS_FULL_GATE = 3  /* the DARTS samplers targeting the whole gate; each
+                                       control-vertex and surface connection lands in
+                                       the bin of its own time (weight 1/N_e), like
+                                       method 1, instead of one bin per path.  No
+                                       adjoint; not in darts_render_batch. */
 } darts_method;
 
 /* sampling.flags */
@@ -105,10 +110,20 @@ typedef struct {
   int32_t width, height;
 } darts_sensor;
 
-/* Time gate [t_min, t_max) in n_bins equal bins. */
+/* Time gate [t_min, t_max) in n_bins equal bins.  weights (optional, host
+ * array of n_bins values >= 0 with a positive sum, NULL for none): the
+ * sensor's temporal response W per bin (Eq. 1-4; Sec. 5.2 samples the
+ * target interval of a path from it, Fig. 7).  DARTS then draws each path's
+ * bin from W by systematic sampling of the cumulative weights (FP64), so a
+ * bin receives N_e W_b / sum W paths in expectation and zero-weight bins none;
+ * the histogram stays the unweighted per-bin estimate (zero where W_b = 0)
+ * and the W-weighted pixel value is sum_b W_b h_b.  The other methods use W
+ * only to count rejected samples (darts_stats).  Not accepted by
+ * darts_render_static or darts_render_batch. */
 typedef struct {
   double t_min, t_max;
   int32_t n_bins;
+  const double* weights;
 } darts_gate;
 
 /* The medium fills the axis-aligned box [lo, hi].  Faces whose bit
@@ -174,6 +189,10 @@ typedef struct {
   uint64_t escapes;              /* rays that left the medium                      */
   uint64_t fp64_ellipse;         /* near-degenerate ellipse solves done in FP64     */
   uint64_t fp64_phi;             /* small-t' DA exponents done in FP64              */
+  uint64_t samples;              /* connection samples that produced a path time    */
+  uint64_t rejected;             /* of them, times of zero temporal weight: outside
+                                    the gate, in a zero-weight bin, or (DARTS)
+                                    outside the path's bin                          */
 } darts_stats;
 
 /* ---- context ------------------------------------------------------------ */

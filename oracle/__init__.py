@@ -53,6 +53,7 @@ class OrcScene(C.Structure):
         ("fov_deg", C.c_double), ("width", C.c_int32), ("height", C.c_int32),
         ("walls", C.c_int32), ("wall_albedo", C.c_double), ("n_spheres", C.c_int32),
         ("spheres", (C.c_double * 5) * 64),
+        ("weights", C.POINTER(C.c_double)),
     ]
 
 
@@ -154,6 +155,12 @@ def make_scene(scene, sampling) -> OrcScene:
     for i, q in enumerate(sph):
         s.spheres[i][:] = [float(v) for v in q]
     s.t_min, s.t_max, s.n_bins = scene.gate.t_min, scene.gate.t_max, scene.gate.n_bins
+    w = getattr(scene.gate, "weights", None)
+    if w is not None:
+        if len(w) != s.n_bins:
+            raise ValueError("gate weights need one value per bin")
+        s._weights = np.ascontiguousarray(w, dtype=np.float64)  # kept alive with the struct
+        s.weights = s._weights.ctypes.data_as(C.POINTER(C.c_double))
     s.max_bounces, s.ris_m = sampling.max_bounces, sampling.ris_m
     s.n_rho, s.n_s, s.n_mu = sampling.table_n_rho, sampling.table_n_s, sampling.table_n_mu
     s.mis_alpha = sampling.mis_alpha
@@ -317,7 +324,7 @@ def sample_emitter(scene, sampling, path_id, q):
 
 
 STAT_NAMES = ("paths", "vertices", "connections", "connections_nonempty", "ris_candidates",
-              "early_exits", "all_invalid", "escapes")
+              "early_exits", "all_invalid", "escapes", "samples", "rejected")
 
 
 def render(scene, sampling, method=ORC_DARTS, n_paths=None, offset=0, threads=None, cdf=None):
@@ -333,7 +340,7 @@ def render(scene, sampling, method=ORC_DARTS, n_paths=None, offset=0, threads=No
     threads = threads or (os.cpu_count() or 1)
     hist = np.zeros(s.n_bins * elements)
     sumsq = np.zeros(s.n_bins * elements)
-    stats = np.zeros(8)
+    stats = np.zeros(len(STAT_NAMES))
     cdf_c = None if cdf is None else np.ascontiguousarray(cdf, dtype=np.float64)
     rc = load().orc_render(C.byref(s), method, _ptr(cdf_c), n, offset, threads, _ptr(hist),
                            _ptr(sumsq), _ptr(stats))

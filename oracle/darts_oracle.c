@@ -495,6 +495,11 @@ typedef struct {
   int dec_sel;
   /* largest (L + S_hi) / (S_hi - S_lo) over the connections */
   double cond;
+  /* weight of a DARTS path in its bin: B / N_e, or sum W / (N_e W_b) */
+  double wpath;
+  /* connection samples with a time, and those whose time has zero weight
+   * (outside the gate, in a zero-weight bin, or outside a DARTS path's bin) */
+  double n_samples, n_rejected;
   /* the path's emitter point and sensor element */
   const emit_pt* E;
   int elem;
@@ -815,12 +820,43 @@ static void path_element(const orc_scene* sc, uint64_t id, int* elem, uint64_t* 
   }
 }
 
-static int darts_bin(const orc_scene* sc, int elem, uint64_t j) {
+static int darts_bin(const orc_scene* sc, int elem, uint64_t j, double* wpath) {
   uint32_t u[4];
   orc_rng4(sc, (uint64_t)elem, ORC_VERTEX_ELEMENT, 0, u);
-  uint64_t oe = (uint64_t)floor(orc_u01(u[0]) * sc->n_bins);
-  if (oe >= (uint64_t)sc->n_bins) oe = sc->n_bins - 1;
-  return (int)((j + oe) % (uint64_t)sc->n_bins);
+  int B = sc->n_bins;
+  uint64_t ne = sc->paths_per_element;
+  if (!sc->weights) {
+    uint64_t oe = (uint64_t)floor(orc_u01(u[0]) * B);
+    if (oe >= (uint64_t)B) oe = B - 1;
+    *wpath = (double)B / (double)ne;
+    return (int)((j + oe) % (uint64_t)B);
+  }
+  /* Interval sampled from W: systematic sampling of the cumulative weights
+   * at x = (i + phi) / N_e, i = (j + o_e) mod N_e, phi uniform per element;
+   * bin b holds x in [C_b, C_{b+1}), C_b = sum_{i<b} W_i / sum W, so bin b
+   * receives N_e P_b paths in expectation, P_b = W_b / sum W. */
+  uint64_t oe = (uint64_t)floor(orc_u01(u[0]) * (double)ne);
+  if (oe >= ne) oe = ne - 1;
+  double x = ((double)((j + oe) % ne) + orc_u01(u[1])) / (double)ne;
+  double tot = 0.0;
+  for (int i = 0; i < B; ++i) tot += sc->weights[i];
+  double cum = 0.0;
+  int b = B - 1;
+  for (int i = 0; i < B; ++i) {
+    double next = cum + sc->weights[i];
+    if (x < next / tot) {
+      b = i;
+      break;
+    }
+    cum = next;
+  }
+  *wpath = tot / ((double)ne * sc->weights[b]);
+  return b;
+}
+
+/* Zero temporal weight: outside the gate or in a zero-weight bin. */
+static int zero_weight(const orc_scene* sc, int b) {
+  return b < 0 || (sc->weights && !(sc->weights[b] > 0.0));
 }
 
 /* Start of a path: the point sensor (direction sampled at vertex 0) or the
@@ -861,7 +897,7 @@ static void trace_darts(const orc_scene* sc, const double* cdf, uint64_t id, pat
   int elem;
   uint64_t j;
   path_element(sc, id, &elem, &j);
-  int b = full ? 0 : darts_bin(sc, elem, j);
+  int b = full ? 0 : darts_bin(sc, elem, j, &pr->wpath);
   emit_pt E;
   pick_emitter(sc, id, &E);
   pr->E = &E;
@@ -877,7 +913,7 @@ static void trace_darts(const orc_scene* sc, const double* cdf, uint64_t id, pat
   double beta = E.wsel;
   double gsum = 0.0;  /* sum of d log HG / dg over medium walk vertices */
   int n_med = 0;      /* medium scattering vertices of the walk */
-  double wb = (double)B / (double)sc->paths_per_element;
+  double wb = pr->wpath;
   for (int k = 0; k < K; ++k) {
     pr->nvert = k + 1;
     pr->n_vert += 1.0;
@@ -908,9 +944,11 @@ static void trace_darts(const orc_scene* sc, const double* cdf, uint64_t id, pat
     double S;
     double c = darts_connect(sc, k, beta, x, w, C, Sm, SM, dm, orc_u01(u[3]), 0, L, pr, &ok, &S);
     pr->n_conn += 1.0;
+    if (ok) pr->n_samples += 1.0;
     if (ok && full) {
       pr->n_conn_nonempty += 1.0;
       int bt = time_bin(sc, E.t0 + (L + S) / sc->v, pr, k);
+      if (zero_weight(sc, bt)) pr->n_rejected += 1.0;
       if (bt >= 0) emit(pr, bt, c);
     } else if (ok) {
       pr->n_conn_nonempty += 1.0;
@@ -948,13 +986,16 @@ static void trace_darts(const orc_scene* sc, const double* cdf, uint64_t id, pat
       double cs = beta * surface_connect(sc, &E, x, nrm, alb, &r);
       double Ltot = L + r;
       double lo = sc->v * (Tm - E.t0), hi = sc->v * (TM - E.t0);
+      if (cs > 0.0) pr->n_samples += 1.0;
       if (full) {
         if (cs > 0.0) {
           int bt = time_bin(sc, E.t0 + Ltot / sc->v, pr, k);
+          if (zero_weight(sc, bt)) pr->n_rejected += 1.0;
           if (bt >= 0) emit(pr, bt, cs);
         }
       } else {
         rec_margin(pr, k, dmin(fabs(Ltot - lo), fabs(Ltot - hi)) / hi);
+        if (cs > 0.0 && !(Ltot >= lo && Ltot < hi)) pr->n_rejected += 1.0;
       }
       if (!full && cs > 0.0 && Ltot >= lo && Ltot < hi) {
         pr->contrib += cs;
@@ -1045,6 +1086,8 @@ static void base_surface(const orc_scene* sc, uint64_t id, int k, const emit_pt*
   pr->n_conn += 1.0;
   if (cs > 0.0) {
     int b = time_bin(sc, E->t0 + (L + r) / sc->v, pr, k);
+    pr->n_samples += 1.0;
+    if (zero_weight(sc, b)) pr->n_rejected += 1.0;
     if (b >= 0) {
       pr->n_conn_nonempty += 1.0;
       emit(pr, b, cs);
@@ -1098,6 +1141,8 @@ static void trace_plain(const orc_scene* sc, uint64_t id, path_rec* pr) {
     if (ok) {
       pr->n_conn_nonempty += 1.0;
       int b = time_bin(sc, E.t0 + (L + S) / sc->v, pr, k);
+      pr->n_samples += 1.0;
+      if (zero_weight(sc, b)) pr->n_rejected += 1.0;
       if (b >= 0) emit(pr, b, c);
     }
     if (k + 1 == K) {
@@ -1176,6 +1221,8 @@ static void trace_vanilla(const orc_scene* sc, uint64_t id, path_rec* pr) {
         pr->n_conn += 1.0;
         if (cs > 0.0) {
           int b = time_bin(sc, E.t0 + (L + r) / sc->v, pr, k);
+          pr->n_samples += 1.0;
+          if (zero_weight(sc, b)) pr->n_rejected += 1.0;
           if (b >= 0) {
             pr->n_conn_nonempty += 1.0;
             emit(pr, b, cs);
@@ -1204,6 +1251,8 @@ static void trace_vanilla(const orc_scene* sc, uint64_t id, path_rec* pr) {
     double c = beta * orc_hg_pdf(cos_s, sc->g) * exp(-st * C) * emit_intensity(&E, x) * vis / (C * C);
     pr->n_conn += 1.0;
     int b = time_bin(sc, E.t0 + (L + C) / sc->v, pr, k);
+    pr->n_samples += 1.0;
+    if (zero_weight(sc, b)) pr->n_rejected += 1.0;
     if (b >= 0) {
       pr->n_conn_nonempty += 1.0;
       emit(pr, b, c);
@@ -1248,6 +1297,14 @@ static int scene_ok(const orc_scene* sc, int method, const double* cdf) {
   if (sc->n_emitters < 1 || sc->n_emitters > ORC_MAX_EMITTERS) return 0;
   if (sc->n_spheres < 0 || sc->n_spheres > ORC_MAX_SPHERES) return 0;
   if (sc->sensor_kind == 1 && (sc->width < 1 || sc->height < 1 || !(sc->fov_deg > 0.0))) return 0;
+  if (sc->weights) {
+    double tot = 0.0;
+    for (int b = 0; b < sc->n_bins; ++b) {
+      if (!(sc->weights[b] >= 0.0) || !isfinite(sc->weights[b])) return 0;
+      tot += sc->weights[b];
+    }
+    if (!(tot > 0.0)) return 0;
+  }
   return 1;
 }
 
@@ -1295,7 +1352,7 @@ typedef struct {
   uint64_t first, count;
   double* hist;
   double* sumsq;
-  double stats[8];
+  double stats[ORC_N_STATS];
   const double* dLdh;
   double grad[3], grad_sq[3];
 } work_t;
@@ -1305,7 +1362,6 @@ static void* render_worker(void* p) {
   const orc_scene* sc = wk->sc;
   int B = sc->n_bins;
   double inv_n = 1.0 / (double)sc->paths_per_element;
-  double wb = (double)B * inv_n;
   path_rec* pr = (path_rec*)malloc(sizeof(path_rec));
   double* tmp = (double*)calloc((size_t)B, sizeof(double));
   for (uint64_t i = 0; i < wk->count; ++i) {
@@ -1319,7 +1375,7 @@ static void* render_worker(void* p) {
       }
     }
     if (wk->method == ORC_DARTS) {
-      double c = wb * pr->contrib;
+      double c = pr->wpath * pr->contrib;
       wk->hist[pr->bin] += c;
       wk->sumsq[pr->bin] += c * c;
     } else {
@@ -1342,6 +1398,8 @@ static void* render_worker(void* p) {
     wk->stats[5] += pr->n_early;
     wk->stats[6] += pr->n_invalid;
     wk->stats[7] += pr->n_escape;
+    wk->stats[8] += pr->n_samples;
+    wk->stats[9] += pr->n_rejected;
   }
   free(tmp);
   free(pr);
@@ -1376,7 +1434,7 @@ static int run_threads(const orc_scene* sc, int method, const double* cdf, uint6
   for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
   if (hist) memset(hist, 0, sizeof(double) * HB);
   if (sumsq) memset(sumsq, 0, sizeof(double) * HB);
-  if (stats) memset(stats, 0, sizeof(double) * 8);
+  if (stats) memset(stats, 0, sizeof(double) * ORC_N_STATS);
   if (grad3) memset(grad3, 0, sizeof(double) * 3);
   if (grad3_sq) memset(grad3_sq, 0, sizeof(double) * 3);
   for (int t = 0; t < n_threads; ++t) {
@@ -1384,7 +1442,7 @@ static int run_threads(const orc_scene* sc, int method, const double* cdf, uint6
       if (hist) hist[b] += wk[t].hist[b];
       if (sumsq) sumsq[b] += wk[t].sumsq[b];
     }
-    for (int j = 0; j < 8 && stats; ++j) stats[j] += wk[t].stats[j];
+    for (int j = 0; j < ORC_N_STATS && stats; ++j) stats[j] += wk[t].stats[j];
     for (int j = 0; j < 3; ++j) {
       if (grad3) grad3[j] += wk[t].grad[j];
       if (grad3_sq) grad3_sq[j] += wk[t].grad_sq[j];

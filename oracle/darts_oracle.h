@@ -92,6 +92,11 @@ typedef struct {
   double wall_albedo;
   int32_t n_spheres;
   double spheres[ORC_MAX_SPHERES][5];
+  /* temporal response W over the gate: weights[n_bins] >= 0, or NULL for 1
+   * on every bin.  DARTS samples the target interval of a path from W
+   * (Sec. 5.2; Fig. 7), so zero-weight bins receive no paths; the other
+   * methods are unaffected except for counting rejected samples. */
+  const double* weights;
 } orc_scene;
 
 /* Philox4x32-10 block (Salmon et al., SC'11). */
@@ -158,9 +163,11 @@ int orc_ris_step(const orc_scene* sc, uint64_t id, int k, const double x[3], con
 /* Full histogram render of n_paths paths starting at path id `offset`,
  * split over n_threads POSIX threads; hist/sumsq are [elements][n_bins]
  * (elements = 1 for the point sensor, width*height for the camera) and are
- * overwritten.  stats (optional, 8 doubles): paths, vertices, connections,
- * nonempty connections, RIS candidates, early exits, all-invalid stops,
- * escapes. */
+ * overwritten.  stats (optional, ORC_N_STATS doubles): paths, vertices,
+ * connections, nonempty connections, RIS candidates, early exits,
+ * all-invalid stops, escapes, connection samples with a time, and those of
+ * them rejected by a zero temporal weight. */
+#define ORC_N_STATS 10
 int orc_render(const orc_scene* sc, int method, const double* cdf,
                uint64_t n_paths, uint64_t offset, int n_threads,
                double* hist, double* sumsq, double* stats);

@@ -59,7 +59,8 @@ class darts_sensor(C.Structure):
 
 
 class darts_gate(C.Structure):
-    _fields_ = [("t_min", C.c_double), ("t_max", C.c_double), ("n_bins", C.c_int32)]
+    _fields_ = [("t_min", C.c_double), ("t_max", C.c_double), ("n_bins", C.c_int32),
+                ("weights", C.POINTER(C.c_double))]
 
 
 class darts_geometry(C.Structure):
@@ -90,7 +91,7 @@ class darts_probe(C.Structure):
 class darts_stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "paths", "vertices", "connections_nonempty", "distance_steps", "early_exits",
-        "all_invalid", "escapes", "fp64_ellipse", "fp64_phi")]
+        "all_invalid", "escapes", "fp64_ellipse", "fp64_phi", "samples", "rejected")]
 
 
 _lib = None
@@ -176,7 +177,12 @@ def to_c_scene(scene: S.Scene):
     cs.sensor.width = int(sen.width)
     cs.sensor.height = int(sen.height)
     cs.gate = darts_gate(float(scene.gate.t_min), float(scene.gate.t_max), int(scene.gate.n_bins))
-    return cs, (arr, sph)
+    gw = getattr(scene.gate, "weights", None)
+    wts = None
+    if gw is not None:
+        wts = (C.c_double * max(len(gw), 1))(*[float(x) for x in gw])
+        cs.gate.weights = C.cast(wts, C.POINTER(C.c_double))
+    return cs, (arr, sph, wts)
 
 
 def to_c_sampling(sp: S.Sampling) -> darts_sampling:

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "darts.h"
 #include "darts_device.cuh"
@@ -37,6 +38,11 @@ struct darts_ctx {
   int block = 0;
   int last_block = 0;
   unsigned long long last_paths = 0;  // paths of the last render
+  bool last_fast = false;              // last launch ran the specialised DARTS kernel
+  // temporal response: cumulative weights and per-bin DARTS weights
+  double* wcdf = nullptr;
+  float* wbin = nullptr;
+  size_t w_bins = 0;
   // kernel timing
   bool timing = false;
   bool timed = false;
@@ -139,6 +145,16 @@ darts_status validate(darts_ctx* ctx, const darts_scene* sc, const darts_samplin
   if (!(m.v > 0.0) || !std::isfinite(m.v)) return fail(ctx, DARTS_ERR_INVALID_ARG, "need v > 0");
   if (sc->gate.n_bins < 1) return fail(ctx, DARTS_ERR_INVALID_ARG, "need n_bins >= 1");
   if (!(sc->gate.t_max > sc->gate.t_min)) return fail(ctx, DARTS_ERR_INVALID_ARG, "need t_max > t_min");
+  if (sc->gate.weights) {
+    double tot = 0.0;
+    for (int b = 0; b < sc->gate.n_bins; ++b) {
+      const double w = sc->gate.weights[b];
+      if (!(w >= 0.0) || !std::isfinite(w))
+        return fail(ctx, DARTS_ERR_INVALID_ARG, "gate weight %d must be finite and >= 0", b);
+      tot += w;
+    }
+    if (!(tot > 0.0)) return fail(ctx, DARTS_ERR_INVALID_ARG, "gate weights must have a positive sum");
+  }
   for (int i = 0; i < 3; ++i)
     if (!(sc->geom.hi[i] > sc->geom.lo[i])) return fail(ctx, DARTS_ERR_INVALID_ARG, "empty medium box");
   if (sc->n_emitters < 1 || !sc->emitters) return fail(ctx, DARTS_ERR_INVALID_ARG, "need an emitter");
@@ -206,7 +222,7 @@ darts_status validate(darts_ctx* ctx, const darts_scene* sc, const darts_samplin
     return fail(ctx, DARTS_ERR_INVALID_ARG, "table dims: n_rho >= 1, n_s >= 1, 2 <= n_mu <= 1024");
   if (!(sp->mis_alpha > 0.0) || !std::isfinite(sp->mis_alpha))
     return fail(ctx, DARTS_ERR_INVALID_ARG, "mis_alpha must be > 0");
-  if (sp->method < DARTS_METHOD_DARTS || sp->method > DARTS_METHOD_VANILLA_DIRECT)
+  if (sp->method < DARTS_METHOD_DARTS || sp->method > DARTS_METHOD_DARTS_FULL_GATE)
     return fail(ctx, DARTS_ERR_INVALID_ARG, "unknown method %d", sp->method);
   return DARTS_OK;
 }
@@ -407,6 +423,59 @@ void make_trace_params(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
   P->status = reinterpret_cast<unsigned int*>(ctx->scratch + 1) + 1;
 }
 
+// The methods with DARTS samplers need the direction table.
+bool uses_table(int method) {
+  return method == DARTS_METHOD_DARTS || method == DARTS_METHOD_DARTS_FULL_GATE;
+}
+
+// Temporal response: cumulative weights C_b = (W_0 + ... + W_{b-1}) / sum W
+// summed left to right in FP64, the per-bin DARTS path weights
+// sum W / (N_e W_b), and the point sensor's systematic-sampling offset and
+// phase (element 0's Philox draw).  Uploaded to context buffers.
+darts_status set_weights(darts_ctx* ctx, const darts_scene* sc, const darts_sampling* sp, TraceParams& P) {
+  P.wcdf = nullptr;
+  P.wbin = nullptr;
+  if (!sc->gate.weights) return DARTS_OK;
+  const int B = sc->gate.n_bins;
+  if (ctx->w_bins < (size_t)B) {
+    cudaFree(ctx->wcdf);
+    cudaFree(ctx->wbin);
+    ctx->wcdf = nullptr;
+    ctx->wbin = nullptr;
+    ctx->w_bins = 0;
+    CK(cudaMalloc((void**)&ctx->wcdf, (B + 1) * sizeof(double)), "weight allocation");
+    CK(cudaMalloc((void**)&ctx->wbin, B * sizeof(float)), "weight allocation");
+    ctx->w_bins = (size_t)B;
+  }
+  std::vector<double> c(B + 1);
+  std::vector<float> wb(B);
+  double tot = 0.0;
+  for (int b = 0; b < B; ++b) tot += sc->gate.weights[b];
+  double cum = 0.0;
+  c[0] = 0.0;
+  const double ne = (double)std::max<uint64_t>(sp->paths_per_element, 1);
+  for (int b = 0; b < B; ++b) {
+    cum = cum + sc->gate.weights[b];
+    c[b + 1] = cum / tot;
+    const double w = sc->gate.weights[b];
+    wb[b] = w > 0.0 ? (float)(sp->method == DARTS_METHOD_DARTS ? tot / (ne * w) : 1.0) : 0.0f;
+  }
+  CK(cudaMemcpyAsync(ctx->wcdf, c.data(), (B + 1) * sizeof(double), cudaMemcpyHostToDevice, ctx->stream),
+     "weight upload");
+  CK(cudaMemcpyAsync(ctx->wbin, wb.data(), B * sizeof(float), cudaMemcpyHostToDevice, ctx->stream),
+     "weight upload");
+  // pageable sources: make the copies complete before the vectors go away
+  CK(cudaStreamSynchronize(ctx->stream), "weight upload");
+  P.wcdf = ctx->wcdf;
+  P.wbin = ctx->wbin;
+  const U4 r = philox4x32_10(0u, 0u, sp->stream, (kVertexElement << 8) | 0u, P.key0, P.key1);
+  const uint64_t n = std::max<uint64_t>(sp->paths_per_element, 1);
+  uint64_t oe = (uint64_t)std::floor((double)(r.x >> 8) * (1.0 / 16777216.0) * (double)n);
+  P.w_oe = std::min(oe, n - 1);
+  P.w_phi = (double)(r.y >> 8) * (1.0 / 16777216.0);
+  return DARTS_OK;
+}
+
 // Common launch of the path kernel for render and debug.
 // Launch shape: the requested (or largest) block size whose shared memory
 // fits, falling back to FP64 atomics straight into the outputs when no tile
@@ -436,6 +505,11 @@ void choose_launch(const darts_ctx* ctx, const darts_sampling* sp, const TracePa
 
 darts_status run_trace(darts_ctx* ctx, const darts_scene* sc, const darts_sampling* sp,
                        TraceParams& P, bool debug) {
+  {
+    const darts_status sw = set_weights(ctx, sc, sp, P);
+    if (sw != DARTS_OK) return sw;
+  }
+  ctx->last_fast = sp->method == DARTS_METHOD_DARTS && !P.general;
   const int grid = ctx->sm_count;
   int block;
   bool tile;
@@ -523,6 +597,8 @@ darts_status darts_destroy(darts_ctx* ctx) {
   cudaFree(ctx->table);
   cudaFree(ctx->host_hist);
   cudaFree(ctx->batch_tables);
+  cudaFree(ctx->wcdf);
+  cudaFree(ctx->wbin);
   cudaFree(ctx->batch_buf);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
@@ -667,7 +743,7 @@ darts_status darts_render(darts_ctx* ctx, const darts_scene* scene, const darts_
     ctx->last_paths = 0;
     return DARTS_OK;
   }
-  if (sampling->method == DARTS_METHOD_DARTS) {
+  if (uses_table(sampling->method)) {
     s = ensure_table(ctx, scene, sampling);
     if (s != DARTS_OK) return s;
   }
@@ -721,8 +797,12 @@ darts_status darts_get_stats(darts_ctx* ctx, darts_stats* out) {
   out->early_exits = s[3];
   out->all_invalid = s[4];
   out->escapes = s[5];
-  out->fp64_ellipse = s[6];
-  out->fp64_phi = s[7];
+  out->fp64_ellipse = s[10];
+  out->fp64_phi = s[11];
+  // the specialised DARTS kernel counts no samples: they are its non-empty
+  // connections, and none can fall outside its bin
+  out->samples = ctx->last_fast ? s[1] : s[6] + s[7];
+  out->rejected = ctx->last_fast ? 0 : s[8] + s[9];
   return DARTS_OK;
 }
 
@@ -745,6 +825,8 @@ darts_status darts_render_batch(darts_ctx* ctx, int n, const darts_scene* scenes
     darts_status st = validate(ctx, &scenes[i], &samplings[i]);
     if (st != DARTS_OK) return st;
     if (!hist_dev[i]) return fail(ctx, DARTS_ERR_INVALID_ARG, "hist_dev[%d] is NULL", i);
+    if (scenes[i].gate.weights)
+      return fail(ctx, DARTS_ERR_UNSUPPORTED, "a batch renders media without a temporal response");
     const darts_sampling& si = samplings[i];
     if (general_scene(&scenes[i]))
       return fail(ctx, DARTS_ERR_UNSUPPORTED, "a batch renders point-emitter, point-sensor media without surfaces");
@@ -824,6 +906,7 @@ darts_status darts_render_batch(darts_ctx* ctx, int n, const darts_scene* scenes
   std::free(host);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "batch upload");
   ctx->last_paths = total_paths;
+  ctx->last_fast = true;
   const bool use_graph = !(flags & DARTS_BATCH_NO_GRAPH);
   auto enqueue = [&](cudaStream_t st) -> cudaError_t {
     cudaError_t r = cudaMemsetAsync(dev + off_cnt, 0, 256, st);
@@ -891,6 +974,11 @@ darts_status darts_adjoint(darts_ctx* ctx, const darts_scene* scene, const darts
   CK(cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), ctx->stream), "memset");
   CK(cudaMemsetAsync(ctx->scratch + 2, 0, kStatCount * sizeof(unsigned long long), ctx->stream), "memset");
   ctx->last_paths = P.N;
+  {
+    const darts_status sw = set_weights(ctx, scene, sampling, P);
+    if (sw != DARTS_OK) return sw;
+  }
+  ctx->last_fast = !P.general;
   CK(launch_adjoint(P, grid, smem, ctx->stream), "adjoint kernel launch");
   return DARTS_OK;
 }
@@ -906,7 +994,7 @@ darts_status darts_debug_paths(darts_ctx* ctx, const darts_scene* scene,
     return fail(ctx, DARTS_ERR_INVALID_ARG, "debug outputs must not be NULL");
   if (count == 0) return DARTS_OK;
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-  if (sampling->method == DARTS_METHOD_DARTS) {
+  if (uses_table(sampling->method)) {
     s = ensure_table(ctx, scene, sampling);
     if (s != DARTS_OK) return s;
   }
@@ -1003,6 +1091,7 @@ extern "C" darts_status darts_render_static(const darts_scene* scene, const dart
   darts_status s = validate(ctx, scene, sampling);
   if (s != DARTS_OK) return s;
   if (!hist_dev) return DARTS_ERR_INVALID_ARG;
+  if (scene->gate.weights) return DARTS_ERR_UNSUPPORTED;  // no scratch for the weight tables
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return DARTS_ERR_CUDA;
   if (dev < 0 || dev >= kStaticMaxDevices) return DARTS_ERR_UNSUPPORTED;
@@ -1035,7 +1124,7 @@ extern "C" darts_status darts_render_static(const darts_scene* scene, const dart
     if (sumsq_dev && cudaMemsetAsync(sumsq_dev, 0, hb, stream) != cudaSuccess) return DARTS_ERR_CUDA;
     return DARTS_OK;
   }
-  if (sampling->method == DARTS_METHOD_DARTS) {
+  if (uses_table(sampling->method)) {
     TableParams tp;
     make_table_params(scene, sampling, &tp);
     tp.cdf = table;

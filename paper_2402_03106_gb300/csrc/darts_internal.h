@@ -9,7 +9,7 @@ namespace darts {
 
 constexpr int kMaxTabMuNodes = 4;   // Gauss-Legendre nodes per cos-theta bin
 constexpr int kMaxTabTNodes = 32;   // Gauss-Legendre nodes per t-panel (two panels)
-constexpr int kStatCount = 9;       // darts_stats fields after `paths`
+constexpr int kStatCount = 12;      // device event counters (see the ST_ slots of trace.cu)
 constexpr int kPathChunk = 64;      // paths a warp claims from the global counter
 constexpr int kMaxEmitters = 8;
 constexpr int kMaxSpheres = 64;
@@ -89,6 +89,13 @@ struct TraceParams {
   unsigned long long path_offset;  // global id = path_offset + local index
   unsigned int chunk;              // paths a warp claims per counter update (0: kPathChunk)
   float wb;                        // weight per path contribution (DARTS n_bins/N_e, else 1/N_e)
+  // temporal response W (null without): cumulative weights C[0..n_bins]
+  // (FP64), per-bin DARTS path weight sum W / (N_e W_b) (0 where W_b = 0),
+  // and the point sensor's systematic-sampling offset and phase
+  const double* wcdf;
+  const float* wbin;
+  unsigned long long w_oe;
+  double w_phi;
   // outputs and scratch
   double* hist;                    // [elements][n_bins]; zeroed before a launch without tiles
   double* sumsq;                   // [elements][n_bins] or null

@@ -37,12 +37,26 @@ namespace {
 constexpr int kMaxM = 32;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-enum : int { kDarts = 0, kPlain = 1, kVanilla = 2 };
+enum : int { kDarts = 0, kPlain = 1, kVanilla = 2, kDartsFull = 3 };
+// DARTS samplers (DA-RIS distances, EDA/MIS directions, truncated-exponential
+// control vertices).  kDartsFull targets the whole gate and commits every
+// connection to the bin of its own time (weight 1/N_e) instead of dedicating
+// the path to one bin.
+template <int M>
+constexpr bool kIsDartsM = M == kDarts || M == kDartsFull;
 enum : int { EV_NONE = 0, EV_EARLY = 1, EV_SCATTER = 2, EV_ESCAPE = 3, EV_INVALID = 4, EV_MAXDEPTH = 5,
              EV_SURFACE = 6 };
 // stats slots (after `paths`)
+// Event counters.  SAMPLE / REJECT: connection samples with a time, and
+// those whose time has zero temporal weight (outside the gate, a zero-weight
+// bin, or outside a DARTS path's bin); the second pair counts surface
+// connections of a step that also made a control-vertex connection.  The
+// specialised DARTS kernel (point sensor, no surfaces) does not count them:
+// its samples are its non-empty connections and none is rejected.
 enum : int { ST_VERT = 0, ST_CONN = 1, ST_DIST = 2, ST_EARLY = 3, ST_INVALID = 4, ST_ESCAPE = 5,
-             ST_FP64E = 6, ST_FP64P = 7, ST_SPARE = 8 };
+             ST_SAMPLE = 6, ST_SAMPLE2 = 7, ST_REJECT = 8, ST_REJECT2 = 9,
+             ST_FP64E = 10, ST_FP64P = 11 };
+static_assert(ST_FP64P + 1 == kStatCount, "statistics layout");
 
 struct Path {
   float x, y, z;     // current vertex
@@ -65,6 +79,10 @@ struct Path {
   int elem, nmed;
   int surf;          // sphere the current vertex lies on, -1 otherwise
   bool fixed, miss;
+  // full-gate DARTS: the step's control-vertex and surface contributions
+  // (flat bin, value; bin -1 when none)
+  int cb, cb2;
+  float cv, cv2;
 };
 
 // Event counting.  Common events set a bit for the current vertex step; the
@@ -310,6 +328,33 @@ __device__ __forceinline__ float hg_dlog_dg(const TraceParams& P, float mu) {
   return fmaf(-3.0f * (P.g - mu), __frcp_rn(fmaf(-P.hg_c, mu, P.hg_b)), P.hg_dlog_a);
 }
 
+// Zero temporal weight of time bin b: outside the gate or a zero-weight bin.
+__device__ __forceinline__ bool zero_w(const TraceParams& P, int b) {
+  return b < 0 || b >= P.n_bins || (P.wbin != nullptr && __ldg(P.wbin + b) == 0.0f);
+}
+
+// DARTS bin of sample s of an element under a temporal response W: the
+// cumulative weights C (FP64, C[0] = 0, C[B] = 1) are sampled systematically
+// at x = ((s + oe) mod N_e + phi) / N_e; the bin is the first b with
+// x < C[b + 1].  FP64, as the host builds C, so the integer decision is the
+// same on every implementation that follows this arithmetic.
+__device__ __forceinline__ int w_bin(const TraceParams& P, unsigned long long s, unsigned long long oe,
+                                     double phi) {
+  const unsigned long long ne = P.spp;
+  const double x = ((double)((s + oe) % ne) + phi) / (double)ne;
+  int lo = 0, n = P.n_bins;
+  while (n > 0) {
+    const int half = n >> 1;
+    if (__ldg(P.wcdf + lo + half + 1) <= x) {
+      lo += half + 1;
+      n -= half + 1;
+    } else {
+      n = half;
+    }
+  }
+  return min(lo, P.n_bins - 1);
+}
+
 template <int METHOD, int MAXM, bool DEBUG, bool ADJ = false, bool GEN = false>
 struct Stepper {
   // Initialise a path with local index j.
@@ -326,8 +371,13 @@ struct Stepper {
     p.wx = 0.0f;
     p.wy = 0.0f;
     p.wz = 1.0f;
-    if (METHOD == kDarts) {
-      p.bin = bin;
+    if (METHOD == kDartsFull) {  // the whole gate is the target interval
+      p.bin = -1;
+      p.Sm0 = P.S_gate_lo;
+      p.SM0 = P.S_gate_hi;
+      p.beta = 1.0f;
+    } else if (METHOD == kDarts) {
+      p.bin = P.wcdf ? w_bin(P, P.path_offset + j, P.w_oe, P.w_phi) : bin;
       p.Sm0 = fmaf((float)p.bin, P.S_bin, P.S_gate_lo);
       p.SM0 = fmaf((float)(p.bin + 1), P.S_bin, P.S_gate_lo);
       p.beta = 1.0f;
@@ -385,8 +435,14 @@ struct Stepper {
     p.beta = E.wsel;
     if (METHOD == kDarts) {
       const U4 uo = philox4x32_10((uint32_t)p.elem, 0u, P.stream, (kVertexElement << 8) | 0u, P.key0, P.key1);
-      const unsigned oe = (unsigned)(((unsigned long long)(uo.x >> 8) * (unsigned)B) >> 24);
-      const int b = (int)((s % (unsigned long long)B + oe) % (unsigned)B);
+      int b;
+      if (P.wcdf) {
+        const unsigned long long oe = (unsigned long long)floor((double)u01(uo.x) * (double)P.spp);
+        b = w_bin(P, s, min(oe, P.spp - 1), (double)u01(uo.y));
+      } else {
+        const unsigned oe = (unsigned)(((unsigned long long)(uo.x >> 8) * (unsigned)B) >> 24);
+        b = (int)((s % (unsigned long long)B + oe) % (unsigned)B);
+      }
       p.bin = p.elem * B + b;
       p.Sm0 = fmaf((float)b, P.S_bin, E.s_lo);
       p.SM0 = fmaf((float)(b + 1), P.S_bin, E.s_lo);
@@ -447,7 +503,7 @@ struct Stepper {
       p.wy = 0.0f;
       p.wz = 1.0f;
       p.fixed = false;
-      if (METHOD != kDarts) {  // the baselines draw the uniform direction here
+      if (!kIsDartsM<METHOD>) {  // the baselines draw the uniform direction here
         const U4 u = rng(P, j, 0, 1);
         float sn, cs;
         sincos_2pi(u01(u.z), &sn, &cs);
@@ -583,6 +639,13 @@ struct Stepper {
       if (!visible(P, qx, qy, qz, p.ey0, p.ey1, p.ey2, -1)) cc = 0.0f;
       p.c = fmaf(p.beta, cc, p.c);
       cnt.add(ST_CONN);
+      cnt.add(ST_SAMPLE);
+      if (METHOD == kDartsFull) {  // committed this step to the bin of its time
+        const int b = min(max((int)floorf(((p.L + S) - p.Sm0) * P.inv_S_bin), 0), P.n_bins - 1);
+        p.cb = p.elem * P.n_bins + b;
+        p.cv = p.beta * cc;
+        if (zero_w(P, b)) cnt.add(ST_REJECT);
+      }
       if (ADJ) {
         const float cv = p.beta * cc, ell = p.L + S;
         p.a0 = fmaf(cv, fmaf((float)(p.nmed + 1), P.inv_sigma_s, -ell), p.a0);
@@ -610,7 +673,22 @@ struct Stepper {
       float r;
       const float cs = surface_bounce(P, p, dm, hit, nx, ny, nz, &r);
       const float Lt = p.L + r;
-      if (cs > 0.0f && Lt >= p.Sm0 && Lt < p.SM0) {
+      if (cs > 0.0f) {
+        cnt.add(ST_SAMPLE2);
+        if (METHOD == kDartsFull) {
+          const float y = (Lt - p.Sm0) * P.inv_S_bin;
+          const int b = (y >= 0.0f && y < (float)P.n_bins) ? min((int)y, P.n_bins - 1) : -1;
+          if (zero_w(P, b)) cnt.add(ST_REJECT2);
+          if (b >= 0) {
+            p.cb2 = p.elem * P.n_bins + b;
+            p.cv2 = cs;
+            p.c += cs;
+          }
+        } else if (!(Lt >= p.Sm0 && Lt < p.SM0)) {
+          cnt.add(ST_REJECT2);
+        }
+      }
+      if (METHOD == kDarts && cs > 0.0f && Lt >= p.Sm0 && Lt < p.SM0) {
         p.c += cs;
         if (ADJ) {
           p.a0 = fmaf(cs, fmaf((float)p.nmed, P.inv_sigma_s, -Lt), p.a0);
@@ -668,7 +746,10 @@ struct Stepper {
         if (!visible(P, qx, qy, qz, p.ey0, p.ey1, p.ey2, -1)) cc = 0.0f;
         cnt.add(ST_CONN);
         const float y = ((p.L + S) - p.Sm0) * P.inv_S_bin;
-        *out_bin = row + min(max((int)floorf(y), 0), P.n_bins - 1);
+        const int b = min(max((int)floorf(y), 0), P.n_bins - 1);
+        cnt.add(ST_SAMPLE);
+        if (zero_w(P, b)) cnt.add(ST_REJECT);
+        *out_bin = row + b;
         *out_c = p.beta * cc;
         p.c += *out_c;
       }
@@ -689,6 +770,8 @@ struct Stepper {
         const float cs = surface_bounce(P, p, dm, hit, nx, ny, nz, &r);
         if (cs > 0.0f) {
           const float y = ((p.L + r) - p.Sm0) * P.inv_S_bin;
+          cnt.add(ST_SAMPLE2);
+          if (zero_w(P, (y >= 0.0f && y < (float)P.n_bins) ? min((int)y, P.n_bins - 1) : -1)) cnt.add(ST_REJECT2);
           if (y >= 0.0f && y < (float)P.n_bins) {
             *out_bin2 = row + min((int)y, P.n_bins - 1);
             *out_c2 = cs;
@@ -731,6 +814,8 @@ struct Stepper {
         if (cs > 0.0f) {
           cnt.add(ST_CONN);
           const float y = ((p.L + r) - p.Sm0) * P.inv_S_bin;
+          cnt.add(ST_SAMPLE);
+          if (zero_w(P, (y >= 0.0f && y < (float)P.n_bins) ? min((int)y, P.n_bins - 1) : -1)) cnt.add(ST_REJECT);
           if (y >= 0.0f && y < (float)P.n_bins) {
             *out_bin = row + min((int)y, P.n_bins - 1);
             *out_c = cs;
@@ -763,6 +848,8 @@ struct Stepper {
       const float C = sqrtf(C2);
       const float cos_s = -__fdividef(ex * p.wx + ey * p.wy + ez * p.wz, C);
       const float y = ((p.L + C) - p.Sm0) * P.inv_S_bin;
+      cnt.add(ST_SAMPLE);
+      if (zero_w(P, (y >= 0.0f && y < (float)P.n_bins) ? min((int)y, P.n_bins - 1) : -1)) cnt.add(ST_REJECT);
       if (y >= 0.0f && y < (float)P.n_bins) {
         cnt.add(ST_CONN);
         float c = p.beta * hg_eval(cos_s, P.hg_a, P.hg_b, P.hg_c) * __expf(-P.sigma_t * C) *
@@ -883,6 +970,13 @@ struct Stepper {
                                ADJ ? &cos_s : nullptr);
       p.c = fmaf(p.beta, cc, p.c);
       cnt.add(ST_CONN);
+      if (METHOD == kDartsFull) {  // committed this step to the bin of its time
+        const int b = min(max((int)floorf(((p.L + S) - p.Sm0) * P.inv_S_bin), 0), P.n_bins - 1);
+        p.cb = b;
+        p.cv = p.beta * cc;
+        cnt.add(ST_SAMPLE);
+        if (zero_w(P, b)) cnt.add(ST_REJECT);
+      }
       if (ADJ) {
         // score of log f: k walk vertices + the control vertex scatter (sigma_s),
         // total length L + S attenuates (sigma_t), HG at every scattering vertex (g)
@@ -1019,6 +1113,8 @@ struct Stepper {
         const float y = ((p.L + S) - P.S_gate_lo) * P.inv_S_bin;
         int b = (int)floorf(y);
         b = min(max(b, 0), P.n_bins - 1);
+        cnt.add(ST_SAMPLE);
+        if (zero_w(P, b)) cnt.add(ST_REJECT);
         *out_bin = b;
         *out_c = p.beta * cc;
         p.c += *out_c;
@@ -1059,6 +1155,8 @@ struct Stepper {
       const float C = sqrtf(C2);
       const float cos_s = -__fdividef(ex * p.wx + ey * p.wy + ez * p.wz, C);
       const float y = ((p.L + C) - P.S_gate_lo) * P.inv_S_bin;
+      cnt.add(ST_SAMPLE);
+      if (zero_w(P, (y >= 0.0f && y < (float)P.n_bins) ? min((int)y, P.n_bins - 1) : -1)) cnt.add(ST_REJECT);
       if (y >= 0.0f && y < (float)P.n_bins) {
         cnt.add(ST_CONN);
         *out_bin = min((int)y, P.n_bins - 1);
@@ -1183,6 +1281,15 @@ __device__ __forceinline__ int add_mod(int a, int r, int B) {
 // warps claim path ids [*counter, N) in chunks of kPathChunk, refill lanes
 // whose path ended, run one vertex step per iteration and commit finished
 // paths into the warp tile (or the adjoint sums).
+// Weight of a finished DARTS path in its bin: B / N_e, or sum W / (N_e W_b)
+// under a temporal response.
+template <bool GEN>
+__device__ __forceinline__ float path_weight(const TraceParams& P, const Path& p) {
+  if (P.wbin == nullptr) return P.wb;
+  const int b = GEN ? p.bin - p.elem * P.n_bins : p.bin;
+  return __ldg(P.wbin + b);
+}
+
 template <int METHOD, int MAXM, bool DEBUG, bool TILE, bool ADJ, bool GEN = false>
 __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab,
                                           unsigned long long* counter, unsigned long long N,
@@ -1191,7 +1298,7 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
                                           float (&g_s)[3], float (&g_c)[3], float (&g_q)[3]) {
   const int lane = threadIdx.x & 31;
   const int B = P.n_bins;
-  constexpr bool kCoop = METHOD == kDarts && MAXM == 8;
+  constexpr bool kCoop = kIsDartsM<METHOD> && MAXM == 8;
   const unsigned long long chunk = P.chunk ? P.chunk : (unsigned long long)kPathChunk;
   Counters cnt;
   Path p;
@@ -1243,10 +1350,14 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
 
     // ---- one vertex step
     cnt.bits = 0;
+    if constexpr (METHOD == kDartsFull) {
+      p.cb = -1;
+      p.cb2 = -1;
+    }
     bool fin = false;
     int cbin = -1, cbin2 = -1;
     float cval = 0.0f, cval2 = 0.0f;
-    if (METHOD == kDarts) {
+    if (kIsDartsM<METHOD>) {
       RisTask task;
       bool need = false;
       if (alive) {
@@ -1266,9 +1377,16 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
         r = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN>::ris_lane(P, task, cnt);
       }
       if (need) fin = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN>::finish_ris(P, p, r, task.nonempty, cnt);
-      if (alive && fin) {
+      if constexpr (METHOD == kDartsFull) {
+        if (alive) {
+          cbin = p.cb;
+          cval = P.wb * p.cv;
+          cbin2 = p.cb2;
+          cval2 = P.wb * p.cv2;
+        }
+      } else if (alive && fin) {
         cbin = p.bin;
-        cval = P.wb * p.c;
+        cval = path_weight<GEN>(P, p) * p.c;
       }
     } else if (alive) {
       if constexpr (GEN) {
@@ -1300,7 +1418,7 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
     }
     if (ADJ) {
       if (alive && fin) {
-        const float wgt = (float)P.dLdh[p.bin] * P.wb;
+        const float wgt = (float)P.dLdh[p.bin] * path_weight<GEN>(P, p);
         const float gv[3] = {wgt * p.a0, wgt * p.a1, wgt * p.a2};
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
@@ -1310,7 +1428,7 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
       }
     } else {
       warp_commit(has, cbin, cval, wsum, wcomp, wsq, TILE, P, do_sq);
-      if constexpr (GEN && METHOD == kPlain) {
+      if constexpr ((GEN && METHOD == kPlain) || METHOD == kDartsFull) {
         if (cbin2 >= 0 && !isfinite(cval2)) {
           atomicOr(P.status, 1u);
           cval2 = 0.0f;
@@ -1321,13 +1439,14 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
     if (fin) alive = false;
     // ---- event counts of this step (lane i keeps counter i of its warp)
     {
+      constexpr int kEvents = (METHOD == kDarts && !GEN) ? ST_SAMPLE : ST_FP64E;
       unsigned mine = 0;
 #pragma unroll
-      for (int e = 0; e < ST_FP64E; ++e) {
+      for (int e = 0; e < kEvents; ++e) {
         const unsigned c = __popc(__ballot_sync(kFull, (cnt.bits >> e) & 1u));
         mine = lane == e ? c : mine;
       }
-      if (lane < ST_FP64E) wev[lane] += mine;
+      if (lane < kEvents) wev[lane] += mine;
     }
   }
 
@@ -1337,14 +1456,14 @@ template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK, bool ADJ = fal
 __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
-  const int tab_floats = METHOD == kDarts ? P.rows * P.row_stride : 0;
+  const int tab_floats = kIsDartsM<METHOD> ? P.rows * P.row_stride : 0;
   float* tab = smem;
   constexpr int nwarps = BLOCK / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int B = P.n_bins;
   const bool do_sq = P.sumsq != nullptr;
   const int tile_stride = (do_sq ? 3 : 2) * B;
-  constexpr bool kCoop = METHOD == kDarts && MAXM == 8;
+  constexpr bool kCoop = kIsDartsM<METHOD> && MAXM == 8;
   RisTask* ris_tasks = reinterpret_cast<RisTask*>(smem + tab_floats);
   RisResult* ris_results = reinterpret_cast<RisResult*>(ris_tasks + (kCoop ? nwarps * 32 : 0));
   RisTask* wtasks = ris_tasks + warp * 32;
@@ -1354,10 +1473,10 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
   float* wcomp = wsum + B;
   float* wsq = wcomp + B;
   __shared__ unsigned long long blk_stats[kStatCount];
-  __shared__ unsigned warp_events[nwarps][8];
+  __shared__ unsigned warp_events[nwarps][ST_FP64E];
 
   // stage the direction table (row stride is a multiple of 4 floats)
-  if (METHOD == kDarts) {
+  if (kIsDartsM<METHOD>) {
     const float4* src = reinterpret_cast<const float4*>(P.table);
     for (int i = threadIdx.x; i < tab_floats / 4; i += BLOCK) smem4[i] = __ldg(src + i);
   }
@@ -1365,7 +1484,7 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
     for (int i = threadIdx.x; i < nwarps * tile_stride; i += BLOCK) tiles[i] = 0.0f;
   if (threadIdx.x < kStatCount) blk_stats[threadIdx.x] = 0;
   if (threadIdx.x < 2) s_rare[threadIdx.x] = 0;
-  if (lane < 8) warp_events[warp][lane] = 0;
+  if (lane < ST_FP64E) warp_events[warp][lane] = 0;
   __syncthreads();
 
   // adjoint: per-lane Kahan sums of the weighted path scores and their squares
@@ -1479,7 +1598,7 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_batch_kernel(const BatchParams
   __shared__ TraceParams Ps;
   __shared__ int s_item;
   __shared__ unsigned long long s_counter;
-  __shared__ unsigned warp_events[BLOCK / 32][8];
+  __shared__ unsigned warp_events[BLOCK / 32][ST_FP64E];
   constexpr int nwarps = BLOCK / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tab_floats = BP.rows * BP.row_stride;
@@ -1491,7 +1610,7 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_batch_kernel(const BatchParams
   float* wsum = tiles + (size_t)warp * tile_stride;
   for (int i = threadIdx.x; i < nwarps * tile_stride; i += BLOCK) tiles[i] = 0.0f;
   if (threadIdx.x < 2) s_rare[threadIdx.x] = 0;
-  if (lane < 8) warp_events[warp][lane] = 0;
+  if (lane < ST_FP64E) warp_events[warp][lane] = 0;
   float g_s[3] = {0.0f, 0.0f, 0.0f}, g_c[3] = {0.0f, 0.0f, 0.0f}, g_q[3] = {0.0f, 0.0f, 0.0f};
   int cur = -1;
   __syncthreads();
@@ -1596,7 +1715,7 @@ cudaError_t launch_method(const TraceParams& p, int grid, int block, bool debug,
     return tile ? launch_one<METHOD, 8, false, true, 512, true>(p, grid, smem, s)
                 : launch_one<METHOD, 8, false, false, 512, true>(p, grid, smem, s);
   }
-  const bool m8 = METHOD != kDarts || p.M == 8;
+  const bool m8 = !kIsDartsM<METHOD> || p.M == 8;
   if (debug) {
     if (!m8) return tile ? launch_one<METHOD, kMaxM, true, true, 512>(p, grid, smem, s)
                          : launch_one<METHOD, kMaxM, true, false, 512>(p, grid, smem, s);
@@ -1606,10 +1725,14 @@ cudaError_t launch_method(const TraceParams& p, int grid, int block, bool debug,
   if (!m8) return tile ? launch_one<METHOD, kMaxM, false, true, 512>(p, grid, smem, s)
                        : launch_one<METHOD, kMaxM, false, false, 512>(p, grid, smem, s);
   if (!tile) return launch_one<METHOD, 8, false, false, 512>(p, grid, smem, s);
-  switch (block) {
-    case 640: return launch_one<METHOD, 8, false, true, 640>(p, grid, smem, s);
-    case 768: return launch_one<METHOD, 8, false, true, 768>(p, grid, smem, s);
-    default: return launch_one<METHOD, 8, false, true, 512>(p, grid, smem, s);
+  if constexpr (METHOD == kDartsFull) {  // built for 512 threads only
+    return launch_one<METHOD, 8, false, true, 512>(p, grid, smem, s);
+  } else {
+    switch (block) {
+      case 640: return launch_one<METHOD, 8, false, true, 640>(p, grid, smem, s);
+      case 768: return launch_one<METHOD, 8, false, true, 768>(p, grid, smem, s);
+      default: return launch_one<METHOD, 8, false, true, 512>(p, grid, smem, s);
+    }
   }
 }
 
@@ -1678,8 +1801,9 @@ cudaError_t launch_adjoint(const TraceParams& p0, int grid, size_t smem, cudaStr
 }
 
 size_t trace_smem_bytes(int method, const TraceParams& p, int block, bool tile) {
-  size_t b = method == kDarts ? (size_t)p.rows * p.row_stride * sizeof(float) : 0;
-  if (method == kDarts && p.M == 8) b += (size_t)(block / 32) * 32 * (sizeof(RisTask) + sizeof(RisResult));
+  const bool darts = method == kDarts || method == kDartsFull;
+  size_t b = darts ? (size_t)p.rows * p.row_stride * sizeof(float) : 0;
+  if (darts && p.M == 8) b += (size_t)(block / 32) * 32 * (sizeof(RisTask) + sizeof(RisResult));
   if (tile) b += (size_t)(block / 32) * (p.sumsq ? 3 : 2) * p.n_bins * sizeof(float);
   return b;
 }
@@ -1687,7 +1811,7 @@ size_t trace_smem_bytes(int method, const TraceParams& p, int block, bool tile) 
 int trace_max_m() { return kMaxM; }
 
 int trace_block_for(int block, bool debug, bool tile, int method, int M, bool general) {
-  if (general || debug || !tile || (method == kDarts && M != 8)) return 512;
+  if (general || debug || !tile || method == kDartsFull || (method == kDarts && M != 8)) return 512;
   return (block == 640 || block == 768) ? block : 512;
 }
 
@@ -1699,6 +1823,7 @@ cudaError_t launch_trace(int method, const TraceParams& p0, int grid, int block,
     case kDarts: return launch_method<kDarts>(p, grid, block, debug, tile, smem, s);
     case kPlain: return launch_method<kPlain>(p, grid, block, debug, tile, smem, s);
     case kVanilla: return launch_method<kVanilla>(p, grid, block, debug, tile, smem, s);
+    case kDartsFull: return launch_method<kDartsFull>(p, grid, block, debug, tile, smem, s);
     default: return cudaErrorInvalidValue;
   }
 }

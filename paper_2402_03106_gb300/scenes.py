@@ -15,7 +15,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field, replace
-from typing import List, Sequence, Tuple
+from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -81,9 +81,14 @@ class Sensor:
 
 @dataclass
 class Gate:
+    """Time gate [t_min, t_max) in n_bins equal bins.  weights (optional):
+    the sensor's temporal response W, one value >= 0 per bin; DARTS then
+    samples each path's target bin from W (zero-weight bins get no paths)
+    and the W-weighted pixel value is sum_b W_b h_b."""
     t_min: float
     t_max: float
     n_bins: int
+    weights: Optional[Sequence[float]] = None
 
 
 # Box faces that carry walls: bit 2*axis + side (side 1 = the high face).

@@ -11,6 +11,8 @@ REL_PATH = 1e-4
 # the length L + S_hi it is measured against carries that error magnified by
 # cond = (L + S_hi) / (S_hi - S_lo), the oracle's per-path conditioning number.
 COND_EPS = 4e-7
+# a decision this close to its threshold is a tie at FP32 resolution
+EXACT_TIE = 1e-6
 
 
 def compare_paths(gpu, ref, K):
@@ -62,13 +64,21 @@ def displaced_sensitivity(sc, sp, first, n, method, ref, shift=1e-6):
 
 
 def check_paths(gpu, ref, K, rel_tol=REL_PATH, max_flip_frac=0.01, extra_tol=None):
+    """Flips must sit at a decision the oracle met within NEAR_TIE of its
+    threshold.  Flips at an exact tie (margin below FP32 resolution, e.g. a
+    bin edge that coincides with a table cell edge, rho = C/S_M = 1/2) may be
+    any number; the others at most max_flip_frac of the paths."""
     same, rel, rep = compare_paths(gpu, ref, K)
     n = len(same)
-    assert (~same).sum() <= max(2, max_flip_frac * n), f"{(~same).sum()} of {n} traces differ"
     if len(rep["margins"]):
         assert rep["margins"].max() < NEAR_TIE, f"trace flip away from a tie: {rep['margins']}"
+    n_soft = int(np.sum(rep["margins"] >= EXACT_TIE)) if len(rep["margins"]) else 0
+    assert n_soft <= max(2, max_flip_frac * n), f"{n_soft} of {n} traces differ away from exact ties"
     nd = (ref["flags"] & O.FLAG_NEAR_DEGENERATE) != 0
-    ok = same & ~nd
+    # a path that met an exact tie may have taken the other branch of a
+    # decision the trace does not record (the table cell of an EDA sample)
+    tie = ref["margin"].min(axis=1) < EXACT_TIE
+    ok = same & ~nd & ~tie
     tol = np.maximum(rel_tol, COND_EPS * ref["cond"])
     if extra_tol is not None:
         tol = np.maximum(tol, extra_tol)

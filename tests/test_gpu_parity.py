@@ -97,7 +97,7 @@ def test_darts_per_path_parity_dense_medium(ctx):
     check_paths(gpu, ref, 50, max_flip_frac=0.03)
 
 
-@pytest.mark.parametrize("method", [S.PLAIN_UNIFORM_T, S.VANILLA_DIRECT])
+@pytest.mark.parametrize("method", [S.PLAIN_UNIFORM_T, S.VANILLA_DIRECT, S.DARTS_FULL_GATE])
 def test_baseline_per_path_parity(ctx, method):
     sc, sp = S.cube_workload(paths=1 << 14, seed=4)
     sp.method = method
@@ -107,7 +107,7 @@ def test_baseline_per_path_parity(ctx, method):
     check_paths(gpu, ref, sp.max_bounces)
 
 
-@pytest.mark.parametrize("method", [S.DARTS, S.PLAIN_UNIFORM_T, S.VANILLA_DIRECT])
+@pytest.mark.parametrize("method", [S.DARTS, S.PLAIN_UNIFORM_T, S.VANILLA_DIRECT, S.DARTS_FULL_GATE])
 def test_histogram_parity_matched_seeds(ctx, method):
     sc, sp = S.cube_workload(paths=1 << 16, seed=0)
     sp.method = method

@@ -56,7 +56,7 @@ SCENES = {
 
 
 @pytest.mark.parametrize("name", sorted(SCENES))
-@pytest.mark.parametrize("method", [S.DARTS, S.PLAIN_UNIFORM_T, S.VANILLA_DIRECT])
+@pytest.mark.parametrize("method", [S.DARTS, S.PLAIN_UNIFORM_T, S.VANILLA_DIRECT, S.DARTS_FULL_GATE])
 def test_general_per_path_parity(ctx, name, method):
     sc = SCENES[name]()
     sp = S.Sampling(seed=5, paths_per_element=8 if sc.sensor.kind == S.SENSOR_PINHOLE else 1 << 14,
@@ -77,7 +77,7 @@ def test_general_per_path_parity(ctx, name, method):
 
 
 @pytest.mark.parametrize("name", sorted(SCENES))
-@pytest.mark.parametrize("method", [S.DARTS, S.PLAIN_UNIFORM_T, S.VANILLA_DIRECT])
+@pytest.mark.parametrize("method", [S.DARTS, S.PLAIN_UNIFORM_T, S.VANILLA_DIRECT, S.DARTS_FULL_GATE])
 def test_general_histogram_parity(ctx, name, method):
     sc = SCENES[name]()
     if sc.sensor.kind == S.SENSOR_PINHOLE:

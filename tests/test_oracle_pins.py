@@ -612,3 +612,66 @@ def test_full_gate_paths_follow_the_darts_decisions():
     assert np.array_equal(a["decisions"][..., :2], b["decisions"][..., :2])
     np.testing.assert_allclose(a["contrib"], b["contrib"], rtol=1e-12)
     assert np.all(b["bin"] == -1)
+
+
+# ---------------------------------------------------------------------------
+# Temporal response W(t): the interval of a path sampled from W (Sec. 5.2,
+# Fig. 7), and the rejection of samples by a zero weight
+# ---------------------------------------------------------------------------
+def _two_peak_weights(n_bins, t_min, t_max, peaks=((1.6, 0.12), (2.6, 0.2))):
+    t = t_min + (np.arange(n_bins) + 0.5) * (t_max - t_min) / n_bins
+    w = np.zeros(n_bins)
+    for c, s_ in peaks:
+        w += np.exp(-0.5 * ((t - c) / s_) ** 2)
+    w[w < 1e-3] = 0.0
+    return w
+
+
+def test_weighted_bins_receive_paths_in_proportion_to_w():
+    sc, _ = S.cube_workload()
+    sc.gate = S.Gate(0.8, 3.6, 28, list(_two_peak_weights(28, 0.8, 3.6)))
+    n = 28 * 300 + 11
+    sp = S.Sampling(seed=4, paths_per_element=n, max_bounces=2)
+    r = O.trace_paths(sc, sp, 0, n)
+    counts = np.bincount(r["bin"], minlength=28)
+    w = np.asarray(sc.gate.weights)
+    expect = n * w / w.sum()
+    assert np.all(counts[w == 0] == 0)
+    # systematic sampling: every bin within one path of its expectation
+    assert np.max(np.abs(counts - expect)) <= 1.0 + 1e-9, (counts, expect)
+
+
+def test_weighted_darts_estimates_the_same_histogram():
+    """With W the DARTS histogram of every bin of non-zero weight has the same
+    expectation as the uniform-temporal tracer's (the W-weighted sum follows)."""
+    sc = S.slab_scene(1.0, 0.02, 0.5, n_bins=14, t_min=0.85, t_max=3.65)
+    w = _two_peak_weights(14, 0.85, 3.65)
+    sc.gate.weights = list(w)
+    n = 1 << 17
+    h, sq, _ = O.render(sc, S.Sampling(seed=41, paths_per_element=n, max_bounces=4))
+    nb = n * w / w.sum()
+    se = O.standard_error(h, sq, np.maximum(nb, 1.0))
+    sc2 = S.slab_scene(1.0, 0.02, 0.5, n_bins=14, t_min=0.85, t_max=3.65)
+    h2, sq2, _ = O.render(sc2, S.Sampling(seed=42, paths_per_element=n, max_bounces=4), O.ORC_PLAIN_UNIFORM_T)
+    se2 = O.standard_error(h2, sq2, n)
+    on = w > 0
+    z = (h[on] - h2[on]) / np.sqrt(se[on] ** 2 + se2[on] ** 2)
+    assert np.max(np.abs(z[1:])) < 4.5, z
+    assert np.all(h[~on] == 0.0)
+    zw = (w @ h - w @ h2) / np.sqrt(np.sum((w * se) ** 2 + (w * se2) ** 2))
+    assert abs(zw) < 4.5
+
+
+def test_rejection_rates_two_peak_response():
+    """Fig. 7's statistic: with a two-peak W most vanilla samples carry zero
+    weight, DARTS rejects almost none (only surface connections outside the
+    path's bin, none in a medium-only scene)."""
+    sc = S.slab_scene(1.0, 0.02, 0.5, n_bins=28, t_min=0.8, t_max=3.6)
+    sc.gate.weights = list(_two_peak_weights(28, 0.8, 3.6))
+    n = 1 << 14
+    rates = {}
+    for name, m in (("darts", O.ORC_DARTS), ("plain", O.ORC_PLAIN_UNIFORM_T), ("vanilla", O.ORC_VANILLA_DIRECT)):
+        _, _, st = O.render(sc, S.Sampling(seed=5, paths_per_element=n, max_bounces=20), m)
+        rates[name] = st["rejected"] / st["samples"]
+    assert rates["darts"] == 0.0
+    assert rates["vanilla"] > 0.5 and rates["plain"] > 0.2, rates
