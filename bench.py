@@ -317,7 +317,8 @@ def mse_time_camera(ctx, S, torch, seeds=16, spps=(16, 64)):
     pixels and bins); ratio = (MSE x time)_base / (MSE x time)_darts with the
     median render time (table build + trace, CUDA events)."""
     sc = S.box_camera_scene(seed=0)
-    methods = (("darts", S.DARTS), ("plain_uniform_t", S.PLAIN_UNIFORM_T), ("vanilla_direct", S.VANILLA_DIRECT))
+    methods = (("darts", S.DARTS), ("plain_uniform_t", S.PLAIN_UNIFORM_T), ("vanilla_direct", S.VANILLA_DIRECT),
+               ("darts_full_gate", S.DARTS_FULL_GATE))
     out = {"workload": "box camera of the benchmark, 64x64, 512 bins, K=50", "seeds": seeds}
     for spp in spps:
         H, T = {}, {}
@@ -325,7 +326,7 @@ def mse_time_camera(ctx, S, torch, seeds=16, spps=(16, 64)):
             acc, ts = [], []
             for s_ in range(seeds):
                 sp = S.Sampling(seed=101 + s_, paths_per_element=spp, max_bounces=50, method=m,
-                                flags=S.FLAG_REBUILD_TABLE if m == S.DARTS else 0)
+                                flags=S.FLAG_REBUILD_TABLE if m in (S.DARTS, S.DARTS_FULL_GATE) else 0)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
                 h = ctx.render(sc, sp)
@@ -342,12 +343,15 @@ def mse_time_camera(ctx, S, torch, seeds=16, spps=(16, 64)):
             mse = (d * d).double().mean(1)
             res[name] = {"seconds_per_render": T[name], "mse_mean": float(mse.mean()),
                          "mse_median": float(mse.median())}
-        for base in ("plain_uniform_t", "vanilla_direct"):
+        for base in ("plain_uniform_t", "vanilla_direct", "darts_full_gate"):
             res[f"ratio_{base}_over_darts"] = {
                 "mse_mean_time": (res[base]["mse_mean"] * res[base]["seconds_per_render"]) /
                                  max(res["darts"]["mse_mean"] * res["darts"]["seconds_per_render"], 1e-300),
                 "mse_median_time": (res[base]["mse_median"] * res[base]["seconds_per_render"]) /
                                    max(res["darts"]["mse_median"] * res["darts"]["seconds_per_render"], 1e-300)}
+        res["ratio_plain_uniform_t_over_darts_full_gate"] = {
+            "mse_mean_time": (res["plain_uniform_t"]["mse_mean"] * res["plain_uniform_t"]["seconds_per_render"]) /
+                             max(res["darts_full_gate"]["mse_mean"] * res["darts_full_gate"]["seconds_per_render"], 1e-300)}
         out[f"spp_{spp}"] = res
         del H
     return out
@@ -394,6 +398,54 @@ def mse_time_gated(ctx, S, torch, seeds=16, spp=64):
                 "mse_median_time": (res[base]["mse_median"] * res[base]["seconds_per_render"]) /
                                    max(res["darts"]["mse_median"] * res["darts"]["seconds_per_render"], 1e-300)}
         out[f"gate_{centre - width / 2:g}_{centre + width / 2:g}"] = res
+    return out
+
+
+def two_peak_response(ctx, S, torch, seeds=16, spp=64):
+    """Fig. 7 on the camera box: a temporal response W with two peaks (t = 5
+    and 9) over 64 bins on [0, 16).  DARTS samples each path's bin from W;
+    the baselines bin every sample by its time.  Reported: MSE x time of the
+    W-weighted image sum_b W_b h_b (pooled mean of DARTS and uniform-temporal
+    as reference), and the fraction of samples rejected by a zero weight."""
+    import numpy as np
+    sc = S.box_camera_scene(seed=0, n_bins=64, t_max=16.0)
+    t = (np.arange(64) + 0.5) * 0.25
+    w = np.exp(-0.5 * ((t - 5.0) / 0.4) ** 2) + np.exp(-0.5 * ((t - 9.0) / 0.6) ** 2)
+    w[w < 1e-3] = 0.0
+    sc.gate.weights = [float(x) for x in w]
+    wt = torch.tensor(w, dtype=torch.float64, device="cuda")
+    methods = (("darts", S.DARTS), ("plain_uniform_t", S.PLAIN_UNIFORM_T), ("vanilla_direct", S.VANILLA_DIRECT))
+    out = {"workload": "box camera 64x64, 64 bins on [0,16), W = two Gaussian peaks (5 +- 0.4, 9 +- 0.6) "
+                       "cut below 1e-3, K=50", "seeds": seeds, "spp": spp}
+    imgs, T = {}, {}
+    for name, m in methods:
+        acc, ts = [], []
+        for s_ in range(seeds):
+            sp = S.Sampling(seed=501 + s_, paths_per_element=spp, max_bounces=50, method=m,
+                            flags=S.FLAG_REBUILD_TABLE if m == S.DARTS else 0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            h = ctx.render(sc, sp)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+            acc.append((h * wt).sum(-1).reshape(-1))
+            if s_ == 0:
+                st = ctx.stats()
+                out.setdefault("rejected_fraction", {})[name] = st["rejected"] / max(st["samples"], 1)
+        imgs[name] = torch.stack(acc)
+        T[name] = statistics.median(ts)
+    ref = torch.cat([imgs["darts"], imgs["plain_uniform_t"]]).mean(0)
+    for name, _ in methods:
+        d = imgs[name] - ref
+        mse = (d * d).mean(1)
+        out[name] = {"seconds_per_render": T[name], "mse_mean": float(mse.mean()), "mse_median": float(mse.median())}
+    for base in ("plain_uniform_t", "vanilla_direct"):
+        out[f"ratio_{base}_over_darts"] = {
+            "mse_mean_time": (out[base]["mse_mean"] * out[base]["seconds_per_render"]) /
+                             max(out["darts"]["mse_mean"] * out["darts"]["seconds_per_render"], 1e-300),
+            "mse_median_time": (out[base]["mse_median"] * out[base]["seconds_per_render"]) /
+                               max(out["darts"]["mse_median"] * out["darts"]["seconds_per_render"], 1e-300)}
     return out
 
 
@@ -592,6 +644,7 @@ def main():
     if not args.no_mse:
         extra["mse_time_box_camera"] = mse_time_camera(ctx, S, torch)
         extra["mse_time_gated"] = mse_time_gated(ctx, S, torch)
+        extra["two_peak_response"] = two_peak_response(ctx, S, torch)
         extra["mse_time_cube"] = mse_time(ctx, S, torch)
     extra["batched"] = batched_compare(ctx, S, torch)
     cpu = cpu_baseline(args.workload) if ws == 1 else None
