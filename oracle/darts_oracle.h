@@ -146,11 +146,15 @@ int orc_table_row(const orc_scene* sc, double C, double SM, double* margin);
  * (0 when it has none) -- how strongly an absolute error in the path length
  * L or in the window bounds [S_lo, S_hi) of Eq. 21 is magnified in the
  * contribution, a conditioning number for reduced-precision comparisons.
- * cdf may be NULL for methods other than DARTS.  Returns 0 on success. */
+ * tabcond[i] (optional): the sum over the path's MIS directions of
+ * gamma n_mu / (2 pi p_mix), the relative change of its throughput per unit
+ * error of the direction table's CDF values (Eq. 19 evaluates p_EDA from
+ * two of them).  cdf may be NULL for methods other than DARTS.  Returns 0 on
+ * success. */
 int orc_trace_paths(const orc_scene* sc, int method, const double* cdf,
                     uint64_t first, uint32_t count, double* contrib,
                     int32_t* bin, uint8_t* decisions, double* margin,
-                    int32_t* flags, int32_t* nbounce, double* cond);
+                    int32_t* flags, int32_t* nbounce, double* cond, double* tabcond);
 
 /* Distance step (Eq. 12-15) of vertex k from an explicit state, for tests:
  * candidate distances, validity, log RIS weights, selected index (-1 when

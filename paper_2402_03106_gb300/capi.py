@@ -333,6 +333,26 @@ def darts_render_static(scene, sampling, hist: torch.Tensor, sumsq: Optional[tor
 # ----------------------------------------------------------------------------
 # Convenience layer
 # ----------------------------------------------------------------------------
+class Prepared:
+    """A scene and sampling converted once into the C structs; render() then
+    calls darts_render directly with them.  Changing the scene objects later
+    does not affect a Prepared: prepare again."""
+
+    def __init__(self, ctx: "Context", scene, sampling):
+        self.ctx = ctx
+        self.cs, self._keep = to_c_scene(scene)
+        self.csp = to_c_sampling(sampling)
+        self.shape = S.histogram_shape(scene)
+        self._lib = load()
+
+    def render(self, out: Optional[torch.Tensor] = None, sumsq: Optional[torch.Tensor] = None,
+               path_offset: int = 0) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device=self.ctx._dev())
+        _check(self.ctx.h, self._lib.darts_render(self.ctx.h, C.byref(self.cs), C.byref(self.csp), _ptr(out),
+                                                  _ptr(sumsq), int(path_offset), None))
+        return out
+
 class Context:
     """A libdarts context on one CUDA device, ordered on a torch stream."""
 
@@ -371,6 +391,12 @@ class Context:
         sq = torch.empty(shape, dtype=torch.float64, device=self._dev()) if sumsq else None
         darts_render(self.h, scene, sampling, hist, sq, path_offset, probe)
         return (hist, sq) if sumsq else hist
+
+    def prepare(self, scene, sampling) -> "Prepared":
+        """Marshal a scene and sampling once for repeated renders (the
+        per-call conversion of render() costs tens of microseconds of host
+        time, comparable to a whole camera frame on the GPU)."""
+        return Prepared(self, scene, sampling)
 
     def render_host(self, scene, sampling, hist_host: torch.Tensor,
                     sumsq_host: Optional[torch.Tensor] = None, path_offset: int = 0):

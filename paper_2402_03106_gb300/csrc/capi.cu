@@ -228,6 +228,7 @@ darts_status validate(darts_ctx* ctx, const darts_scene* sc, const darts_samplin
 }
 
 void make_table_params(const darts_scene* sc, const darts_sampling* sp, TableParams* tp) {
+  std::memset(tp, 0, sizeof(*tp));
   const darts_medium& m = sc->medium;
   const double D = 1.0 / (3.0 * (m.sigma_a + m.sigma_s * (1.0 - m.g)));
   tp->sigma_t = (float)(m.sigma_s + m.sigma_a);
@@ -267,7 +268,16 @@ void table_key(const darts_scene* sc, const darts_sampling* sp, double key[9]) {
 }
 
 // Build (or reuse) the context's cached table for this scene.
-darts_status ensure_table(darts_ctx* ctx, const darts_scene* sc, const darts_sampling* sp) {
+// Outputs the table launch may zero for the path launch that follows it.
+struct ZeroSpec {
+  double* a = nullptr;
+  double* b = nullptr;
+  unsigned long long n = 0;
+  bool zeroed = false;  // set when the table launch did it (and the scratch counters)
+};
+
+darts_status ensure_table(darts_ctx* ctx, const darts_scene* sc, const darts_sampling* sp,
+                          ZeroSpec* z = nullptr) {
   double key[9];
   table_key(sc, sp, key);
   const bool hit = ctx->table_valid && std::memcmp(key, ctx->table_key, sizeof(key)) == 0 &&
@@ -278,7 +288,15 @@ darts_status ensure_table(darts_ctx* ctx, const darts_scene* sc, const darts_sam
   const size_t bytes = (size_t)tp.n_rho * tp.n_s * tp.row_stride * sizeof(float);
   CK(ensure((void**)&ctx->table, &ctx->table_bytes, bytes), "table allocation");
   tp.cdf = ctx->table;
+  if (z) {  // the path counter and the statistics (not the ticket/status word), and the outputs
+    tp.zero_a = z->a;
+    tp.zero_b = z->b;
+    tp.zero_n = z->a ? z->n : 0;
+    tp.zero_scratch = ctx->scratch;
+    tp.zero_scratch_n = 2 + kStatCount;
+  }
   CK(launch_table(tp, ctx->stream), "table kernel launch");
+  if (z) z->zeroed = true;
   std::memcpy(ctx->table_key, key, sizeof(key));
   ctx->table_valid = true;
   return DARTS_OK;
@@ -504,7 +522,7 @@ void choose_launch(const darts_ctx* ctx, const darts_sampling* sp, const TracePa
 }
 
 darts_status run_trace(darts_ctx* ctx, const darts_scene* sc, const darts_sampling* sp,
-                       TraceParams& P, bool debug) {
+                       TraceParams& P, bool debug, bool zeroed = false) {
   {
     const darts_status sw = set_weights(ctx, sc, sp, P);
     if (sw != DARTS_OK) return sw;
@@ -521,14 +539,16 @@ darts_status run_trace(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
   const size_t pbytes = (size_t)grid * 2 * P.n_bins * sizeof(double);
   CK(ensure((void**)&ctx->partials, &ctx->partials_bytes, pbytes), "partials allocation");
   P.partials = ctx->partials;
-  if (!tile) {  // contributions go straight into the (zeroed) outputs
-    const size_t ob = elements_of(sc) * (size_t)P.n_bins * sizeof(double);
-    CK(cudaMemsetAsync(P.hist, 0, ob, ctx->stream), "memset");
-    if (P.sumsq) CK(cudaMemsetAsync(P.sumsq, 0, ob, ctx->stream), "memset");
+  if (!zeroed) {  // else the table launch just before did this
+    if (!tile) {  // contributions go straight into the (zeroed) outputs
+      const size_t ob = elements_of(sc) * (size_t)P.n_bins * sizeof(double);
+      CK(cudaMemsetAsync(P.hist, 0, ob, ctx->stream), "memset");
+      if (P.sumsq) CK(cudaMemsetAsync(P.sumsq, 0, ob, ctx->stream), "memset");
+    }
+    // zero the path counter and the statistics (ticket and status persist)
+    CK(cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), ctx->stream), "memset");
+    CK(cudaMemsetAsync(ctx->scratch + 2, 0, kStatCount * sizeof(unsigned long long), ctx->stream), "memset");
   }
-  // zero the path counter and the statistics (ticket and status persist)
-  CK(cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), ctx->stream), "memset");
-  CK(cudaMemsetAsync(ctx->scratch + 2, 0, kStatCount * sizeof(unsigned long long), ctx->stream), "memset");
   ctx->last_paths = P.N;
   if (ctx->timing) CK(cudaEventRecord(ctx->ev_start, ctx->stream), "event record");
   CK(launch_trace(sp->method, P, grid, block, debug, tile, smem, ctx->stream), "trace kernel launch");
@@ -743,8 +763,12 @@ darts_status darts_render(darts_ctx* ctx, const darts_scene* scene, const darts_
     ctx->last_paths = 0;
     return DARTS_OK;
   }
+  ZeroSpec z;
+  z.a = hist_dev;
+  z.b = sumsq_dev;
+  z.n = elements_of(scene) * (unsigned long long)scene->gate.n_bins;
   if (uses_table(sampling->method)) {
-    s = ensure_table(ctx, scene, sampling);
+    s = ensure_table(ctx, scene, sampling, &z);
     if (s != DARTS_OK) return s;
   }
   TraceParams P;
@@ -760,7 +784,7 @@ darts_status darts_render(darts_ctx* ctx, const darts_scene* scene, const darts_
     P.probe_c = probe->contrib_dev;
     P.probe_b = probe->bin_dev;
   }
-  return run_trace(ctx, scene, sampling, P, false);
+  return run_trace(ctx, scene, sampling, P, false, z.zeroed);
 }
 
 darts_status darts_render_host(darts_ctx* ctx, const darts_scene* scene,

@@ -36,6 +36,12 @@ struct TableParams {
   float mu_x[kMaxTabMuNodes], mu_w[kMaxTabMuNodes];
   float t_x[kMaxTabTNodes], t_w[kMaxTabTNodes];
   float* cdf;      // [rows][row_stride]
+  // outputs of the path launch that follows, zeroed by this launch (null: none)
+  double* zero_a;
+  double* zero_b;
+  unsigned long long zero_n;       // doubles in each of zero_a, zero_b
+  unsigned long long* zero_scratch; // the context's scratch words; word 1 is kept
+  int zero_scratch_n;
 };
 
 // Path kernels.  Everything the step functions read, in FP32 unless noted.

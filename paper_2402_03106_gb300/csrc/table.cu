@@ -17,7 +17,8 @@
 namespace darts {
 namespace {
 
-constexpr int kTableThreads = 256;
+constexpr int kTableThreads = 1024;  // 4 lanes per cos bin: one Gauss node each
+constexpr int kScanThreads = 256;    // bins per pass of the CDF scan
 constexpr int kMaxMu = 1024;
 
 __device__ __forceinline__ float warp_incl_scan(float v, int lane) {
@@ -29,10 +30,24 @@ __device__ __forceinline__ float warp_incl_scan(float v, int lane) {
   return v;
 }
 
+// Zero the outputs of the path launch that follows (grid-stride over all
+// table blocks), so that a render needs no separate memset launches.
+__device__ __forceinline__ void zero_outputs(const TableParams& P, int block, int nblocks) {
+  if (P.zero_n) {
+    const unsigned long long stride = (unsigned long long)nblocks * kTableThreads;
+    for (unsigned long long i = (unsigned long long)block * kTableThreads + threadIdx.x; i < P.zero_n; i += stride) {
+      P.zero_a[i] = 0.0;
+      if (P.zero_b) P.zero_b[i] = 0.0;
+    }
+  }
+  // scratch word 1 (last-block ticket and device status) persists
+  if (block == 0 && (int)threadIdx.x < P.zero_scratch_n && threadIdx.x != 1) P.zero_scratch[threadIdx.x] = 0ull;
+}
+
 __device__ __forceinline__ void table_row(const TableParams& P, const int row) {
   __shared__ float logF[kMaxMu];
-  __shared__ float wsum[kTableThreads / 32];
-  __shared__ float wmax[kTableThreads / 32];
+  __shared__ float wsum[kScanThreads / 32];
+  __shared__ float wmax[kScanThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i_rho = row / P.n_s, i_s = row - i_rho * P.n_s;
   const float rho = (i_rho + 0.5f) / P.n_rho;
@@ -40,21 +55,23 @@ __device__ __forceinline__ void table_row(const TableParams& P, const int row) {
   const float C = rho * S;
   const float SmC = S * (1.0f - rho);  // S - C
   const float h = 2.0f / P.n_mu;
-  const int per = (P.n_mu + kTableThreads - 1) / kTableThreads;
 
-  float local_max = -FLT_MAX;
-  for (int q = 0; q < per; ++q) {
-    const int i = tid * per + q;
-    if (i >= P.n_mu) break;
+  // ---- bin integrals: lane group g = tid / 4 takes bins g, g + 256, ...;
+  // lane a = tid % 4 integrates Gauss node a of the bin, the group merges
+  // its four partial sums (online log-sum-exp) with shuffles
+  const int a = tid & 3;
+  const float xa1 = P.mu_x[a] + 1.0f;
+  const float wa = 0.5f * h * P.mu_w[a];
+  for (int i0 = tid >> 2; i0 < kMaxMu; i0 += kTableThreads / 4) {
+    if (i0 - (tid >> 2) >= P.n_mu) break;  // uniform across the block
+    const int i = i0;
     float m = -FLT_MAX, s = 0.0f;
-    for (int a = 0; a < kMaxTabMuNodes; ++a) {
-      const float xa1 = P.mu_x[a] + 1.0f;
+    if (i < P.n_mu) {
       const float onem = h * ((float)(P.n_mu - i) - 0.5f * xa1);  // 1 - mu
       const float mu = 1.0f - onem;
       const float tM = SmC * (S + C) / (2.0f * fmaf(C, onem, SmC));
       const float cmu = C * mu;
       const float split = (cmu > 0.0f && cmu < tM) ? cmu : 0.5f * tM;
-      const float wa = 0.5f * h * P.mu_w[a];
 #pragma unroll 1
       for (int panel = 0; panel < 2; ++panel) {
         const float lo = panel == 0 ? 0.0f : split;
@@ -73,19 +90,34 @@ __device__ __forceinline__ void table_row(const TableParams& P, const int row) {
         }
       }
     }
-    const float lf = m + __logf(s);
-    logF[i] = lf;
-    local_max = fmaxf(local_max, lf);
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+      const float mo = __shfl_xor_sync(0xFFFFFFFFu, m, o);
+      const float so = __shfl_xor_sync(0xFFFFFFFFu, s, o);
+      const float mn = fmaxf(m, mo);
+      s = (s > 0.0f ? s * __expf(m - mn) : 0.0f) + (so > 0.0f ? so * __expf(mo - mn) : 0.0f);
+      m = mn;
+    }
+    if (a == 0 && i < P.n_mu) logF[i] = m + __logf(s);
   }
-  // row maximum of log F
+  __syncthreads();
+  if (tid >= kScanThreads) return;
+
+  // ---- row maximum of log F, then per-thread runs of consecutive bins and
+  // a block-wide exclusive scan (the first kScanThreads threads)
+  const int per = (P.n_mu + kScanThreads - 1) / kScanThreads;
+  float local_max = -FLT_MAX;
+  for (int q = 0; q < per; ++q) {
+    const int i = tid * per + q;
+    if (i < P.n_mu) local_max = fmaxf(local_max, logF[i]);
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) local_max = fmaxf(local_max, __shfl_xor_sync(0xFFFFFFFFu, local_max, o));
   if (lane == 0) wmax[warp] = local_max;
-  __syncthreads();
+  asm volatile("bar.sync 1, %0;" ::"r"(kScanThreads));
   float M = wmax[0];
-  for (int w = 1; w < kTableThreads / 32; ++w) M = fmaxf(M, wmax[w]);
+  for (int w = 1; w < kScanThreads / 32; ++w) M = fmaxf(M, wmax[w]);
 
-  // per-thread run of consecutive bins, then a block-wide exclusive scan
   float run[4];
   float tsum = 0.0f;
   for (int q = 0; q < per; ++q) {
@@ -96,9 +128,9 @@ __device__ __forceinline__ void table_row(const TableParams& P, const int row) {
   }
   const float incl = warp_incl_scan(tsum, lane);
   if (lane == 31) wsum[warp] = incl;
-  __syncthreads();
+  asm volatile("bar.sync 1, %0;" ::"r"(kScanThreads));
   float woff = 0.0f, total = 0.0f;
-  for (int w = 0; w < kTableThreads / 32; ++w) {
+  for (int w = 0; w < kScanThreads / 32; ++w) {
     if (w < warp) woff += wsum[w];
     total += wsum[w];
   }
@@ -113,10 +145,11 @@ __device__ __forceinline__ void table_row(const TableParams& P, const int row) {
     out[i + 1] = (i + 1 == P.n_mu) ? 1.0f : fminf(v, 1.0f);
   }
   if (tid == 0) out[0] = 0.0f;
-  for (int j = P.n_mu + 1 + tid; j < P.row_stride; j += kTableThreads) out[j] = 1.0f;
+  for (int j = P.n_mu + 1 + tid; j < P.row_stride; j += kScanThreads) out[j] = 1.0f;
 }
 
 __global__ void __launch_bounds__(kTableThreads) eda_table_kernel(const TableParams P) {
+  zero_outputs(P, blockIdx.x, gridDim.x);
   table_row(P, blockIdx.x);
 }
 
@@ -135,7 +168,7 @@ cudaError_t launch_table_batch(const TableParams* ps_dev, int n_media, int rows,
 }
 
 cudaError_t launch_table(const TableParams& p, cudaStream_t s) {
-  if (p.n_mu > kMaxMu || p.n_mu > 4 * kTableThreads) return cudaErrorInvalidValue;
+  if (p.n_mu > kMaxMu || p.n_mu > 4 * kScanThreads) return cudaErrorInvalidValue;
   eda_table_kernel<<<p.n_rho * p.n_s, kTableThreads, 0, s>>>(p);
   return cudaGetLastError();
 }

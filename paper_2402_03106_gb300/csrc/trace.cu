@@ -26,6 +26,7 @@
 // commit each contribution to the bin of its time.  Tiles are reduced in FP64
 // per block; the last block to finish sums the block partials in fixed order.
 #include <algorithm>
+#include <atomic>
 #include <cfloat>
 
 #include "darts_device.cuh"
@@ -1693,10 +1694,30 @@ unsigned int chunk_for(unsigned long long N, int grid, int block) {
   return (unsigned int)std::max<unsigned long long>(1, std::min<unsigned long long>(per, kPathChunk));
 }
 
+// Raise a kernel's dynamic shared-memory limit only when a launch needs more
+// than was already granted on the current device (the attribute persists;
+// setting it on every launch costs a driver call per render).
+template <auto KERN>
+cudaError_t smem_limit(size_t smem) {
+  constexpr int kDevices = 64;
+  static std::atomic<int> granted[kDevices];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < kDevices && (int)smem <= granted[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+  e = cudaFuncSetAttribute(KERN, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && dev >= 0 && dev < kDevices) {
+    int cur = granted[dev].load(std::memory_order_relaxed);
+    while (cur < (int)smem && !granted[dev].compare_exchange_weak(cur, (int)smem)) {
+    }
+  }
+  return e;
+}
+
 template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK, bool GEN = false>
 cudaError_t launch_one(const TraceParams& p0, int grid, size_t smem, cudaStream_t s) {
-  auto kern = trace_kernel<METHOD, MAXM, DEBUG, TILE, BLOCK, false, GEN>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  constexpr auto kern = trace_kernel<METHOD, MAXM, DEBUG, TILE, BLOCK, false, GEN>;
+  cudaError_t e = smem_limit<kern>(smem);
   if (e != cudaSuccess) return e;
   TraceParams p = p0;
   p.chunk = chunk_for(p.N, grid, BLOCK);

@@ -13,6 +13,11 @@ REL_PATH = 1e-4
 COND_EPS = 4e-7
 # a decision this close to its threshold is a tie at FP32 resolution
 EXACT_TIE = 1e-6
+# the GPU builds its own FP32 direction table: its bin masses may differ from
+# the oracle's by up to 2e-6 (asserted by the table parity test; measured
+# <= 9e-7), which moves the throughput of a path by at most half that times
+# the oracle's per-path table sensitivity (two CDF entries per p_EDA)
+TABLE_EPS = 1e-6
 
 
 def compare_paths(gpu, ref, K):
@@ -79,7 +84,7 @@ def check_paths(gpu, ref, K, rel_tol=REL_PATH, max_flip_frac=0.01, extra_tol=Non
     # decision the trace does not record (the table cell of an EDA sample)
     tie = ref["margin"].min(axis=1) < EXACT_TIE
     ok = same & ~nd & ~tie
-    tol = np.maximum(rel_tol, COND_EPS * ref["cond"])
+    tol = np.maximum(rel_tol, COND_EPS * ref["cond"] + TABLE_EPS * ref["tabcond"])
     if extra_tol is not None:
         tol = np.maximum(tol, extra_tol)
     bad = np.nonzero(ok & (rel > tol))[0]

@@ -5,7 +5,7 @@ Tolerances:
     (a trace may differ only where the oracle met a decision within 1e-3 of
     its threshold -- FP32 and FP64 then legitimately take different sides --
     and on at most 1 % of paths);
-  * direction tables: |cdf_gpu - cdf_oracle| <= 1e-5;
+  * direction tables: |cdf_gpu - cdf_oracle| <= 2e-6, bin masses too;
   * per-path contributions of paths with identical traces: relative 1e-4;
   * histograms at matched seeds: relative L2 <= 1e-3 and every bin within
     3 standard errors.
@@ -61,7 +61,10 @@ def test_direction_table_matches_oracle(ctx, case):
     cdf = ctx.build_table(sc, sp).cpu().numpy().astype(np.float64)
     ref = O.build_table(sc, sp)
     nb = sp.table_n_mu
-    np.testing.assert_allclose(cdf[:, : nb + 1], ref, atol=1e-5, rtol=0)
+    # FP32 quadrature and scan against FP64: CDF values and bin masses within
+    # 2e-6 (the per-path tolerances rely on the mass bound)
+    np.testing.assert_allclose(cdf[:, : nb + 1], ref, atol=2e-6, rtol=0)
+    np.testing.assert_allclose(np.diff(cdf[:, : nb + 1], axis=1), np.diff(ref, axis=1), atol=2e-6, rtol=0)
     assert np.all(cdf[:, 0] == 0.0) and np.all(cdf[:, nb] == 1.0)
 
 

@@ -187,3 +187,23 @@ def test_camera_shards_continue_the_sample_index(ctx):
     assert np.linalg.norm(h - ref) <= 1e-3 * np.linalg.norm(ref)
     h0 = ctx.render(sc, sp).cpu().numpy().reshape(-1)
     assert not np.allclose(h0, h)
+
+
+def test_prepared_render_equals_render(ctx):
+    """A Prepared (structs marshalled once) renders what render() renders, and
+    a render that rebuilds the table zeroes the outputs and counters in the
+    table launch (no stale values from a previous frame)."""
+    sc = S.box_camera_scene(seed=0, width=16, height=16, n_bins=64)
+    sp = S.Sampling(seed=3, paths_per_element=16, max_bounces=20, flags=S.FLAG_REBUILD_TABLE)
+    a = ctx.render(sc, sp)
+    st_a = ctx.stats()
+    prep = ctx.prepare(sc, sp)
+    out = torch.full(S.histogram_shape(sc), 7.0, dtype=torch.float64, device="cuda")
+    prep.render(out=out)
+    st_b = ctx.stats()
+    torch.testing.assert_close(out, a, rtol=1e-9, atol=1e-15)
+    assert st_a == st_b
+    sp2 = S.Sampling(seed=3, paths_per_element=16, max_bounces=20)  # cached table: memsets instead
+    out.fill_(5.0)
+    ctx.prepare(sc, sp2).render(out=out)
+    torch.testing.assert_close(out, a, rtol=1e-9, atol=1e-15)
