@@ -168,7 +168,9 @@ def make_scene(scene, sampling) -> OrcScene:
     s.stream = sampling.stream & 0xFFFFFFFF
     s.sensor_uniform_only = 1 if (sampling.flags & 1) else 0
     s.paths_per_element = sampling.paths_per_element
-    s.ablation = (1 if (sampling.flags & (1 << 2)) else 0) | (2 if (sampling.flags & (1 << 3)) else 0)
+    f = sampling.flags
+    s.ablation = ((1 if f & (1 << 2) else 0) | (2 if f & (1 << 3) else 0) | (4 if f & (1 << 4) else 0)
+                  | (8 if f & (1 << 5) else 0) | (16 if f & (1 << 6) else 0))
     return s
 
 

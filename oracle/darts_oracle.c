@@ -673,36 +673,81 @@ static void cosine_dir(const double n[3], double u1, double u2, double out[3]) {
   frame_dir(n, mu, 2.0 * M_PI * u2, out);
 }
 
+/* Candidate distances of the RIS step (Sec. 4.3).  eps_j: by default one
+ * random row of the 32x8 base-2 radical-inverse table shifted by eps0 modulo
+ * 1 on 24-bit integers (exact); with ablation bit 2 (i.i.d. candidates) the
+ * uniforms come from Philox groups 4 + j/4, word j mod 4, of the vertex.
+ * d_j: truncated exponential on [0, d_m) (Eq. 13-14, sign of Eq. 14 fixed);
+ * with ablation bit 3 the equiangular density about the emitter's closest
+ * approach on the ray (Kulla and Fajardo 2012, the alternative proposal the
+ * paper mentions).  Writes d_j and log p_c(d_j), the candidate density
+ * conditioned on d < d_m. */
+static void ris_candidates(const orc_scene* sc, uint64_t id, int k, const uint32_t u0[4],
+                           const double x[3], const double w[3], const double y[3], double dm,
+                           double pm, double* d, double* lpc) {
+  int M = sc->ris_m;
+  double st = sc->sigma_s + sc->sigma_a;
+  uint32_t row = (uint32_t)floor(orc_u01(u0[1]) * 32.0);
+  uint32_t e0 = u0[2] >> 8; /* eps0 as a 24-bit fraction */
+  /* closest approach of the emitter point to the ray: t_c, h */
+  double e[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]};
+  double tc = dot3(w, e);
+  double h2 = dot3(e, e) - tc * tc;
+  double hh = sqrt(dmax(h2, 1e-30));
+  double th_a = atan2(-tc, hh), th_b = atan2(dm - tc, hh);
+  for (int j = 0; j < M; ++j) {
+    double eps;
+    if (sc->ablation & 4) {
+      uint32_t uj[4];
+      orc_rng4(sc, id, (uint32_t)k, (uint32_t)(4 + j / 4), uj);
+      eps = orc_u01(uj[j % 4]);
+    } else {
+      uint32_t idx = (8u * row + (uint32_t)j) & 255u;
+      uint32_t ri24 = (uint32_t)(orc_radical_inverse2(idx) * 16777216.0);
+      eps = (double)((ri24 + e0) & 0xFFFFFFu) * (1.0 / 16777216.0);
+    }
+    if (sc->ablation & 8) {
+      double th = th_a + eps * (th_b - th_a);
+      double t = tc + hh * tan(th);
+      if (t < 0.0) t = 0.0;
+      if (t >= dm) t = dm * (1.0 - 1e-12);
+      d[j] = t;
+      lpc[j] = log(hh / ((th_b - th_a) * (h2 + (t - tc) * (t - tc))));
+    } else {
+      d[j] = -log1p(-pm * eps) / st;
+      lpc[j] = log(st) - st * d[j] - log(pm);
+    }
+  }
+}
+
 /* DA distance sampling by RIS (Sec. 4.3, Eq. 12-15).  Returns 0 = escape,
  * 1 = moved, 2 = every candidate invalid.  On success writes the new vertex
- * and multiplies *beta by sigma_s exp(-sigma_t d) W_RIS / p_m. */
+ * and multiplies *beta by sigma_s exp(-sigma_t d) W_RIS / p_m with
+ * W_RIS = (1/p_hat(d)) (1/M) sum_i w_i, w_i = p_hat(d_i) / p_c(d_i).
+ * Selection: one uniform against the prefix sums of the weights, or with
+ * ablation bit 4 weighted reservoir sampling (the streaming form the paper
+ * mentions): candidate j replaces the kept one when u_j < w_j / W_j (W_j the
+ * sum of w_0..w_j), u_j from Philox groups 12 + j/4, word j mod 4 -- the same
+ * selection law. */
 static int darts_distance(const orc_scene* sc, int k, uint64_t id, const double x[3],
                           const double w[3], double SM, double dm, double* beta,
                           double xnew[3], double* dsel, path_rec* pr) {
   double st = sc->sigma_s + sc->sigma_a;
   uint32_t u[4];
   orc_rng4(sc, id, (uint32_t)k, 0, u);
-  double u0 = orc_u01(u[0]), u1 = orc_u01(u[1]), u3 = orc_u01(u[3]);
+  double u0 = orc_u01(u[0]), u3 = orc_u01(u[3]);
   /* Eq. 12: scattering-event Bernoulli */
   double pm = 1.0 - exp(-st * dm);
   rec_margin(pr, k, fabs(u0 - pm));
   if (!(u0 < pm)) return 0;
-  /* candidates from one random row of the 32x8 base-2 radical-inverse table,
-   * shifted by eps0 modulo 1 (Sec. 4.3); integer arithmetic keeps it exact */
   int M = sc->ris_m;
-  uint32_t row = (uint32_t)floor(u1 * 32.0);
-  uint32_t e0 = u[2] >> 8; /* eps0 as a 24-bit fraction */
-  double lw[64], d[64], lphat[64];
+  double lw[64], d[64], lphat[64], lpc[64];
   int valid[64];
   double xs[64][3];
+  ris_candidates(sc, id, k, u, x, w, pr->E->y, dm, pm, d, lpc);
   int any = 0;
   double lmax = -INFINITY;
   for (int j = 0; j < M; ++j) {
-    uint32_t idx = (8u * row + (uint32_t)j) & 255u;
-    uint32_t ri24 = (uint32_t)(orc_radical_inverse2(idx) * 16777216.0);
-    double eps = (double)((ri24 + e0) & 0xFFFFFFu) * (1.0 / 16777216.0);
-    /* Eq. 13-14: truncated exponential on [0, d_m); sign of Eq. 14 fixed */
-    d[j] = -log1p(-pm * eps) / st;
     for (int i = 0; i < 3; ++i) xs[j][i] = x[i] + w[i] * d[j];
     double r = dist3(xs[j], pr->E->y);
     double s = SM - d[j]; /* remaining length budget to the upper gate edge */
@@ -712,18 +757,17 @@ static int darts_distance(const orc_scene* sc, int k, uint64_t id, const double 
     pr->n_cand += 1.0;
     if (sc->ablation & 1) {
       /* ablation: the target equals the candidate density -> every candidate
-       * has weight 1 and the selection is a plain truncated-exponential draw */
-      lphat[j] = log(st) - st * d[j] - log(pm);
+       * has weight 1 and the selection is a plain draw from p_c */
+      lphat[j] = lpc[j];
       lw[j] = 0.0;
       valid[j] = 1;
       if (lw[j] > lmax) lmax = lw[j];
       any = 1;
     } else if (valid[j]) {
-      /* Eq. 10 target (unnormalised) and Eq. 13 candidate density */
+      /* Eq. 10 target (unnormalised) over the candidate density */
       double lphi = orc_log_phi(r, s / sc->v, sc->sigma_s, sc->sigma_a, sc->g, sc->v);
       lphat[j] = log(st) - st * d[j] + lphi;
-      double lpc = log(st) - st * d[j] - log(pm);
-      lw[j] = lphat[j] - lpc; /* w = p_hat / p_candidate */
+      lw[j] = lphat[j] - lpc[j];
       if (lw[j] > lmax) lmax = lw[j];
       any = 1;
     } else {
@@ -733,20 +777,34 @@ static int darts_distance(const orc_scene* sc, int k, uint64_t id, const double 
   if (!any) return 2;
   double wsum = 0.0;
   for (int j = 0; j < M; ++j) wsum += valid[j] ? exp(lw[j] - lmax) : 0.0;
-  double target = u3 * wsum, prefix = 0.0;
   int sel = -1;
   double selm = 1.0;
-  for (int j = 0; j < M; ++j) {
-    prefix += valid[j] ? exp(lw[j] - lmax) : 0.0;
-    if (valid[j]) selm = dmin(selm, fabs(prefix - target) / wsum);
-    if (sel < 0 && prefix > target) sel = j;
-  }
-  if (sel < 0) { /* u3 * wsum rounding at the top end */
-    for (int j = M - 1; j >= 0; --j)
-      if (valid[j]) { sel = j; break; }
+  if (sc->ablation & 16) {
+    double W = 0.0;
+    for (int j = 0; j < M; ++j) {
+      double wj = valid[j] ? exp(lw[j] - lmax) : 0.0;
+      W += wj;
+      if (!(wj > 0.0)) continue;
+      uint32_t uj[4];
+      orc_rng4(sc, id, (uint32_t)k, (uint32_t)(12 + j / 4), uj);
+      double uu = orc_u01(uj[j % 4]);
+      selm = dmin(selm, fabs(uu - wj / W));
+      if (uu * W < wj) sel = j;
+    }
+  } else {
+    double target = u3 * wsum, prefix = 0.0;
+    for (int j = 0; j < M; ++j) {
+      prefix += valid[j] ? exp(lw[j] - lmax) : 0.0;
+      if (valid[j]) selm = dmin(selm, fabs(prefix - target) / wsum);
+      if (sel < 0 && prefix > target) sel = j;
+    }
+    if (sel < 0) { /* u3 * wsum rounding at the top end */
+      for (int j = M - 1; j >= 0; --j)
+        if (valid[j]) { sel = j; break; }
+    }
   }
   rec_margin(pr, k, selm);
-  /* Eq. 15: W = (1/p_hat(d)) (1/N) sum_i w_i; throughput sigma_s exp(-sigma_t d) W / p_m */
+  /* Eq. 15: W = (1/p_hat(d)) (1/M) sum_i w_i; throughput sigma_s exp(-sigma_t d) W / p_m */
   double log_mean_w = lmax + log(wsum) - log((double)M);
   double Wris = exp(log_mean_w - lphat[sel]);
   *beta *= sc->sigma_s * exp(-st * d[sel]) * Wris / pm;
@@ -774,18 +832,15 @@ int orc_ris_step(const orc_scene* sc, uint64_t id, int k, const double x[3], con
   uint32_t u[4];
   orc_rng4(sc, id, (uint32_t)k, 0, u);
   double pm = 1.0 - exp(-st * dm);
-  uint32_t row = (uint32_t)floor(orc_u01(u[1]) * 32.0);
-  uint32_t e0 = u[2] >> 8;
+  double lpc[64];
+  ris_candidates(sc, id, k, u, x, w, E.y, dm, pm, d_out, lpc);
   for (int j = 0; j < sc->ris_m; ++j) {
-    uint32_t idx = (8u * row + (uint32_t)j) & 255u;
-    uint32_t ri24 = (uint32_t)(orc_radical_inverse2(idx) * 16777216.0);
-    double eps = (double)((ri24 + e0) & 0xFFFFFFu) * (1.0 / 16777216.0);
-    d_out[j] = -log1p(-pm * eps) / st;
     double xs_[3] = {x[0] + w[0] * d_out[j], x[1] + w[1] * d_out[j], x[2] + w[2] * d_out[j]};
     double rr = dist3(xs_, E.y), ss = SM - d_out[j];
     valid_out[j] = rr < ss;
-    lw_out[j] = valid_out[j] ? orc_log_phi(rr, ss / sc->v, sc->sigma_s, sc->sigma_a, sc->g, sc->v) + log(pm)
-                             : -INFINITY;
+    double lphat = log(st) - st * d_out[j] +
+                   orc_log_phi(rr, ss / sc->v, sc->sigma_s, sc->sigma_a, sc->g, sc->v);
+    lw_out[j] = valid_out[j] ? lphat - lpc[j] : -INFINITY;
   }
   *sel_out = (r == 1) ? (int32_t)pr.dec_sel : -1;
   *factor_out = (r == 1) ? beta : 0.0;

@@ -75,7 +75,9 @@ typedef struct {
   uint64_t paths_per_element;   /* N_e, the per-bin weight is n_bins / N_e   */
   int32_t ablation;             /* bit 0: exponential distance sampling (RIS
                                    weights all 1, no DA target); bit 1: no EDA
-                                   direction sampling (gamma = 0)             */
+                                   direction sampling (gamma = 0); bit 2:
+                                   i.i.d. RIS candidates; bit 3: equiangular
+                                   candidates; bit 4: reservoir selection     */
   /* emitters (em[0] repeats xe/t0/energy for the single point emitter) */
   int32_t n_emitters;
   orc_emitter em[ORC_MAX_EMITTERS];

@@ -224,6 +224,11 @@ darts_status validate(darts_ctx* ctx, const darts_scene* sc, const darts_samplin
     return fail(ctx, DARTS_ERR_INVALID_ARG, "mis_alpha must be > 0");
   if (sp->method < DARTS_METHOD_DARTS || sp->method > DARTS_METHOD_DARTS_FULL_GATE)
     return fail(ctx, DARTS_ERR_INVALID_ARG, "unknown method %d", sp->method);
+  // the general kernel runs the cooperative 8-candidate RIS (its shared
+  // memory holds the 8-candidate task exchange)
+  if ((sp->method == DARTS_METHOD_DARTS || sp->method == DARTS_METHOD_DARTS_FULL_GATE) && general_scene(sc) &&
+      sp->ris_m != 8)
+    return fail(ctx, DARTS_ERR_UNSUPPORTED, "scenes with surfaces, a camera or area emitters need ris_m = 8");
   return DARTS_OK;
 }
 

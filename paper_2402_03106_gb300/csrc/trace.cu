@@ -1440,13 +1440,17 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
     if (fin) alive = false;
     // ---- event counts of this step (lane i keeps counter i of its warp)
     {
+      // Five events per word: multiplying the 5 event bits by
+      // 1 + 2^5 + 2^10 + 2^15 + 2^20 puts bit i at position 6i (the shifted
+      // copies land on distinct positions, so nothing carries), one warp
+      // reduction sums the 6-bit fields (each at most 32), and lane e takes
+      // field e.
       constexpr int kEvents = (METHOD == kDarts && !GEN) ? ST_SAMPLE : ST_FP64E;
-      unsigned mine = 0;
-#pragma unroll
-      for (int e = 0; e < kEvents; ++e) {
-        const unsigned c = __popc(__ballot_sync(kFull, (cnt.bits >> e) & 1u));
-        mine = lane == e ? c : mine;
-      }
+      constexpr unsigned kSpread = 0x108421u, kFields = 0x1041041u;
+      const unsigned w0 = __reduce_add_sync(kFull, ((cnt.bits & 31u) * kSpread) & kFields);
+      unsigned w1 = 0;
+      if constexpr (kEvents > 5) w1 = __reduce_add_sync(kFull, (((cnt.bits >> 5) & 31u) * kSpread) & kFields);
+      const unsigned mine = (lane < 5 ? w0 >> (6 * lane) : w1 >> (6 * (lane - 5))) & 63u;
       if (lane < kEvents) wev[lane] += mine;
     }
   }
@@ -1731,6 +1735,7 @@ template <int METHOD>
 cudaError_t launch_method(const TraceParams& p, int grid, int block, bool debug, bool tile,
                           size_t smem, cudaStream_t s) {
   if (p.general) {  // general scenes: 512 threads, M = 8
+    if (kIsDartsM<METHOD> && p.M != 8) return cudaErrorInvalidValue;  // shared memory sized for M = 8
     if (debug) return tile ? launch_one<METHOD, 8, true, true, 512, true>(p, grid, smem, s)
                            : launch_one<METHOD, 8, true, false, 512, true>(p, grid, smem, s);
     return tile ? launch_one<METHOD, 8, false, true, 512, true>(p, grid, smem, s)
@@ -1803,6 +1808,7 @@ cudaError_t launch_adjoint(const TraceParams& p0, int grid, size_t smem, cudaStr
   p.bin_base = (p0.path_offset + p0.o_e) % (unsigned long long)p0.n_bins;
   p.chunk = chunk_for(p.N, grid, 512);
   if (p.general) {
+    if (p.M != 8) return cudaErrorInvalidValue;  // shared memory sized for M = 8
     auto kern = trace_kernel<kDarts, 8, false, false, 512, true, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -32,6 +32,9 @@ FLAG_SENSOR_UNIFORM_ONLY = 1 << 0
 FLAG_REBUILD_TABLE = 1 << 1
 FLAG_NO_DA_DISTANCE = 1 << 2  # ablation: truncated-exponential distances (no DA target)
 FLAG_NO_EDA = 1 << 3          # ablation: phase-function directions only (gamma = 0)
+FLAG_IID_CANDIDATES = 1 << 4  # RIS candidates from independent uniforms (not the Sobol row)
+FLAG_EQUIANGULAR = 1 << 5     # RIS candidates from the equiangular density about the emitter
+FLAG_RESERVOIR = 1 << 6       # RIS selection by weighted reservoir sampling
 
 Vec3 = Tuple[float, float, float]
 

@@ -207,3 +207,16 @@ def test_prepared_render_equals_render(ctx):
     out.fill_(5.0)
     ctx.prepare(sc, sp2).render(out=out)
     torch.testing.assert_close(out, a, rtol=1e-9, atol=1e-15)
+
+
+def test_general_scenes_reject_other_ris_m(ctx):
+    """The general kernel runs the cooperative 8-candidate RIS; other M are
+    refused on the host before any launch."""
+    from paper_2402_03106_gb300 import capi
+    sc = S.box_camera_scene(width=4, height=4, n_bins=16)
+    for m in (S.DARTS, S.DARTS_FULL_GATE):
+        with pytest.raises(capi.DartsError) as ei:
+            ctx.render(sc, S.Sampling(paths_per_element=4, ris_m=4, method=m))
+        assert ei.value.status == 6
+    # the baselines draw no RIS candidates: any M is accepted
+    ctx.render(sc, S.Sampling(paths_per_element=4, ris_m=4, method=S.PLAIN_UNIFORM_T))

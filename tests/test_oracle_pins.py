@@ -402,7 +402,9 @@ def test_ris_selection_frequencies_follow_the_da_target():
     assert chi2 < 30.0, (counts, expect)
 
 
-@pytest.mark.parametrize("flags", [S.FLAG_NO_DA_DISTANCE, S.FLAG_NO_EDA])
+@pytest.mark.parametrize("flags", [S.FLAG_NO_DA_DISTANCE, S.FLAG_NO_EDA, S.FLAG_IID_CANDIDATES,
+                                   S.FLAG_EQUIANGULAR, S.FLAG_RESERVOIR,
+                                   S.FLAG_IID_CANDIDATES | S.FLAG_EQUIANGULAR | S.FLAG_RESERVOIR])
 def test_ablations_stay_unbiased(flags):
     """The ablated samplers (Fig. 13 study) estimate the same truncated sum."""
     sc = S.slab_scene(1.0, 0.02, 0.5, n_bins=8, t_min=0.85, t_max=2.5)
@@ -675,3 +677,77 @@ def test_rejection_rates_two_peak_response():
         rates[name] = st["rejected"] / st["samples"]
     assert rates["darts"] == 0.0
     assert rates["vanilla"] > 0.5 and rates["plain"] > 0.2, rates
+
+
+# ---------------------------------------------------------------------------
+# RIS variants: i.i.d. and equiangular candidates, reservoir selection
+# ---------------------------------------------------------------------------
+def _ris_geometry():
+    x = np.array([0.5, 0.5, 0.9])
+    w = np.array([0.0, 0.6, -0.8])
+    return x, w, 1.3, 0.6
+
+
+def test_equiangular_candidates_follow_their_cdf():
+    """Equiangular candidates about the emitter's closest approach to the ray:
+    F(t) = (atan((t - t_c)/h) - atan(-t_c/h)) / (atan((d_m - t_c)/h) - atan(-t_c/h))."""
+    sc, _ = S.cube_workload()
+    x, w, SM, dm = _ris_geometry()
+    sp = S.Sampling(seed=7, ris_m=8, flags=S.FLAG_EQUIANGULAR | S.FLAG_IID_CANDIDATES)
+    xe = np.array(sc.emitters[0].pos)
+    tc = float(w @ (xe - x))
+    h = math.sqrt(float((xe - x) @ (xe - x)) - tc * tc)
+    ta, tb = math.atan2(-tc, h), math.atan2(dm - tc, h)
+    ds = []
+    for pid in range(3000):
+        r = O.ris_step(sc, sp, pid, 0, x, w, SM, dm)
+        ds.extend(r["d"])
+    ds = np.sort(np.asarray(ds))
+    F = (np.arctan((ds - tc) / h) - ta) / (tb - ta)
+    ecdf = (np.arange(len(ds)) + 0.5) / len(ds)
+    assert np.max(np.abs(F - ecdf)) < 1.36 / math.sqrt(len(ds)) * 1.5
+    assert ds.min() >= 0.0 and ds.max() < dm
+
+
+def test_iid_candidates_are_uniform_and_independent():
+    """i.i.d. candidates: truncated-exponential marginals (KS) and no
+    stratification between candidates of one step (the Sobol row spreads its
+    eight candidates over eight strata; i.i.d. ones repeat strata)."""
+    sc, _ = S.cube_workload()
+    x, w, SM, dm = _ris_geometry()
+    st = sc.medium.sigma_s + sc.medium.sigma_a
+    pm = 1.0 - math.exp(-st * dm)
+    same_stratum = []
+    eps_all = []
+    for flags in (S.FLAG_IID_CANDIDATES, 0):
+        sp = S.Sampling(seed=8, ris_m=8, flags=flags)
+        rep = 0
+        for pid in range(1500):
+            r = O.ris_step(sc, sp, pid, 0, x, w, SM, dm)
+            eps = -np.expm1(-st * np.asarray(r["d"])) / pm
+            rep += len(eps) - len(set(np.floor(eps * 8).astype(int)))
+            if flags:
+                eps_all.extend(eps)
+        same_stratum.append(rep)
+    e = np.sort(np.asarray(eps_all))
+    assert np.max(np.abs(e - (np.arange(len(e)) + 0.5) / len(e))) < 1.36 / math.sqrt(len(e)) * 1.5
+    assert same_stratum[0] > 1000 and same_stratum[1] == 0, same_stratum
+
+
+def test_reservoir_selection_follows_the_weights():
+    """Weighted reservoir selection picks candidate j with probability
+    w_j / sum w, the law of the one-shot RIS selection."""
+    sc, _ = S.cube_workload()
+    x, w, SM, dm = _ris_geometry()
+    sp = S.Sampling(seed=9, ris_m=8, flags=S.FLAG_RESERVOIR)
+    counts, expect = np.zeros(8), np.zeros(8)
+    for pid in range(4000):
+        r = O.ris_step(sc, sp, pid, 0, x, w, SM, dm)
+        if r["status"] != 1:
+            continue
+        lw = np.asarray(r["logw"])
+        p = np.where(np.isfinite(lw), np.exp(lw - lw[np.isfinite(lw)].max()), 0.0)
+        expect += p / p.sum()
+        counts[r["sel"]] += 1
+    chi2 = np.sum((counts - expect) ** 2 / np.maximum(expect, 1e-9))
+    assert counts.sum() > 1000 and chi2 < 30.0, (counts, expect)
