@@ -165,7 +165,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("trace.cu", "darts_device.cuh", "darts_internal.h"):
+    for f in ("trace_kernels.cuh", "trace.cu", "darts_device.cuh", "darts_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2402_03106_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

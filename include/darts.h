@@ -66,6 +66,14 @@ typedef enum {
 #define DARTS_FLAG_NO_DA_DISTANCE (1u << 2) /* distances: plain truncated-exponential draw
                                                (every RIS weight 1, no DA target)       */
 #define DARTS_FLAG_NO_EDA (1u << 3)         /* directions: phase function only (gamma = 0) */
+/* RIS variants of Sec. 4.3 (ablations): candidates from independent uniforms
+ * instead of the shifted Sobol row; candidates from the equiangular density
+ * about the emitter's closest approach to the ray instead of the truncated
+ * exponential; selection by weighted reservoir sampling.  Path ids must stay
+ * below 2^48 with the first or the last. */
+#define DARTS_FLAG_IID_CANDIDATES (1u << 4)
+#define DARTS_FLAG_EQUIANGULAR (1u << 5)
+#define DARTS_FLAG_RESERVOIR (1u << 6)
 
 typedef struct darts_ctx darts_ctx;
 

@@ -17,8 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdarts.so")
-SOURCES = ["capi.cu", "table.cu", "trace.cu"]
-HEADERS = ["darts_device.cuh", "darts_internal.h"]
+SOURCES = ["capi.cu", "table.cu", "trace.cu", "trace_var.cu"]
+HEADERS = ["darts_device.cuh", "darts_internal.h", "trace_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -131,6 +131,8 @@ uint64_t elements_of(const darts_scene* sc) {
 
 // Scenes beyond one point emitter seen by a point sensor in an open box run
 // the general variant of the path kernel.
+constexpr uint32_t kRisVariantFlags = DARTS_FLAG_IID_CANDIDATES | DARTS_FLAG_EQUIANGULAR | DARTS_FLAG_RESERVOIR;
+
 bool general_scene(const darts_scene* sc) {
   if (sc->n_emitters != 1 || sc->emitters[0].kind != DARTS_EMITTER_POINT) return true;
   return sc->sensor.kind != DARTS_SENSOR_POINT || sc->geom.walls != 0 || sc->geom.n_spheres > 0;
@@ -229,6 +231,8 @@ darts_status validate(darts_ctx* ctx, const darts_scene* sc, const darts_samplin
   if ((sp->method == DARTS_METHOD_DARTS || sp->method == DARTS_METHOD_DARTS_FULL_GATE) && general_scene(sc) &&
       sp->ris_m != 8)
     return fail(ctx, DARTS_ERR_UNSUPPORTED, "scenes with surfaces, a camera or area emitters need ris_m = 8");
+  if ((sp->flags & kRisVariantFlags) && general_scene(sc))
+    return fail(ctx, DARTS_ERR_UNSUPPORTED, "the RIS variants run on medium-only scenes with a point emitter and sensor");
   return DARTS_OK;
 }
 
@@ -360,6 +364,8 @@ void make_trace_params(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
   P->uniform_sensor = (sp->flags & DARTS_FLAG_SENSOR_UNIFORM_ONLY) ? 1 : 0;
   P->no_eda = (sp->flags & DARTS_FLAG_NO_EDA) ? 1 : 0;
   P->no_da = (sp->flags & DARTS_FLAG_NO_DA_DISTANCE) ? 1 : 0;
+  P->ris_mode = ((sp->flags & DARTS_FLAG_IID_CANDIDATES) ? 1 : 0) | ((sp->flags & DARTS_FLAG_EQUIANGULAR) ? 2 : 0) |
+                ((sp->flags & DARTS_FLAG_RESERVOIR) ? 4 : 0);
   P->table = ctx->table;
   P->K = sp->max_bounces;
   P->M = sp->ris_m;
@@ -856,6 +862,8 @@ darts_status darts_render_batch(darts_ctx* ctx, int n, const darts_scene* scenes
     if (!hist_dev[i]) return fail(ctx, DARTS_ERR_INVALID_ARG, "hist_dev[%d] is NULL", i);
     if (scenes[i].gate.weights)
       return fail(ctx, DARTS_ERR_UNSUPPORTED, "a batch renders media without a temporal response");
+    if (samplings[i].flags & kRisVariantFlags)
+      return fail(ctx, DARTS_ERR_UNSUPPORTED, "a batch runs the default RIS");
     const darts_sampling& si = samplings[i];
     if (general_scene(&scenes[i]))
       return fail(ctx, DARTS_ERR_UNSUPPORTED, "a batch renders point-emitter, point-sensor media without surfaces");
@@ -979,6 +987,8 @@ darts_status darts_adjoint(darts_ctx* ctx, const darts_scene* scene, const darts
   if (!dLdh_dev || !grad3_dev) return fail(ctx, DARTS_ERR_INVALID_ARG, "dLdh_dev and grad3_dev must not be NULL");
   if (sampling->method != DARTS_METHOD_DARTS)
     return fail(ctx, DARTS_ERR_UNSUPPORTED, "the adjoint is implemented for the DARTS method");
+  if (sampling->flags & kRisVariantFlags)
+    return fail(ctx, DARTS_ERR_UNSUPPORTED, "the adjoint runs the default RIS");
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   if (sampling->paths_per_element == 0) {
     CK(cudaMemsetAsync(grad3_dev, 0, 3 * sizeof(double), ctx->stream), "memset");

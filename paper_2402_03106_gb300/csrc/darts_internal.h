@@ -85,6 +85,7 @@ struct TraceParams {
   int uniform_sensor;
   int no_eda;                      // ablation: phase-function directions only
   int no_da;                       // ablation: truncated-exponential distances (RIS weights 1)
+  int ris_mode;                    // bit 0: i.i.d. candidates, 1: equiangular candidates, 2: reservoir
   const float* table;              // [rows][row_stride]
   // sampling
   int K, M;
@@ -146,6 +147,10 @@ struct BatchParams {
 cudaError_t launch_table(const TableParams& p, cudaStream_t s);
 cudaError_t launch_trace(int method, const TraceParams& p, int grid, int block, bool debug,
                          bool tile, size_t smem, cudaStream_t s);
+// The DARTS path kernels built for the RIS variants (ris_mode != 0; point
+// sensor, medium only, 512 threads); called by launch_trace.
+cudaError_t launch_trace_var(int method, const TraceParams& p, int grid, bool debug, bool tile,
+                             size_t smem, cudaStream_t s);
 cudaError_t launch_table_batch(const TableParams* ps_dev, int n_media, int rows, cudaStream_t s);
 cudaError_t launch_batch(const BatchParams& bp, int grid, int block, size_t smem, cudaStream_t s);
 size_t batch_smem_bytes(const BatchParams& bp, int block);

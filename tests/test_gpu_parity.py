@@ -79,11 +79,18 @@ def test_darts_per_path_parity(ctx, K):
     check_paths(gpu, ref, K)
 
 
+@pytest.mark.parametrize("ris_m", [8, 4])
 @pytest.mark.parametrize("flags", [S.FLAG_NO_DA_DISTANCE, S.FLAG_NO_EDA,
-                                   S.FLAG_NO_DA_DISTANCE | S.FLAG_NO_EDA, S.FLAG_SENSOR_UNIFORM_ONLY])
-def test_ablation_per_path_parity(ctx, flags):
+                                   S.FLAG_NO_DA_DISTANCE | S.FLAG_NO_EDA, S.FLAG_SENSOR_UNIFORM_ONLY,
+                                   S.FLAG_IID_CANDIDATES, S.FLAG_EQUIANGULAR, S.FLAG_RESERVOIR,
+                                   S.FLAG_IID_CANDIDATES | S.FLAG_EQUIANGULAR | S.FLAG_RESERVOIR,
+                                   S.FLAG_EQUIANGULAR | S.FLAG_NO_DA_DISTANCE])
+def test_ablation_per_path_parity(ctx, flags, ris_m):
+    """Ablations and RIS variants, on the warp-cooperative RIS (M = 8) and on
+    the per-lane RIS (M = 4)."""
     sc, sp = S.cube_workload(paths=1 << 16, seed=6)
     sp.flags = flags
+    sp.ris_m = ris_m
     n = 2048
     gpu = ctx.debug_paths(sc, sp, 0, n)
     ref = O.trace_paths(sc, sp, 0, n)
@@ -108,6 +115,22 @@ def test_baseline_per_path_parity(ctx, method):
     gpu = ctx.debug_paths(sc, sp, 0, n)
     ref = O.trace_paths(sc, sp, 0, n, method=method)
     check_paths(gpu, ref, sp.max_bounces)
+
+
+def test_ris_variants_histogram_and_unsupported_combinations(ctx):
+    from paper_2402_03106_gb300 import capi
+    sc, sp = S.cube_workload(paths=1 << 16, seed=31)
+    sp.flags = S.FLAG_IID_CANDIDATES | S.FLAG_EQUIANGULAR | S.FLAG_RESERVOIR
+    h = ctx.render(sc, sp).cpu().numpy()
+    href, _, _ = O.render(sc, sp, O.ORC_DARTS)
+    assert np.linalg.norm(h - href) <= 1e-3 * np.linalg.norm(href)
+    cam = S.box_camera_scene(width=4, height=4, n_bins=16)
+    for call in (lambda: ctx.render(cam, S.Sampling(paths_per_element=4, flags=S.FLAG_RESERVOIR)),
+                 lambda: ctx.adjoint(sc, sp, torch.ones(sc.gate.n_bins, dtype=torch.float64)),
+                 lambda: ctx.render_batch([sc], [sp])):
+        with pytest.raises(capi.DartsError) as ei:
+            call()
+        assert ei.value.status == 6
 
 
 @pytest.mark.parametrize("method", [S.DARTS, S.PLAIN_UNIFORM_T, S.VANILLA_DIRECT, S.DARTS_FULL_GATE])
