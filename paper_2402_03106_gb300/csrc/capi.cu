@@ -879,10 +879,28 @@ darts_status darts_render_batch(darts_ctx* ctx, int n, const darts_scene* scenes
   CK(ensure((void**)&ctx->batch_tables, &ctx->batch_tables_bytes, (size_t)n * tab_floats * sizeof(float)),
      "batch table allocation");
 
-  // host-side parameter blocks and work items (chunks of at most 2^16 paths)
-  const uint64_t chunk = 1ull << 16;
+  // Work items.  A CTA traces an item alone, so items are sized by estimated
+  // cost: per-path cost ~ 1 + sigma_s x box diagonal (the expected vertices of
+  // a path grow with the optical size), and a medium is cut into chunks of
+  // about 1/8 of a CTA's share of the total, between 2^11 and 2^16 paths, so
+  // that no single item outlasts the rest of the launch.
+  std::vector<double> cpp(n);
+  double total_cost = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const darts_geometry& g = scenes[i].geom;
+    double diag = 0.0;
+    for (int a = 0; a < 3; ++a) diag += (g.hi[a] - g.lo[a]) * (g.hi[a] - g.lo[a]);
+    cpp[i] = 1.0 + scenes[i].medium.sigma_s * std::sqrt(diag);
+    total_cost += cpp[i] * (double)samplings[i].paths_per_element;
+  }
+  const double item_cost = total_cost / (8.0 * std::max(ctx->sm_count, 1));
+  std::vector<uint64_t> chunk(n);
   size_t n_items = 0;
-  for (int i = 0; i < n; ++i) n_items += (samplings[i].paths_per_element + chunk - 1) / chunk;
+  for (int i = 0; i < n; ++i) {
+    const double c = std::floor(item_cost / cpp[i]);
+    chunk[i] = (uint64_t)std::min(65536.0, std::max(2048.0, c));
+    n_items += (samplings[i].paths_per_element + chunk[i] - 1) / chunk[i];
+  }
   const size_t off_tp = 0, off_trp = ((size_t)n * sizeof(TableParams) + 255) / 256 * 256;
   const size_t off_items = off_trp + ((size_t)n * sizeof(TraceParams) + 255) / 256 * 256;
   const size_t off_cnt = off_items + (n_items * sizeof(BatchItem) + 255) / 256 * 256;
@@ -897,6 +915,14 @@ darts_status darts_render_batch(darts_ctx* ctx, int n, const darts_scene* scenes
   BatchItem* items = reinterpret_cast<BatchItem*>(host + off_items);
   size_t k = 0;
   uint64_t total_paths = 0;
+  // Media in order of decreasing total estimated cost (heavy media start
+  // early, light ones fill the tail); the items of one medium stay contiguous
+  // so that a CTA restages a table only when the medium changes.
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return cpp[a] * (double)samplings[a].paths_per_element > cpp[b] * (double)samplings[b].paths_per_element;
+  });
   for (int i = 0; i < n; ++i) {
     make_table_params(&scenes[i], &samplings[i], &tps[i]);
     tps[i].cdf = ctx->batch_tables + (size_t)i * tab_floats;
@@ -906,13 +932,16 @@ darts_status darts_render_batch(darts_ctx* ctx, int n, const darts_scene* scenes
     trps[i].path_offset = 0;
     trps[i].bin_base = trps[i].o_e % (unsigned long long)scenes[i].gate.n_bins;
     trps[i].hist = hist_dev[i];
-    for (uint64_t f = 0; f < samplings[i].paths_per_element; f += chunk) {
+    total_paths += samplings[i].paths_per_element;
+  }
+  for (int oi = 0; oi < n; ++oi) {
+    const int i = order[oi];
+    for (uint64_t f = 0; f < samplings[i].paths_per_element; f += chunk[i]) {
       items[k].medium = (unsigned)i;
       items[k].first = f;
-      items[k].count = std::min<uint64_t>(chunk, samplings[i].paths_per_element - f);
+      items[k].count = std::min<uint64_t>(chunk[i], samplings[i].paths_per_element - f);
       ++k;
     }
-    total_paths += samplings[i].paths_per_element;
   }
   BatchParams bp;
   bp.params = reinterpret_cast<const TraceParams*>(dev + off_trp);
@@ -924,7 +953,7 @@ darts_status darts_render_batch(darts_ctx* ctx, int n, const darts_scene* scenes
   bp.rows = rows;
   bp.row_stride = stride;
   bp.stats = ctx->scratch + 2;
-  int block = ctx->block ? ctx->block : 512;
+  int block = ctx->block ? ctx->block : 768;  // 24 warps per SM: measured fastest for the batch
   size_t smem = batch_smem_bytes(bp, block);
   while (smem > (size_t)ctx->smem_optin && block > 512) {
     block = block == 768 ? 640 : 512;
