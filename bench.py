@@ -252,7 +252,8 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 def mse_time(ctx, S, torch, n_paths=1 << 20, seeds=16):
     """Efficiency of DARTS against the plain uniform-temporal path tracer (and
-    the vanilla direct-connection tracer and the ablations of Fig. 13) at
+    the vanilla direct-connection tracer, the ablations of Fig. 13 and the
+    RIS variants of Sec. 4.3) at
     equal path counts, on the benchmark's unit cube and on a paper-shaped dense
     variant (sigma_s = 13.5: about 3.2 transport mean free paths between
     emitter and sensor).
@@ -266,6 +267,9 @@ def mse_time(ctx, S, torch, n_paths=1 << 20, seeds=16):
     methods = (("darts", S.DARTS, 0), ("darts_no_da", S.DARTS, S.FLAG_NO_DA_DISTANCE),
                ("darts_no_eda", S.DARTS, S.FLAG_NO_EDA),
                ("darts_no_da_no_eda", S.DARTS, S.FLAG_NO_DA_DISTANCE | S.FLAG_NO_EDA),
+               ("darts_iid_candidates", S.DARTS, S.FLAG_IID_CANDIDATES),
+               ("darts_equiangular", S.DARTS, S.FLAG_EQUIANGULAR),
+               ("darts_reservoir", S.DARTS, S.FLAG_RESERVOIR),
                ("plain_uniform_t", S.PLAIN_UNIFORM_T, 0), ("vanilla_direct", S.VANILLA_DIRECT, 0))
     out = {"paths_per_render": n_paths, "seeds": seeds}
     for label, sc in (("unit_cube", S.slab_scene()), ("unit_cube_sigma_s_13.5", S.slab_scene(sigma_s=13.5))):
@@ -292,7 +296,8 @@ def mse_time(ctx, S, torch, n_paths=1 << 20, seeds=16):
             q = torch.quantile(H[name], torch.tensor([0.25, 0.75], dtype=torch.float64), dim=0)
             res[name] = {"seconds_per_render": T[name], "mse_mean": float(mse.mean()),
                          "mse_median": float(mse.median()), "_iqr": (q[1] - q[0])}
-        for base in ("plain_uniform_t", "vanilla_direct", "darts_no_da", "darts_no_eda", "darts_no_da_no_eda"):
+        for base in ("plain_uniform_t", "vanilla_direct", "darts_no_da", "darts_no_eda", "darts_no_da_no_eda",
+                     "darts_iid_candidates", "darts_equiangular", "darts_reservoir"):
             a = res[base]["_iqr"] ** 2 * res[base]["seconds_per_render"]
             b = res["darts"]["_iqr"] ** 2 * res["darts"]["seconds_per_render"]
             ok = (a > 0) & (b > 0)
