@@ -65,3 +65,66 @@ def test_sharded_render_equals_single_render(world, method):
     sp.max_bounces = 10
     ref, _, _ = O.render(sc, sp, method, threads=4)
     np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-300)
+
+
+def _camera_worker(rank, world, port, spp, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import sys
+        sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+        import oracle as O
+        from paper_2402_03106_gb300 import scenes as S, sharding
+        sc = S.box_camera_scene(seed=1, width=4, height=4, n_bins=32, t_max=8.0)
+        sp = S.Sampling(seed=21, paths_per_element=spp, max_bounces=6)
+        n = S.total_paths(sc, sp)
+        off = sharding.path_offset(rank, n)
+        h, sq, _ = O.render(sc, sp, O.ORC_DARTS, offset=off, threads=2)
+        bins = O.trace_paths(sc, sp, off, n)["bin"]
+        t = torch.from_numpy(h)
+        s2 = torch.from_numpy(sq)
+        sharding.combine(t, world)
+        dist.all_reduce(s2)
+        if rank == 0:
+            q.put((t.numpy().copy(), s2.numpy().copy()))
+        q.put((rank, bins))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_camera_render_is_a_consistent_estimate():
+    """Camera shards (path offset = rank x frame) keep the pixel layout and
+    continue the DARTS sample index: their average agrees with a single
+    render of world x spp within standard errors, and the ranks' paths land
+    on different bins of each pixel."""
+    import oracle as O
+    from paper_2402_03106_gb300 import scenes as S
+    world, spp = 2, 200
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_camera_worker, args=(r, world, port, spp, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    items = [q.get(timeout=300) for _ in range(world + 1)]
+    for p in procs:
+        p.join(timeout=300)
+        assert p.exitcode == 0
+    hist = [it for it in items if isinstance(it[0], np.ndarray)][0]
+    bins = dict(it for it in items if not isinstance(it[0], np.ndarray))
+    h, sq = hist
+    sc = S.box_camera_scene(seed=1, width=4, height=4, n_bins=32, t_max=8.0)
+    sp = S.Sampling(seed=22, paths_per_element=spp * world, max_bounces=6)
+    ref, sqref, _ = O.render(sc, sp, O.ORC_DARTS, threads=4)
+    # per-pixel totals (sums over bins) with their standard errors
+    B = 32
+    tot, tref = h.reshape(16, B).sum(1), ref.reshape(16, B).sum(1)
+    se = np.sqrt(np.maximum(sq.reshape(16, B).sum(1) / world ** 2, 0.0) / 1.0)
+    se_ref = np.sqrt(sqref.reshape(16, B).sum(1))
+    z = (tot - tref) / np.sqrt(se ** 2 + se_ref ** 2 + 1e-300)
+    assert np.max(np.abs(z)) < 4.5, z
+    # rank 1 covers the bins spp further along in each pixel
+    b0, b1 = bins[0], bins[1]
+    assert np.array_equal(b0 // B, b1 // B)
+    assert np.array_equal((b0 % B + spp) % B, b1 % B)
