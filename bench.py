@@ -375,15 +375,16 @@ def mse_time_gated(ctx, S, torch, seeds=16, spp=64):
     uniform-temporal renders; ratio = (MSE x time)_base / (MSE x time)_darts."""
     out = {"workload": "box camera of the benchmark, 64x64, one gate bin, K=100", "seeds": seeds, "spp": spp}
     methods = (("darts", S.DARTS), ("plain_uniform_t", S.PLAIN_UNIFORM_T), ("vanilla_direct", S.VANILLA_DIRECT))
-    cases = [(6.125, 0.25), (10.125, 0.25), (8.0, 0.0625), (8.0, 1.0), (8.0, 4.0)]
-    for centre, width in cases:
+    cases = [(6.125, 0.25, spp), (10.125, 0.25, spp), (8.0, 0.0625, spp), (8.0, 1.0, spp), (8.0, 4.0, spp),
+             (6.125, 0.25, 1024), (10.125, 0.25, 1024)]  # the last two GPU-saturating (4 M paths)
+    for centre, width, spp_c in cases:
         sc = S.box_camera_scene(seed=0, n_bins=1, t_max=centre + width / 2)
         sc.gate.t_min = centre - width / 2
         H, T = {}, {}
         for name, m in methods:
             acc, ts = [], []
             for s_ in range(seeds):
-                sp = S.Sampling(seed=301 + s_, paths_per_element=spp, max_bounces=100, method=m,
+                sp = S.Sampling(seed=301 + s_, paths_per_element=spp_c, max_bounces=100, method=m,
                                 flags=S.FLAG_REBUILD_TABLE if m == S.DARTS else 0)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
@@ -395,7 +396,7 @@ def mse_time_gated(ctx, S, torch, seeds=16, spp=64):
             H[name] = torch.stack(acc)
             T[name] = statistics.median(ts)
         ref = torch.cat([H["darts"], H["plain_uniform_t"]]).mean(0)
-        res = {"gate": [centre - width / 2, centre + width / 2], "mean_signal": float(ref.mean())}
+        res = {"gate": [centre - width / 2, centre + width / 2], "spp": spp_c, "mean_signal": float(ref.mean())}
         for name, _ in methods:
             d = H[name] - ref
             mse = (d * d).mean(1)
@@ -407,7 +408,7 @@ def mse_time_gated(ctx, S, torch, seeds=16, spp=64):
                                  max(res["darts"]["mse_mean"] * res["darts"]["seconds_per_render"], 1e-300),
                 "mse_median_time": (res[base]["mse_median"] * res[base]["seconds_per_render"]) /
                                    max(res["darts"]["mse_median"] * res["darts"]["seconds_per_render"], 1e-300)}
-        out[f"gate_{centre - width / 2:g}_{centre + width / 2:g}"] = res
+        out[f"gate_{centre - width / 2:g}_{centre + width / 2:g}_spp{spp_c}"] = res
     return out
 
 
