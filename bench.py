@@ -642,6 +642,26 @@ def main():
                     "paths_per_s": N2 / (t2 * 1e-3),
                     "roofline": roofline(per2, statistics.fmean(k2), other == "box_camera", other, N2)}
 
+    # ---- the largest configuration: 512x512 camera, 32 spheres, two
+    # emitters, 1000 bins, 64 spp, K = 100 (16.7 M paths, a 2.1 GB histogram)
+    scs = S.spheres_camera_scene(seed=0)
+    sps = S.Sampling(seed=0, paths_per_element=64, max_bounces=100, flags=S.FLAG_REBUILD_TABLE)
+    Ns = S.total_paths(scs, sps)
+    hs = torch.empty(S.histogram_shape(scs), dtype=torch.float64, device="cuda")
+    preps = ctx.prepare(scs, sps)
+    preps.render(out=hs)
+    torch.cuda.synchronize()
+    ctx.set_kernel_timing(True)
+    ts, ks, pers = time_steps(ctx, torch, lambda: preps.render(out=hs), 3, flush)
+    ctx.set_kernel_timing(False)
+    extra["spheres_512"] = {
+        "workload": "512x512 pinhole camera inside a 4x4x4 medium (sigma_s 0.8, sigma_a 0.005, g 0.8) with 32 "
+                    "seeded Lambertian spheres, two point pulse emitters (t0 = 0, 1.5), 1000 bins on [0,20), "
+                    "64 spp, K=100", "paths_per_step": Ns, "ms_per_step": statistics.fmean(ts),
+        "paths_per_s": Ns / (statistics.fmean(ts) * 1e-3), "histogram_bytes": hs.numel() * 8,
+        "roofline": roofline(pers, statistics.fmean(ks), True, "spheres_512", Ns)}
+    del hs, preps
+
     # ---- the cube as configured: 2^16 paths per render (latency-bound)
     sc16, sp16 = S.cube_workload(paths=1 << 16, seed=0)
     sp16.flags |= S.FLAG_REBUILD_TABLE
