@@ -20,6 +20,11 @@ LIB = os.path.join(HERE, "libdarts.so")
 SOURCES = ["capi.cu", "table.cu", "trace.cu", "trace_var.cu"]
 HEADERS = ["darts_device.cuh", "darts_internal.h", "trace_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The path kernels take FP32 division and square root at 2 ulp / 1 ulp
+# (div.full, sqrt.approx) instead of IEEE rounding: shorter dependent chains,
+# well inside the per-path FP32 error budget.  The table build keeps IEEE.
+APPROX_SOURCES = {"trace.cu", "trace_var.cu"}
+APPROX_FLAGS = ["-prec-div=false", "-prec-sqrt=false"]
 
 
 def nvcc() -> str:
@@ -55,7 +60,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [cc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
+        extra = APPROX_FLAGS if src in APPROX_SOURCES else []
+        cmd = [cc] + flags + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

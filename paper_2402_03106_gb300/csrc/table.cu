@@ -72,20 +72,36 @@ __device__ __forceinline__ void table_row(const TableParams& P, const int row) {
       const float tM = SmC * (S + C) / (2.0f * fmaf(C, onem, SmC));
       const float cmu = C * mu;
       const float split = (cmu > 0.0f && cmu < tM) ? cmu : 0.5f * tM;
+      // the integrand is exp(lg) tp^(-3/2) with lg = phi_k0 - r^2 / (4 v D tp)
+      // - sigma_a v tp - sigma_t t: one reciprocal square root gives both
+      // tp^(-3/2) and 1 / tp, and the running log-sum-exp is rescaled once per
+      // group of kGroup nodes (two MUFU operations per node)
+      constexpr int kGroup = 8;
+      const float inv_v = 1.0f / P.v;
 #pragma unroll 1
       for (int panel = 0; panel < 2; ++panel) {
         const float lo = panel == 0 ? 0.0f : split;
         const float hw = 0.5f * ((panel == 0 ? split : tM) - lo);
-#pragma unroll 4
-        for (int b = 0; b < kMaxTabTNodes; ++b) {
-          const float t = fmaf(hw, P.t_x[b] + 1.0f, lo);
-          const float tc = t - C;
-          const float r2 = fmaf(tc, tc, 2.0f * C * t * onem);
-          const float tp = (S - t) * (1.0f / P.v);  // t' > 0 inside the ellipse
-          const float li = P.phi_k0 - 1.5f * __logf(tp) - __fdividef(r2 * P.phi_invk, tp) -
-                           P.sa_v * tp - P.sigma_t * t;
-          const float mn = fmaxf(m, li);
-          s = fmaf(s, __expf(m - mn), wa * hw * P.t_w[b] * __expf(li - mn));
+#pragma unroll 1
+        for (int b0 = 0; b0 < kMaxTabTNodes; b0 += kGroup) {
+          float lg[kGroup], rs[kGroup];
+          float gm = -FLT_MAX;
+#pragma unroll
+          for (int q = 0; q < kGroup; ++q) {
+            const float t = fmaf(hw, P.t_x[b0 + q] + 1.0f, lo);
+            const float tc = t - C;
+            const float r2 = fmaf(tc, tc, 2.0f * C * t * onem);
+            const float tp = (S - t) * inv_v;  // t' > 0 inside the ellipse
+            rs[q] = rsqrtf(tp);
+            lg[q] = P.phi_k0 - r2 * P.phi_invk * (rs[q] * rs[q]) - P.sa_v * tp - P.sigma_t * t;
+            gm = fmaxf(gm, lg[q]);
+          }
+          const float mn = fmaxf(m, gm);
+          float acc = 0.0f;
+#pragma unroll
+          for (int q = 0; q < kGroup; ++q)
+            acc = fmaf(P.t_w[b0 + q] * __expf(lg[q] - mn), rs[q] * rs[q] * rs[q], acc);
+          s = fmaf(s, __expf(m - mn), wa * hw * acc);
           m = mn;
         }
       }

@@ -378,6 +378,26 @@ __device__ __forceinline__ bool visible(const TraceParams& P, float ax, float ay
   return true;
 }
 
+// Inverse CDF search of a table row (row[0] = 0 <= v < 1 = row[n]): the
+// largest lo in [0, n) with row[lo] <= v.  Three independent probes split
+// the range in four per round (half the dependent shared-memory loads of a
+// binary search), then binary steps below four.
+__device__ __forceinline__ int row_search(const float* row, int n, float v) {
+  int lo = 0;
+  while (n > 3) {
+    const int q = n >> 2;
+    const bool a = row[lo + q] <= v, b = row[lo + 2 * q] <= v, c = row[lo + 3 * q] <= v;
+    lo += c ? 3 * q : (b ? 2 * q : (a ? q : 0));
+    n = c ? n - 3 * q : q;
+  }
+  while (n > 1) {
+    const int half = n >> 1;
+    lo = (row[lo + half] > v) ? lo : lo + half;
+    n -= half;
+  }
+  return lo;
+}
+
 // Radiant intensity of the path's emitter point toward x.
 __device__ __forceinline__ float emit_intensity(const Path& p, float x, float y, float z) {
   if (p.en0 == 0.0f && p.en1 == 0.0f && p.en2 == 0.0f) return p.ie;
@@ -635,7 +655,9 @@ struct Stepper {
       return 1;
     }
     float wx = p.wx, wy = p.wy, wz = p.wz;
+    // both draws of the vertex up front: two independent Philox chains
     const U4 u1 = rng(P, p.j, (uint32_t)p.k, 1);
+    const U4 u0 = rng(P, p.j, (uint32_t)p.k, 0);
     if (!p.fixed) {
       // MIS of the EDA table and HG (uniform sphere at the point sensor), Eq. 19
       const float rho = __fdividef(C, SM);
@@ -652,12 +674,7 @@ struct Stepper {
       float sphi, cphi;
       sincos_2pi(u01(u1.z), &sphi, &cphi);
       const bool eda = v0 < gamma;
-      int lo = 0, n = P.n_mu;
-      while (n > 1) {
-        const int half = n >> 1;
-        lo = (row[lo + half] > v1) ? lo : lo + half;
-        n -= half;
-      }
+      const int lo = row_search(row, P.n_mu, v1);
       const float c_lo = row[lo], c_hi = row[lo + 1];
       const float fr = __fdividef(v1 - c_lo, c_hi - c_lo);
       const float mu_eda = fmaf((float)lo + fr, P.inv_mu_scale, -1.0f);
@@ -724,7 +741,6 @@ struct Stepper {
       record(P, p, 0, EV_MAXDEPTH | nonempty);
       return 1;
     }
-    const U4 u0 = rng(P, p.j, (uint32_t)p.k, 0);
     const float pm = -expm1_neg(-P.sigma_t * dm);
     if (!(u01(u0.x) < pm)) {
       if (hit == 0) {
@@ -974,6 +990,9 @@ struct Stepper {
       record(P, p, 0, EV_EARLY);
       return true;
     }
+    // both draws of the vertex up front: two independent Philox chains
+    const U4 u1 = rng(P, p.j, (uint32_t)p.k, 1);
+    const U4 u0 = rng(P, p.j, (uint32_t)p.k, 0);
     // ---- direction: MIS of the EDA table and HG / uniform (Eq. 19)
     const float rho = __fdividef(C, SM);
     int i_rho = (int)(rho * (float)P.n_rho);
@@ -986,18 +1005,12 @@ struct Stepper {
     if ((sensor && P.uniform_sensor) || P.no_eda) gamma = 0.0f;
     const float gb = sensor ? 0.0f : P.g;
     const float bx = sensor ? 0.0f : p.wx, by = sensor ? 0.0f : p.wy, bz = sensor ? 1.0f : p.wz;
-    const U4 u1 = rng(P, p.j, (uint32_t)p.k, 1);
     const float v0 = u01(u1.x), v1 = u01(u1.y);
     float sphi, cphi;
     sincos_2pi(u01(u1.z), &sphi, &cphi);
     const bool eda = v0 < gamma;
     // inverse CDF of the row: first bin whose upper edge exceeds v1
-    int lo = 0, n = P.n_mu;
-    while (n > 1) {
-      const int half = n >> 1;
-      lo = (row[lo + half] > v1) ? lo : lo + half;
-      n -= half;
-    }
+    const int lo = row_search(row, P.n_mu, v1);
     const float c_lo = row[lo], c_hi = row[lo + 1];
     const float fr = __fdividef(v1 - c_lo, c_hi - c_lo);
     const float mu_eda = fmaf((float)lo + fr, P.inv_mu_scale, -1.0f);
@@ -1064,7 +1077,6 @@ struct Stepper {
       return true;
     }
     // ---- Bernoulli medium event (Eq. 12)
-    const U4 u0 = rng(P, p.j, (uint32_t)p.k, 0);
     const float pm = -expm1_neg(-P.sigma_t * dm);
     if (!(u01(u0.x) < pm)) {
       cnt.add(ST_ESCAPE);
@@ -1369,6 +1381,29 @@ __device__ __forceinline__ void ris_warp(const TraceParams& P, bool need, const 
   __syncwarp();
 }
 
+// Warp sum of the lanes' packed event counts (five 6-bit fields per word,
+// each at most 63).  A sum over the warp needs up to 11 bits, so the fields
+// are regrouped 12 bits apart before the reductions: fields 0 and 2 of a
+// word, fields 1 and 3, and field 4 of both words.  Lane e adds event e to
+// the warp's counters.  Warp-uniform.
+template <int kEvents>
+__device__ __forceinline__ void flush_events(unsigned& ev0, unsigned& ev1, unsigned* wev, int lane) {
+  constexpr unsigned kEven = 0x3F03Fu, kOdd = 0xFC0FC0u;  // fields 0, 2 / 1, 3
+  const unsigned a0 = __reduce_add_sync(kFull, ev0 & kEven);
+  const unsigned b0 = __reduce_add_sync(kFull, (ev0 & kOdd) >> 6);
+  unsigned a1 = 0, b1 = 0;
+  if constexpr (kEvents > 5) {
+    a1 = __reduce_add_sync(kFull, ev1 & kEven);
+    b1 = __reduce_add_sync(kFull, (ev1 & kOdd) >> 6);
+  }
+  const unsigned c = __reduce_add_sync(kFull, (ev0 >> 24) | ((ev1 >> 24) << 12));
+  const int w = lane < 5 ? 0 : 1, f = lane - 5 * w;
+  const unsigned a = w ? a1 : a0, b = w ? b1 : b0;
+  const unsigned v = f == 4 ? c >> (12 * w) : ((f & 1) ? b >> (6 * (f - 1)) : a >> (6 * f));
+  if (lane < kEvents) wev[lane] += v & 0xFFFu;
+  ev0 = ev1 = 0;
+}
+
 // (a + r) mod B for 0 <= a < B and 0 <= r < 64 without a division when B >= 64.
 __device__ __forceinline__ int add_mod(int a, int r, int B) {
   const int v = a + r;
@@ -1376,9 +1411,11 @@ __device__ __forceinline__ int add_mod(int a, int r, int B) {
 }
 
 // The per-warp path loop shared by the single-scene and the batched kernels:
-// warps claim path ids [*counter, N) in chunks of kPathChunk, refill lanes
-// whose path ended, run one vertex step per iteration and commit finished
-// paths into the warp tile (or the adjoint sums).
+// a warp starts with the ids [first, first_end) and then claims ids
+// dyn_base + *counter in chunks of kPathChunk (none once dyn_base >= N, so a
+// launch that fits in one wave makes no counter atomics), refills lanes whose
+// path ended, runs one vertex step per iteration and commits finished paths
+// into the warp tile (or the adjoint sums).
 // Weight of a finished DARTS path in its bin: B / N_e, or sum W / (N_e W_b)
 // under a temporal response.
 template <bool GEN>
@@ -1393,7 +1430,9 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
                                           unsigned long long* counter, unsigned long long N,
                                           float* wsum, float* wcomp, float* wsq, RisTaskT<VAR>* wtasks,
                                           RisResult* wresults, unsigned* wev, bool do_sq,
-                                          float (&g_s)[3], float (&g_c)[3], float (&g_q)[3]) {
+                                          float (&g_s)[3], float (&g_c)[3], float (&g_q)[3],
+                                          unsigned long long first = 0, unsigned long long first_end = 0,
+                                          unsigned long long dyn_base = 0) {
   const int lane = threadIdx.x & 31;
   const int B = P.n_bins;
   constexpr bool kCoop = kIsDartsM<METHOD> && MAXM == 8;
@@ -1401,9 +1440,13 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
   Counters cnt;
   Path p;
   bool alive = false;
-  unsigned long long pool_next = 0, pool_end = 0;
-  int pool_bin = 0;  // DARTS bin of path pool_next
+  unsigned long long pool_next = min(first, N), pool_end = min(first_end, N);
+  int pool_bin = (int)((P.bin_base + pool_next) % (unsigned long long)B);  // DARTS bin of path pool_next
   bool drained = false;
+  constexpr int kEvents = (METHOD == kDarts && !GEN) ? ST_SAMPLE : ST_FP64E;
+  constexpr unsigned kSpread = 0x108421u, kFields = 0x1041041u;
+  unsigned ev0 = 0, ev1 = 0;  // packed per-lane event counts (6-bit fields)
+  int ev_steps = 0;
 
   for (;;) {
     // ---- refill lanes whose path ended (ballot + popc, warp-private id pool)
@@ -1418,9 +1461,11 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
         alive = true;
       }
       if ((unsigned long long)n_dead > avail) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(counter, chunk);
-        base = __shfl_sync(kFull, base, 0);
+        unsigned long long base = N;
+        if (dyn_base < N) {
+          if (lane == 0) base = dyn_base + atomicAdd(counter, chunk);
+          base = __shfl_sync(kFull, base, 0);
+        }
         if (base >= N) {
           drained = true;
           pool_next = pool_end = 0;
@@ -1535,23 +1580,18 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
       }
     }
     if (fin) alive = false;
-    // ---- event counts of this step (lane i keeps counter i of its warp)
-    {
-      // Five events per word: multiplying the 5 event bits by
-      // 1 + 2^5 + 2^10 + 2^15 + 2^20 puts bit i at position 6i (the shifted
-      // copies land on distinct positions, so nothing carries), one warp
-      // reduction sums the 6-bit fields (each at most 32), and lane e takes
-      // field e.
-      constexpr int kEvents = (METHOD == kDarts && !GEN) ? ST_SAMPLE : ST_FP64E;
-      constexpr unsigned kSpread = 0x108421u, kFields = 0x1041041u;
-      const unsigned w0 = __reduce_add_sync(kFull, ((cnt.bits & 31u) * kSpread) & kFields);
-      unsigned w1 = 0;
-      if constexpr (kEvents > 5) w1 = __reduce_add_sync(kFull, (((cnt.bits >> 5) & 31u) * kSpread) & kFields);
-      const unsigned mine = (lane < 5 ? w0 >> (6 * lane) : w1 >> (6 * (lane - 5))) & 63u;
-      if (lane < kEvents) wev[lane] += mine;
+    // ---- event counts of this step, kept per lane: multiplying the 5 event
+    // bits of a word by 1 + 2^5 + 2^10 + 2^15 + 2^20 puts bit i at position
+    // 6i (the shifted copies land on distinct positions, so nothing carries);
+    // the 6-bit fields count up to 63 steps before the warp sums them
+    ev0 += ((cnt.bits & 31u) * kSpread) & kFields;
+    if constexpr (kEvents > 5) ev1 += (((cnt.bits >> 5) & 31u) * kSpread) & kFields;
+    if (++ev_steps == 63) {
+      flush_events<kEvents>(ev0, ev1, wev, lane);
+      ev_steps = 0;
     }
   }
-
+  flush_events<kEvents>(ev0, ev1, wev, lane);
 }
 
 template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK, bool ADJ = false, bool GEN = false,
@@ -1592,8 +1632,13 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
 
   // adjoint: per-lane Kahan sums of the weighted path scores and their squares
   float g_s[3] = {0.0f, 0.0f, 0.0f}, g_c[3] = {0.0f, 0.0f, 0.0f}, g_q[3] = {0.0f, 0.0f, 0.0f};
+  // each warp's first chunk is fixed by its index; the counter hands out the rest
+  const unsigned long long chunk = P.chunk ? P.chunk : (unsigned long long)kPathChunk;
+  const unsigned long long first = ((unsigned long long)blockIdx.x * nwarps + warp) * chunk;
+  const unsigned long long dyn_base = (unsigned long long)gridDim.x * nwarps * chunk;
   path_loop<METHOD, MAXM, DEBUG, TILE, ADJ, GEN, VAR>(P, tab, P.counter, P.N, wsum, wcomp, wsq, wtasks,
-                                                 wresults, warp_events[warp], do_sq, g_s, g_c, g_q);
+                                                 wresults, warp_events[warp], do_sq, g_s, g_c, g_q, first,
+                                                 first + chunk, dyn_base);
 
   // ---- statistics
   __syncthreads();
