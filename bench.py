@@ -17,6 +17,11 @@ frame), 50 bounces, 8 RIS candidates, 16x8x256 direction table.
 2^24 paths per step (the GPU saturated); the default run reports it too.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+  python bench.py --only {timed,batched,differentiable,spheres}
+
+``--only`` runs one measurement alone, for ncu captures of its kernels: the
+timed steps, the batched 256-media launch, the differentiable step (forward
+render + path-replay adjoint on the 32x32 cube camera), the 512x512 frame.
 
 Under torchrun every rank traces its own path-id range (weak scaling) and the
 per-rank histograms are combined with one FP64 all-reduce per step.  The
@@ -83,7 +88,12 @@ def parse():
     ap.add_argument("--no-mse", action="store_true", help="skip the MSE x time comparisons")
     ap.add_argument("--only-timed", action="store_true",
                     help="run only the timed steps (for profiler launch lists)")
+    ap.add_argument("--only", default=None, choices=["timed", "batched", "differentiable", "spheres"],
+                    help="run one measurement alone (for ncu captures of its kernels): the timed "
+                         "steps, the batched launch, the differentiable step, the 512x512 frame")
     a = ap.parse_args()
+    if a.only_timed:
+        a.only = "timed"
     if a.steps is None:
         a.steps = 2000 if a.workload == "box_camera" else 60
     return a
@@ -481,6 +491,7 @@ def batched_compare(ctx, S, torch, reps=5):
         return e0.elapsed_time(e1) / k
 
     t_batch = timed(lambda: ctx.render_batch(scenes, samplings, outs=outs), reps)
+    events = ctx.stats()  # of the last batched launch
     singles = [torch.empty(sc.gate.n_bins, dtype=torch.float64, device="cuda") for sc in scenes]
 
     def loop():
@@ -492,9 +503,70 @@ def batched_compare(ctx, S, torch, reps=5):
     return {"media": len(scenes), "paths": total, "ms_batched_graph": t_batch,
             "ms_one_launch_per_medium": t_loop, "paths_per_s_batched": total / (t_batch * 1e-3),
             "paths_per_s_per_medium_launches": total / (t_loop * 1e-3),
-            "speedup": t_loop / t_batch,
+            "speedup": t_loop / t_batch, "events_per_launch": events,
+            "vertices_per_s_batched": events["vertices"] / (t_batch * 1e-3),
             "workload": "256 slab media: sigma_s log-uniform [0.1,10], albedo U[0.5,0.999], "
                         "g U[-0.3,0.9], side U[0.5,4], budgets 2^U[12,20], 128 bins, K=50, M=8"}
+
+
+def spheres_frame(ctx, S, torch, flush, reps=3):
+    """The largest configuration: 512x512 camera, 32 spheres, two emitters,
+    1000 bins, 64 spp, K = 100 (16.7 M paths, a 2.1 GB histogram)."""
+    scs = S.spheres_camera_scene(seed=0)
+    sps = S.Sampling(seed=0, paths_per_element=64, max_bounces=100, flags=S.FLAG_REBUILD_TABLE)
+    Ns = S.total_paths(scs, sps)
+    hs = torch.empty(S.histogram_shape(scs), dtype=torch.float64, device="cuda")
+    preps = ctx.prepare(scs, sps)
+    preps.render(out=hs)
+    torch.cuda.synchronize()
+    ctx.set_kernel_timing(True)
+    ts, ks, pers = time_steps(ctx, torch, lambda: preps.render(out=hs), reps, flush)
+    ctx.set_kernel_timing(False)
+    out = {"workload": "512x512 pinhole camera inside a 4x4x4 medium (sigma_s 0.8, sigma_a 0.005, g 0.8) with 32 "
+                       "seeded Lambertian spheres, two point pulse emitters (t0 = 0, 1.5), 1000 bins on [0,20), "
+                       "64 spp, K=100", "paths_per_step": Ns, "ms_per_step": statistics.fmean(ts),
+           "paths_per_s": Ns / (statistics.fmean(ts) * 1e-3), "histogram_bytes": hs.numel() * 8,
+           "roofline": roofline(pers, statistics.fmean(ks), True, "spheres_512", Ns)}
+    del hs, preps
+    return out
+
+
+def differentiable_step(ctx, S, torch, flush, reps=10):
+    """The differentiable configuration: the unit-cube medium seen by a 32x32
+    camera, 256 bins, 2^20 paths (1024 per pixel); L2 loss against a target
+    rendered at (sigma_s, sigma_a, g) = (1.3, 0.02, 0.6), gradient at
+    (1.0, 0.01, 0.7).  A gradient step is the forward render, the loss
+    weights 2 (h - target) and the path-replay adjoint pass with an
+    independent seed; the forward render alone is timed beside it."""
+    import dataclasses
+    sc = S.cube_camera_scene(32, 32)
+    star = dataclasses.replace(sc, medium=dataclasses.replace(sc.medium, sigma_s=1.3, sigma_a=0.02, g=0.6))
+    sp = S.Sampling(seed=0, paths_per_element=1024)
+    spa = dataclasses.replace(sp, seed=1)
+    n = S.total_paths(sc, sp)
+    target = ctx.render(star, sp)
+    h = torch.empty_like(target)
+    grad = [None]
+
+    def forward():
+        ctx.render(sc, sp, out=h)
+
+    def gradient_step():
+        ctx.render(sc, sp, out=h)
+        grad[0] = ctx.adjoint(sc, spa, (2.0 * (h - target)).reshape(-1))
+
+    for _ in range(3):
+        gradient_step()
+    torch.cuda.synchronize()
+    tf, _, _ = time_steps(ctx, torch, forward, reps, flush, kernel_timing=False)
+    tg, _, _ = time_steps(ctx, torch, gradient_step, reps, flush, kernel_timing=False)
+    mf, mg = statistics.median(tf), statistics.median(tg)
+    g = grad[0].cpu().tolist()
+    return {"workload": "32x32 pinhole view of the unit-cube medium (sigma_s 1, sigma_a 0.01, g 0.7), 256 bins, "
+                        "2^20 paths (1024 spp), K=50; L2 loss against a render at (1.3, 0.02, 0.6)",
+            "paths": n, "ms_forward": mf, "ms_gradient_step": mg, "ms_adjoint": mg - mf,
+            "adjoint_over_forward": (mg - mf) / mf, "gradient_steps_per_s": 1e3 / mg,
+            "adjoint_paths_per_s": n / ((mg - mf) * 1e-3), "dL_dsigma_s_sigma_a_g": g}
 
 
 def time_steps(ctx, torch, step, steps, flush, kernel_timing=True):
@@ -557,6 +629,16 @@ def main():
         pg = dist
     ctx = capi.Context(local)
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+    if args.only in ("batched", "differentiable", "spheres"):
+        run = {"batched": lambda: batched_compare(ctx, S, torch),
+               "differentiable": lambda: differentiable_step(ctx, S, torch, flush),
+               "spheres": lambda: spheres_frame(ctx, S, torch, flush)}[args.only]
+        if rank == 0:
+            print(json.dumps({"only": args.only, **run()}), flush=True)
+        ctx.close()
+        if pg is not None:
+            pg.destroy_process_group()
+        return 0
     sc, sp, N = make_workload(args.workload, S)
     general = args.workload == "box_camera"
     hist = torch.zeros(S.histogram_shape(sc), dtype=torch.float64, device="cuda")
@@ -600,7 +682,7 @@ def main():
     K = args.steps
     kms = statistics.fmean(kern_ms)
     roof = roofline(per, kms, general, args.workload, N)
-    if args.only_timed:
+    if args.only == "timed":
         print(json.dumps({"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws,
                           "steps": K, "warmup": args.warmup, "ms_per_step": t_step,
                           "workload": args.workload, "roofline": roof, "block": tuned_block,
@@ -642,25 +724,7 @@ def main():
                     "paths_per_s": N2 / (t2 * 1e-3),
                     "roofline": roofline(per2, statistics.fmean(k2), other == "box_camera", other, N2)}
 
-    # ---- the largest configuration: 512x512 camera, 32 spheres, two
-    # emitters, 1000 bins, 64 spp, K = 100 (16.7 M paths, a 2.1 GB histogram)
-    scs = S.spheres_camera_scene(seed=0)
-    sps = S.Sampling(seed=0, paths_per_element=64, max_bounces=100, flags=S.FLAG_REBUILD_TABLE)
-    Ns = S.total_paths(scs, sps)
-    hs = torch.empty(S.histogram_shape(scs), dtype=torch.float64, device="cuda")
-    preps = ctx.prepare(scs, sps)
-    preps.render(out=hs)
-    torch.cuda.synchronize()
-    ctx.set_kernel_timing(True)
-    ts, ks, pers = time_steps(ctx, torch, lambda: preps.render(out=hs), 3, flush)
-    ctx.set_kernel_timing(False)
-    extra["spheres_512"] = {
-        "workload": "512x512 pinhole camera inside a 4x4x4 medium (sigma_s 0.8, sigma_a 0.005, g 0.8) with 32 "
-                    "seeded Lambertian spheres, two point pulse emitters (t0 = 0, 1.5), 1000 bins on [0,20), "
-                    "64 spp, K=100", "paths_per_step": Ns, "ms_per_step": statistics.fmean(ts),
-        "paths_per_s": Ns / (statistics.fmean(ts) * 1e-3), "histogram_bytes": hs.numel() * 8,
-        "roofline": roofline(pers, statistics.fmean(ks), True, "spheres_512", Ns)}
-    del hs, preps
+    extra["spheres_512"] = spheres_frame(ctx, S, torch, flush)
 
     # ---- the cube as configured: 2^16 paths per render (latency-bound)
     sc16, sp16 = S.cube_workload(paths=1 << 16, seed=0)
@@ -679,6 +743,7 @@ def main():
         extra["two_peak_response"] = two_peak_response(ctx, S, torch)
         extra["mse_time_cube"] = mse_time(ctx, S, torch)
     extra["batched"] = batched_compare(ctx, S, torch)
+    extra["differentiable_32x32"] = differentiable_step(ctx, S, torch, flush)
     cpu = cpu_baseline(args.workload) if ws == 1 else None
 
     line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws, "steps": K,
