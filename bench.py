@@ -221,9 +221,16 @@ def cpu_baseline(workload: str, budget_s: float = 12.0):
         t_tot += time.perf_counter() - t0
         done += 1
     unit = "frames" if workload == "box_camera" else f"batches of {n} paths"
+    # one thread, on a quarter of the same sample size
+    n1 = max(1, n // 4)
+    t0 = time.perf_counter()
+    O.render(sc, sp, O.ORC_DARTS, n_paths=n1, offset=done * n, cdf=cdf, threads=1)
+    t1 = time.perf_counter() - t0
     return {"value": done * n / t_tot, "unit": "paths/s", "cores": cores, "kind": "oracle",
             "sample": f"{done} {unit} of the benchmark workload ({done * n} paths, table prebuilt), "
-                      f"FP64 C oracle, {cores} POSIX threads, {t_tot:.2f} s wall"}
+                      f"FP64 C oracle, {cores} POSIX threads, {t_tot:.2f} s wall",
+            "single_thread": {"value": n1 / t1, "unit": "paths/s", "cores": 1,
+                              "sample": f"{n1} paths of the same workload, {t1:.2f} s wall"}}
 
 
 def run_reference(args):
