@@ -12,8 +12,9 @@ a brute-force baseline.  Parity status per oracle function:
   orc_ellipse (Eq. 18)    pinned: t + |x_k + w t - x_e| = S, vertex limits
   orc_control_pdf (Eq.22) pinned: numerical dS/dt and unit mass
   table (Eq. 16-18)       pinned: adaptive Gauss-Kronrod quadrature
-  DARTS path (Eq. 5-22)   pinned: single-scatter closed form (K = 1) and the
-                          brute-force plain estimator (K = 2, 3)
+  DARTS path (Eq. 5-22)   pinned: single-scatter closed form (K = 1), the
+                          brute-force plain estimator (K = 2, 3) and the
+                          absorption identity (sigma_a as a path-length weight)
   plain / vanilla PT      pinned: single-scatter closed form; each other
   adjoint score           pinned: central finite differences (CRN)
 """
@@ -273,6 +274,35 @@ def test_darts_converges_to_plain_pt(K, where, sigma_s):
     assert abs(z[0]) < 6.0
     zsum = (np.sum(h[1:]) - np.sum(h2[1:])) / np.sqrt(np.sum(se[1:] ** 2 + se2[1:] ** 2))
     assert abs(zsum) < 4.5
+
+
+@pytest.mark.parametrize("method", [O.ORC_DARTS, O.ORC_PLAIN_UNIFORM_T])
+def test_absorption_scales_each_bin_by_its_path_length(method):
+    """Absorption only attenuates: in an infinite medium every contribution
+    to a bin has travelled the bin's length l = v (t - t0), so
+    E[h_b(sigma_a)] = E[h_b(0)] x (the bin average of e^(-sigma_a l)) for
+    any unbiased estimator, though sigma_a changes sigma_t and with it every
+    sampling decision.  A dropped or misplaced sigma_a (albedo, attenuation,
+    the Bernoulli event, Phi) breaks the proportion."""
+    sa, t0, t1, nb = 0.35, 1.05, 3.0, 12
+    lo = t0 + (t1 - t0) * np.arange(nb) / nb
+    hi = lo + (t1 - t0) / nb
+    factor = (np.exp(-sa * lo) - np.exp(-sa * hi)) / (sa * (hi - lo))  # v = 1
+    n = 1 << 18
+    hs, ses = [], []
+    for k, sig_a in enumerate((sa, 0.0)):
+        sc = S.infinite_scene(1.0, sig_a, 0.3, separation=1.0, n_bins=nb, t_min=t0, t_max=t1)
+        sp = S.Sampling(seed=40 + k, paths_per_element=n, max_bounces=3)
+        h, sq, _ = O.render(sc, sp, method)
+        hs.append(h)
+        ses.append(O.standard_error(h, sq, n / nb if method == O.ORC_DARTS else n))
+    pred, se_pred = hs[1] * factor, ses[1] * factor
+    z = (hs[0] - pred) / np.sqrt(ses[0] ** 2 + se_pred ** 2)
+    # bin 0 starts at the straight-line time (heavy tail); checked loosely
+    assert np.max(np.abs(z[1:])) < 4.5, z
+    assert abs(z[0]) < 6.0
+    # the proportion is not trivially met: the attenuation spans 0.67 .. 0.36
+    assert factor[0] / factor[-1] > 1.8
 
 
 def test_bins_receive_equal_path_counts():
