@@ -700,10 +700,10 @@ def main():
     # ---- end to end through the C ABI with host buffers
     hh = torch.zeros(S.histogram_shape(sc), dtype=torch.float64).pin_memory()
     ne = max(3, min(args.steps, 20))
-    ctx.render_host(sc, sp, hh)
+    prepared.render_host(hh)
     te = time.perf_counter()
     for i in range(ne):
-        ctx.render_host(sc, sp, hh, path_offset=i * N)
+        prepared.render_host(hh, path_offset=i * N)
     te = time.perf_counter() - te
     cs, keep = capi.to_c_scene(sc)
     import ctypes
@@ -711,7 +711,8 @@ def main():
            + len(sc.emitters) * ctypes.sizeof(capi.darts_emitter) + 40 * len(sc.geometry.spheres))
     e2e = {"value": N * ne / te, "unit": "paths/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": hh.numel() * 8,
-           "note": "darts_render_host: scene/sampling structs marshalled into the launches, "
+           "note": "darts_render_host through the prepared scene (Context.prepare): scene/sampling structs "
+                   "marshalled into the launches, "
                    "histograms copied back to pinned host memory, stream synchronised per step"}
 
     extra = {}

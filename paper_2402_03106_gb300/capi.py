@@ -353,6 +353,14 @@ class Prepared:
                                                   _ptr(sumsq), int(path_offset), None))
         return out
 
+    def render_host(self, hist_host: torch.Tensor, sumsq_host: Optional[torch.Tensor] = None,
+                    path_offset: int = 0) -> torch.Tensor:
+        """darts_render_host with the marshalled structs: host (pinned) buffers in
+        and out, synchronised on return."""
+        _check(self.ctx.h, self._lib.darts_render_host(self.ctx.h, C.byref(self.cs), C.byref(self.csp),
+                                                       _ptr(hist_host), _ptr(sumsq_host), int(path_offset)))
+        return hist_host
+
 class Context:
     """A libdarts context on one CUDA device, ordered on a torch stream."""
 

@@ -29,6 +29,7 @@ struct darts_ctx {
   size_t partials_bytes = 0;
   double* host_hist = nullptr; // device histogram for darts_render_host
   size_t host_hist_bytes = 0;
+  unsigned int* status_host = nullptr;  // pinned copy of the scratch status words
   // direction-table cache
   float* table = nullptr;
   size_t table_bytes = 0;
@@ -610,8 +611,10 @@ darts_status darts_create(darts_ctx** out, int cuda_device, void* cuda_stream) {
   const size_t sbytes = (2 + kStatCount) * sizeof(unsigned long long);
   e = cudaMalloc((void**)&ctx->scratch, sbytes);
   if (e == cudaSuccess) e = cudaMemset(ctx->scratch, 0, sbytes);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->status_host, 2 * sizeof(unsigned int));
   if (e != cudaSuccess) {
     if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->status_host) cudaFreeHost(ctx->status_host);
     delete ctx;
     return e == cudaErrorMemoryAllocation ? DARTS_ERR_OOM : DARTS_ERR_CUDA;
   }
@@ -624,6 +627,7 @@ darts_status darts_destroy(darts_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   cudaFree(ctx->scratch);
+  cudaFreeHost(ctx->status_host);
   cudaFree(ctx->partials);
   cudaFree(ctx->table);
   cudaFree(ctx->host_hist);
@@ -655,9 +659,12 @@ darts_status darts_last_error(const darts_ctx* ctx, char* buf, size_t n) {
 darts_status darts_sync(darts_ctx* ctx) {
   if (!ctx) return DARTS_ERR_INVALID_ARG;
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  // the status words travel behind the stream's work into pinned memory: one
+  // synchronisation, no separate blocking copy
+  CK(cudaMemcpyAsync(ctx->status_host, ctx->scratch + 1, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                     ctx->stream), "status read");
   CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");
-  unsigned int st[2] = {0, 0};
-  CK(cudaMemcpy(st, ctx->scratch + 1, sizeof(st), cudaMemcpyDeviceToHost), "status read");
+  const unsigned int st[2] = {ctx->status_host[0], ctx->status_host[1]};
   if (st[1]) {
     CK(cudaMemset(reinterpret_cast<unsigned int*>(ctx->scratch + 1) + 1, 0, sizeof(unsigned int)), "status clear");
     if (st[1] & 2u) return fail(ctx, DARTS_ERR_TIMEOUT, "a bounded device wait expired");

@@ -253,6 +253,17 @@ def test_render_host_matches_device(ctx):
     ctx.render_host(sc, sp, hh)
     # path-to-block assignment is dynamic: equal up to FP64 summation order
     torch.testing.assert_close(hh, h_dev, rtol=1e-6, atol=1e-15)
+    # the prepared form, with a sum of squares and a path offset (camera frame)
+    sc2, sp2 = S.box_camera_workload(seed=1)
+    sp2.paths_per_element = 2
+    pr = ctx.prepare(sc2, sp2)
+    d_h, d_q = ctx.render(sc2, sp2, sumsq=True, path_offset=4096 * 2)
+    hh2 = torch.zeros(S.histogram_shape(sc2), dtype=torch.float64).pin_memory()
+    hq2 = torch.zeros_like(hh2).pin_memory()
+    pr.render_host(hh2, hq2, path_offset=4096 * 2)
+    torch.testing.assert_close(hh2, d_h.cpu(), rtol=1e-6, atol=1e-15)
+    torch.testing.assert_close(hq2, d_q.cpu(), rtol=1e-6, atol=1e-15)
+    assert float(hh2.sum()) > 0.0
 
 
 def test_other_ris_m_and_table_dims(ctx):
