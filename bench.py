@@ -24,7 +24,8 @@ timed steps, the batched 256-media launch, the differentiable step (forward
 render + path-replay adjoint on the 32x32 cube camera), the 512x512 frame.
 
 Under torchrun every rank traces its own path-id range (weak scaling) and the
-per-rank histograms are combined with one FP64 all-reduce per step.  The
+per-rank histograms are combined with one FP64 all-reduce per step, which
+runs while the next step renders (two histogram buffers alternate).  The
 ``--impl reference`` arm times the FP64 CPU oracle on this host's cores on a
 bounded sample of the same workload.
 """
@@ -576,15 +577,18 @@ def differentiable_step(ctx, S, torch, flush, reps=10):
             "adjoint_paths_per_s": n / ((mg - mf) * 1e-3), "dL_dsigma_s_sigma_a_g": g}
 
 
-def time_steps(ctx, torch, step, steps, flush, kernel_timing=True):
+def time_steps(ctx, torch, step, steps, flush, kernel_timing=True, finish=None):
     """CUDA-event time of each step (L2 flushed before each), the path
-    kernel's own time and the summed event counts."""
+    kernel's own time and the summed event counts.  finish() (the last
+    exchange of a pipelined multi-rank loop) runs inside the last step."""
     step_ms, kern_ms, stats_acc = [], [], {}
-    for _ in range(steps):
+    for i in range(steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         step()
+        if finish is not None and i == steps - 1:
+            finish()
         e1.record()
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -648,17 +652,21 @@ def main():
         return 0
     sc, sp, N = make_workload(args.workload, S)
     general = args.workload == "box_camera"
-    hist = torch.zeros(S.histogram_shape(sc), dtype=torch.float64, device="cuda")
     offset = sharding.path_offset(rank, N)
     prepared = ctx.prepare(sc, sp)  # structs marshalled once, as a renderer loop would
+    # under torchrun the all-reduce of step k - 1 runs while step k renders
+    pipe = sharding.PipelinedCombine(
+        lambda: torch.zeros(S.histogram_shape(sc), dtype=torch.float64, device="cuda"), ws)
 
     def step():
+        hist = pipe.begin_step()
         prepared.render(out=hist, path_offset=offset)
-        sharding.combine(hist, ws)
+        pipe.end_step(hist)
 
     tuned_block = ctx.autotune(sc, sp)
     for _ in range(args.warmup):
         step()
+    pipe.finish()
     torch.cuda.synchronize()
     ctx.set_kernel_timing(True)
     clocks = ClockSampler(local)
@@ -667,7 +675,7 @@ def main():
         pg.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    step_ms, kern_ms, per = time_steps(ctx, torch, step, args.steps, flush)
+    step_ms, kern_ms, per = time_steps(ctx, torch, step, args.steps, flush, finish=pipe.finish)
     torch.cuda.synchronize()
     if pg is not None:
         pg.barrier()
@@ -760,7 +768,8 @@ def main():
             "config": {"workload": WORKLOADS[args.workload], "paths_per_gpu_per_step": N,
                        "block": tuned_block, "grid": "one CTA per SM (persistent)",
                        "l2": "256 MiB buffer written between timed steps (flush)",
-                       "parallelism": f"path-id shards x{ws}, FP64 histogram all-reduce" if ws > 1
+                       "parallelism": f"path-id shards x{ws}, FP64 histogram all-reduce of step k-1 "
+                                      f"overlapped with the render of step k" if ws > 1
                        else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 2 * K,

@@ -21,3 +21,51 @@ def combine(hist, world_size: int, group=None):
         dist.all_reduce(hist, op=dist.ReduceOp.SUM, group=group)
         hist.div_(world_size)
     return hist
+
+
+class PipelinedCombine:
+    """The combine of step k - 1 overlapped with the render of step k.
+
+    Two histogram buffers alternate.  `begin_step()` starts the all-reduce
+    of the previous step's histogram (asynchronous, ordered after the work
+    already queued on the stream) and returns the other buffer for this
+    step's render; `end_step()` waits for that all-reduce (a wait on the
+    stream under NCCL, on the host under gloo), so every exchange completes
+    within the step that overlaps it.  `finish()` exchanges the last step's
+    histogram, waits, and returns the ranks' average of that step.  With one
+    rank there is nothing to exchange: one buffer, no collective.
+    """
+
+    def __init__(self, make_buffer, world_size: int, group=None):
+        self.world_size = int(world_size)
+        self.group = group
+        n = 2 if self.world_size > 1 else 1
+        self.buffers = [make_buffer() for _ in range(n)]
+        self.step = 0
+        self.prev = None      # histogram of the previous step, not yet exchanged
+        self.work = None      # the all-reduce in flight
+
+    def _reduce(self, hist):
+        import torch.distributed as dist
+        return dist.all_reduce(hist, op=dist.ReduceOp.SUM, group=self.group, async_op=True)
+
+    def begin_step(self):
+        if self.world_size > 1 and self.prev is not None:
+            self.work = self._reduce(self.prev)
+        buf = self.buffers[self.step % len(self.buffers)]
+        self.step += 1
+        return buf
+
+    def end_step(self, hist):
+        if self.work is not None:
+            self.work.wait()
+            self.work = None
+        self.prev = hist
+
+    def finish(self):
+        last = self.prev
+        if last is not None and self.world_size > 1:
+            self._reduce(last).wait()
+            last.div_(self.world_size)
+        self.prev = None
+        return last

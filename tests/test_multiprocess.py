@@ -128,3 +128,61 @@ def test_sharded_camera_render_is_a_consistent_estimate():
     b0, b1 = bins[0], bins[1]
     assert np.array_equal(b0 // B, b1 // B)
     assert np.array_equal((b0 % B + spp) % B, b1 % B)
+
+
+def _pipelined_worker(rank, world, port, n, steps, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import sys
+        sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+        import oracle as O
+        from paper_2402_03106_gb300 import scenes as S, sharding
+        sc, sp = S.cube_workload(paths=n, seed=19)
+        sp.max_bounces = 8
+        pipe = sharding.PipelinedCombine(lambda: torch.zeros(256, dtype=torch.float64), world)
+        seen = []
+        for k in range(steps):
+            buf = pipe.begin_step()
+            seen.append(id(buf))
+            h, _, _ = O.render(sc, sp, O.ORC_DARTS, n_paths=n,
+                               offset=(k * world + rank) * n, threads=2)
+            buf.copy_(torch.from_numpy(h))
+            pipe.end_step(buf)
+        last = pipe.finish()
+        other = [b for b in pipe.buffers if b is not last][0]
+        if rank == 0:
+            q.put((last.numpy().copy(), other.numpy().copy(), len(set(seen))))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_pipelined_combine_averages_the_last_step():
+    """Two buffers alternate between steps; each step's render overlaps the
+    all-reduce of the previous step's buffer.  After finish() the last
+    buffer holds the ranks' average of the last step, equal to a single
+    render of its world x n paths."""
+    import oracle as O
+    from paper_2402_03106_gb300 import scenes as S
+    world, n, steps = 2, 2048, 3
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_pipelined_worker, args=(r, world, port, n, steps, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got, prev, nbuf = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=300)
+        assert p.exitcode == 0
+    assert nbuf == 2
+    sc, sp = S.cube_workload(paths=n * world, seed=19)
+    sp.max_bounces = 8
+    # the last step's ids: [(steps - 1) * world * n, steps * world * n)
+    ref, _, _ = O.render(sc, sp, O.ORC_DARTS, n_paths=world * n, offset=(steps - 1) * world * n, threads=4)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-300)
+    # the other buffer holds the ranks' sum of the step before, exchanged
+    # while the last step rendered
+    ref1, _, _ = O.render(sc, sp, O.ORC_DARTS, n_paths=world * n, offset=(steps - 2) * world * n, threads=4)
+    np.testing.assert_allclose(prev, world * ref1, rtol=1e-12, atol=1e-300)
