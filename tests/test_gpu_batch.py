@@ -41,6 +41,24 @@ def test_batch_equals_single_renders(ctx):
         torch.testing.assert_close(h, ref, rtol=1e-5, atol=1e-14 * float(ref.abs().max()) + 1e-300)
 
 
+def test_full_size_batch_equals_single_renders(ctx):
+    """The batched configuration at full size: 256 media, budgets
+    2^U[12,20] (about 47 M paths), 128 bins, in the benchmark's launch (one
+    graph-captured persistent kernel); each medium's histogram equals its
+    single render up to FP64 summation order.  The single renders are
+    checked against the oracle elsewhere."""
+    media = S.batched_media(n_media=256, seed=0)
+    scenes = [m[0] for m in media]
+    samplings = [m[1] for m in media]
+    outs = ctx.render_batch(scenes, samplings)
+    ctx.sync()
+    st = ctx.stats()
+    assert st["paths"] == sum(sp.paths_per_element for sp in samplings) > 40_000_000
+    for sc, sp, h in zip(scenes, samplings, outs):
+        ref = ctx.render(sc, sp)
+        torch.testing.assert_close(h, ref, rtol=1e-5, atol=1e-14 * float(ref.abs().max()) + 1e-300)
+
+
 def test_batch_matches_oracle(ctx):
     media = _media(4, seed=5, lo=12.0, hi=13.0)
     scenes = [m[0] for m in media]

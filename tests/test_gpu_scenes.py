@@ -222,14 +222,19 @@ def test_general_scenes_reject_other_ris_m(ctx):
     ctx.render(sc, S.Sampling(paths_per_element=4, ris_m=4, method=S.PLAIN_UNIFORM_T))
 
 
-@pytest.mark.parametrize("name", ["box_64", "spheres_512"])
+@pytest.mark.parametrize("name", ["box_64", "cube_camera_32", "spheres_512"])
 def test_full_size_frames_sampled_paths(ctx, name):
     """The camera configurations at full size in the benchmark's launch
     configuration (one render call): 2048 sampled paths recomputed one by one
-    by the oracle.  64x64 box at 16 spp (65536 paths); 512x512 spheres
-    scene at 64 spp, K = 100 (16.7 M paths, 2.1 GB histogram)."""
+    by the oracle.  64x64 box at 16 spp (65536 paths); the 32x32 view of the
+    unit cube at 1024 spp (2^20 paths, the differentiable configuration);
+    512x512 spheres scene at 64 spp, K = 100 (16.7 M paths, 2.1 GB
+    histogram)."""
     if name == "box_64":
         sc, sp = S.box_camera_workload(seed=0)
+    elif name == "cube_camera_32":
+        sc = S.cube_camera_scene(32, 32)
+        sp = S.Sampling(seed=0, paths_per_element=1024)
     else:
         sc = S.spheres_camera_scene(seed=0)
         sp = S.Sampling(seed=0, paths_per_element=64, max_bounces=100)
