@@ -17,7 +17,7 @@ torch = pytest.importorskip("torch")
 
 import oracle as O  # noqa: E402
 from paper_2402_03106_gb300 import scenes as S  # noqa: E402
-from parity_util import NEAR_TIE, REL_PATH, check_paths  # noqa: E402,F401
+from parity_util import NEAR_TIE, REL_PATH, check_paths, displaced_sensitivity  # noqa: E402,F401
 
 pytestmark = pytest.mark.gpu
 
@@ -77,6 +77,28 @@ def test_darts_per_path_parity(ctx, K):
     torch.cuda.synchronize()
     ref = O.trace_paths(sc, sp, 12345, n)
     check_paths(gpu, ref, K)
+
+
+def test_path_ids_across_the_32_bit_boundary(ctx):
+    """Global path ids past 2^32 (a path offset of a long progressive render
+    or a high rank): the Philox counter carries the id's high word, DARTS
+    bins and camera elements follow the 64-bit id.  2048 paths straddling
+    2^32, on the specialised kernel (point sensor) and on the general one
+    (a camera frame, whose ids wrap over the pixels with the sample index
+    continuing)."""
+    first = (1 << 32) - 1000
+    sc, sp = S.cube_workload(paths=1 << 16, seed=4)
+    sp.max_bounces = 20
+    gpu = ctx.debug_paths(sc, sp, first, 2048)
+    ref = O.trace_paths(sc, sp, first, 2048)
+    check_paths(gpu, ref, sp.max_bounces)
+    sc = S.box_camera_scene(seed=0, width=16, height=16, n_bins=128)
+    sp = S.Sampling(seed=5, paths_per_element=8, max_bounces=20)
+    gpu = ctx.debug_paths(sc, sp, first, 2048)
+    ref = O.trace_paths(sc, sp, first, 2048)
+    sens = 5.0 * displaced_sensitivity(sc, sp, first, 2048, S.DARTS, ref)
+    check_paths(gpu, ref, sp.max_bounces, extra_tol=sens)
+    assert np.count_nonzero(ref["contrib"]) > 100
 
 
 @pytest.mark.parametrize("ris_m", [8, 4])
