@@ -177,6 +177,30 @@ def test_histogram_parity_matched_seeds(ctx, method):
         assert np.all(sq.cpu().numpy() >= 0) and sq.cpu().numpy().sum() <= 1.0001 * sqref.sum()
 
 
+@pytest.mark.parametrize("method", [S.DARTS, S.PLAIN_UNIFORM_T])
+def test_many_bins_without_shared_tiles(ctx, method):
+    """A point sensor with 8192 bins: the warp tiles (warps x 3 x bins
+    floats) no longer fit beside the table, so the launch commits with FP64
+    atomics straight into the zeroed output.  Matched seeds against the
+    oracle, histogram and sums of squares."""
+    sc, sp = S.cube_workload(paths=1 << 17, seed=9)
+    sc.gate.n_bins = 8192
+    sp.method = method
+    sp.max_bounces = 20
+    hist, sq = ctx.render(sc, sp, sumsq=True)
+    ctx.sync()
+    h = hist.cpu().numpy()
+    href, sqref, _ = O.render(sc, sp, method)
+    assert np.count_nonzero(href) > 1500
+    l2 = np.linalg.norm(h - href) / np.linalg.norm(href)
+    assert l2 < 1e-3, l2
+    if method == S.DARTS:
+        # about 16 paths per bin: one path within its per-path allowance
+        # moves its bin's square visibly, so the squares are compared in L2
+        q = sq.cpu().numpy()
+        assert np.linalg.norm(q - sqref) / np.linalg.norm(sqref) < 1e-3
+
+
 def test_full_size_sampled_paths(ctx):
     """2^24 paths in the benchmark's launch configuration; 2048 sampled paths
     recomputed one by one by the oracle."""
