@@ -262,6 +262,18 @@ darts_status darts_render_host(darts_ctx* ctx, const darts_scene* scene,
                                const darts_sampling* sampling, double* hist_host,
                                double* sumsq_host, uint64_t path_offset);
 
+/* darts_render into HOST buffers without waiting: the render is queued on
+ * the context's stream and the copy back on a second stream of the
+ * context, so the copy of one call overlaps the render of the next.  Two
+ * device histograms alternate between calls; a render waits (on the
+ * device) for the copy that last used its buffer.  hist_host / sumsq_host
+ * (page-locked for an asynchronous copy) must stay valid and unread until
+ * darts_sync returns, which waits for both streams and reports device
+ * errors.  Same arguments and errors as darts_render_host. */
+darts_status darts_render_host_async(darts_ctx* ctx, const darts_scene* scene,
+                                     const darts_sampling* sampling, double* hist_host,
+                                     double* sumsq_host, uint64_t path_offset);
+
 /* Path-replay adjoint of the DARTS estimator (not in the paper; its Sec. 7
  * lists differentiable transient rendering as future work).  Traces the paths
  * path_offset .. +N-1 of `sampling` (use a seed independent of the forward

@@ -33,7 +33,7 @@ EXPORTED = ("darts_create", "darts_destroy", "darts_set_stream", "darts_status_s
             "darts_render", "darts_render_host", "darts_get_stats", "darts_debug_paths",
             "darts_debug_philox", "darts_set_kernel_timing", "darts_last_kernel_ms",
             "darts_render_static", "darts_set_launch", "darts_autotune", "darts_adjoint",
-            "darts_render_batch")
+            "darts_render_batch", "darts_render_host_async")
 BATCH_NO_GRAPH = 1
 
 
@@ -122,6 +122,7 @@ def load(path: str = LIB_PATH):
         lib.darts_table_row_stride.restype = C.c_int32
         lib.darts_render.argtypes = [vp, sc_p, sp_p, vp, vp, C.c_uint64, C.POINTER(darts_probe)]
         lib.darts_render_host.argtypes = [vp, sc_p, sp_p, vp, vp, C.c_uint64]
+        lib.darts_render_host_async.argtypes = [vp, sc_p, sp_p, vp, vp, C.c_uint64]
         lib.darts_get_stats.argtypes = [vp, C.POINTER(darts_stats)]
         lib.darts_debug_paths.argtypes = [vp, sc_p, sp_p, C.c_uint64, C.c_uint32, vp, vp, vp, vp]
         lib.darts_debug_philox.argtypes = [vp, vp, C.c_uint64, C.c_uint32, vp]
@@ -359,6 +360,15 @@ class Prepared:
         and out, synchronised on return."""
         _check(self.ctx.h, self._lib.darts_render_host(self.ctx.h, C.byref(self.cs), C.byref(self.csp),
                                                        _ptr(hist_host), _ptr(sumsq_host), int(path_offset)))
+        return hist_host
+
+    def render_host_async(self, hist_host: torch.Tensor, sumsq_host: Optional[torch.Tensor] = None,
+                          path_offset: int = 0) -> torch.Tensor:
+        """darts_render_host_async: queued render and copy back into pinned
+        host buffers; the buffers are complete after Context.sync()."""
+        _check(self.ctx.h, self._lib.darts_render_host_async(self.ctx.h, C.byref(self.cs), C.byref(self.csp),
+                                                             _ptr(hist_host), _ptr(sumsq_host),
+                                                             int(path_offset)))
         return hist_host
 
 class Context:

@@ -30,6 +30,14 @@ struct darts_ctx {
   double* host_hist = nullptr; // device histogram for darts_render_host
   size_t host_hist_bytes = 0;
   unsigned int* status_host = nullptr;  // pinned copy of the scratch status words
+  // darts_render_host_async: two device histograms, a copy stream, and per
+  // buffer the events "rendered" (compute stream) and "copied" (copy stream)
+  double* async_hist[2] = {nullptr, nullptr};
+  size_t async_bytes[2] = {0, 0};
+  int async_slot = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_rendered[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
+  bool copied_pending[2] = {false, false};
   // direction-table cache
   float* table = nullptr;
   size_t table_bytes = 0;
@@ -631,6 +639,15 @@ darts_status darts_destroy(darts_ctx* ctx) {
   cudaFree(ctx->partials);
   cudaFree(ctx->table);
   cudaFree(ctx->host_hist);
+  if (ctx->copy_stream) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamDestroy(ctx->copy_stream);
+  }
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(ctx->async_hist[i]);
+    if (ctx->ev_rendered[i]) cudaEventDestroy(ctx->ev_rendered[i]);
+    if (ctx->ev_copied[i]) cudaEventDestroy(ctx->ev_copied[i]);
+  }
   cudaFree(ctx->batch_tables);
   cudaFree(ctx->wcdf);
   cudaFree(ctx->wbin);
@@ -659,6 +676,7 @@ darts_status darts_last_error(const darts_ctx* ctx, char* buf, size_t n) {
 darts_status darts_sync(darts_ctx* ctx) {
   if (!ctx) return DARTS_ERR_INVALID_ARG;
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (ctx->copy_stream) CK(cudaStreamSynchronize(ctx->copy_stream), "copy stream synchronize");
   // the status words travel behind the stream's work into pinned memory: one
   // synchronisation, no separate blocking copy
   CK(cudaMemcpyAsync(ctx->status_host, ctx->scratch + 1, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost,
@@ -823,6 +841,46 @@ darts_status darts_render_host(darts_ctx* ctx, const darts_scene* scene,
   if (sumsq_host)
     CK(cudaMemcpyAsync(sumsq_host, ctx->host_hist + nh, hb, cudaMemcpyDeviceToHost, ctx->stream), "histogram copy");
   return darts_sync(ctx);
+}
+
+darts_status darts_render_host_async(darts_ctx* ctx, const darts_scene* scene,
+                                     const darts_sampling* sampling, double* hist_host,
+                                     double* sumsq_host, uint64_t path_offset) {
+  if (!ctx) return DARTS_ERR_INVALID_ARG;
+  if (!hist_host) return fail(ctx, DARTS_ERR_INVALID_ARG, "hist_host must not be NULL");
+  darts_status s = validate(ctx, scene, sampling);
+  if (s != DARTS_OK) return s;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (!ctx->copy_stream) {
+    CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "copy stream");
+    for (int i = 0; i < 2; ++i) {
+      CK(cudaEventCreateWithFlags(&ctx->ev_rendered[i], cudaEventDisableTiming), "event");
+      CK(cudaEventCreateWithFlags(&ctx->ev_copied[i], cudaEventDisableTiming), "event");
+    }
+  }
+  const int k = ctx->async_slot;
+  const size_t nh = elements_of(scene) * (size_t)scene->gate.n_bins;
+  const size_t hb = nh * sizeof(double);
+  if (2 * hb > ctx->async_bytes[k]) {  // growing: nothing may still read the old buffer
+    CK(cudaStreamSynchronize(ctx->copy_stream), "copy stream synchronize");
+    CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+    ctx->copied_pending[k] = false;
+    CK(ensure((void**)&ctx->async_hist[k], &ctx->async_bytes[k], 2 * hb), "histogram allocation");
+  }
+  // the copy that last read this buffer (two calls ago) precedes the render into it
+  if (ctx->copied_pending[k]) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[k], 0), "stream wait");
+  double* dev = ctx->async_hist[k];
+  s = darts_render(ctx, scene, sampling, dev, sumsq_host ? dev + nh : nullptr, path_offset, nullptr);
+  if (s != DARTS_OK) return s;
+  CK(cudaEventRecord(ctx->ev_rendered[k], ctx->stream), "event record");
+  CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_rendered[k], 0), "stream wait");
+  CK(cudaMemcpyAsync(hist_host, dev, hb, cudaMemcpyDeviceToHost, ctx->copy_stream), "histogram copy");
+  if (sumsq_host)
+    CK(cudaMemcpyAsync(sumsq_host, dev + nh, hb, cudaMemcpyDeviceToHost, ctx->copy_stream), "histogram copy");
+  CK(cudaEventRecord(ctx->ev_copied[k], ctx->copy_stream), "event record");
+  ctx->copied_pending[k] = true;
+  ctx->async_slot = k ^ 1;
+  return DARTS_OK;
 }
 
 darts_status darts_get_stats(darts_ctx* ctx, darts_stats* out) {

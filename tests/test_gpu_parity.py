@@ -312,6 +312,33 @@ def test_render_host_matches_device(ctx):
     assert float(hh2.sum()) > 0.0
 
 
+def test_render_host_async_pipeline(ctx):
+    """Queued host renders: four frames in a row into four pinned buffers
+    (the copy of each overlapping the next render, two device histograms
+    alternating), then a larger scene (the device buffers grow); after
+    sync every buffer equals the device render of its path range."""
+    sc, sp = S.box_camera_workload(seed=2)
+    sp.paths_per_element = 4
+    n = S.total_paths(sc, sp)
+    shape = S.histogram_shape(sc)
+    pr = ctx.prepare(sc, sp)
+    hs = [torch.zeros(shape, dtype=torch.float64).pin_memory() for _ in range(4)]
+    qs = [torch.zeros(shape, dtype=torch.float64).pin_memory() for _ in range(4)]
+    for i in range(4):
+        pr.render_host_async(hs[i], qs[i] if i % 2 else None, path_offset=i * n)
+    big = S.box_camera_scene(seed=2, width=96, height=64)
+    hb = torch.zeros(S.histogram_shape(big), dtype=torch.float64).pin_memory()
+    ctx.prepare(big, sp).render_host_async(hb)
+    ctx.sync()
+    for i in range(4):
+        ref, refq = ctx.render(sc, sp, sumsq=True, path_offset=i * n)
+        torch.testing.assert_close(hs[i], ref.cpu(), rtol=1e-6, atol=1e-15)
+        if i % 2:
+            torch.testing.assert_close(qs[i], refq.cpu(), rtol=1e-6, atol=1e-15)
+    torch.testing.assert_close(hb, ctx.render(big, sp).cpu(), rtol=1e-6, atol=1e-15)
+    assert float(hs[3].sum()) > 0.0
+
+
 def test_other_ris_m_and_table_dims(ctx):
     sc, _ = S.cube_workload()
     sp = S.Sampling(seed=8, paths_per_element=1 << 12, ris_m=5, table_n_rho=7, table_n_s=5,
