@@ -377,6 +377,30 @@ def test_invalid_arguments_are_rejected(ctx):
     ctx.sync()
 
 
+def test_non_finite_contributions_are_reported(ctx):
+    """Failure detection without a fault: an emitter energy beyond FP32
+    range makes every contribution infinite.  The kernels drop them, set the
+    device status word, and darts_sync reports DARTS_ERR_NUMERIC once; the
+    next render is clean.  Point sensor (specialised kernel) and camera
+    (general kernel)."""
+    import copy
+    from paper_2402_03106_gb300 import capi
+    cube, sp = S.cube_workload(paths=1 << 12, seed=1)
+    cam = S.box_camera_scene(seed=0, width=8, height=8, n_bins=64)
+    for sc, spp in ((cube, sp.paths_per_element), (cam, 8)):
+        hot = copy.deepcopy(sc)
+        hot.emitters[0].energy = 1e40  # finite in FP64, infinite in FP32
+        sp2 = S.Sampling(seed=3, paths_per_element=spp, max_bounces=10)
+        h = ctx.render(hot, sp2)
+        with pytest.raises(capi.DartsError) as ei:
+            ctx.sync()
+        assert ei.value.status == 4
+        assert torch.isfinite(h).all()
+        h = ctx.render(sc, sp2)
+        ctx.sync()
+        assert torch.isfinite(h).all() and float(h.sum()) > 0.0
+
+
 # ---------------------------------------------------------------------------
 # Physics on the GPU (statistical)
 # ---------------------------------------------------------------------------
