@@ -69,3 +69,18 @@ class PipelinedCombine:
             last.div_(self.world_size)
         self.prev = None
         return last
+
+
+def sharded_gradient(render_fn, adjoint_fn, loss_grad_fn, world_size: int, group=None):
+    """One gradient evaluation of a histogram loss across ranks.
+
+    Each rank renders its path-id shard (`render_fn() -> h_r`) and the
+    estimates are averaged (the first exchange: the histogram, since dL/dh
+    needs the whole image).  Every rank then forms the same loss weights
+    `w = loss_grad_fn(h)`, replays its own shard with an independent seed
+    (`adjoint_fn(w) -> g_r`, three values) and the gradients are averaged
+    (the second exchange: three numbers).  Returns (h, g).
+    """
+    h = combine(render_fn(), world_size, group)
+    g = adjoint_fn(loss_grad_fn(h))
+    return h, combine(g, world_size, group)

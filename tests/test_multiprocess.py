@@ -186,3 +186,60 @@ def test_pipelined_combine_averages_the_last_step():
     # while the last step rendered
     ref1, _, _ = O.render(sc, sp, O.ORC_DARTS, n_paths=world * n, offset=(steps - 2) * world * n, threads=4)
     np.testing.assert_allclose(prev, world * ref1, rtol=1e-12, atol=1e-300)
+
+
+def _gradient_worker(rank, world, port, n, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import sys
+        sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+        import oracle as O
+        from paper_2402_03106_gb300 import scenes as S, sharding
+        sc, sp, spa, target = _gradient_case(S)
+        off = sharding.path_offset(rank, n)
+        h, g = sharding.sharded_gradient(
+            lambda: torch.from_numpy(O.render(sc, sp, O.ORC_DARTS, n_paths=n, offset=off, threads=2)[0]),
+            lambda w: torch.from_numpy(O.adjoint(sc, spa, w.numpy(), n_paths=n, offset=off, threads=2)[0]),
+            lambda h: 2.0 * (h - torch.from_numpy(target)), world)
+        if rank == 0:
+            q.put((h.numpy().copy(), g.numpy().copy()))
+    finally:
+        dist.destroy_process_group()
+
+
+def _gradient_case(S):
+    sc, sp = S.cube_workload(paths=1 << 12, seed=23)
+    sc.gate.n_bins = 32
+    sp.max_bounces = 6
+    spa = S.Sampling(seed=24, paths_per_element=sp.paths_per_element, max_bounces=6)
+    target = np.linspace(0.0, 0.05, 32)
+    return sc, sp, spa, target
+
+
+def test_sharded_gradient_equals_single_process():
+    """Render shards, average the histogram, form the L2 loss weights,
+    replay each shard with the adjoint seed, average the gradients: equal to
+    one render and one adjoint pass over all the paths."""
+    import oracle as O
+    from paper_2402_03106_gb300 import scenes as S
+    world, n = 2, 4096
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_gradient_worker, args=(r, world, port, n, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    h, g = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=300)
+        assert p.exitcode == 0
+    sc, sp, spa, target = _gradient_case(S)
+    # one pass over all world x n paths: the per-element budget is world x n
+    sp.paths_per_element = spa.paths_per_element = world * n
+    href, _, _ = O.render(sc, sp, O.ORC_DARTS, threads=4)
+    np.testing.assert_allclose(h, href, rtol=1e-12, atol=1e-300)
+    gref, _ = O.adjoint(sc, spa, 2.0 * (href - target), threads=4)
+    np.testing.assert_allclose(g, gref, rtol=1e-10, atol=1e-300)
+    assert np.all(np.abs(gref) > 0)
