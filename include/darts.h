@@ -26,6 +26,9 @@
  *     unit emitted energy (not a rate: divide by the bin width for one).
  *   - Functions never throw; they return a darts_status.  The message of the
  *     last failure on a context is available from darts_last_error().
+ *   - A context is not thread-safe: calls on one context from several host
+ *     threads must be serialised by the caller.  Separate contexts (one per
+ *     thread or per device) are independent.
  */
 #ifndef DARTS_H
 #define DARTS_H
