@@ -421,6 +421,15 @@ class Context:
         darts_render_host(self.h, scene, sampling, hist_host, sumsq_host, path_offset)
         return hist_host
 
+    def render_host_async(self, scene, sampling, hist_host: torch.Tensor,
+                          sumsq_host: Optional[torch.Tensor] = None, path_offset: int = 0):
+        """Queued render into pinned host buffers (complete after sync())."""
+        cs, keep = to_c_scene(scene)
+        csp = to_c_sampling(sampling)
+        _check(self.h, load().darts_render_host_async(self.h, C.byref(cs), C.byref(csp), _ptr(hist_host),
+                                                      _ptr(sumsq_host), int(path_offset)))
+        return hist_host
+
     def build_table(self, scene, sampling) -> torch.Tensor:
         rows = sampling.table_n_rho * sampling.table_n_s
         stride = darts_table_row_stride(sampling.table_n_mu)

@@ -328,7 +328,7 @@ def test_render_host_async_pipeline(ctx):
         pr.render_host_async(hs[i], qs[i] if i % 2 else None, path_offset=i * n)
     big = S.box_camera_scene(seed=2, width=96, height=64)
     hb = torch.zeros(S.histogram_shape(big), dtype=torch.float64).pin_memory()
-    ctx.prepare(big, sp).render_host_async(hb)
+    ctx.render_host_async(big, sp, hb)
     ctx.sync()
     for i in range(4):
         ref, refq = ctx.render(sc, sp, sumsq=True, path_offset=i * n)
