@@ -55,6 +55,33 @@ SCENES = {
 }
 
 
+def maximum_scene():
+    """The largest scene the interface takes: 64 spheres and 8 emitters
+    (points and Lambertian quads, pulse starts 0 to 3, uneven energies)
+    around a camera inside the medium."""
+    sc = S.spheres_camera_scene(seed=1, width=16, height=16, n_spheres=64, n_bins=200)
+    sc.emitters = sc.emitters + [
+        S.Emitter((0.5, 3.6, 0.5), 0.4, 0.7), S.Emitter((3.5, 3.6, 0.5), 0.9, 1.3),
+        S.Emitter((0.5, 3.6, 3.5), 2.0, 0.5), S.Emitter((3.5, 3.6, 3.5), 3.0, 2.0),
+        S.Emitter((1.7, 3.95, 1.7), 0.2, 1.0, S.EMITTER_AREA, (0.3, 0.0, 0.0), (0.0, 0.0, 0.3)),
+        S.Emitter((2.5, 3.95, 2.5), 1.0, 0.8, S.EMITTER_AREA, (0.4, 0.0, 0.0), (0.0, 0.0, 0.2))]
+    return sc
+
+
+@pytest.mark.parametrize("method", [S.DARTS, S.PLAIN_UNIFORM_T])
+def test_maximum_scene_per_path_parity(ctx, method):
+    sc = maximum_scene()
+    assert len(sc.emitters) == 8 and len(sc.geometry.spheres) == 64
+    sp = S.Sampling(seed=9, paths_per_element=8, max_bounces=30, method=method)
+    n, first = 2048, 777
+    gpu = ctx.debug_paths(sc, sp, first, n)
+    ref = O.trace_paths(sc, sp, first, n, method=method)
+    sens = 5.0 * displaced_sensitivity(sc, sp, first, n, method, ref)
+    check_paths(gpu, ref, sp.max_bounces, extra_tol=sens)
+    assert np.count_nonzero(ref["contrib"]) > n // 20
+    assert np.mean(sens > 1e-3) < 0.02
+
+
 @pytest.mark.parametrize("name", sorted(SCENES))
 @pytest.mark.parametrize("method", [S.DARTS, S.PLAIN_UNIFORM_T, S.VANILLA_DIRECT, S.DARTS_FULL_GATE])
 def test_general_per_path_parity(ctx, name, method):
