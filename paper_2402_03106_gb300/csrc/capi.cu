@@ -150,12 +150,14 @@ bool general_scene(const darts_scene* sc) {
 darts_status validate(darts_ctx* ctx, const darts_scene* sc, const darts_sampling* sp) {
   if (!sc || !sp) return fail(ctx, DARTS_ERR_INVALID_ARG, "scene and sampling must not be NULL");
   const darts_medium& m = sc->medium;
-  if (!(m.sigma_s >= 0.0) || !(m.sigma_a >= 0.0) || !(m.sigma_s + m.sigma_a > 0.0))
-    return fail(ctx, DARTS_ERR_INVALID_ARG, "need sigma_s >= 0, sigma_a >= 0, sigma_t > 0");
+  if (!(m.sigma_s >= 0.0) || !(m.sigma_a >= 0.0) || !(m.sigma_s + m.sigma_a > 0.0) ||
+      !std::isfinite(m.sigma_s + m.sigma_a))
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "need finite sigma_s >= 0, sigma_a >= 0, sigma_t > 0");
   if (!(std::fabs(m.g) < 1.0)) return fail(ctx, DARTS_ERR_INVALID_ARG, "need |g| < 1");
   if (!(m.v > 0.0) || !std::isfinite(m.v)) return fail(ctx, DARTS_ERR_INVALID_ARG, "need v > 0");
   if (sc->gate.n_bins < 1) return fail(ctx, DARTS_ERR_INVALID_ARG, "need n_bins >= 1");
-  if (!(sc->gate.t_max > sc->gate.t_min)) return fail(ctx, DARTS_ERR_INVALID_ARG, "need t_max > t_min");
+  if (!(sc->gate.t_max > sc->gate.t_min) || !std::isfinite(sc->gate.t_max - sc->gate.t_min))
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "need finite t_min < t_max");
   if (sc->gate.weights) {
     double tot = 0.0;
     for (int b = 0; b < sc->gate.n_bins; ++b) {
@@ -167,7 +169,8 @@ darts_status validate(darts_ctx* ctx, const darts_scene* sc, const darts_samplin
     if (!(tot > 0.0)) return fail(ctx, DARTS_ERR_INVALID_ARG, "gate weights must have a positive sum");
   }
   for (int i = 0; i < 3; ++i)
-    if (!(sc->geom.hi[i] > sc->geom.lo[i])) return fail(ctx, DARTS_ERR_INVALID_ARG, "empty medium box");
+    if (!(sc->geom.hi[i] > sc->geom.lo[i]) || !std::isfinite(sc->geom.hi[i] - sc->geom.lo[i]))
+      return fail(ctx, DARTS_ERR_INVALID_ARG, "the medium box needs finite lo < hi");
   if (sc->n_emitters < 1 || !sc->emitters) return fail(ctx, DARTS_ERR_INVALID_ARG, "need an emitter");
   if (sc->n_emitters > kMaxEmitters)
     return fail(ctx, DARTS_ERR_UNSUPPORTED, "at most %d emitters", kMaxEmitters);
@@ -182,6 +185,9 @@ darts_status validate(darts_ctx* ctx, const darts_scene* sc, const darts_samplin
       if (!(e.pos[i] >= sc->geom.lo[i] && e.pos[i] <= sc->geom.hi[i]))
         return fail(ctx, DARTS_ERR_INVALID_ARG, "emitter %d outside the medium box", k);
     if (e.kind == DARTS_EMITTER_AREA) {
+      for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(e.u[i]) || !std::isfinite(e.v[i]))
+          return fail(ctx, DARTS_ERR_INVALID_ARG, "emitter %d: edge vectors must be finite", k);
       const double cx = e.u[1] * e.v[2] - e.u[2] * e.v[1], cy = e.u[2] * e.v[0] - e.u[0] * e.v[2],
                    cz = e.u[0] * e.v[1] - e.u[1] * e.v[0];
       if (!(cx * cx + cy * cy + cz * cz > 0.0)) return fail(ctx, DARTS_ERR_INVALID_ARG, "emitter %d: zero area", k);
@@ -210,9 +216,18 @@ darts_status validate(darts_ctx* ctx, const darts_scene* sc, const darts_samplin
   } else if (sen.kind == DARTS_SENSOR_PINHOLE) {
     if (sen.width < 1 || sen.height < 1 || !(sen.fov_deg > 0.0 && sen.fov_deg < 180.0))
       return fail(ctx, DARTS_ERR_INVALID_ARG, "camera needs width, height >= 1 and 0 < fov < 180");
-    double f2 = 0.0;
-    for (int i = 0; i < 3; ++i) f2 += (sen.look_at[i] - sen.pos[i]) * (sen.look_at[i] - sen.pos[i]);
+    double f[3], f2 = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      if (!std::isfinite(sen.pos[i]) || !std::isfinite(sen.look_at[i]) || !std::isfinite(sen.up[i]))
+        return fail(ctx, DARTS_ERR_INVALID_ARG, "camera position, look_at and up must be finite");
+      f[i] = sen.look_at[i] - sen.pos[i];
+      f2 += f[i] * f[i];
+    }
     if (!(f2 > 0.0)) return fail(ctx, DARTS_ERR_INVALID_ARG, "camera look_at equals its position");
+    const double rx = f[1] * sen.up[2] - f[2] * sen.up[1], ry = f[2] * sen.up[0] - f[0] * sen.up[2],
+                 rz = f[0] * sen.up[1] - f[1] * sen.up[0];
+    if (!(rx * rx + ry * ry + rz * rz > 1e-24 * f2))
+      return fail(ctx, DARTS_ERR_INVALID_ARG, "camera up must not be parallel to the view direction");
   } else {
     return fail(ctx, DARTS_ERR_INVALID_ARG, "unknown sensor kind %d", sen.kind);
   }
@@ -220,11 +235,13 @@ darts_status validate(darts_ctx* ctx, const darts_scene* sc, const darts_samplin
     return fail(ctx, DARTS_ERR_INVALID_ARG, "0..%d spheres with a host array", kMaxSpheres);
   for (int k = 0; k < sc->geom.n_spheres; ++k) {
     const double* q = sc->geom.spheres + 5 * k;
-    if (!(q[3] > 0.0) || !(q[4] >= 0.0 && q[4] <= 1.0))
-      return fail(ctx, DARTS_ERR_INVALID_ARG, "sphere %d needs radius > 0 and albedo in [0, 1]", k);
+    if (!(q[3] > 0.0) || !(q[4] >= 0.0 && q[4] <= 1.0) || !std::isfinite(q[0] + q[1] + q[2] + q[3]))
+      return fail(ctx, DARTS_ERR_INVALID_ARG, "sphere %d needs a finite centre, radius > 0 and albedo in [0, 1]", k);
   }
   if (sc->geom.walls < 0 || sc->geom.walls >= 64 || !(sc->geom.wall_albedo >= 0.0 && sc->geom.wall_albedo <= 1.0))
     return fail(ctx, DARTS_ERR_INVALID_ARG, "walls is a 6-bit face mask and wall_albedo in [0, 1]");
+  if (sp->paths_per_element > UINT64_MAX / elements_of(sc))
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "paths_per_element x sensor elements exceeds 2^64");
   if (sp->max_bounces < 1 || sp->max_bounces > 1024)
     return fail(ctx, DARTS_ERR_INVALID_ARG, "max_bounces must be in 1..1024");
   if (sp->ris_m < 1 || sp->ris_m > trace_max_m())

@@ -198,9 +198,25 @@ def test_invalid_general_scenes_are_rejected(ctx):
     bad.append(dataclasses.replace(sc, emitters=[S.Emitter((1.0, 1.0, 1.0))] * 9))
     bad.append(dataclasses.replace(sc, geometry=dataclasses.replace(sc.geometry, spheres=[(1, 1, 1, -0.1, 0.5)])))
     bad.append(dataclasses.replace(sc, geometry=dataclasses.replace(sc.geometry, wall_albedo=1.5)))
+    # non-finite or degenerate values that would only show up as NaN later
+    inf, nan = float("inf"), float("nan")
+    bad.append(dataclasses.replace(sc, medium=dataclasses.replace(sc.medium, sigma_s=inf)))
+    bad.append(dataclasses.replace(sc, gate=dataclasses.replace(sc.gate, t_max=inf)))
+    bad.append(dataclasses.replace(sc, geometry=dataclasses.replace(sc.geometry, hi=(2.0, inf, 2.0))))
+    bad.append(dataclasses.replace(sc, sensor=dataclasses.replace(sc.sensor, up=(0.0, 0.0, 1.0))))
+    bad.append(dataclasses.replace(sc, sensor=dataclasses.replace(sc.sensor, up=(0.0, nan, 0.0))))
+    bad.append(dataclasses.replace(sc, geometry=dataclasses.replace(sc.geometry, spheres=[(1, nan, 1, 0.1, 0.5)])))
+    bad.append(dataclasses.replace(sc, emitters=[S.Emitter((0.85, 2.0, 0.85), 0.0, 1.0, S.EMITTER_AREA,
+                                                           (0.3, 0.0, 0.0), (0.0, 0.0, nan))]))
     for b in bad:
-        with pytest.raises(capi.DartsError):
+        with pytest.raises(capi.DartsError) as ei:
             ctx.render(b, S.Sampling(paths_per_element=4))
+        assert ei.value.status in (1, 6)
+    # more paths than 64-bit ids can number
+    with pytest.raises(capi.DartsError) as ei:
+        ctx.render(sc, S.Sampling(paths_per_element=(1 << 62)))
+    assert ei.value.status == 1
+    ctx.sync()
 
 
 def test_camera_shards_continue_the_sample_index(ctx):
