@@ -2,6 +2,7 @@
 
 Test infrastructure: builds the checker, never the product.
 """
+import fcntl
 import os
 import subprocess
 import sys
@@ -20,11 +21,16 @@ def _stale() -> bool:
 
 
 def build(force: bool = False) -> str:
-    if force or _stale():
-        cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-pthread",
-               "-Wall", "-o", LIB + ".tmp"] + [os.path.join(HERE, s) for s in SOURCES] + ["-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(LIB + ".tmp", LIB)
+    if not (force or _stale()):
+        return LIB
+    # one builder at a time (ranks of a multi-process launch build together)
+    with open(os.path.join(HERE, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if force or _stale():
+            cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-pthread",
+                   "-Wall", "-o", LIB + ".tmp"] + [os.path.join(HERE, s) for s in SOURCES] + ["-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(LIB + ".tmp", LIB)
     return LIB
 
 

@@ -6,6 +6,7 @@ paper_2402_03106_gb300/libdarts.so next to this file.
 """
 from __future__ import annotations
 
+import fcntl
 import os
 import shutil
 import subprocess
@@ -55,6 +56,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not (force or _stale()):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    # one builder at a time (ranks of a multi-process launch build together)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not (force or _stale()):
+            return LIB
+        return _build_locked(verbose)
+
+
+def _build_locked(verbose: bool) -> str:
     cc = nvcc()
     flags = _flags(verbose)
 
