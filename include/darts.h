@@ -77,6 +77,11 @@ typedef enum {
 #define DARTS_FLAG_IID_CANDIDATES (1u << 4)
 #define DARTS_FLAG_EQUIANGULAR (1u << 5)
 #define DARTS_FLAG_RESERVOIR (1u << 6)
+/* darts_render adds its estimate into hist_dev (and sumsq_dev) instead of
+ * overwriting them: k renders of disjoint path ranges leave the sum of k
+ * estimates (divide by k for their average).  Device outputs of darts_render
+ * only; the host, batched, static and adjoint calls refuse it. */
+#define DARTS_FLAG_ACCUMULATE (1u << 7)
 
 typedef struct darts_ctx darts_ctx;
 
@@ -247,7 +252,8 @@ int32_t darts_table_row_stride(int32_t table_n_mu);
 /* Render sampling->paths_per_element paths per sensor element (N paths in
  * all, ids path_offset .. +N-1; the camera's pixel p owns ids
  * p * paths_per_element onwards) and write the histogram estimate
- * hist_dev[elements][n_bins] (double, overwritten):
+ * hist_dev[elements][n_bins] (double, overwritten; added to with
+ * DARTS_FLAG_ACCUMULATE):
  * DARTS dedicates each path to one bin (Sec. 6.2) and weights it by
  * n_bins / N; the baselines bin each contribution by its time and weight it
  * by 1 / N.  sumsq_dev (optional, [n_bins]) receives the sum over paths of

@@ -390,6 +390,7 @@ void make_trace_params(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
   P->uniform_sensor = (sp->flags & DARTS_FLAG_SENSOR_UNIFORM_ONLY) ? 1 : 0;
   P->no_eda = (sp->flags & DARTS_FLAG_NO_EDA) ? 1 : 0;
   P->no_da = (sp->flags & DARTS_FLAG_NO_DA_DISTANCE) ? 1 : 0;
+  P->accumulate = (sp->flags & DARTS_FLAG_ACCUMULATE) ? 1 : 0;
   P->ris_mode = ((sp->flags & DARTS_FLAG_IID_CANDIDATES) ? 1 : 0) | ((sp->flags & DARTS_FLAG_EQUIANGULAR) ? 2 : 0) |
                 ((sp->flags & DARTS_FLAG_RESERVOIR) ? 4 : 0);
   P->table = ctx->table;
@@ -577,7 +578,7 @@ darts_status run_trace(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
   CK(ensure((void**)&ctx->partials, &ctx->partials_bytes, pbytes), "partials allocation");
   P.partials = ctx->partials;
   if (!zeroed) {  // else the table launch just before did this
-    if (!tile) {  // contributions go straight into the (zeroed) outputs
+    if (!tile && !P.accumulate) {  // contributions go straight into the (zeroed) outputs
       const size_t ob = elements_of(sc) * (size_t)P.n_bins * sizeof(double);
       CK(cudaMemsetAsync(P.hist, 0, ob, ctx->stream), "memset");
       if (P.sumsq) CK(cudaMemsetAsync(P.sumsq, 0, ob, ctx->stream), "memset");
@@ -808,17 +809,18 @@ darts_status darts_render(darts_ctx* ctx, const darts_scene* scene, const darts_
     return fail(ctx, DARTS_ERR_INVALID_ARG, "probe needs stride >= 1 and output buffers");
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   const size_t hb = elements_of(scene) * (size_t)scene->gate.n_bins * sizeof(double);
+  const bool acc = (sampling->flags & DARTS_FLAG_ACCUMULATE) != 0;
   if (sampling->paths_per_element == 0) {
-    CK(cudaMemsetAsync(hist_dev, 0, hb, ctx->stream), "memset");
-    if (sumsq_dev) CK(cudaMemsetAsync(sumsq_dev, 0, hb, ctx->stream), "memset");
+    if (!acc) CK(cudaMemsetAsync(hist_dev, 0, hb, ctx->stream), "memset");
+    if (sumsq_dev && !acc) CK(cudaMemsetAsync(sumsq_dev, 0, hb, ctx->stream), "memset");
     CK(cudaMemsetAsync(ctx->scratch, 0, sizeof(unsigned long long), ctx->stream), "memset");
     CK(cudaMemsetAsync(ctx->scratch + 2, 0, kStatCount * sizeof(unsigned long long), ctx->stream), "memset");
     ctx->last_paths = 0;
     return DARTS_OK;
   }
-  ZeroSpec z;
-  z.a = hist_dev;
-  z.b = sumsq_dev;
+  ZeroSpec z;  // the outputs are zeroed unless the render adds into them
+  z.a = acc ? nullptr : hist_dev;
+  z.b = acc ? nullptr : sumsq_dev;
   z.n = elements_of(scene) * (unsigned long long)scene->gate.n_bins;
   if (uses_table(sampling->method)) {
     s = ensure_table(ctx, scene, sampling, &z);
@@ -847,6 +849,8 @@ darts_status darts_render_host(darts_ctx* ctx, const darts_scene* scene,
   if (!hist_host) return fail(ctx, DARTS_ERR_INVALID_ARG, "hist_host must not be NULL");
   darts_status s = validate(ctx, scene, sampling);
   if (s != DARTS_OK) return s;
+  if (sampling->flags & DARTS_FLAG_ACCUMULATE)
+    return fail(ctx, DARTS_ERR_UNSUPPORTED, "DARTS_FLAG_ACCUMULATE applies to darts_render's device outputs");
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   const size_t nh = elements_of(scene) * (size_t)scene->gate.n_bins;
   const size_t hb = nh * sizeof(double);
@@ -867,6 +871,8 @@ darts_status darts_render_host_async(darts_ctx* ctx, const darts_scene* scene,
   if (!hist_host) return fail(ctx, DARTS_ERR_INVALID_ARG, "hist_host must not be NULL");
   darts_status s = validate(ctx, scene, sampling);
   if (s != DARTS_OK) return s;
+  if (sampling->flags & DARTS_FLAG_ACCUMULATE)
+    return fail(ctx, DARTS_ERR_UNSUPPORTED, "DARTS_FLAG_ACCUMULATE applies to darts_render's device outputs");
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   if (!ctx->copy_stream) {
     CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "copy stream");
@@ -944,8 +950,8 @@ darts_status darts_render_batch(darts_ctx* ctx, int n, const darts_scene* scenes
     if (!hist_dev[i]) return fail(ctx, DARTS_ERR_INVALID_ARG, "hist_dev[%d] is NULL", i);
     if (scenes[i].gate.weights)
       return fail(ctx, DARTS_ERR_UNSUPPORTED, "a batch renders media without a temporal response");
-    if (samplings[i].flags & kRisVariantFlags)
-      return fail(ctx, DARTS_ERR_UNSUPPORTED, "a batch runs the default RIS");
+    if (samplings[i].flags & (kRisVariantFlags | DARTS_FLAG_ACCUMULATE))
+      return fail(ctx, DARTS_ERR_UNSUPPORTED, "a batch runs the default RIS and overwrites its outputs");
     const darts_sampling& si = samplings[i];
     if (general_scene(&scenes[i]))
       return fail(ctx, DARTS_ERR_UNSUPPORTED, "a batch renders point-emitter, point-sensor media without surfaces");
@@ -1098,8 +1104,8 @@ darts_status darts_adjoint(darts_ctx* ctx, const darts_scene* scene, const darts
   if (!dLdh_dev || !grad3_dev) return fail(ctx, DARTS_ERR_INVALID_ARG, "dLdh_dev and grad3_dev must not be NULL");
   if (sampling->method != DARTS_METHOD_DARTS)
     return fail(ctx, DARTS_ERR_UNSUPPORTED, "the adjoint is implemented for the DARTS method");
-  if (sampling->flags & kRisVariantFlags)
-    return fail(ctx, DARTS_ERR_UNSUPPORTED, "the adjoint runs the default RIS");
+  if (sampling->flags & (kRisVariantFlags | DARTS_FLAG_ACCUMULATE))
+    return fail(ctx, DARTS_ERR_UNSUPPORTED, "the adjoint runs the default RIS and overwrites grad3");
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   if (sampling->paths_per_element == 0) {
     CK(cudaMemsetAsync(grad3_dev, 0, 3 * sizeof(double), ctx->stream), "memset");
@@ -1242,6 +1248,7 @@ extern "C" darts_status darts_render_static(const darts_scene* scene, const dart
   if (s != DARTS_OK) return s;
   if (!hist_dev) return DARTS_ERR_INVALID_ARG;
   if (scene->gate.weights) return DARTS_ERR_UNSUPPORTED;  // no scratch for the weight tables
+  if (sampling->flags & DARTS_FLAG_ACCUMULATE) return DARTS_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return DARTS_ERR_CUDA;
   if (dev < 0 || dev >= kStaticMaxDevices) return DARTS_ERR_UNSUPPORTED;

@@ -86,6 +86,7 @@ struct TraceParams {
   int no_eda;                      // ablation: phase-function directions only
   int no_da;                       // ablation: truncated-exponential distances (RIS weights 1)
   int ris_mode;                    // bit 0: i.i.d. candidates, 1: equiangular candidates, 2: reservoir
+  int accumulate;                  // add the estimate into hist / sumsq instead of overwriting
   const float* table;              // [rows][row_stride]
   // sampling
   int K, M;

@@ -1720,8 +1720,8 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
         s += __ldcg(pg + b);
         q += __ldcg(pg + B + b);
       }
-      P.hist[b] = s;
-      if (P.sumsq) P.sumsq[b] = q;
+      P.hist[b] = P.accumulate ? P.hist[b] + s : s;
+      if (P.sumsq) P.sumsq[b] = P.accumulate ? P.sumsq[b] + q : q;
     }
   }
   if (threadIdx.x == 0) *P.ticket = 0u;

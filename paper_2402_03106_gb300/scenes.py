@@ -35,6 +35,7 @@ FLAG_NO_EDA = 1 << 3          # ablation: phase-function directions only (gamma 
 FLAG_IID_CANDIDATES = 1 << 4  # RIS candidates from independent uniforms (not the Sobol row)
 FLAG_EQUIANGULAR = 1 << 5     # RIS candidates from the equiangular density about the emitter
 FLAG_RESERVOIR = 1 << 6       # RIS selection by weighted reservoir sampling
+FLAG_ACCUMULATE = 1 << 7      # darts_render adds into its outputs instead of overwriting them
 
 Vec3 = Tuple[float, float, float]
 

@@ -339,6 +339,38 @@ def test_render_host_async_pipeline(ctx):
     assert float(hs[3].sum()) > 0.0
 
 
+@pytest.mark.parametrize("kind", ["point", "camera"])
+def test_accumulate_adds_into_the_outputs(ctx, kind):
+    """DARTS_FLAG_ACCUMULATE: a second render of the next path range adds its
+    estimate (and squares) into the first one's buffers -- the block-partial
+    reduction of a point sensor and the atomics of a camera alike -- and the
+    host-buffer, batched and adjoint calls refuse the flag."""
+    import copy
+    from paper_2402_03106_gb300 import capi
+    if kind == "point":
+        sc, sp = S.cube_workload(paths=1 << 14, seed=4)
+    else:
+        sc, sp = S.box_camera_workload(seed=4)
+        sp.paths_per_element = 2
+    n = S.total_paths(sc, sp)
+    a, qa = ctx.render(sc, sp, sumsq=True)
+    b, qb = ctx.render(sc, sp, sumsq=True, path_offset=n)
+    acc = copy.deepcopy(sp)
+    acc.flags |= S.FLAG_ACCUMULATE
+    h, q = a.clone(), qa.clone()
+    ctx.prepare(sc, acc).render(out=h, sumsq=q, path_offset=n)
+    ctx.sync()
+    torch.testing.assert_close(h, a + b, rtol=1e-9, atol=1e-300)
+    torch.testing.assert_close(q, qa + qb, rtol=1e-9, atol=1e-300)
+    assert float(b.abs().sum()) > 0.0
+    hh = torch.zeros(S.histogram_shape(sc), dtype=torch.float64).pin_memory()
+    for call in (lambda: ctx.render_host(sc, acc, hh),
+                 lambda: ctx.adjoint(sc, acc, torch.ones(h.numel(), dtype=torch.float64))):
+        with pytest.raises(capi.DartsError) as ei:
+            call()
+        assert ei.value.status == 6
+
+
 def test_other_ris_m_and_table_dims(ctx):
     sc, _ = S.cube_workload()
     sp = S.Sampling(seed=8, paths_per_element=1 << 12, ris_m=5, table_n_rho=7, table_n_s=5,
