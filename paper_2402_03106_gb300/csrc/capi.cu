@@ -81,6 +81,7 @@ darts_status fail(darts_ctx* c, darts_status s, const char* fmt, ...) {
 }
 
 darts_status cuda_fail(darts_ctx* c, cudaError_t e, const char* what) {
+  cudaGetLastError();  // reported here: a recoverable error must not resurface at a later launch
   if (e == cudaErrorMemoryAllocation) return fail(c, DARTS_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
   return fail(c, DARTS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
@@ -99,6 +100,7 @@ cudaError_t ensure(void** ptr, size_t* cap, size_t bytes) {
   *cap = 0;
   cudaError_t e = cudaMalloc(ptr, bytes);
   if (e == cudaSuccess) *cap = bytes;
+  else cudaGetLastError();  // a failed allocation must not surface later as a launch error
   return e;
 }
 
@@ -216,6 +218,8 @@ darts_status validate(darts_ctx* ctx, const darts_scene* sc, const darts_samplin
   } else if (sen.kind == DARTS_SENSOR_PINHOLE) {
     if (sen.width < 1 || sen.height < 1 || !(sen.fov_deg > 0.0 && sen.fov_deg < 180.0))
       return fail(ctx, DARTS_ERR_INVALID_ARG, "camera needs width, height >= 1 and 0 < fov < 180");
+    if ((uint64_t)sen.width * (uint64_t)sen.height > (1ull << 30))  // pixel indices stay 32-bit
+      return fail(ctx, DARTS_ERR_INVALID_ARG, "camera needs at most 2^30 pixels");
     double f[3], f2 = 0.0;
     for (int i = 0; i < 3; ++i) {
       if (!std::isfinite(sen.pos[i]) || !std::isfinite(sen.look_at[i]) || !std::isfinite(sen.up[i]))

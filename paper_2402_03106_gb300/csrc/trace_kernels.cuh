@@ -487,7 +487,7 @@ struct Stepper {
     p.elem = 0;
     if (P.camera) {  // sample s of pixel elem; ids past the last pixel wrap with s continuing
       const unsigned long long e = gid / P.spp;
-      const unsigned long long pixels = (unsigned long long)(P.width * P.height);
+      const unsigned long long pixels = (unsigned long long)P.width * (unsigned long long)P.height;
       const unsigned long long wrap = e / pixels;
       s = wrap * P.spp + (gid - e * P.spp);
       p.elem = (int)(e - wrap * pixels);

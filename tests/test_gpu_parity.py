@@ -371,6 +371,64 @@ def test_accumulate_adds_into_the_outputs(ctx, kind):
         assert ei.value.status == 6
 
 
+def test_progressive_render_resumes_from_a_checkpoint(ctx):
+    """Checkpoint / resume of a progressive render: Philox is keyed by the
+    global path id, so a render is the sum of renders of consecutive path
+    ranges.  Two ranges accumulate, the histogram and the next path offset
+    are saved to the host, a new context restores them and accumulates two
+    more; the result equals the uninterrupted run of four ranges in one
+    context (up to FP64 summation order)."""
+    from paper_2402_03106_gb300 import capi
+    sc, sp = S.box_camera_workload(seed=6)
+    sp.paths_per_element = 2
+    n = S.total_paths(sc, sp)
+    acc = S.Sampling(**{**sp.__dict__, "flags": sp.flags | S.FLAG_ACCUMULATE})
+    h = torch.zeros(S.histogram_shape(sc), dtype=torch.float64, device="cuda")
+    pr = ctx.prepare(sc, acc)
+    for k in range(2):
+        pr.render(out=h, path_offset=k * n)
+    ctx.sync()
+    saved, next_offset = h.cpu(), 2 * n  # the checkpoint
+    del h
+    ctx2 = capi.Context(0)
+    try:
+        h2 = saved.cuda()
+        pr2 = ctx2.prepare(sc, acc)
+        for k in range(2):
+            pr2.render(out=h2, path_offset=next_offset + k * n)
+        ctx2.sync()
+        ref = torch.zeros_like(h2)
+        pr3 = ctx2.prepare(sc, acc)
+        for k in range(4):
+            pr3.render(out=ref, path_offset=k * n)
+        ctx2.sync()
+        torch.testing.assert_close(h2, ref, rtol=1e-9, atol=1e-300)
+        assert float(ref.sum()) > 0.0
+    finally:
+        ctx2.close()
+
+
+def test_allocation_failure_is_reported(ctx):
+    """A host render whose histogram cannot be allocated on the device (a
+    2^15 x 2^15 camera x 4096 bins: 32 TB) returns DARTS_ERR_OOM before
+    anything is launched, and the context stays usable.  A camera beyond
+    2^30 pixels is refused outright."""
+    from paper_2402_03106_gb300 import capi
+    hh = torch.zeros(1, dtype=torch.float64)
+    sc = S.box_camera_scene(seed=0, width=1 << 15, height=1 << 15, n_bins=4096)
+    with pytest.raises(capi.DartsError) as ei:
+        capi.darts_render_host(ctx.h, sc, S.Sampling(paths_per_element=1), hh, None, 0)
+    assert ei.value.status == 3
+    sc = S.box_camera_scene(seed=0, width=1 << 16, height=1 << 15, n_bins=1)
+    with pytest.raises(capi.DartsError) as ei:
+        capi.darts_render_host(ctx.h, sc, S.Sampling(paths_per_element=1), hh, None, 0)
+    assert ei.value.status == 1
+    small, sp = S.cube_workload(paths=1 << 10, seed=1)
+    h = ctx.render(small, sp)
+    ctx.sync()
+    assert float(h.sum()) > 0.0
+
+
 def test_other_ris_m_and_table_dims(ctx):
     sc, _ = S.cube_workload()
     sp = S.Sampling(seed=8, paths_per_element=1 << 12, ris_m=5, table_n_rho=7, table_n_s=5,
