@@ -1,6 +1,7 @@
 // capi.cu -- host side of libdarts: contexts, validation, the table cache and
 // the C entry points declared in include/darts.h.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -69,6 +70,16 @@ struct darts_ctx {
 };
 
 namespace {
+
+// NVTX range over a library call (host side: it brackets the launches the
+// call enqueues; a profiler can select kernels by it).  Costs a pointer test
+// when no tool is attached.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 darts_status fail(darts_ctx* c, darts_status s, const char* fmt, ...) {
   if (c) {
@@ -317,6 +328,7 @@ struct ZeroSpec {
 
 darts_status ensure_table(darts_ctx* ctx, const darts_scene* sc, const darts_sampling* sp,
                           ZeroSpec* z = nullptr) {
+  const Range nvtx_range("darts:table");
   double key[9];
   table_key(sc, sp, key);
   const bool hit = ctx->table_valid && std::memcmp(key, ctx->table_key, sizeof(key)) == 0 &&
@@ -565,6 +577,7 @@ void choose_launch(const darts_ctx* ctx, const darts_sampling* sp, const TracePa
 
 darts_status run_trace(darts_ctx* ctx, const darts_scene* sc, const darts_sampling* sp,
                        TraceParams& P, bool debug, bool zeroed = false) {
+  const Range nvtx_range("darts:trace");
   {
     const darts_status sw = set_weights(ctx, sc, sp, P);
     if (sw != DARTS_OK) return sw;
@@ -805,6 +818,7 @@ darts_status darts_build_table(darts_ctx* ctx, const darts_scene* scene,
 darts_status darts_render(darts_ctx* ctx, const darts_scene* scene, const darts_sampling* sampling,
                           double* hist_dev, double* sumsq_dev, uint64_t path_offset,
                           const darts_probe* probe) {
+  const Range nvtx_range("darts_render");
   if (!ctx) return DARTS_ERR_INVALID_ARG;
   darts_status s = validate(ctx, scene, sampling);
   if (s != DARTS_OK) return s;
@@ -849,6 +863,7 @@ darts_status darts_render(darts_ctx* ctx, const darts_scene* scene, const darts_
 darts_status darts_render_host(darts_ctx* ctx, const darts_scene* scene,
                                const darts_sampling* sampling, double* hist_host,
                                double* sumsq_host, uint64_t path_offset) {
+  const Range nvtx_range("darts_render_host");
   if (!ctx) return DARTS_ERR_INVALID_ARG;
   if (!hist_host) return fail(ctx, DARTS_ERR_INVALID_ARG, "hist_host must not be NULL");
   darts_status s = validate(ctx, scene, sampling);
@@ -871,6 +886,7 @@ darts_status darts_render_host(darts_ctx* ctx, const darts_scene* scene,
 darts_status darts_render_host_async(darts_ctx* ctx, const darts_scene* scene,
                                      const darts_sampling* sampling, double* hist_host,
                                      double* sumsq_host, uint64_t path_offset) {
+  const Range nvtx_range("darts_render_host_async");
   if (!ctx) return DARTS_ERR_INVALID_ARG;
   if (!hist_host) return fail(ctx, DARTS_ERR_INVALID_ARG, "hist_host must not be NULL");
   darts_status s = validate(ctx, scene, sampling);
@@ -943,6 +959,7 @@ static uint64_t fnv1a(const void* data, size_t n, uint64_t h) {
 darts_status darts_render_batch(darts_ctx* ctx, int n, const darts_scene* scenes,
                                 const darts_sampling* samplings, double* const* hist_dev,
                                 uint32_t flags) {
+  const Range nvtx_range("darts_render_batch");
   if (!ctx) return DARTS_ERR_INVALID_ARG;
   if (n < 1 || !scenes || !samplings || !hist_dev)
     return fail(ctx, DARTS_ERR_INVALID_ARG, "need n >= 1 media, scenes, samplings and outputs");
@@ -1102,6 +1119,7 @@ darts_status darts_render_batch(darts_ctx* ctx, int n, const darts_scene* scenes
 darts_status darts_adjoint(darts_ctx* ctx, const darts_scene* scene, const darts_sampling* sampling,
                            const double* dLdh_dev, double* grad3_dev, double* grad3_sq_dev,
                            uint64_t path_offset) {
+  const Range nvtx_range("darts_adjoint");
   if (!ctx) return DARTS_ERR_INVALID_ARG;
   darts_status s = validate(ctx, scene, sampling);
   if (s != DARTS_OK) return s;
