@@ -47,7 +47,9 @@ typedef enum {
   DARTS_ERR_OOM = 3,         /* device memory could not be allocated                     */
   DARTS_ERR_NUMERIC = 4,     /* a kernel produced a non-finite contribution              */
   DARTS_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired                       */
-  DARTS_ERR_UNSUPPORTED = 6  /* a feature this build does not implement                  */
+  DARTS_ERR_UNSUPPORTED = 6, /* a feature this build does not implement                  */
+  DARTS_ERR_BOUNDS = 7       /* an index left its range on the device (checked build only,
+                                libdarts_checked.so; the access was skipped)              */
 } darts_status;
 
 typedef enum {

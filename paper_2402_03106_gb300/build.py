@@ -2,7 +2,8 @@
 
 Each translation unit under csrc/ is compiled in parallel into
 paper_2402_03106_gb300/_build/, then linked into
-paper_2402_03106_gb300/libdarts.so next to this file.
+paper_2402_03106_gb300/libdarts.so next to this file.  The checked variant
+(libdarts_checked.so, objects in _build_checked/) is built beside it.
 """
 from __future__ import annotations
 
@@ -43,51 +44,67 @@ def _flags(verbose: bool) -> list:
     return f
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+# Variants: (library, object directory, extra nvcc flags).  The checked
+# library tests every output, tile and table index on the device
+# (-DDARTS_CHECKS); it shares all sources with the production one.
+CHECKED_LIB = os.path.join(HERE, "libdarts_checked.so")
+VARIANTS = [(LIB, BUILD, []), (CHECKED_LIB, os.path.join(HERE, "_build_checked"), ["-DDARTS_CHECKS"])]
+
+
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [
         os.path.join(ROOT, "include", "darts.h"), os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not (force or _stale()):
+def build(force: bool = False, verbose: bool = False, checked: bool = True) -> str:
+    """Build libdarts.so (and libdarts_checked.so) when a source is newer;
+    returns the production library's path."""
+    variants = VARIANTS if checked else VARIANTS[:1]
+    if not force and not any(_stale(lib) for lib, _, _ in variants):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     # one builder at a time (ranks of a multi-process launch build together)
     with open(os.path.join(BUILD, ".lock"), "w") as lock:
         fcntl.flock(lock, fcntl.LOCK_EX)
-        if not (force or _stale()):
-            return LIB
-        return _build_locked(verbose)
+        todo = [v for v in variants if force or _stale(v[0])]
+        if todo:
+            _build_locked(todo, verbose)
+    return LIB
 
 
-def _build_locked(verbose: bool) -> str:
+def _build_locked(variants, verbose: bool) -> None:
     cc = nvcc()
     flags = _flags(verbose)
 
-    def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+    def compile_one(job) -> str:
+        src, out_dir, defs = job
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
         extra = APPROX_FLAGS if src in APPROX_SOURCES else []
-        cmd = [cc] + flags + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc] + flags + extra + defs + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
+            raise RuntimeError(f"nvcc failed for {src} {' '.join(defs)}:\n{r.stderr}")
         if verbose:
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp"
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    jobs = []
+    for _, out_dir, defs in variants:
+        os.makedirs(out_dir, exist_ok=True)
+        jobs += [(src, out_dir, defs) for src in SOURCES]
+    with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    for k, (lib, _, _) in enumerate(variants):
+        tmp = lib + ".tmp"
+        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs[k * len(SOURCES):(k + 1) * len(SOURCES)] + ["-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr}")
+        os.replace(tmp, lib)
 
 
 if __name__ == "__main__":

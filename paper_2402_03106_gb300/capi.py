@@ -23,10 +23,15 @@ from . import scenes as S
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdarts.so")
+# the same library with every output, tile and table index checked on the
+# device (DARTS_ERR_BOUNDS instead of an out-of-range access); load it with
+# load(CHECKED_LIB_PATH) before the first context
+CHECKED_LIB_PATH = os.path.join(HERE, "libdarts_checked.so")
 
 DARTS_OK = 0
 STATUS_NAMES = {0: "DARTS_OK", 1: "DARTS_ERR_INVALID_ARG", 2: "DARTS_ERR_CUDA", 3: "DARTS_ERR_OOM",
-                4: "DARTS_ERR_NUMERIC", 5: "DARTS_ERR_TIMEOUT", 6: "DARTS_ERR_UNSUPPORTED"}
+                4: "DARTS_ERR_NUMERIC", 5: "DARTS_ERR_TIMEOUT", 6: "DARTS_ERR_UNSUPPORTED",
+                7: "DARTS_ERR_BOUNDS"}
 
 EXPORTED = ("darts_create", "darts_destroy", "darts_set_stream", "darts_status_string",
             "darts_last_error", "darts_sync", "darts_build_table", "darts_table_row_stride",

@@ -627,6 +627,7 @@ const char* darts_status_string(darts_status s) {
     case DARTS_ERR_NUMERIC: return "non-finite value produced on the device";
     case DARTS_ERR_TIMEOUT: return "bounded device wait expired";
     case DARTS_ERR_UNSUPPORTED: return "unsupported by this build";
+    case DARTS_ERR_BOUNDS: return "device index out of range (checked build)";
   }
   return "unknown status";
 }
@@ -720,6 +721,7 @@ darts_status darts_sync(darts_ctx* ctx) {
   const unsigned int st[2] = {ctx->status_host[0], ctx->status_host[1]};
   if (st[1]) {
     CK(cudaMemset(reinterpret_cast<unsigned int*>(ctx->scratch + 1) + 1, 0, sizeof(unsigned int)), "status clear");
+    if (st[1] & 4u) return fail(ctx, DARTS_ERR_BOUNDS, "a device index left its range (access skipped)");
     if (st[1] & 2u) return fail(ctx, DARTS_ERR_TIMEOUT, "a bounded device wait expired");
     return fail(ctx, DARTS_ERR_NUMERIC, "a kernel produced a non-finite contribution");
   }

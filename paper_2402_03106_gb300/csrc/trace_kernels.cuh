@@ -96,6 +96,21 @@ struct Path {
 // shared memory.
 __shared__ unsigned long long s_rare[2];
 
+// Checked builds (-DDARTS_CHECKS, libdarts_checked.so): every index into an
+// output, a tile or the table is tested; one out of range sets status bit 2
+// (reported as DARTS_ERR_BOUNDS by darts_sync) and the access is skipped.
+// The production build compiles the tests away.
+#ifdef DARTS_CHECKS
+__device__ __forceinline__ bool index_ok(const TraceParams& P, long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(P.status, 4u);
+  return false;
+}
+#define DARTS_INDEX_OK(P, i, n) index_ok((P), (long long)(i), (long long)(n))
+#else
+#define DARTS_INDEX_OK(P, i, n) true
+#endif
+
 struct Counters {
   unsigned bits;
   __device__ __forceinline__ void add(int slot) { bits |= 1u << slot; }
@@ -664,7 +679,8 @@ struct Stepper {
       int i_rho = min(max((int)(rho * (float)P.n_rho), 0), P.n_rho - 1);
       int i_s = (int)floorf((__log2f(SM * P.inv_smax) + 8.0f) * P.n_s_over_8);
       i_s = min(max(i_s, 0), P.n_s - 1);
-      const float* row = tab + (i_rho * P.n_s + i_s) * P.row_stride;
+      const int row_i = i_rho * P.n_s + i_s;
+      const float* row = tab + (DARTS_INDEX_OK(P, row_i, P.rows) ? row_i : 0) * P.row_stride;
       float gamma = __fdividef(rho, rho + P.mis_alpha);
       const bool sensor = p.k == 0;
       if ((sensor && P.uniform_sensor) || P.no_eda) gamma = 0.0f;
@@ -999,7 +1015,8 @@ struct Stepper {
     i_rho = min(max(i_rho, 0), P.n_rho - 1);
     int i_s = (int)floorf((__log2f(SM * P.inv_smax) + 8.0f) * P.n_s_over_8);
     i_s = min(max(i_s, 0), P.n_s - 1);
-    const float* row = tab + (i_rho * P.n_s + i_s) * P.row_stride;
+    const int row_i = i_rho * P.n_s + i_s;
+    const float* row = tab + (DARTS_INDEX_OK(P, row_i, P.rows) ? row_i : 0) * P.row_stride;
     float gamma = __fdividef(rho, rho + P.mis_alpha);
     const bool sensor = p.k == 0;
     if ((sensor && P.uniform_sensor) || P.no_eda) gamma = 0.0f;
@@ -1292,12 +1309,13 @@ __device__ __forceinline__ void warp_commit(bool has, int bin, float val, float*
                                             float* wsq, bool tile, const TraceParams& P,
                                             bool do_sq) {
   if (!tile) {  // outputs zeroed before the launch
-    if (has) {
+    if (has && DARTS_INDEX_OK(P, bin, (P.camera ? (long long)P.width * P.height : 1ll) * P.n_bins)) {
       atomicAdd(&P.hist[bin], (double)val);
       if (do_sq) atomicAdd(&P.sumsq[bin], (double)val * (double)val);
     }
     return;
   }
+  if (has && !DARTS_INDEX_OK(P, bin, P.n_bins)) has = false;
   unsigned pending = __ballot_sync(kFull, has);
   const int lane = threadIdx.x & 31;
   while (pending) {
@@ -1561,7 +1579,8 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
     }
     if (ADJ) {
       if (alive && fin) {
-        const float wgt = (float)P.dLdh[p.bin] * path_weight<GEN>(P, p);
+        const float wgt = DARTS_INDEX_OK(P, p.bin, (P.camera ? (long long)P.width * P.height : 1ll) * P.n_bins)
+                              ? (float)P.dLdh[p.bin] * path_weight<GEN>(P, p) : 0.0f;
         const float gv[3] = {wgt * p.a0, wgt * p.a1, wgt * p.a2};
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
