@@ -815,6 +815,12 @@ def main():
     t16, _, _ = time_steps(ctx, torch, lambda: ctx.render(sc16, sp16), 20, flush, kernel_timing=False)
     extra["cube_as_configured_2e16"] = {"paths": 1 << 16, "ms_per_render": statistics.median(t16),
                                         "paths_per_s": (1 << 16) / (statistics.median(t16) * 1e-3)}
+    # the direction table alone (darts_build_table: one launch, no outputs to zero)
+    cdf = ctx.build_table(sc, sp)
+    tt, _, _ = time_steps(ctx, torch, lambda: ctx.build_table(sc, sp), 20, flush, kernel_timing=False)
+    extra["table_build"] = {"workload": "direction table of the benchmark medium, %dx%dx%d" %
+                                        (sp.table_n_rho, sp.table_n_s, sp.table_n_mu),
+                            "ms": statistics.median(tt), "bytes": cdf.numel() * 4}
     ctx.set_launch(0)
 
     if not args.no_mse:
