@@ -322,9 +322,10 @@ darts_status darts_get_stats(darts_ctx* ctx, darts_stats* out);
 
 /* Kernel timing: when enabled, every darts_render records a pair of CUDA
  * events on the context's stream immediately around the path kernel launch
- * (the direction-table kernel and the small scratch resets are outside).
+ * (the direction-table kernel and the small scratch resets are outside),
+ * and every darts_build_table around its table kernel.
  * darts_last_kernel_ms() synchronises on the stop event and returns the
- * elapsed time of the most recent path kernel in milliseconds. */
+ * elapsed time of the most recent timed kernel in milliseconds. */
 darts_status darts_set_kernel_timing(darts_ctx* ctx, int enable);
 darts_status darts_last_kernel_ms(darts_ctx* ctx, float* ms);
 

@@ -435,10 +435,10 @@ class Context:
                                                       _ptr(sumsq_host), int(path_offset)))
         return hist_host
 
-    def build_table(self, scene, sampling) -> torch.Tensor:
+    def build_table(self, scene, sampling, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         rows = sampling.table_n_rho * sampling.table_n_s
         stride = darts_table_row_stride(sampling.table_n_mu)
-        cdf = torch.empty(rows, stride, dtype=torch.float32, device=self._dev())
+        cdf = out if out is not None else torch.empty(rows, stride, dtype=torch.float32, device=self._dev())
         darts_build_table(self.h, scene, sampling, cdf)
         return cdf
 

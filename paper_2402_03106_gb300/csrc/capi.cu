@@ -292,17 +292,28 @@ void make_table_params(const darts_scene* sc, const darts_sampling* sp, TablePar
   tp->n_s = sp->table_n_s;
   tp->n_mu = sp->table_n_mu;
   tp->row_stride = row_stride_of(sp->table_n_mu);
-  double x[kMaxTabTNodes], w[kMaxTabTNodes];
-  gauss_legendre(kMaxTabMuNodes, x, w);
-  for (int i = 0; i < kMaxTabMuNodes; ++i) {
-    tp->mu_x[i] = (float)x[i];
-    tp->mu_w[i] = (float)w[i];
-  }
-  gauss_legendre(kMaxTabTNodes, x, w);
-  for (int i = 0; i < kMaxTabTNodes; ++i) {
-    tp->t_x[i] = (float)x[i];
-    tp->t_w[i] = (float)w[i];
-  }
+  // the rules depend only on the node counts: computed once per process
+  struct Rules {
+    float mu_x[kMaxTabMuNodes], mu_w[kMaxTabMuNodes], t_x[kMaxTabTNodes], t_w[kMaxTabTNodes];
+    Rules() {
+      double x[kMaxTabTNodes], w[kMaxTabTNodes];
+      gauss_legendre(kMaxTabMuNodes, x, w);
+      for (int i = 0; i < kMaxTabMuNodes; ++i) {
+        mu_x[i] = (float)x[i];
+        mu_w[i] = (float)w[i];
+      }
+      gauss_legendre(kMaxTabTNodes, x, w);
+      for (int i = 0; i < kMaxTabTNodes; ++i) {
+        t_x[i] = (float)x[i];
+        t_w[i] = (float)w[i];
+      }
+    }
+  };
+  static const Rules rules;
+  std::memcpy(tp->mu_x, rules.mu_x, sizeof(rules.mu_x));
+  std::memcpy(tp->mu_w, rules.mu_w, sizeof(rules.mu_w));
+  std::memcpy(tp->t_x, rules.t_x, sizeof(rules.t_x));
+  std::memcpy(tp->t_w, rules.t_w, sizeof(rules.t_w));
 }
 
 void table_key(const darts_scene* sc, const darts_sampling* sp, double key[9]) {
@@ -813,7 +824,12 @@ darts_status darts_build_table(darts_ctx* ctx, const darts_scene* scene,
   TableParams tp;
   make_table_params(scene, sampling, &tp);
   tp.cdf = cdf_dev;
+  if (ctx->timing) CK(cudaEventRecord(ctx->ev_start, ctx->stream), "event record");
   CK(launch_table(tp, ctx->stream), "table kernel launch");
+  if (ctx->timing) {  // darts_last_kernel_ms then reports the table kernel
+    CK(cudaEventRecord(ctx->ev_stop, ctx->stream), "event record");
+    ctx->timed = true;
+  }
   return DARTS_OK;
 }
 
