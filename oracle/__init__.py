@@ -1,7 +1,7 @@
 """FP64 CPU oracle for DARTS transient path tracing -- TEST INFRASTRUCTURE.
 
-Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` may import this package.  The CUDA library never reads, links
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg and
+reference arm of ``bench.py`` may import this package.  The CUDA library never reads, links
 or calls it, and it never imports the CUDA library: the two share no code.
 Inputs arrive as plain scene/sampling objects (attribute access only).
 
