@@ -38,8 +38,9 @@ def test_library_exports_every_declared_function(lib):
 
 def test_status_strings_and_row_stride(lib):
     from paper_2402_03106_gb300 import capi
-    for s in range(7):
-        assert lib.darts_status_string(s)
+    for s in range(8):
+        assert lib.darts_status_string(s) != b"unknown status"
+        assert s in capi.STATUS_NAMES
     assert lib.darts_status_string(99) == b"unknown status"
     assert capi.darts_table_row_stride(256) == 260
     assert capi.darts_table_row_stride(255) == 256
