@@ -781,3 +781,39 @@ def test_reservoir_selection_follows_the_weights():
         counts[r["sel"]] += 1
     chi2 = np.sum((counts - expect) ** 2 / np.maximum(expect, 1e-9))
     assert counts.sum() > 1000 and chi2 < 30.0, (counts, expect)
+
+
+# ---------------------------------------------------------------------------
+# The parameters the paper prints (tests/golden/paper_parameters.txt)
+# ---------------------------------------------------------------------------
+def _paper_parameters():
+    path = __file__.rsplit("/", 1)[0] + "/golden/paper_parameters.txt"
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                name, value = line.split()[:2]
+                vals[name] = float(value)
+    return vals
+
+
+def test_defaults_follow_the_paper_parameters():
+    """The default sampling parameters are the ones Sec. 4.3-4.4 print, the
+    RIS row table holds 32 rows of 8 stratified entries, and the oracle
+    traces paths as deep as the paper's experiments (Sec. 6)."""
+    P = _paper_parameters()
+    sp = S.Sampling()
+    assert sp.ris_m == P["ris_candidates"]
+    assert sp.table_n_mu == P["eda_cos_bins"]
+    assert sp.mis_alpha == P["mis_alpha"]
+    rows, cols = int(P["sobol_table_rows"]), int(P["sobol_table_cols"])
+    table = np.array([[O.radical_inverse2(cols * r + j) for j in range(cols)] for r in range(rows)])
+    # the rows together are the first rows * cols points of the base-2 sequence
+    assert sorted((table * rows * cols).round().astype(int).ravel()) == list(range(rows * cols))
+    deep = S.Sampling(seed=3, paths_per_element=256, max_bounces=int(P["max_bounces_scale"]))
+    sc = S.slab_scene(sigma_s=13.5, sigma_a=0.01, g=0.0, n_bins=16)
+    h, _, st = O.render(sc, deep)
+    assert np.isfinite(h).all() and float(h.sum()) > 0.0
+    nvert = O.trace_paths(sc, deep, 0, 256)["nvert"]
+    assert st["paths"] == 256 and nvert.max() > 50   # deeper than the default cap of 50
