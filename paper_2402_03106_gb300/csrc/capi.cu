@@ -731,7 +731,9 @@ darts_status darts_sync(darts_ctx* ctx) {
   CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");
   const unsigned int st[2] = {ctx->status_host[0], ctx->status_host[1]};
   if (st[1]) {
-    CK(cudaMemset(reinterpret_cast<unsigned int*>(ctx->scratch + 1) + 1, 0, sizeof(unsigned int)), "status clear");
+    // cleared on the context's stream, so the next launch on it sees the cleared word
+    CK(cudaMemsetAsync(reinterpret_cast<unsigned int*>(ctx->scratch + 1) + 1, 0, sizeof(unsigned int), ctx->stream),
+       "status clear");
     if (st[1] & 4u) return fail(ctx, DARTS_ERR_BOUNDS, "a device index left its range (access skipped)");
     if (st[1] & 2u) return fail(ctx, DARTS_ERR_TIMEOUT, "a bounded device wait expired");
     return fail(ctx, DARTS_ERR_NUMERIC, "a kernel produced a non-finite contribution");
@@ -742,8 +744,8 @@ darts_status darts_sync(darts_ctx* ctx) {
 darts_status darts_set_kernel_timing(darts_ctx* ctx, int enable) {
   if (!ctx) return DARTS_ERR_INVALID_ARG;
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-  if (enable && !ctx->ev_start) {
-    CK(cudaEventCreate(&ctx->ev_start), "event create");
+  if (enable && !ctx->ev_stop) {
+    if (!ctx->ev_start) CK(cudaEventCreate(&ctx->ev_start), "event create");
     CK(cudaEventCreate(&ctx->ev_stop), "event create");
   }
   ctx->timing = enable != 0;
@@ -912,12 +914,11 @@ darts_status darts_render_host_async(darts_ctx* ctx, const darts_scene* scene,
   if (sampling->flags & DARTS_FLAG_ACCUMULATE)
     return fail(ctx, DARTS_ERR_UNSUPPORTED, "DARTS_FLAG_ACCUMULATE applies to darts_render's device outputs");
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-  if (!ctx->copy_stream) {
-    CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "copy stream");
-    for (int i = 0; i < 2; ++i) {
-      CK(cudaEventCreateWithFlags(&ctx->ev_rendered[i], cudaEventDisableTiming), "event");
-      CK(cudaEventCreateWithFlags(&ctx->ev_copied[i], cudaEventDisableTiming), "event");
-    }
+  // created on first use; a creation that failed part way is completed by the next call
+  if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "copy stream");
+  for (int i = 0; i < 2; ++i) {
+    if (!ctx->ev_rendered[i]) CK(cudaEventCreateWithFlags(&ctx->ev_rendered[i], cudaEventDisableTiming), "event");
+    if (!ctx->ev_copied[i]) CK(cudaEventCreateWithFlags(&ctx->ev_copied[i], cudaEventDisableTiming), "event");
   }
   const int k = ctx->async_slot;
   const size_t nh = elements_of(scene) * (size_t)scene->gate.n_bins;
@@ -1032,10 +1033,10 @@ darts_status darts_render_batch(darts_ctx* ctx, int n, const darts_scene* scenes
   const size_t off_items = off_trp + ((size_t)n * sizeof(TraceParams) + 255) / 256 * 256;
   const size_t off_cnt = off_items + (n_items * sizeof(BatchItem) + 255) / 256 * 256;
   const size_t total = off_cnt + 256;
+  CK(ensure(&ctx->batch_buf, &ctx->batch_buf_bytes, total), "batch buffer allocation");
   unsigned char* host = static_cast<unsigned char*>(std::malloc(total));
   if (!host) return fail(ctx, DARTS_ERR_OOM, "host staging buffer");
   std::memset(host, 0, total);
-  CK(ensure(&ctx->batch_buf, &ctx->batch_buf_bytes, total), "batch buffer allocation");
   unsigned char* dev = static_cast<unsigned char*>(ctx->batch_buf);
   TableParams* tps = reinterpret_cast<TableParams*>(host + off_tp);
   TraceParams* trps = reinterpret_cast<TraceParams*>(host + off_trp);
