@@ -596,6 +596,51 @@ def spheres_frame(ctx, S, torch, flush, reps=3):
     return out
 
 
+def frames_in_flight(capi, S, torch, sc, sp, N, frames=600, reps=5):
+    """Throughput of a frame sequence (video rendering) with 1, 2 and 3
+    frames in flight: one context per CUDA stream, frame i on stream i mod n,
+    so that a frame's tail (a few long paths on a few SMs) overlaps the next
+    frame's busy phase.  No L2 flush between frames (the streams run
+    concurrently); the 1-stream row is measured the same way for the ratio."""
+    rows = {}
+    for n in (1, 2, 3):
+        streams = [torch.cuda.Stream() for _ in range(n)]
+        ctxs = [capi.Context(torch.cuda.current_device(), st) for st in streams]
+        preps = [c.prepare(sc, sp) for c in ctxs]
+        outs = [torch.zeros(S.histogram_shape(sc), dtype=torch.float64, device="cuda") for _ in range(n)]
+
+        def run(k):
+            for i in range(k):
+                preps[i % n].render(out=outs[i % n], path_offset=i * N)
+
+        run(30)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for st in streams:
+                st.wait_event(e0)
+            run(frames)
+            for st in streams:
+                ev = torch.cuda.Event()
+                ev.record(st)
+                torch.cuda.current_stream().wait_event(ev)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / frames)
+        for c in ctxs:
+            c.sync()
+            c.close()
+        ms = statistics.median(ts)
+        rows[str(n)] = {"ms_per_frame": ms, "paths_per_s": N / (ms * 1e-3)}
+    for r in rows.values():
+        r["vs_one_stream"] = rows["1"]["ms_per_frame"] / r["ms_per_frame"]
+    return {"workload": "the timed camera frame", "frames": frames, "streams": rows,
+            "note": "throughput, not the latency of a frame; median of %d repetitions" % reps}
+
+
 def differentiable_step(ctx, S, torch, flush, reps=10):
     """The differentiable configuration: the unit-cube medium seen by a 32x32
     camera, 256 bins, 2^20 paths (1024 per pixel); L2 loss against a target
@@ -839,6 +884,7 @@ def main():
         extra["mse_time_cube"] = mse_time(ctx, S, torch)
     extra["batched"] = batched_compare(ctx, S, torch)
     extra["differentiable_32x32"] = differentiable_step(ctx, S, torch, flush)
+    extra["frames_in_flight"] = frames_in_flight(capi, S, torch, sc, sp, N)
     cpu = cpu_baseline(args.workload) if ws == 1 else None
 
     line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws, "steps": K,
