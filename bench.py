@@ -608,6 +608,7 @@ def frames_in_flight(capi, S, torch, sc, sp, N, frames=600, reps=5):
         ctxs = [capi.Context(torch.cuda.current_device(), st) for st in streams]
         preps = [c.prepare(sc, sp) for c in ctxs]
         outs = [torch.zeros(S.histogram_shape(sc), dtype=torch.float64, device="cuda") for _ in range(n)]
+        torch.cuda.synchronize()  # allocated on the current stream, rendered on the others
 
         def run(k):
             for i in range(k):
