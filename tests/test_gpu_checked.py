@@ -37,6 +37,15 @@ full = S.Sampling(seed=2, paths_per_element=4, method=S.DARTS_FULL_GATE)
 out["full_gate"] = ctx.render(cam, full).cpu().numpy()
 w = torch.ones(out["camera"].size, dtype=torch.float64)
 out["adjoint"] = ctx.adjoint(cam, spc, w).cpu().numpy()
+sv, spv = S.cube_workload(paths=1 << 14, seed=2)                 # RIS variants (trace_var.cu)
+for k, fl in enumerate((S.FLAG_IID_CANDIDATES, S.FLAG_EQUIANGULAR, S.FLAG_RESERVOIR, S.FLAG_NO_EDA)):
+    spv.flags = fl
+    out["variant%d" % k] = ctx.render(sv, spv).cpu().numpy()
+sw, spw = S.cube_workload(paths=1 << 14, seed=2)                 # temporal response W
+sw.gate.weights = [0.0 if 40 <= b < 200 else 1.0 + (b % 7) for b in range(sw.gate.n_bins)]
+for m in (S.DARTS, S.PLAIN_UNIFORM_T):
+    spw.method = m
+    out["weighted%d" % m] = ctx.render(sw, spw).cpu().numpy()
 media = S.batched_media(n_media=6, seed=2, log2_budget=(10.0, 12.0))
 outs = ctx.render_batch([m[0] for m in media], [m[1] for m in media])
 out["batch"] = torch.cat(outs).cpu().numpy()
