@@ -596,50 +596,40 @@ def spheres_frame(ctx, S, torch, flush, reps=3):
     return out
 
 
-def frames_in_flight(capi, S, torch, sc, sp, N, frames=600, reps=5):
-    """Throughput of a frame sequence (video rendering) with 1, 2 and 3
-    frames in flight: one context per CUDA stream, frame i on stream i mod n,
-    so that a frame's tail (a few long paths on a few SMs) overlaps the next
-    frame's busy phase.  No L2 flush between frames (the streams run
-    concurrently); the 1-stream row is measured the same way for the ratio."""
+def frames_in_flight(ctx, S, torch, sc, sp, N, frames=60, calls=10, reps=5):
+    """Throughput of a frame sequence (video rendering) through
+    darts_render_frames with 1, 2 and 3 frames in flight: frame i runs on
+    lane i mod n (a stream of its own), so that a frame's tail (a few long
+    paths on a few SMs) overlaps the next frame's start.  `calls` calls of
+    `frames` frames each, into `frames` distinct 16 MiB outputs; no L2 flush
+    between frames (the lanes run concurrently), the 1-lane row measured the
+    same way for the ratio."""
+    prep = ctx.prepare(sc, sp)
+    outs = [torch.empty(S.histogram_shape(sc), dtype=torch.float64, device="cuda") for _ in range(frames)]
     rows = {}
     for n in (1, 2, 3):
-        streams = [torch.cuda.Stream() for _ in range(n)]
-        ctxs = [capi.Context(torch.cuda.current_device(), st) for st in streams]
-        preps = [c.prepare(sc, sp) for c in ctxs]
-        outs = [torch.zeros(S.histogram_shape(sc), dtype=torch.float64, device="cuda") for _ in range(n)]
-        torch.cuda.synchronize()  # allocated on the current stream, rendered on the others
-
         def run(k):
-            for i in range(k):
-                preps[i % n].render(out=outs[i % n], path_offset=i * N)
+            for c in range(k):
+                prep.render_frames(outs, path_offset=c * frames * N, in_flight=n)
 
-        run(30)
+        run(2)
         torch.cuda.synchronize()
         ts = []
         for _ in range(reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
             e0.record()
-            for st in streams:
-                st.wait_event(e0)
-            run(frames)
-            for st in streams:
-                ev = torch.cuda.Event()
-                ev.record(st)
-                torch.cuda.current_stream().wait_event(ev)
+            run(calls)
             e1.record()
             e1.synchronize()
-            ts.append(e0.elapsed_time(e1) / frames)
-        for c in ctxs:
-            c.sync()
-            c.close()
+            ts.append(e0.elapsed_time(e1) / (frames * calls))
         ms = statistics.median(ts)
         rows[str(n)] = {"ms_per_frame": ms, "paths_per_s": N / (ms * 1e-3)}
+    ctx.sync()
+    del outs
     for r in rows.values():
-        r["vs_one_stream"] = rows["1"]["ms_per_frame"] / r["ms_per_frame"]
-    return {"workload": "the timed camera frame", "frames": frames, "streams": rows,
-            "note": "throughput, not the latency of a frame; median of %d repetitions" % reps}
+        r["vs_one_lane"] = rows["1"]["ms_per_frame"] / r["ms_per_frame"]
+    return {"workload": "the timed camera frame", "frames": frames * calls, "call": "darts_render_frames",
+            "lanes": rows, "note": "throughput, not the latency of a frame; median of %d repetitions" % reps}
 
 
 def differentiable_step(ctx, S, torch, flush, reps=10):
@@ -885,7 +875,7 @@ def main():
         extra["mse_time_cube"] = mse_time(ctx, S, torch)
     extra["batched"] = batched_compare(ctx, S, torch)
     extra["differentiable_32x32"] = differentiable_step(ctx, S, torch, flush)
-    extra["frames_in_flight"] = frames_in_flight(capi, S, torch, sc, sp, N)
+    extra["frames_in_flight"] = frames_in_flight(ctx, S, torch, sc, sp, N)
     cpu = cpu_baseline(args.workload) if ws == 1 else None
 
     line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws, "steps": K,

@@ -285,6 +285,28 @@ darts_status darts_render_host_async(darts_ctx* ctx, const darts_scene* scene,
                                      const darts_sampling* sampling, double* hist_host,
                                      double* sumsq_host, uint64_t path_offset);
 
+/* A sequence of n_frames frames of one scene (Eq. 4 per frame, as
+ * darts_render computes it), with up to `in_flight` frames running at once.
+ * Frame i traces the path ids path_offset + i*N .. path_offset + (i+1)*N - 1
+ * (N = paths_per_element x sensor elements) into hist_dev[i], and into
+ * sumsq_dev[i] when sumsq_dev is not NULL: exactly what darts_render with
+ * that path offset writes (up to FP64 summation order).  Frames go round
+ * robin to in_flight (1..4) lanes, each a stream, scratch and direction-table
+ * cache of its own that the context creates on first use and keeps.  A
+ * frame's tail (a few long paths on a few SMs) then overlaps the next
+ * frame's start.  Ordering: the frames start after the work enqueued on the
+ * context's stream before the call, and work enqueued on it afterwards
+ * waits for all of them.  The outputs must be distinct, non-overlapping
+ * device buffers of elements x n_bins doubles (overwritten;
+ * DARTS_FLAG_ACCUMULATE is refused).  darts_sync also reports the lanes'
+ * device status; darts_get_stats and the kernel timing do not cover the
+ * frames of this call.  Errors: as darts_render, and DARTS_ERR_INVALID_ARG
+ * for n_frames 0, in_flight outside 1..4 or a NULL output. */
+darts_status darts_render_frames(darts_ctx* ctx, const darts_scene* scene,
+                                 const darts_sampling* sampling, uint32_t n_frames,
+                                 double* const* hist_dev, double* const* sumsq_dev,
+                                 uint64_t path_offset, int32_t in_flight);
+
 /* Path-replay adjoint of the DARTS estimator (not in the paper; its Sec. 7
  * lists differentiable transient rendering as future work).  Traces the paths
  * path_offset .. +N-1 of `sampling` (use a seed independent of the forward

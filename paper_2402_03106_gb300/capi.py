@@ -15,7 +15,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 import threading
-from typing import Optional
+from typing import Optional, Sequence
 
 import torch
 
@@ -38,7 +38,7 @@ EXPORTED = ("darts_create", "darts_destroy", "darts_set_stream", "darts_status_s
             "darts_render", "darts_render_host", "darts_get_stats", "darts_debug_paths",
             "darts_debug_philox", "darts_set_kernel_timing", "darts_last_kernel_ms",
             "darts_render_static", "darts_set_launch", "darts_autotune", "darts_adjoint",
-            "darts_render_batch", "darts_render_host_async")
+            "darts_render_batch", "darts_render_host_async", "darts_render_frames")
 BATCH_NO_GRAPH = 1
 
 
@@ -128,6 +128,7 @@ def load(path: str = LIB_PATH):
         lib.darts_render.argtypes = [vp, sc_p, sp_p, vp, vp, C.c_uint64, C.POINTER(darts_probe)]
         lib.darts_render_host.argtypes = [vp, sc_p, sp_p, vp, vp, C.c_uint64]
         lib.darts_render_host_async.argtypes = [vp, sc_p, sp_p, vp, vp, C.c_uint64]
+        lib.darts_render_frames.argtypes = [vp, sc_p, sp_p, C.c_uint32, vp, vp, C.c_uint64, C.c_int32]
         lib.darts_get_stats.argtypes = [vp, C.POINTER(darts_stats)]
         lib.darts_debug_paths.argtypes = [vp, sc_p, sp_p, C.c_uint64, C.c_uint32, vp, vp, vp, vp]
         lib.darts_debug_philox.argtypes = [vp, vp, C.c_uint64, C.c_uint32, vp]
@@ -207,6 +208,13 @@ def to_c_sampling(sp: S.Sampling) -> darts_sampling:
 
 def _ptr(t: Optional[torch.Tensor]):
     return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _ptr_array(ts: Optional[Sequence[torch.Tensor]]):
+    """A C array of device pointers (double* const*), or None."""
+    if ts is None:
+        return None
+    return (C.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
 
 
 # ----------------------------------------------------------------------------
@@ -367,6 +375,18 @@ class Prepared:
                                                        _ptr(hist_host), _ptr(sumsq_host), int(path_offset)))
         return hist_host
 
+    def render_frames(self, outs: Sequence[torch.Tensor], sumsq: Optional[Sequence[torch.Tensor]] = None,
+                      path_offset: int = 0, in_flight: int = 2) -> Sequence[torch.Tensor]:
+        """darts_render_frames: frame i (path ids path_offset + i*N ...) into
+        outs[i], up to in_flight frames running at once on the context's
+        lanes; ordered on the context's stream like render()."""
+        if sumsq is not None and len(sumsq) != len(outs):
+            raise ValueError("one sumsq buffer per frame")
+        _check(self.ctx.h, self._lib.darts_render_frames(self.ctx.h, C.byref(self.cs), C.byref(self.csp),
+                                                         len(outs), _ptr_array(outs), _ptr_array(sumsq),
+                                                         int(path_offset), int(in_flight)))
+        return outs
+
     def render_host_async(self, hist_host: torch.Tensor, sumsq_host: Optional[torch.Tensor] = None,
                           path_offset: int = 0) -> torch.Tensor:
         """darts_render_host_async: queued render and copy back into pinned
@@ -434,6 +454,17 @@ class Context:
         _check(self.h, load().darts_render_host_async(self.h, C.byref(cs), C.byref(csp), _ptr(hist_host),
                                                       _ptr(sumsq_host), int(path_offset)))
         return hist_host
+
+    def render_frames(self, scene, sampling, n_frames: int, path_offset: int = 0, in_flight: int = 2,
+                      sumsq: bool = False):
+        """n_frames frames of one scene (frame i: path ids path_offset + i*N
+        ...), up to in_flight of them running at once; returns the list of
+        histograms (and of sums of squares when sumsq)."""
+        shape = S.histogram_shape(scene)
+        outs = [torch.empty(shape, dtype=torch.float64, device=self._dev()) for _ in range(n_frames)]
+        sqs = [torch.empty(shape, dtype=torch.float64, device=self._dev()) for _ in range(n_frames)] if sumsq else None
+        self.prepare(scene, sampling).render_frames(outs, sqs, path_offset, in_flight)
+        return (outs, sqs) if sumsq else outs
 
     def build_table(self, scene, sampling, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         rows = sampling.table_n_rho * sampling.table_n_s

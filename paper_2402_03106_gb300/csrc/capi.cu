@@ -66,6 +66,13 @@ struct darts_ctx {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   uint64_t graph_key = 0;
+  // darts_render_frames: lanes (child contexts, each on a stream of its own),
+  // the fork event recorded on this context's stream and one join event per lane
+  static constexpr int kMaxLanes = 4;
+  darts_ctx* lanes[kMaxLanes] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t lane_stream[kMaxLanes] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kMaxLanes] = {nullptr, nullptr, nullptr, nullptr};
   char err[512] = {0};
 };
 
@@ -704,6 +711,12 @@ darts_status darts_destroy(darts_ctx* ctx) {
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
   if (ctx->ev_stop) cudaEventDestroy(ctx->ev_stop);
+  for (int j = 0; j < darts_ctx::kMaxLanes; ++j) {
+    if (ctx->lanes[j]) darts_destroy(ctx->lanes[j]);  // synchronises the lane's stream
+    if (ctx->lane_stream[j]) cudaStreamDestroy(ctx->lane_stream[j]);
+    if (ctx->ev_join[j]) cudaEventDestroy(ctx->ev_join[j]);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   delete ctx;
   return DARTS_OK;
 }
@@ -723,6 +736,16 @@ darts_status darts_last_error(const darts_ctx* ctx, char* buf, size_t n) {
 darts_status darts_sync(darts_ctx* ctx) {
   if (!ctx) return DARTS_ERR_INVALID_ARG;
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  // the lanes of darts_render_frames first: each reports (and clears) its own status
+  darts_status lane_status = DARTS_OK;
+  for (int j = 0; j < darts_ctx::kMaxLanes; ++j) {
+    if (!ctx->lanes[j]) continue;
+    const darts_status sj = darts_sync(ctx->lanes[j]);
+    if (sj != DARTS_OK && lane_status == DARTS_OK) {
+      lane_status = sj;
+      std::snprintf(ctx->err, sizeof(ctx->err), "frame lane %d: %s", j, ctx->lanes[j]->err);
+    }
+  }
   if (ctx->copy_stream) CK(cudaStreamSynchronize(ctx->copy_stream), "copy stream synchronize");
   // the status words travel behind the stream's work into pinned memory: one
   // synchronisation, no separate blocking copy
@@ -738,7 +761,7 @@ darts_status darts_sync(darts_ctx* ctx) {
     if (st[1] & 2u) return fail(ctx, DARTS_ERR_TIMEOUT, "a bounded device wait expired");
     return fail(ctx, DARTS_ERR_NUMERIC, "a kernel produced a non-finite contribution");
   }
-  return DARTS_OK;
+  return lane_status;
 }
 
 darts_status darts_set_kernel_timing(darts_ctx* ctx, int enable) {
@@ -943,6 +966,55 @@ darts_status darts_render_host_async(darts_ctx* ctx, const darts_scene* scene,
   ctx->copied_pending[k] = true;
   ctx->async_slot = k ^ 1;
   return DARTS_OK;
+}
+
+darts_status darts_render_frames(darts_ctx* ctx, const darts_scene* scene, const darts_sampling* sampling,
+                                 uint32_t n_frames, double* const* hist_dev, double* const* sumsq_dev,
+                                 uint64_t path_offset, int32_t in_flight) {
+  const Range nvtx_range("darts_render_frames");
+  if (!ctx) return DARTS_ERR_INVALID_ARG;
+  darts_status s = validate(ctx, scene, sampling);
+  if (s != DARTS_OK) return s;
+  if (n_frames == 0 || !hist_dev) return fail(ctx, DARTS_ERR_INVALID_ARG, "need n_frames >= 1 and outputs");
+  if (in_flight < 1 || in_flight > darts_ctx::kMaxLanes)
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "in_flight must be in 1..%d", darts_ctx::kMaxLanes);
+  if (sampling->flags & DARTS_FLAG_ACCUMULATE)
+    return fail(ctx, DARTS_ERR_UNSUPPORTED, "darts_render_frames overwrites its outputs");
+  for (uint32_t i = 0; i < n_frames; ++i)
+    if (!hist_dev[i] || (sumsq_dev && !sumsq_dev[i]))
+      return fail(ctx, DARTS_ERR_INVALID_ARG, "frame %u: NULL output", i);
+  const uint64_t N = sampling->paths_per_element * elements_of(scene);
+  if (N > 0 && (uint64_t)(n_frames - 1) > (UINT64_MAX - path_offset) / N)
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "path ids of the last frame exceed 2^64");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const int lanes = (int)std::min<uint32_t>((uint32_t)in_flight, n_frames);
+  for (int j = 0; j < lanes; ++j) {  // created on first use and kept
+    if (!ctx->lane_stream[j])
+      CK(cudaStreamCreateWithFlags(&ctx->lane_stream[j], cudaStreamNonBlocking), "lane stream");
+    if (!ctx->ev_join[j]) CK(cudaEventCreateWithFlags(&ctx->ev_join[j], cudaEventDisableTiming), "event");
+    if (!ctx->lanes[j]) {
+      const darts_status c = darts_create(&ctx->lanes[j], ctx->device, ctx->lane_stream[j]);
+      if (c != DARTS_OK) return fail(ctx, c, "frame lane %d: context creation failed", j);
+    }
+    ctx->lanes[j]->block = ctx->block;
+  }
+  if (!ctx->ev_fork) CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming), "event");
+  CK(cudaEventRecord(ctx->ev_fork, ctx->stream), "event record");
+  for (int j = 0; j < lanes; ++j) CK(cudaStreamWaitEvent(ctx->lane_stream[j], ctx->ev_fork, 0), "stream wait");
+  darts_status r = DARTS_OK;
+  for (uint32_t i = 0; i < n_frames && r == DARTS_OK; ++i) {
+    darts_ctx* lane = ctx->lanes[i % (uint32_t)lanes];
+    r = darts_render(lane, scene, sampling, hist_dev[i], sumsq_dev ? sumsq_dev[i] : nullptr, path_offset + i * N,
+                     nullptr);
+    if (r != DARTS_OK) std::snprintf(ctx->err, sizeof(ctx->err), "frame %u: %s", i, lane->err);
+  }
+  // joined even after a failed enqueue: later work on the context's stream
+  // waits for every frame that was enqueued
+  for (int j = 0; j < lanes; ++j) {
+    CK(cudaEventRecord(ctx->ev_join[j], ctx->lane_stream[j]), "event record");
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join[j], 0), "stream wait");
+  }
+  return r;
 }
 
 darts_status darts_get_stats(darts_ctx* ctx, darts_stats* out) {

@@ -60,3 +60,59 @@ def test_frames_in_flight_equal_sequential_frames(capi, n_streams, which):
         torch.testing.assert_close(a, b, rtol=1e-9, atol=1e-12 * scale, msg=f"{name} frame {i}")
     # different frames are different path ids: they must not coincide
     assert not torch.equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("in_flight", [1, 2, 4])
+@pytest.mark.parametrize("which", [0, 1])
+def test_render_frames_equals_sequential_frames(capi, in_flight, which):
+    """darts_render_frames: frame i holds what darts_render writes at path
+    offset path_offset + i*N, sums of squares included; work enqueued on the
+    context's stream after the call sees every frame complete."""
+    name, sc, sp = _workloads()[which]
+    N = S.total_paths(sc, sp)
+    frames, off = 5, 3 * N
+    ctx = capi.Context(0)
+    ref = [ctx.render(sc, sp, sumsq=True, path_offset=off + i * N) for i in range(frames)]
+    ref = [(h.clone(), q.clone()) for h, q in ref]
+    outs, sqs = ctx.render_frames(sc, sp, frames, path_offset=off, in_flight=in_flight, sumsq=True)
+    totals = torch.stack([o.sum() for o in outs])  # on the context's stream, no synchronisation
+    ctx.sync()
+    for i in range(frames):
+        for a, b, what in ((outs[i], ref[i][0], "hist"), (sqs[i], ref[i][1], "sumsq")):
+            scale = float(b.abs().max())
+            assert scale > 0.0, (name, i, what)
+            torch.testing.assert_close(a, b, rtol=1e-9, atol=1e-12 * scale, msg=f"{name} frame {i} {what}")
+    torch.testing.assert_close(totals, torch.stack([r[0].sum() for r in ref]), rtol=1e-9, atol=0.0)
+    ctx.close()
+
+
+def test_render_frames_arguments_and_lane_status(capi):
+    """Invalid arguments are refused before any launch; a non-finite frame
+    on a lane is reported by the parent's darts_sync, once."""
+    import copy
+    sc, sp = S.cube_workload(paths=1 << 12, seed=4)
+    ctx = capi.Context(0)
+    prep = ctx.prepare(sc, sp)
+    outs = [torch.empty(S.histogram_shape(sc), dtype=torch.float64, device="cuda") for _ in range(3)]
+    for bad in (0, 5):
+        with pytest.raises(capi.DartsError) as ei:
+            prep.render_frames(outs, in_flight=bad)
+        assert ei.value.status == 1
+    with pytest.raises(capi.DartsError) as ei:
+        prep.render_frames([])
+    assert ei.value.status == 1
+    acc = copy.deepcopy(sp)
+    acc.flags |= S.FLAG_ACCUMULATE
+    with pytest.raises(capi.DartsError) as ei:
+        ctx.prepare(sc, acc).render_frames(outs)
+    assert ei.value.status == 6
+    hot = copy.deepcopy(sc)
+    hot.emitters[0].energy = 1e40  # finite in FP64, infinite in FP32
+    ctx.prepare(hot, sp).render_frames(outs, in_flight=3)
+    with pytest.raises(capi.DartsError) as ei:
+        ctx.sync()
+    assert ei.value.status == 4
+    prep.render_frames(outs, in_flight=3)
+    ctx.sync()
+    assert all(torch.isfinite(o).all() and float(o.sum()) > 0.0 for o in outs)
+    ctx.close()
