@@ -596,7 +596,7 @@ def spheres_frame(ctx, S, torch, flush, reps=3):
     return out
 
 
-def frames_in_flight(ctx, S, torch, sc, sp, N, frames=60, calls=10, reps=5):
+def frames_in_flight(ctx, S, torch, sc, sp, N, workload, frames=60, calls=10, reps=5):
     """Throughput of a frame sequence (video rendering) through
     darts_render_frames with 1, 2 and 3 frames in flight: frame i runs on
     lane i mod n (a stream of its own), so that a frame's tail (a few long
@@ -628,7 +628,7 @@ def frames_in_flight(ctx, S, torch, sc, sp, N, frames=60, calls=10, reps=5):
     del outs
     for r in rows.values():
         r["vs_one_lane"] = rows["1"]["ms_per_frame"] / r["ms_per_frame"]
-    return {"workload": "the timed camera frame", "frames": frames * calls, "call": "darts_render_frames",
+    return {"workload": workload, "frames": frames * calls, "call": "darts_render_frames",
             "lanes": rows, "note": "throughput, not the latency of a frame; median of %d repetitions" % reps}
 
 
@@ -875,7 +875,9 @@ def main():
         extra["mse_time_cube"] = mse_time(ctx, S, torch)
     extra["batched"] = batched_compare(ctx, S, torch)
     extra["differentiable_32x32"] = differentiable_step(ctx, S, torch, flush)
-    extra["frames_in_flight"] = frames_in_flight(ctx, S, torch, sc, sp, N)
+    extra["frames_in_flight"] = frames_in_flight(ctx, S, torch, sc, sp, N, "the timed camera frame")
+    extra["frames_in_flight_cube_2e16"] = frames_in_flight(
+        ctx, S, torch, sc16, sp16, 1 << 16, "the unit cube as configured, 2^16 paths per render")
     cpu = cpu_baseline(args.workload) if ws == 1 else None
 
     line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws, "steps": K,
