@@ -2,26 +2,30 @@
 """Throughput benchmark of the DARTS hot path on GB300.
 
 One step = one pass of the whole path over one frame of the workload: the
-elliptical DA direction table is rebuilt on the GPU, then every path of the
-frame is traced (DA-RIS distance sampling, EDA/MIS directions, elliptical
-control vertices, surface bounces) and accumulated into per-pixel time-bin
-histograms.
+elliptical DA direction table is rebuilt on the GPU (the same launch zeroes
+the frame's histograms), then every path of the frame is traced (DA-RIS
+distance sampling, EDA/MIS directions, elliptical control vertices, surface
+bounces) and accumulated into per-pixel time-bin histograms.
 
-Default workload (``--workload box_camera``): a 64x64 pinhole camera (40 deg
-FOV) views a 2x2x2 box with five Lambertian walls (albedo 0.5, the front
-face open) filled with a medium drawn from seed 0 (sigma_s U[0.5, 2], albedo
-U[0.9, 0.99], g U[0, 0.9]) and lit by a 0.3 x 0.3 Lambertian area pulse
-emitter on the ceiling; 512 bins on [0, 16); 16 paths per pixel (65536 per
-frame), 50 bounces, 8 RIS candidates, 16x8x256 direction table.
-``--workload cube`` is the unit-cube medium with point emitter and sensor at
-2^24 paths per step (the GPU saturated); the default run reports it too.
+Default workload (``--workload spheres_512``), the largest configuration that
+fits one GPU: a 512x512 pinhole camera (40 deg FOV) inside a 4x4x4 medium
+(sigma_s 0.8, sigma_a 0.005, g 0.8) holding 32 seeded Lambertian spheres,
+lit by two point pulse emitters (t0 = 0 and 1.5); 1000 bins on [0, 20);
+64 paths per pixel (16.7 M per frame), 100 bounces, 8 RIS candidates,
+16x8x256 direction table; a 2.1 GB FP64 histogram per frame.
+``--workload box_camera`` is the 64x64 walled box with the area emitter
+(512 bins, 16 spp); ``--workload cube`` the unit-cube medium with point
+emitter and sensor at 2^24 paths per step.  The default run also reports
+those two, compactly.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
-  python bench.py --only {timed,batched,differentiable,spheres}
+  python bench.py --studies OUT.json     # efficiency and side studies, to a file
+  python bench.py --only {timed,batched,differentiable}
 
-``--only`` runs one measurement alone, for ncu captures of its kernels: the
-timed steps, the batched 256-media launch, the differentiable step (forward
-render + path-replay adjoint on the 32x32 cube camera), the 512x512 frame.
+stdout carries exactly one line: the JSON headline.  The efficiency
+comparisons (MSE x time against the uniform-temporal and vanilla tracers,
+ablations, gates), the batched launch, the differentiable step and frames
+in flight run only with ``--studies`` and are written to that file.
 
 Under torchrun every rank traces its own path-id range (weak scaling) and the
 per-rank histograms are combined with one FP64 all-reduce per step, which
@@ -48,31 +52,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DARTS transient path samples/s on 1 GB300; MSE×time vs plain transient PT"
 WORKLOADS = {
+    "spheres_512": ("512x512 pinhole camera (FOV 40 deg) at (2,2,0.05) looking +z inside a 4x4x4 medium "
+                    "sigma_s 0.8 sigma_a 0.005 g 0.8; 32 seeded Lambertian spheres (r U[0.05,0.3], albedo "
+                    "U[0.2,0.8]); two point pulse emitters (1,3.5,1) t0=0 and (3,3.5,3) t0=1.5; 1000 bins on "
+                    "[0,20); 64 spp (16.7 M paths per frame), K=100, N_RIS=8, table 16x8x256; 2.1 GB FP64 "
+                    "histogram; one frame per GPU per step"),
     "box_camera": ("64x64 pinhole camera (FOV 40 deg) at (1,1,-2.5) viewing a 2x2x2 box, five Lambertian "
                    "walls albedo 0.5 (front face open); medium from seed 0: sigma_s U[0.5,2], albedo "
                    "U[0.9,0.99], g U[0,0.9]; 0.3x0.3 Lambertian area pulse emitter on the ceiling, t0=0; "
-                   "512 bins on [0,16); 16 spp (65536 paths per frame), K=50, N_RIS=8, table 16x8x256; "
-                   "one frame per GPU per step"),
+                   "512 bins on [0,16); 16 spp (65536 paths per frame), K=50, N_RIS=8, table 16x8x256"),
     "cube": ("unit-cube medium sigma_s=1 sigma_a=0.01 g=0.7 v=1; isotropic point pulse emitter "
              "(0.5,0.5,0.1) t0=0; point fluence sensor (0.5,0.5,0.9); 256 bins on [0.8,6.0); "
              "K=50 bounces, N_RIS=8, table 16x8x256; 2^24 paths per GPU per step"),
 }
-
-# Algorithmic FP32 work of the DARTS step (counted from the equations of the
-# stable formulation; add/sub/mul/compare/convert = 1, FMA = 2; special
-# functions counted separately as MUFU operations).  The general kernel
-# (surfaces, camera, area emitters) adds the box slab test and the
-# medium/surface branch to every vertex and the control-vertex point and the
-# emitter cosine to every connection.
-FLOPS_PER_VERTEX = 120
-FLOPS_PER_CONNECTION = 80
-FLOPS_PER_CANDIDATE = 52
-FLOPS_PER_DISTANCE_STEP = 30
-FLOPS_PER_VERTEX_GEN = 150
-FLOPS_PER_CONNECTION_GEN = 95
-MUFU_PER_VERTEX = 10
-MUFU_PER_CONNECTION = 6
-MUFU_PER_CANDIDATE = 5
+DEFAULT_STEPS = {"spheres_512": 30, "box_camera": 2000, "cube": 60}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 MUFU_PER_SM_CLK = 16
@@ -82,32 +75,48 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default: 2000 camera frames, about 1 s; 60 cube steps)")
-    ap.add_argument("--warmup", type=int, default=5)
+                    help="timed steps (default: 30 frames of the 512x512 workload, 2000 box frames, 60 cube steps)")
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="box_camera", choices=sorted(WORKLOADS))
-    ap.add_argument("--no-mse", action="store_true", help="skip the MSE x time comparisons")
-    ap.add_argument("--only-timed", action="store_true",
-                    help="run only the timed steps (for profiler launch lists)")
-    ap.add_argument("--only", default=None, choices=["timed", "batched", "differentiable", "spheres"],
-                    help="run one measurement alone (for ncu captures of its kernels): the timed "
-                         "steps, the batched launch, the differentiable step, the 512x512 frame")
+    ap.add_argument("--workload", default="spheres_512", choices=sorted(WORKLOADS))
+    ap.add_argument("--studies", default=None, metavar="OUT.json",
+                    help="also run the efficiency and side studies and write them to this file")
+    ap.add_argument("--only", default=None, choices=["timed", "batched", "differentiable"],
+                    help="run one measurement alone (for ncu captures of its kernels)")
+    ap.add_argument("--only-timed", action="store_true", help="same as --only timed")
     a = ap.parse_args()
     if a.only_timed:
         a.only = "timed"
     if a.steps is None:
-        a.steps = 2000 if a.workload == "box_camera" else 60
+        a.steps = DEFAULT_STEPS[a.workload]
     return a
 
 
 def make_workload(name, S):
     """(scene, sampling, paths per step) of a named workload."""
-    if name == "box_camera":
+    if name == "spheres_512":
+        sc = S.spheres_camera_scene(seed=0)
+        sp = S.Sampling(seed=0, paths_per_element=64, max_bounces=100)
+    elif name == "box_camera":
         sc, sp = S.box_camera_workload(seed=0)
     else:
         sc, sp = S.cube_workload(paths=1 << 24, seed=0)
     sp.flags |= S.FLAG_REBUILD_TABLE
     return sc, sp, S.total_paths(sc, sp)
+
+
+def oracle_sample(name, S):
+    """The bounded oracle sample of a workload: a list of (first path id,
+    path count, (first element, element count)) pieces and its description.
+    512x512 frame: rows 32 + 64 i (i < 8), 1/64 of the pixels at 64 spp."""
+    sc, sp, n = make_workload(name, S)
+    if name == "spheres_512":
+        row = 512 * 64
+        pieces = [((32 + 64 * i) * row, row, ((32 + 64 * i) * 512, 512)) for i in range(8)]
+        return pieces, "rows 32 + 64 i (i < 8) of the 512x512 frame: 1/64 of its pixels, 64 spp each"
+    if name == "box_camera":
+        return [(0, n, None)], "one whole 64x64 frame (65536 paths)"
+    return [(0, 1 << 22, None)], "2^22 paths of the 2^24-path step"
 
 
 # ----------------------------------------------------------------------------
@@ -203,35 +212,55 @@ def profiled_traffic(workload: str, paths_per_launch: int):
     return v
 
 
+def algorithmic_work(workload: str):
+    """Work per vertex of a workload from the oracle's op-count summary
+    (profiles/op_counts.md, written by oracle/opcount.py): FP operations
+    (add, mul, div), special functions (sqrt, exp, log, trig, pow) and
+    Philox integer operations."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", "op_counts.md")).read()
+    except OSError:
+        return None
+    for line in text.splitlines():
+        if line.startswith("data: "):
+            d = json.loads(line[len("data: "):])
+            if d.get("workload") == workload:
+                return d
+    return None
+
+
 # ----------------------------------------------------------------------------
-def cpu_baseline(workload: str, budget_s: float = 12.0):
-    """The FP64 oracle, as it stands, on this host's cores: whole frames (or
-    2^22-path batches of the cube) of the benchmark workload until about
-    budget_s of CPU time has passed."""
+def cpu_baseline(workload: str, budget_s: float = 10.0):
+    """The FP64 oracle, as it stands, on this host's cores: the bounded
+    sample of the workload (for the 512x512 frame, 1/64 of its pixels),
+    repeated over successive frames until about budget_s has passed;
+    paths/s of the sample extrapolate to the whole frame by path count."""
     import oracle as O
     from paper_2402_03106_gb300 import scenes as S
-    sc, sp, n = make_workload(workload, S)
-    if workload == "cube":
-        n = 1 << 22
+    sc, sp, N = make_workload(workload, S)
+    pieces, what = oracle_sample(workload, S)
     cores = os.cpu_count() or 1
     cdf = O.build_table(sc, sp)
-    done, t_tot = 0, 0.0
+    done, paths, t_tot = 0, 0, 0.0
     while t_tot < budget_s and done < 64:
-        t0 = time.perf_counter()
-        O.render(sc, sp, O.ORC_DARTS, n_paths=n, offset=done * n, cdf=cdf, threads=cores)
-        t_tot += time.perf_counter() - t0
+        for first, count, window in pieces:
+            t0 = time.perf_counter()
+            O.render(sc, sp, O.ORC_DARTS, n_paths=count, offset=first + done * N, cdf=cdf, threads=cores,
+                     window=window)
+            t_tot += time.perf_counter() - t0
+            paths += count
         done += 1
-    unit = "frames" if workload == "box_camera" else f"batches of {n} paths"
-    # one thread, on a quarter of the same sample size
-    n1 = max(1, n // 4)
+    first, count, window = pieces[0]
+    n1 = max(1, count // 16)
     t0 = time.perf_counter()
-    O.render(sc, sp, O.ORC_DARTS, n_paths=n1, offset=done * n, cdf=cdf, threads=1)
+    O.render(sc, sp, O.ORC_DARTS, n_paths=n1, offset=first, cdf=cdf, threads=1, window=window)
     t1 = time.perf_counter() - t0
-    return {"value": done * n / t_tot, "unit": "paths/s", "cores": cores, "kind": "oracle",
-            "sample": f"{done} {unit} of the benchmark workload ({done * n} paths, table prebuilt), "
-                      f"FP64 C oracle, {cores} POSIX threads, {t_tot:.2f} s wall",
+    return {"value": paths / t_tot, "unit": "paths/s", "cores": cores, "kind": "oracle",
+            "sample": f"{what}; {done} frame(s) of that sample ({paths} paths, direction table prebuilt), "
+                      f"FP64 C oracle, {cores} POSIX threads, {t_tot:.2f} s wall; paths/s of the sample "
+                      f"(a whole frame extrapolates by its path count)",
             "single_thread": {"value": n1 / t1, "unit": "paths/s", "cores": 1,
-                              "sample": f"{n1} paths of the same workload, {t1:.2f} s wall"}}
+                              "sample": f"{n1} paths of the same sample, {t1:.2f} s wall"}}
 
 
 def run_reference(args):
@@ -241,32 +270,33 @@ def run_reference(args):
     import oracle as O
     from paper_2402_03106_gb300 import scenes as S
     cores = os.cpu_count() or 1
-    sc, sp, n = make_workload(args.workload, S)
-    # whole frames: the oracle's per-call set-up (per-thread [pixels][bins]
-    # histograms) would dominate smaller samples of a camera frame
-    sample = n if args.workload == "box_camera" else 1 << 18
+    sc, sp, N = make_workload(args.workload, S)
+    pieces, what = oracle_sample(args.workload, S)
     # the FP64 table build (about 0.1 s) is done once, before the timed steps,
     # so that any step count stays within minutes
     cdf = O.build_table(sc, sp)
-    times = []
+    times, paths = [], 0
     for i in range(args.warmup + args.steps):
+        first, count, window = pieces[i % len(pieces)]
         t0 = time.perf_counter()
-        O.render(sc, sp, O.ORC_DARTS, n_paths=sample, cdf=cdf, threads=cores, offset=i * sample)
+        O.render(sc, sp, O.ORC_DARTS, n_paths=count, offset=first + (i // len(pieces)) * N, cdf=cdf,
+                 threads=cores, window=window)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
+            paths += count
     tot = sum(times)
-    value = sample * len(times) / tot
-    what = (f"one whole frame ({sample} paths) per step; direction table built once before the timed steps"
-            if args.workload == "box_camera" else
-            f"{sample} paths per step (bounded CPU sample; direction table built once before the timed steps)")
+    value = paths / tot
+    step_what = (f"one piece of the sample per step ({pieces[0][1]} paths), cycling over: {what}; "
+                 f"direction table built once before the timed steps")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "paths/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "reference_sample": what},
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
+                       "reference_sample": step_what},
             "cpu_baseline": {"value": value, "unit": "paths/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{what}, {cores} POSIX threads"},
+                             "sample": f"{step_what}, {cores} POSIX threads"},
             "e2e": {"value": value, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -574,28 +604,6 @@ def batched_compare(ctx, S, torch, reps=5):
                         "g U[-0.3,0.9], side U[0.5,4], budgets 2^U[12,20], 128 bins, K=50, M=8"}
 
 
-def spheres_frame(ctx, S, torch, flush, reps=3):
-    """The largest configuration: 512x512 camera, 32 spheres, two emitters,
-    1000 bins, 64 spp, K = 100 (16.7 M paths, a 2.1 GB histogram)."""
-    scs = S.spheres_camera_scene(seed=0)
-    sps = S.Sampling(seed=0, paths_per_element=64, max_bounces=100, flags=S.FLAG_REBUILD_TABLE)
-    Ns = S.total_paths(scs, sps)
-    hs = torch.empty(S.histogram_shape(scs), dtype=torch.float64, device="cuda")
-    preps = ctx.prepare(scs, sps)
-    preps.render(out=hs)
-    torch.cuda.synchronize()
-    ctx.set_kernel_timing(True)
-    ts, ks, pers = time_steps(ctx, torch, lambda: preps.render(out=hs), reps, flush)
-    ctx.set_kernel_timing(False)
-    out = {"workload": "512x512 pinhole camera inside a 4x4x4 medium (sigma_s 0.8, sigma_a 0.005, g 0.8) with 32 "
-                       "seeded Lambertian spheres, two point pulse emitters (t0 = 0, 1.5), 1000 bins on [0,20), "
-                       "64 spp, K=100", "paths_per_step": Ns, "ms_per_step": statistics.fmean(ts),
-           "paths_per_s": Ns / (statistics.fmean(ts) * 1e-3), "histogram_bytes": hs.numel() * 8,
-           "roofline": roofline(pers, statistics.fmean(ks), True, "spheres_512", Ns)}
-    del hs, preps
-    return out
-
-
 def frames_in_flight(ctx, S, torch, sc, sp, N, workload, frames=60, calls=10, reps=5):
     """Throughput of a frame sequence (video rendering) through
     darts_render_frames with 1, 2 and 3 frames in flight: frame i runs on
@@ -692,27 +700,163 @@ def time_steps(ctx, torch, step, steps, flush, kernel_timing=True, finish=None):
     return step_ms, kern_ms, {k: v / steps for k, v in stats_acc.items()}
 
 
-def roofline(per, kms, general, workload, paths):
+def mse_time_spheres(ctx, S, torch, seeds=16, spps=(64, 256)):
+    """MSE x time on the largest configuration (512x512 camera, 32 spheres,
+    two emitters, 1000 bins, K = 100): DARTS, full-gate DARTS, the plain
+    uniform-temporal tracer and the vanilla tracer, `seeds` seeds at 64 and
+    256 spp.  The reference is the path-weighted mean of every DARTS and
+    uniform-temporal render (both unbiased; 160x the paths of one 64-spp
+    render), formed on the device in a first pass; a second pass re-renders
+    each seed (deterministic) and takes its MSE over all pixels and bins.
+    Also one-bin gates on the same scene (the paper's time-gated regime).
+    ratio = (MSE x time)_base / (MSE x time)_darts with the median render
+    time (table build + trace, CUDA events)."""
+    sc = S.spheres_camera_scene(seed=0)
+    methods = (("darts", S.DARTS), ("darts_full_gate", S.DARTS_FULL_GATE),
+               ("plain_uniform_t", S.PLAIN_UNIFORM_T), ("vanilla_direct", S.VANILLA_DIRECT))
+    out = {"workload": "512x512 spheres frame of the benchmark, 1000 bins on [0,20), K=100", "seeds": seeds}
+
+    def render(scene, m, spp, seed, buf):
+        sp = S.Sampling(seed=seed, paths_per_element=spp, max_bounces=100, method=m,
+                        flags=S.FLAG_REBUILD_TABLE if m in (S.DARTS, S.DARTS_FULL_GATE) else 0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.render(scene, sp, out=buf)
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
+    def compare(scene, label, spps_, seed0):
+        shape = S.histogram_shape(scene)
+        buf = torch.empty(shape, dtype=torch.float64, device="cuda")
+        ref = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        wsum = 0.0
+        for spp in spps_:  # pass 1: the pooled reference
+            for name, m in methods[:3:2]:
+                for s_ in range(seeds):
+                    render(scene, m, spp, seed0 + s_, buf)
+                    ref.add_(buf, alpha=float(spp))
+                    wsum += spp
+        ref.div_(wsum)
+        res = {"reference_paths_per_pixel": int(wsum)}
+        for spp in spps_:  # pass 2: per-seed MSE
+            rows = {}
+            for name, m in methods:
+                mse, ts = [], []
+                for s_ in range(seeds):
+                    ts.append(render(scene, m, spp, seed0 + s_, buf))
+                    buf.sub_(ref)
+                    mse.append(float(torch.mean(buf * buf)))
+                mse.sort()
+                rows[name] = {"seconds_per_render": statistics.median(ts),
+                              "mse_mean": statistics.fmean(mse), "mse_median": statistics.median(mse)}
+            for base in ("plain_uniform_t", "vanilla_direct", "darts_full_gate"):
+                b, d = rows[base], rows["darts"]
+                rows[f"ratio_{base}_over_darts"] = {
+                    "mse_mean_time": b["mse_mean"] * b["seconds_per_render"] /
+                                     max(d["mse_mean"] * d["seconds_per_render"], 1e-300),
+                    "mse_median_time": b["mse_median"] * b["seconds_per_render"] /
+                                       max(d["mse_median"] * d["seconds_per_render"], 1e-300)}
+            b, d = rows["plain_uniform_t"], rows["darts_full_gate"]
+            rows["ratio_plain_uniform_t_over_darts_full_gate"] = {
+                "mse_mean_time": b["mse_mean"] * b["seconds_per_render"] /
+                                 max(d["mse_mean"] * d["seconds_per_render"], 1e-300),
+                "mse_median_time": b["mse_median"] * b["seconds_per_render"] /
+                                   max(d["mse_median"] * d["seconds_per_render"], 1e-300)}
+            res[f"spp_{spp}"] = rows
+        del buf, ref
+        out[label] = res
+
+    compare(sc, "transient_1000_bins", spps, 1001)
+    for t0, t1 in ((6.0, 6.25), (10.0, 10.25)):
+        g = S.spheres_camera_scene(seed=0, n_bins=1)
+        g.gate.t_min, g.gate.t_max = t0, t1
+        compare(g, f"gate_{t0:g}_{t1:g}", spps, 2001)
+    return out
+
+
+def roofline(per, kms, workload, traffic_workload=None, paths=None):
     """Algorithmic FP32 work of one launch of the path kernel over its
     measured duration, against the FP32 pipe peak derived from the SM count,
-    lanes and the measured maximum clock."""
-    fv = FLOPS_PER_VERTEX_GEN if general else FLOPS_PER_VERTEX
-    fc = FLOPS_PER_CONNECTION_GEN if general else FLOPS_PER_CONNECTION
-    flops = (fv * per["vertices"] + fc * per["connections_nonempty"]
-             + (FLOPS_PER_DISTANCE_STEP + 8 * FLOPS_PER_CANDIDATE) * per["distance_steps"])
-    mufu = (MUFU_PER_VERTEX * per["vertices"] + MUFU_PER_CONNECTION * per["connections_nonempty"]
-            + 8 * MUFU_PER_CANDIDATE * per["distance_steps"])
+    lanes and the measured maximum clock.  Work per vertex comes from the
+    oracle's op-count summary of the same workload; vertices from the
+    launch's own event counts."""
+    w = algorithmic_work(workload)
     clock_mhz = measured_peaks().get("sm_max_mhz", 2070.0)
     peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
     peak_mufu = SM_COUNT * MUFU_PER_SM_CLK * clock_mhz * 1e6 / 1e12
-    achieved = flops / (kms * 1e-3) / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-            "frac": achieved / peak_fp32, "traffic": profiled_traffic(workload, paths),
-            "kernel": "trace_kernel<DARTS%s> (persistent path kernel)" % (", general" if general else ""),
-            "kernel_ms": kms, "flops_per_launch": flops,
-            "peak_note": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clock_mhz:.0f} MHz",
-            "mufu_achieved_tops": mufu / (kms * 1e-3) / 1e12, "mufu_peak_tops": peak_mufu,
-            "mufu_frac": mufu / (kms * 1e-3) / 1e12 / peak_mufu, "events_per_launch": per}
+    out = {"bound": "alu", "achieved": None, "peak": peak_fp32, "unit": "TFLOP/s", "frac": None,
+           "traffic": profiled_traffic(traffic_workload or workload, paths) if paths else None,
+           "kernel": "trace_kernel (persistent path kernel)", "kernel_ms": kms,
+           "peak_note": f"derived nominal: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                        f"{clock_mhz:.0f} MHz (measured max SM clock)",
+           "vertices_per_launch": per.get("vertices")}
+    if w is None or not kms:
+        out["note"] = "no op-count summary for this workload"
+        return out
+    flops = w["flops_per_vertex"] * per["vertices"]
+    special = w["special_per_vertex"] * per["vertices"]
+    out.update({"achieved": flops / (kms * 1e-3) / 1e12, "flops_per_launch": flops,
+                "work_per_vertex": {"flops": w["flops_per_vertex"], "special": w["special_per_vertex"],
+                                    "int": w["int_per_vertex"], "source": "profiles/op_counts.md"},
+                "special_frac": special / (kms * 1e-3) / 1e12 / peak_mufu})
+    out["frac"] = out["achieved"] / peak_fp32
+    return out
+
+
+def time_workload(ctx, S, torch, name, flush, steps):
+    """Compact timing of a secondary workload: paths/s, step and kernel ms,
+    FP32 fraction."""
+    sc, sp, N = make_workload(name, S)
+    prep = ctx.prepare(sc, sp)
+    h = torch.empty(S.histogram_shape(sc), dtype=torch.float64, device="cuda")
+    if sc.sensor.kind != S.SENSOR_PINHOLE:
+        ctx.autotune(sc, sp)
+    for _ in range(3):
+        prep.render(out=h)
+    torch.cuda.synchronize()
+    ctx.set_kernel_timing(True)
+    st, kt, per = time_steps(ctx, torch, lambda: prep.render(out=h), steps, flush)
+    ctx.set_kernel_timing(False)
+    ctx.set_launch(0)
+    t = statistics.fmean(st)
+    roof = roofline(per, statistics.fmean(kt), name)
+    del h
+    return {"paths_per_step": N, "ms_per_step": t, "paths_per_s": N / (t * 1e-3),
+            "kernel_ms": roof["kernel_ms"], "fp32_frac": roof["frac"]}
+
+
+def run_studies(ctx, S, torch, flush, sc, sp, N, path):
+    """Every side study, written to `path` (one JSON object)."""
+    out = {}
+    sc16, sp16 = S.cube_workload(paths=1 << 16, seed=0)
+    sp16.flags |= S.FLAG_REBUILD_TABLE
+    for _ in range(3):
+        ctx.render(sc16, sp16)
+    torch.cuda.synchronize()
+    t16, _, _ = time_steps(ctx, torch, lambda: ctx.render(sc16, sp16), 20, flush, kernel_timing=False)
+    out["cube_as_configured_2e16"] = {"paths": 1 << 16, "ms_per_render": statistics.median(t16),
+                                      "paths_per_s": (1 << 16) / (statistics.median(t16) * 1e-3)}
+    cdf = ctx.build_table(sc, sp)
+    ctx.set_kernel_timing(True)
+    tt, kt, _ = time_steps(ctx, torch, lambda: ctx.build_table(sc, sp, out=cdf), 20, flush)
+    ctx.set_kernel_timing(False)
+    out["table_build"] = {"kernel_ms": statistics.median(kt), "call_ms": statistics.median(tt),
+                          "bytes": cdf.numel() * 4}
+    out["mse_time_spheres_512"] = mse_time_spheres(ctx, S, torch)
+    out["mse_time_box_camera"] = mse_time_camera(ctx, S, torch)
+    out["mse_time_gated"] = mse_time_gated(ctx, S, torch)
+    out["mse_time_gated_dense"] = mse_time_gated_dense(ctx, S, torch)
+    out["two_peak_response"] = two_peak_response(ctx, S, torch)
+    out["mse_time_cube"] = mse_time(ctx, S, torch)
+    out["batched"] = batched_compare(ctx, S, torch)
+    out["differentiable_32x32"] = differentiable_step(ctx, S, torch, flush)
+    scb, spb, Nb = make_workload("box_camera", S)
+    out["frames_in_flight_box_camera"] = frames_in_flight(ctx, S, torch, scb, spb, Nb, "the 64x64 box frame")
+    out["frames_in_flight_cube_2e16"] = frames_in_flight(
+        ctx, S, torch, sc16, sp16, 1 << 16, "the unit cube as configured, 2^16 paths per render")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
 
 
 def main():
@@ -733,18 +877,18 @@ def main():
         pg = dist
     ctx = capi.Context(local)
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MiB > L2
-    if args.only in ("batched", "differentiable", "spheres"):
+    if args.only in ("batched", "differentiable"):
         run = {"batched": lambda: batched_compare(ctx, S, torch),
-               "differentiable": lambda: differentiable_step(ctx, S, torch, flush),
-               "spheres": lambda: spheres_frame(ctx, S, torch, flush)}[args.only]
+               "differentiable": lambda: differentiable_step(ctx, S, torch, flush)}[args.only]
+        res = run()
         if rank == 0:
-            print(json.dumps({"only": args.only, **run()}), flush=True)
+            print(json.dumps({"only": args.only, **res}), flush=True)
         ctx.close()
         if pg is not None:
             pg.destroy_process_group()
         return 0
     sc, sp, N = make_workload(args.workload, S)
-    general = args.workload == "box_camera"
+    camera = sc.sensor.kind == S.SENSOR_PINHOLE
     offset = sharding.path_offset(rank, N)
     prepared = ctx.prepare(sc, sp)  # structs marshalled once, as a renderer loop would
     # under torchrun the all-reduce of step k - 1 runs while step k renders
@@ -756,7 +900,8 @@ def main():
         prepared.render(out=hist, path_offset=offset)
         pipe.end_step(hist)
 
-    tuned_block = ctx.autotune(sc, sp)
+    # a camera always runs 512-thread blocks; the point sensor's block is tuned
+    tuned_block = 512 if camera else ctx.autotune(sc, sp)
     for _ in range(args.warmup):
         step()
     pipe.finish()
@@ -789,20 +934,24 @@ def main():
         return 0
     K = args.steps
     kms = statistics.fmean(kern_ms)
-    roof = roofline(per, kms, general, args.workload, N)
+    roof = roofline(per, kms, args.workload, paths=N)
     if args.only == "timed":
         print(json.dumps({"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws,
                           "steps": K, "warmup": args.warmup, "ms_per_step": t_step,
-                          "workload": args.workload, "roofline": roof, "block": tuned_block,
+                          "config": {"workload": args.workload}, "roofline": roof,
                           "note": "timed steps only"}), flush=True)
         ctx.close()
         return 0
+    del pipe
+    torch.cuda.empty_cache()
 
-    # ---- end to end through the C ABI with host buffers
-    # queued host renders: the copy of frame i overlaps the render of frame
-    # i + 1; every frame's histogram reaches pinned host memory
-    hh = [torch.zeros(S.histogram_shape(sc), dtype=torch.float64).pin_memory() for _ in range(2)]
-    ne = max(3, min(args.steps, 20))
+    # ---- end to end through the C ABI with host buffers: queued host renders
+    # (darts_render_host_async), the copy of frame i back to pinned host
+    # memory overlapping the render of frame i + 1; every frame's histogram
+    # reaches the host
+    shape = S.histogram_shape(sc)
+    hh = [torch.empty(shape, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    ne = max(3, min(K, 8))
     prepared.render_host(hh[0])
     te = time.perf_counter()
     for i in range(ne):
@@ -819,80 +968,39 @@ def main():
     h2d = (ctypes.sizeof(cs) + ctypes.sizeof(capi.darts_sampling)
            + len(sc.emitters) * ctypes.sizeof(capi.darts_emitter) + 40 * len(sc.geometry.spheres))
     e2e = {"value": N * ne / te, "unit": "paths/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": hh[0].numel() * 8,
+           "d2h_bytes_per_step": hh[0].numel() * 8, "frames": ne,
            "synchronous_value": N * ne / ts_,
-           "note": "darts_render_host_async through the prepared scene (Context.prepare): scene/sampling "
-                   "structs marshalled into the launches, each frame's histogram copied back to pinned host "
-                   "memory on a copy stream that overlaps the next frame's render, one synchronisation "
-                   "after the last frame; synchronous_value: darts_render_host, synchronised per frame"}
+           "call": "darts_render_host_async (queued; one darts_sync after the last frame); "
+                   "synchronous_value: darts_render_host"}
+    del hh
+    ctx.sync()
+    # the device histograms of the host renders are the context's: released
+    # with the context below
 
-    extra = {}
-    # ---- the other workload: the saturated cube (2^24 paths) or the camera frame
-    other = "cube" if args.workload == "box_camera" else "box_camera"
-    sc2, sp2, N2 = make_workload(other, S)
-    h2 = torch.zeros(S.histogram_shape(sc2), dtype=torch.float64, device="cuda")
-    ctx.autotune(sc2, sp2)
-    for _ in range(3):
-        ctx.render(sc2, sp2, out=h2)
-    torch.cuda.synchronize()
-    ctx.set_kernel_timing(True)
-    s2, k2, per2 = time_steps(ctx, torch, lambda: ctx.render(sc2, sp2, out=h2), 20, flush)
-    ctx.set_kernel_timing(False)
-    t2 = statistics.fmean(s2)
-    extra[other] = {"workload": WORKLOADS[other], "paths_per_step": N2, "ms_per_step": t2,
-                    "paths_per_s": N2 / (t2 * 1e-3),
-                    "roofline": roofline(per2, statistics.fmean(k2), other == "box_camera", other, N2)}
-
-    extra["spheres_512"] = spheres_frame(ctx, S, torch, flush)
-
-    # ---- the cube as configured: 2^16 paths per render (latency-bound)
-    sc16, sp16 = S.cube_workload(paths=1 << 16, seed=0)
-    sp16.flags |= S.FLAG_REBUILD_TABLE
-    for _ in range(3):
-        ctx.render(sc16, sp16)
-    torch.cuda.synchronize()
-    t16, _, _ = time_steps(ctx, torch, lambda: ctx.render(sc16, sp16), 20, flush, kernel_timing=False)
-    extra["cube_as_configured_2e16"] = {"paths": 1 << 16, "ms_per_render": statistics.median(t16),
-                                        "paths_per_s": (1 << 16) / (statistics.median(t16) * 1e-3)}
-    # the direction table alone (darts_build_table: one launch, no outputs to zero)
-    cdf = ctx.build_table(sc, sp)
-    ctx.set_kernel_timing(True)
-    tt, kt, _ = time_steps(ctx, torch, lambda: ctx.build_table(sc, sp, out=cdf), 20, flush)
-    ctx.set_kernel_timing(False)
-    extra["table_build"] = {"workload": "direction table of the benchmark medium, %dx%dx%d" %
-                                        (sp.table_n_rho, sp.table_n_s, sp.table_n_mu),
-                            "kernel_ms": statistics.median(kt), "call_ms": statistics.median(tt),
-                            "bytes": cdf.numel() * 4,
-                            "note": "kernel_ms: CUDA events around the table kernel; call_ms: the whole "
-                                    "darts_build_table call from Python, host-bound at this size"}
-    ctx.set_launch(0)
-
-    if not args.no_mse:
-        extra["mse_time_box_camera"] = mse_time_camera(ctx, S, torch)
-        extra["mse_time_gated"] = mse_time_gated(ctx, S, torch)
-        extra["mse_time_gated_dense"] = mse_time_gated_dense(ctx, S, torch)
-        extra["two_peak_response"] = two_peak_response(ctx, S, torch)
-        extra["mse_time_cube"] = mse_time(ctx, S, torch)
-    extra["batched"] = batched_compare(ctx, S, torch)
-    extra["differentiable_32x32"] = differentiable_step(ctx, S, torch, flush)
-    extra["frames_in_flight"] = frames_in_flight(ctx, S, torch, sc, sp, N, "the timed camera frame")
-    extra["frames_in_flight_cube_2e16"] = frames_in_flight(
-        ctx, S, torch, sc16, sp16, 1 << 16, "the unit cube as configured, 2^16 paths per render")
+    secondary = {}
+    for other in ("box_camera", "cube"):
+        if other != args.workload:
+            secondary[other] = time_workload(ctx, S, torch, other, flush,
+                                             200 if other == "box_camera" else 20)
+    if args.studies:
+        run_studies(ctx, S, torch, flush, sc, sp, N, args.studies)
     cpu = cpu_baseline(args.workload) if ws == 1 else None
 
     line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws, "steps": K,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "paths_per_gpu_per_step": N,
-                       "block": tuned_block, "grid": "one CTA per SM (persistent)",
-                       "l2": "256 MiB buffer written between timed steps (flush)",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
+                       "paths_per_gpu_per_step": N, "block": tuned_block,
+                       "grid": "one CTA per SM (persistent)",
+                       "l2": "256 MiB buffer written between timed steps (flush); histogram of "
+                             "%.3f GB per step" % (math.prod(S.histogram_shape(sc)) * 8e-9),
                        "parallelism": f"path-id shards x{ws}, FP64 histogram all-reduce of step k-1 "
-                                      f"overlapped with the render of step k" if ws > 1
-                       else "single GPU"},
+                                      f"overlapped with the render of step k" if ws > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 2 * K,
-            "clocks": clk, "wall_s_timed_region": wall}
-    line.update(extra)
+            "gpu_launches": 2 * K, "clocks": clk, "wall_s_timed_region": wall,
+            "secondary": secondary}
+    if args.studies:
+        line["studies"] = args.studies
     print(json.dumps(line), flush=True)
     ctx.close()
     if pg is not None:

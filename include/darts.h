@@ -377,17 +377,21 @@ darts_status darts_autotune(darts_ctx* ctx, const darts_scene* scene,
  *
  * Runs on the calling thread's current device, ordered on cuda_stream
  * (cudaStream_t, NULL = legacy default stream).  The caller passes the
- * outputs, exactly as for darts_render: hist_dev[n_bins] (overwritten) and
- * optional sumsq_dev[n_bins].  No per-path probe, no statistics, no table
- * cache: the direction table is rebuilt on every call.
+ * outputs, exactly as for darts_render: hist_dev (overwritten) and optional
+ * sumsq_dev, each [n_bins] for a point sensor and [height][width][n_bins]
+ * for a pinhole camera.  No per-path probe, no statistics, no table cache:
+ * the direction table is rebuilt on every call.
  *
  * Scratch: one file-scope device array of 4 MiB, present on every GPU that
  * loads the library until the process exits.  It holds the path counter and
  * statistics (256 B), the direction table (at most 256 KiB:
  * table_n_rho * table_n_s * darts_table_row_stride(table_n_mu) <= 65536
- * floats) and the block partials (number of SMs * 2 * n_bins doubles, at most
- * 4 MiB - 256 KiB - 256 B, i.e. n_bins <= 1616 on a 152-SM GB300).  Larger
- * requests return DARTS_ERR_UNSUPPORTED before anything is launched.
+ * floats) and, for a point sensor whose histogram tiles fit in shared
+ * memory, the block partials (number of SMs * 2 * n_bins doubles, at most
+ * 4 MiB - 256 KiB - 256 B).  A camera, and a point sensor with too many bins
+ * for the tiles, add straight into the zeroed outputs and need no partials.
+ * Requests beyond these limits return DARTS_ERR_UNSUPPORTED before anything
+ * is enqueued.
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) and caches it; make that first call before any
@@ -397,7 +401,8 @@ darts_status darts_autotune(darts_ctx* ctx, const darts_scene* scene,
  * caller.  Device-side non-finite contributions are zeroed as in
  * darts_render but are not reported (there is no context to sync).
  * Returns DARTS_ERR_INVALID_ARG for invalid scenes or a NULL hist_dev,
- * DARTS_ERR_CUDA when a launch or the set-up fails. */
+ * DARTS_ERR_CUDA when a launch or the set-up fails; either way the CUDA
+ * runtime's last error is cleared, so a later call is not affected. */
 darts_status darts_render_static(const darts_scene* scene, const darts_sampling* sampling,
                                  double* hist_dev, double* sumsq_dev, uint64_t path_offset,
                                  void* cuda_stream);

@@ -97,6 +97,9 @@ def load():
     lib.orc_trace_paths.restype = C.c_int
     lib.orc_render.argtypes = [sp, C.c_int, dp, C.c_uint64, C.c_uint64, C.c_int, dp, dp, dp]
     lib.orc_render.restype = C.c_int
+    lib.orc_render_window.argtypes = [sp, C.c_int, dp, C.c_uint64, C.c_uint64, C.c_int, C.c_uint64,
+                                      C.c_uint64, dp, dp, dp]
+    lib.orc_render_window.restype = C.c_int
     lib.orc_ris_step.argtypes = [sp, C.c_uint64, C.c_int, dp, dp, C.c_double, C.c_double, dp, dp,
                                  C.POINTER(C.c_int32), C.POINTER(C.c_int32), dp]
     lib.orc_ris_step.restype = C.c_int
@@ -330,25 +333,33 @@ STAT_NAMES = ("paths", "vertices", "connections", "connections_nonempty", "ris_c
               "early_exits", "all_invalid", "escapes", "samples", "rejected")
 
 
-def render(scene, sampling, method=ORC_DARTS, n_paths=None, offset=0, threads=None, cdf=None):
+def render(scene, sampling, method=ORC_DARTS, n_paths=None, offset=0, threads=None, cdf=None,
+           window=None):
     """Histogram [elements * n_bins] (time-integrated fluence per bin, unit
     energy; one row of n_bins per camera pixel), sum of squared per-path bin
     contributions, and event statistics.  n_paths defaults to every path of
-    every element."""
+    every element.  window = (first element, element count) keeps only those
+    rows (every traced path must fall in them): a sample of a large frame
+    without full-frame buffers."""
     s = make_scene(scene, sampling)
     elements = s.width * s.height if s.sensor_kind == 1 else 1
     n = sampling.paths_per_element * elements if n_paths is None else n_paths
     if method in (ORC_DARTS, ORC_DARTS_FULL_GATE) and cdf is None:
         cdf = build_table(scene, sampling)
     threads = threads or (os.cpu_count() or 1)
-    hist = np.zeros(s.n_bins * elements)
-    sumsq = np.zeros(s.n_bins * elements)
+    rows = elements if window is None else int(window[1])
+    hist = np.zeros(s.n_bins * rows)
+    sumsq = np.zeros(s.n_bins * rows)
     stats = np.zeros(len(STAT_NAMES))
     cdf_c = None if cdf is None else np.ascontiguousarray(cdf, dtype=np.float64)
-    rc = load().orc_render(C.byref(s), method, _ptr(cdf_c), n, offset, threads, _ptr(hist),
-                           _ptr(sumsq), _ptr(stats))
+    if window is None:
+        rc = load().orc_render(C.byref(s), method, _ptr(cdf_c), n, offset, threads, _ptr(hist),
+                               _ptr(sumsq), _ptr(stats))
+    else:
+        rc = load().orc_render_window(C.byref(s), method, _ptr(cdf_c), n, offset, threads,
+                                      int(window[0]), rows, _ptr(hist), _ptr(sumsq), _ptr(stats))
     if rc != 0:
-        raise ValueError(f"orc_render rejected the scene ({rc})")
+        raise ValueError(f"orc_render rejected the scene or window ({rc})")
     return hist, sumsq, dict(zip(STAT_NAMES, stats.tolist()))
 
 

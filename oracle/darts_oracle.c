@@ -28,6 +28,29 @@
 #define M_PI 3.14159265358979323846
 #endif
 
+/* Op-count mode (ORC_OPCOUNT: this file compiled as C++ with the counting
+ * number type of opcount.hpp) tallies the arithmetic of the forward
+ * estimator only.  Checker bookkeeping -- decision margins, conditioning
+ * numbers, event statistics, flags -- and the adjoint's score terms still
+ * run but are not counted.  Outside that mode these are plain statements. */
+#ifdef ORC_OPCOUNT
+#define ORC_NOT_COUNTED(stmt) \
+  do {                        \
+    ++orc_oc::tally.paused;   \
+    stmt;                     \
+    --orc_oc::tally.paused;   \
+  } while (0)
+#define ORC_COUNT_PHILOX() orc_oc::bump(orc_oc::PHILOX)
+typedef orc_oc_plain orc_tally;
+#else
+#define ORC_NOT_COUNTED(stmt) \
+  do {                        \
+    stmt;                     \
+  } while (0)
+#define ORC_COUNT_PHILOX() ((void)0)
+typedef double orc_tally;
+#endif
+
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10, written from its published definition (Salmon, Moraes,    */
 /* Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11): ten   */
@@ -36,6 +59,7 @@
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
   uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
   uint32_t k0 = key[0], k1 = key[1];
+  ORC_COUNT_PHILOX();
   for (int round = 0; round < 10; ++round) {
     uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
     uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
@@ -485,7 +509,7 @@ typedef struct {
   uint8_t* dec;   /* [K][4] */
   double* margin; /* [K]    */
   /* statistics */
-  double n_vert, n_conn, n_conn_nonempty, n_cand, n_early, n_invalid, n_escape;
+  orc_tally n_vert, n_conn, n_conn_nonempty, n_cand, n_early, n_invalid, n_escape;
   /* per-connection output for binned methods (plain / vanilla) */
   int n_out;
   int32_t out_bin[1024];
@@ -494,15 +518,15 @@ typedef struct {
   double score[3];
   int dec_sel;
   /* largest (L + S_hi) / (S_hi - S_lo) over the connections */
-  double cond;
+  orc_tally cond;
   /* sum over the MIS directions of gamma n_mu / (2 pi p_mix): the relative
    * change of the path's throughput per unit error of the table's CDF values */
-  double tabcond;
+  orc_tally tabcond;
   /* weight of a DARTS path in its bin: B / N_e, or sum W / (N_e W_b) */
   double wpath;
   /* connection samples with a time, and those whose time has zero weight
    * (outside the gate, in a zero-weight bin, or outside a DARTS path's bin) */
-  double n_samples, n_rejected;
+  orc_tally n_samples, n_rejected;
   /* the path's emitter point and sensor element */
   const emit_pt* E;
   int elem;
@@ -532,9 +556,11 @@ static void pick_emitter(const orc_scene* sc, uint64_t id, emit_pt* e) {
   e->wsel = m->energy > 0.0 ? tot / m->energy : 0.0;
 }
 
-static void rec_margin(path_rec* pr, int k, double m) {
+static void rec_margin_at(path_rec* pr, int k, double m) {
   if (pr->margin && m < pr->margin[k]) pr->margin[k] = m;
 }
+/* decision margins are checker bookkeeping (argument included) */
+#define rec_margin(pr, k, m) ORC_NOT_COUNTED(rec_margin_at(pr, k, m))
 
 /* Direction at vertex k (Sec. 5.1): one-sample MIS (balance heuristic) of the
  * EDA table and the base strategy -- HG about the previous direction for
@@ -595,7 +621,7 @@ static double darts_direction(const orc_scene* sc, const double* cdf, int k, uin
     mu_bin = i;
   }
   double p_mix = gamma * pE + (1.0 - gamma) * pB;
-  if (gamma > 0.0) pr->tabcond += gamma * nb / (2.0 * M_PI) / p_mix;
+  if (gamma > 0.0) ORC_NOT_COUNTED(pr->tabcond += (orc_tally)(gamma * nb / (2.0 * M_PI) / p_mix));
   double f = (k == 0) ? 1.0 : orc_hg_pdf(mu_b, sc->g);
   if (pr->dec) {
     pr->dec[k * 4 + 2] = (uint8_t)mis_choice;
@@ -623,7 +649,7 @@ static double darts_connect(const orc_scene* sc, int k, double beta, const doubl
   rec_margin(pr, k, fabs(S_hi - S_lo) / dmax(S_hi, 1e-300));
   if (!(S_hi > S_lo)) return 0.0;
   double Wd = S_hi - S_lo;
-  if ((L + S_hi) / Wd > pr->cond) pr->cond = (L + S_hi) / Wd;
+  ORC_NOT_COUNTED(if ((L + S_hi) / Wd > pr->cond) pr->cond = (orc_tally)((L + S_hi) / Wd));
   double S, pS;
   if (!uniform_S) {
     double dS = -log1p(-(1.0 - exp(-st * Wd)) * u3) / st;
@@ -641,13 +667,13 @@ static double darts_connect(const orc_scene* sc, int k, double beta, const doubl
   double xell[3] = {x[0] + w[0] * t, x[1] + w[1] * t, x[2] + w[2] * t};
   double cos_s = 0.0;
   for (int i = 0; i < 3; ++i) cos_s += (xell[i] - E->y[i]) / r1 * (-w[i]);
-  if ((S - C) / C < 1.0 / 4096.0) pr->flags |= ORC_FLAG_NEAR_DEGENERATE;
+  ORC_NOT_COUNTED(if ((S - C) / C < 1.0 / 4096.0) pr->flags |= ORC_FLAG_NEAR_DEGENERATE);
   double Ie = emit_intensity(E, xell);
   double vis = (sc->n_spheres && !visible(sc, xell, E->y)) ? 0.0 : 1.0;
   double c = beta * sc->sigma_s * exp(-st * S) * orc_hg_pdf(cos_s, sc->g) * Ie * vis / (r1 * r1) / pt;
   *ok = 1;
   *S_out = S;
-  pr->score[2] = hg_dlog_dg(cos_s, sc->g);
+  ORC_NOT_COUNTED(pr->score[2] = hg_dlog_dg(cos_s, sc->g));
   return c;
 }
 
@@ -991,7 +1017,7 @@ static void trace_darts(const orc_scene* sc, const double* cdf, uint64_t id, pat
     if (!fixed) {
       double wn[3], mu_b;
       beta *= darts_direction(sc, cdf, k, id, a, C, SM, wprev, wn, &mu_b, pr);
-      if (k >= 1) gsum += hg_dlog_dg(mu_b, sc->g);
+      if (k >= 1) ORC_NOT_COUNTED(gsum += hg_dlog_dg(mu_b, sc->g));
       for (int i = 0; i < 3; ++i) w[i] = wn[i];
     }
     int32_t hit;
@@ -1411,6 +1437,8 @@ typedef struct {
   int method;
   const double* cdf;
   uint64_t first, count;
+  uint64_t elem_first, n_elem;  /* histogram rows held: elements [elem_first, +n_elem) */
+  int outside;                  /* a path of an element outside the rows */
   double* hist;
   double* sumsq;
   double stats[ORC_N_STATS];
@@ -1435,12 +1463,17 @@ static void* render_worker(void* p) {
         wk->grad_sq[j] += g3[j] * g3[j];
       }
     }
+    if ((uint64_t)pr->elem < wk->elem_first || (uint64_t)pr->elem - wk->elem_first >= wk->n_elem) {
+      wk->outside = 1;
+      continue;
+    }
+    size_t row = (size_t)((uint64_t)pr->elem - wk->elem_first) * B;
     if (wk->method == ORC_DARTS) {
       double c = pr->wpath * pr->contrib;
-      wk->hist[pr->bin] += c;
-      wk->sumsq[pr->bin] += c * c;
+      size_t at = row + (size_t)(pr->bin - pr->elem * B);
+      wk->hist[at] += c;
+      wk->sumsq[at] += c * c;
     } else {
-      size_t row = (size_t)pr->elem * B;
       for (int j = 0; j < pr->n_out; ++j) tmp[pr->out_bin[j]] += inv_n * pr->out_c[j];
       for (int j = 0; j < pr->n_out; ++j) {
         int b = pr->out_bin[j];
@@ -1468,13 +1501,20 @@ static void* render_worker(void* p) {
 }
 
 static int run_threads(const orc_scene* sc, int method, const double* cdf, uint64_t n_paths,
-                       uint64_t offset, int n_threads, double* hist, double* sumsq,
+                       uint64_t offset, int n_threads, uint64_t elem_first, uint64_t n_elem,
+                       double* hist, double* sumsq,
                        double* stats, const double* dLdh, double* grad3, double* grad3_sq) {
   if (!scene_ok(sc, method, cdf)) return -1;
   if (n_threads < 1) n_threads = 1;
   if ((uint64_t)n_threads > n_paths && n_paths > 0) n_threads = (int)n_paths;
   int B = sc->n_bins;
-  size_t HB = (size_t)B * (sc->sensor_kind == 1 ? (size_t)sc->width * sc->height : 1);
+  uint64_t elements = sc->sensor_kind == 1 ? (uint64_t)sc->width * sc->height : 1;
+  if (n_elem == 0) {  /* every element */
+    elem_first = 0;
+    n_elem = elements;
+  }
+  if (elem_first >= elements || n_elem > elements - elem_first) return -1;
+  size_t HB = (size_t)B * (size_t)n_elem;
   work_t* wk = (work_t*)calloc((size_t)n_threads, sizeof(work_t));
   pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
   if (!wk || !th) return -2;
@@ -1487,12 +1527,18 @@ static int run_threads(const orc_scene* sc, int method, const double* cdf, uint6
     wk[t].first = start;
     wk[t].count = per + ((uint64_t)t < rem ? 1 : 0);
     start += wk[t].count;
+    wk[t].elem_first = elem_first;
+    wk[t].n_elem = n_elem;
     wk[t].hist = (double*)calloc(HB, sizeof(double));
     wk[t].sumsq = (double*)calloc(HB, sizeof(double));
     wk[t].dLdh = dLdh;
     pthread_create(&th[t], NULL, render_worker, &wk[t]);
   }
-  for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+  int outside = 0;
+  for (int t = 0; t < n_threads; ++t) {
+    pthread_join(th[t], NULL);
+    outside |= wk[t].outside;
+  }
   if (hist) memset(hist, 0, sizeof(double) * HB);
   if (sumsq) memset(sumsq, 0, sizeof(double) * HB);
   if (stats) memset(stats, 0, sizeof(double) * ORC_N_STATS);
@@ -1513,18 +1559,48 @@ static int run_threads(const orc_scene* sc, int method, const double* cdf, uint6
   }
   free(wk);
   free(th);
-  return 0;
+  return outside ? -3 : 0;
 }
 
 int orc_render(const orc_scene* sc, int method, const double* cdf, uint64_t n_paths,
                uint64_t offset, int n_threads, double* hist, double* sumsq, double* stats) {
-  return run_threads(sc, method, cdf, n_paths, offset, n_threads, hist, sumsq, stats, NULL,
-                     NULL, NULL);
+  return run_threads(sc, method, cdf, n_paths, offset, n_threads, 0, 0, hist, sumsq, stats,
+                     NULL, NULL, NULL);
+}
+
+int orc_render_window(const orc_scene* sc, int method, const double* cdf, uint64_t n_paths,
+                      uint64_t offset, int n_threads, uint64_t elem_first, uint64_t n_elem,
+                      double* hist, double* sumsq, double* stats) {
+  if (n_elem == 0) return -1;
+  return run_threads(sc, method, cdf, n_paths, offset, n_threads, elem_first, n_elem, hist,
+                     sumsq, stats, NULL, NULL, NULL);
 }
 
 int orc_adjoint(const orc_scene* sc, const double* cdf, uint64_t n_paths, uint64_t offset,
                 int n_threads, const double* dLdh, double* grad3, double* grad3_sq) {
   if (!dLdh || !grad3) return -1;
-  return run_threads(sc, ORC_DARTS, cdf, n_paths, offset, n_threads, NULL, NULL, NULL, dLdh,
-                     grad3, grad3_sq);
+  return run_threads(sc, ORC_DARTS, cdf, n_paths, offset, n_threads, 0, 0, NULL, NULL, NULL,
+                     dLdh, grad3, grad3_sq);
 }
+
+#ifdef ORC_OPCOUNT
+/* Per-path tallies of the forward estimator's arithmetic (op-count mode
+ * only): out[i][ORC_OC_TALLIES] for path first + i, in the order of
+ * opcount.hpp (add, mul, div, sqrt, cmp, exp, log, trig, pow, philox), and
+ * the path's vertex count in nvert[i].  Single-threaded. */
+int orc_opcount_paths(const orc_scene* sc, int method, const double* cdf, uint64_t first,
+                      uint32_t count, uint64_t* out, double* nvert) {
+  if (!scene_ok(sc, method, cdf)) return -1;
+  path_rec* pr = (path_rec*)malloc(sizeof(path_rec));
+  if (!pr) return -2;
+  for (uint32_t i = 0; i < count; ++i) {
+    memset(pr, 0, sizeof(*pr));
+    memset(&orc_oc::tally, 0, sizeof(orc_oc::tally));
+    trace_one(sc, method, cdf, first + i, pr, NULL, NULL);
+    for (int j = 0; j < orc_oc::N; ++j) out[(size_t)i * orc_oc::N + j] = orc_oc::tally.n[j];
+    if (nvert) nvert[i] = pr->n_vert;
+  }
+  free(pr);
+  return 0;
+}
+#endif

@@ -178,6 +178,15 @@ int orc_render(const orc_scene* sc, int method, const double* cdf,
                uint64_t n_paths, uint64_t offset, int n_threads,
                double* hist, double* sumsq, double* stats);
 
+/* orc_render restricted to the sensor elements [elem_first, elem_first +
+ * n_elem): hist/sumsq are [n_elem][n_bins] (row i = element elem_first + i),
+ * so a sample of a large camera frame needs no full-frame buffers.  Every
+ * traced path must belong to the window (returns -3 otherwise). */
+int orc_render_window(const orc_scene* sc, int method, const double* cdf,
+                      uint64_t n_paths, uint64_t offset, int n_threads,
+                      uint64_t elem_first, uint64_t n_elem,
+                      double* hist, double* sumsq, double* stats);
+
 /* Geometry test hooks: nearest surface along a ray from inside the medium
  * box (returns the distance; *kind = 0 open boundary, 1 wall, 2 sphere;
  * normal[3] the surface normal facing the ray's origin); pinhole ray of a
@@ -197,6 +206,14 @@ void orc_sample_emitter(const orc_scene* sc, uint64_t id, const double q[3], dou
 int orc_adjoint(const orc_scene* sc, const double* cdf, uint64_t n_paths,
                 uint64_t offset, int n_threads, const double* dLdh,
                 double* grad3, double* grad3_sq);
+
+/* Op-count mode only (the library oracle/opcount.py builds with
+ * -DORC_OPCOUNT): per-path tallies of the forward estimator's arithmetic,
+ * out[count][ORC_OC_TALLIES] = add, mul, div, sqrt, cmp, exp, log, trig, pow,
+ * Philox blocks; nvert[count] (optional) the vertices of each path. */
+#define ORC_OC_TALLIES 10
+int orc_opcount_paths(const orc_scene* sc, int method, const double* cdf, uint64_t first,
+                      uint32_t count, uint64_t* out, double* nvert);
 
 #ifdef __cplusplus
 }

@@ -1330,6 +1330,14 @@ struct StaticDevice {
 StaticDevice g_static_dev[kStaticMaxDevices];
 std::mutex g_static_mutex;
 
+// A failed CUDA call of the static path: the runtime's last error is taken
+// here, as cuda_fail does for context calls, so that it cannot resurface at a
+// later, valid launch on this thread.
+darts_status static_cuda_fail(cudaError_t e) {
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? DARTS_ERR_OOM : DARTS_ERR_CUDA;
+}
+
 // Per-device set-up: device address of the scratch array and launch limits.
 cudaError_t static_setup(int dev, StaticDevice** out) {
   std::lock_guard<std::mutex> lock(g_static_mutex);
@@ -1363,22 +1371,18 @@ extern "C" darts_status darts_render_static(const darts_scene* scene, const dart
   if (scene->gate.weights) return DARTS_ERR_UNSUPPORTED;  // no scratch for the weight tables
   if (sampling->flags & DARTS_FLAG_ACCUMULATE) return DARTS_ERR_UNSUPPORTED;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return DARTS_ERR_CUDA;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return static_cuda_fail(e);
   if (dev < 0 || dev >= kStaticMaxDevices) return DARTS_ERR_UNSUPPORTED;
   StaticDevice* sd = nullptr;
-  if (static_setup(dev, &sd) != cudaSuccess) return DARTS_ERR_CUDA;
+  e = static_setup(dev, &sd);
+  if (e != cudaSuccess) return static_cuda_fail(e);
   const cudaStream_t stream = (cudaStream_t)cuda_stream;
   const int B = scene->gate.n_bins;
   const size_t hb = elements_of(scene) * (size_t)B * sizeof(double);
   unsigned long long* header = reinterpret_cast<unsigned long long*>(sd->base);
   float* table = reinterpret_cast<float*>(sd->base + kStaticHeaderBytes);
   double* partials = reinterpret_cast<double*>(sd->base + kStaticHeaderBytes + kStaticTableBytes);
-
-  // sizes beyond the static maximum are rejected before anything is launched
-  const size_t table_bytes = (size_t)sampling->table_n_rho * sampling->table_n_s *
-                             row_stride_of(sampling->table_n_mu) * sizeof(float);
-  const size_t partial_bytes = (size_t)sd->sm_count * 2 * (size_t)B * sizeof(double);
-  if (table_bytes > kStaticTableBytes || partial_bytes > kStaticPartialBytes) return DARTS_ERR_UNSUPPORTED;
 
   tmp.device = dev;
   tmp.stream = stream;
@@ -1387,19 +1391,12 @@ extern "C" darts_status darts_render_static(const darts_scene* scene, const dart
   tmp.scratch = header;
   tmp.table = table;
 
-  // the array keeps the previous call's contents: reset counter, ticket, status, statistics
-  if (cudaMemsetAsync(header, 0, kStaticHeaderBytes, stream) != cudaSuccess) return DARTS_ERR_CUDA;
-  if (sampling->paths_per_element == 0) {
-    if (cudaMemsetAsync(hist_dev, 0, hb, stream) != cudaSuccess) return DARTS_ERR_CUDA;
-    if (sumsq_dev && cudaMemsetAsync(sumsq_dev, 0, hb, stream) != cudaSuccess) return DARTS_ERR_CUDA;
-    return DARTS_OK;
-  }
-  if (uses_table(sampling->method)) {
-    TableParams tp;
-    make_table_params(scene, sampling, &tp);
-    tp.cdf = table;
-    if (launch_table(tp, stream) != cudaSuccess) return DARTS_ERR_CUDA;
-  }
+  // Every size check comes before the first enqueued operation: a refused
+  // request leaves the stream, the outputs and the scratch untouched.
+  const bool with_table = uses_table(sampling->method);
+  const size_t table_bytes = (size_t)sampling->table_n_rho * sampling->table_n_s *
+                             row_stride_of(sampling->table_n_mu) * sizeof(float);
+  if (with_table && table_bytes > kStaticTableBytes) return DARTS_ERR_UNSUPPORTED;
   TraceParams P;
   make_trace_params(ctx, scene, sampling, &P);
   P.N = sampling->paths_per_element * elements_of(scene);
@@ -1411,12 +1408,28 @@ extern "C" darts_status darts_render_static(const darts_scene* scene, const dart
   bool tile;
   size_t smem;
   choose_launch(&tmp, sampling, P, false, &block, &tile, &smem);
-  if (!tile) {  // contributions go straight into the (zeroed) outputs
-    if (cudaMemsetAsync(hist_dev, 0, hb, stream) != cudaSuccess) return DARTS_ERR_CUDA;
-    if (sumsq_dev && cudaMemsetAsync(sumsq_dev, 0, hb, stream) != cudaSuccess) return DARTS_ERR_CUDA;
-  }
   if (smem > (size_t)tmp.smem_optin) return DARTS_ERR_UNSUPPORTED;
-  if (launch_trace(sampling->method, P, tmp.sm_count, block, false, tile, smem, stream) != cudaSuccess)
-    return DARTS_ERR_CUDA;
+  // block partials are used only by the shared-memory tiles of a point sensor
+  const size_t partial_bytes = (size_t)sd->sm_count * 2 * (size_t)B * sizeof(double);
+  if (tile && partial_bytes > kStaticPartialBytes) return DARTS_ERR_UNSUPPORTED;
+
+  // the array keeps the previous call's contents: reset counter, ticket, status, statistics
+  e = cudaMemsetAsync(header, 0, kStaticHeaderBytes, stream);
+  if (e != cudaSuccess) return static_cuda_fail(e);
+  if (sampling->paths_per_element == 0 || !tile) {  // zero outputs: empty render, or FP64 atomics into them
+    e = cudaMemsetAsync(hist_dev, 0, hb, stream);
+    if (e == cudaSuccess && sumsq_dev) e = cudaMemsetAsync(sumsq_dev, 0, hb, stream);
+    if (e != cudaSuccess) return static_cuda_fail(e);
+    if (sampling->paths_per_element == 0) return DARTS_OK;
+  }
+  if (with_table) {
+    TableParams tp;
+    make_table_params(scene, sampling, &tp);
+    tp.cdf = table;
+    e = launch_table(tp, stream);
+    if (e != cudaSuccess) return static_cuda_fail(e);
+  }
+  e = launch_trace(sampling->method, P, tmp.sm_count, block, false, tile, smem, stream);
+  if (e != cudaSuccess) return static_cuda_fail(e);
   return DARTS_OK;
 }

@@ -29,15 +29,34 @@ def test_profiles_match_the_current_kernels(bench, workload, paths):
     assert 0 < t < 16e6
 
 
-def test_roofline_arithmetic(bench):
-    per = {"vertices": 1000.0, "connections_nonempty": 100.0, "distance_steps": 10.0}
-    r = bench.roofline(per, 1.0, False, "cube", 1 << 24)
-    flops = (bench.FLOPS_PER_VERTEX * 1000 + bench.FLOPS_PER_CONNECTION * 100
-             + (bench.FLOPS_PER_DISTANCE_STEP + 8 * bench.FLOPS_PER_CANDIDATE) * 10)
+@pytest.mark.parametrize("workload", ["spheres_512", "box_camera", "cube"])
+def test_roofline_arithmetic(bench, workload):
+    """The numerator is the oracle's op count per vertex (profiles/op_counts.md)
+    times the vertices the launch reports, over the kernel time."""
+    per = {"vertices": 1000.0}
+    w = bench.algorithmic_work(workload)
+    assert w is not None and w["flops_per_vertex"] > 0
+    r = bench.roofline(per, 1.0, workload)
+    flops = w["flops_per_vertex"] * 1000
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert r["flops_per_launch"] == pytest.approx(flops)
     assert r["achieved"] == pytest.approx(flops / 1e-3 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    clock = bench.measured_peaks().get("sm_max_mhz", 2070.0)
+    assert r["peak"] == pytest.approx(152 * 128 * 2 * clock * 1e6 / 1e12)
+
+
+def test_bench_sample_pieces_cover_one_64th_of_the_frame(bench):
+    """The oracle's sample of the 512x512 frame: 8 whole rows spread over
+    the image, each a contiguous path range of its own window."""
+    from paper_2402_03106_gb300 import scenes as S
+    pieces, _ = bench.oracle_sample("spheres_512", S)
+    assert len(pieces) == 8
+    rows = set()
+    for first, count, (e0, ne) in pieces:
+        assert count == 512 * 64 and ne == 512 and first == e0 * 64 and e0 % 512 == 0
+        rows.add(e0 // 512)
+    assert len(rows) == 8 and sum(ne for _, _, (_, ne) in pieces) * 64 == 512 * 512
 
 
 def test_single_rank_combine_is_a_no_op():
