@@ -57,6 +57,8 @@ WORKLOADS = {
                     "U[0.2,0.8]); two point pulse emitters (1,3.5,1) t0=0 and (3,3.5,3) t0=1.5; 1000 bins on "
                     "[0,20); 64 spp (16.7 M paths per frame), K=100, N_RIS=8, table 16x8x256; 2.1 GB FP64 "
                     "histogram; one frame per GPU per step"),
+    "spheres_256": ("the spheres_512 scene seen at 256x256 (4.2 M paths, a 0.52 GB histogram): the small "
+                    "case of the same kernel for profiler captures"),
     "box_camera": ("64x64 pinhole camera (FOV 40 deg) at (1,1,-2.5) viewing a 2x2x2 box, five Lambertian "
                    "walls albedo 0.5 (front face open); medium from seed 0: sigma_s U[0.5,2], albedo "
                    "U[0.9,0.99], g U[0,0.9]; 0.3x0.3 Lambertian area pulse emitter on the ceiling, t0=0; "
@@ -65,7 +67,7 @@ WORKLOADS = {
              "(0.5,0.5,0.1) t0=0; point fluence sensor (0.5,0.5,0.9); 256 bins on [0.8,6.0); "
              "K=50 bounces, N_RIS=8, table 16x8x256; 2^24 paths per GPU per step"),
 }
-DEFAULT_STEPS = {"spheres_512": 30, "box_camera": 2000, "cube": 60}
+DEFAULT_STEPS = {"spheres_512": 30, "spheres_256": 60, "box_camera": 2000, "cube": 60}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 MUFU_PER_SM_CLK = 16
@@ -94,8 +96,9 @@ def parse():
 
 def make_workload(name, S):
     """(scene, sampling, paths per step) of a named workload."""
-    if name == "spheres_512":
-        sc = S.spheres_camera_scene(seed=0)
+    if name in ("spheres_512", "spheres_256"):
+        side = 512 if name == "spheres_512" else 256
+        sc = S.spheres_camera_scene(seed=0, width=side, height=side)
         sp = S.Sampling(seed=0, paths_per_element=64, max_bounces=100)
     elif name == "box_camera":
         sc, sp = S.box_camera_workload(seed=0)
@@ -114,6 +117,10 @@ def oracle_sample(name, S):
         row = 512 * 64
         pieces = [((32 + 64 * i) * row, row, ((32 + 64 * i) * 512, 512)) for i in range(8)]
         return pieces, "rows 32 + 64 i (i < 8) of the 512x512 frame: 1/64 of its pixels, 64 spp each"
+    if name == "spheres_256":
+        row = 256 * 64
+        pieces = [((16 + 32 * i) * row, row, ((16 + 32 * i) * 256, 256)) for i in range(8)]
+        return pieces, "rows 16 + 32 i (i < 8) of the 256x256 frame: 1/32 of its pixels, 64 spp each"
     if name == "box_camera":
         return [(0, n, None)], "one whole 64x64 frame (65536 paths)"
     return [(0, 1 << 22, None)], "2^22 paths of the 2^24-path step"
@@ -781,7 +788,8 @@ def roofline(per, kms, workload, traffic_workload=None, paths=None):
     lanes and the measured maximum clock.  Work per vertex comes from the
     oracle's op-count summary of the same workload; vertices from the
     launch's own event counts."""
-    w = algorithmic_work(workload)
+    # the 256x256 profiling case is the 512x512 scene: its op counts per vertex
+    w = algorithmic_work("spheres_512" if workload == "spheres_256" else workload)
     clock_mhz = measured_peaks().get("sm_max_mhz", 2070.0)
     peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
     peak_mufu = SM_COUNT * MUFU_PER_SM_CLK * clock_mhz * 1e6 / 1e12

@@ -248,6 +248,21 @@ darts_status darts_sync(darts_ctx* ctx);
 darts_status darts_build_table(darts_ctx* ctx, const darts_scene* scene,
                                const darts_sampling* sampling, float* cdf_dev);
 
+/* Install a direction table built elsewhere -- for example tabulated
+ * offline, as the paper does (Sec. 5.1, Fig. 6a) -- as the context's cached
+ * table for this scene's medium, gate and table dims.  cdf_dev is device
+ * memory, [table_n_rho * table_n_s][darts_table_row_stride(table_n_mu)]
+ * floats in the layout darts_build_table writes: per row the CDF over the
+ * n_mu cos-theta bins, entries 0 .. n_mu non-decreasing from 0 to 1 (the
+ * rest of a row is ignored).  It is copied on the context's stream, so the
+ * caller may release it after the next darts_sync.  Later renders of a
+ * scene with the same medium, gate and dims use it until a render with
+ * DARTS_FLAG_REBUILD_TABLE or another medium replaces it.  A table that is
+ * not a CDF biases the samples but never makes a kernel read outside it.
+ * Returns DARTS_ERR_INVALID_ARG for an invalid scene or a NULL pointer. */
+darts_status darts_load_table(darts_ctx* ctx, const darts_scene* scene,
+                              const darts_sampling* sampling, const float* cdf_dev);
+
 /* Row stride (floats) of the table written by darts_build_table. */
 int32_t darts_table_row_stride(int32_t table_n_mu);
 

@@ -38,7 +38,8 @@ EXPORTED = ("darts_create", "darts_destroy", "darts_set_stream", "darts_status_s
             "darts_render", "darts_render_host", "darts_get_stats", "darts_debug_paths",
             "darts_debug_philox", "darts_set_kernel_timing", "darts_last_kernel_ms",
             "darts_render_static", "darts_set_launch", "darts_autotune", "darts_adjoint",
-            "darts_render_batch", "darts_render_host_async", "darts_render_frames")
+            "darts_render_batch", "darts_render_host_async", "darts_render_frames",
+            "darts_load_table")
 BATCH_NO_GRAPH = 1
 
 
@@ -123,6 +124,7 @@ def load(path: str = LIB_PATH):
         lib.darts_last_error.argtypes = [vp, C.c_char_p, C.c_size_t]
         lib.darts_sync.argtypes = [vp]
         lib.darts_build_table.argtypes = [vp, sc_p, sp_p, vp]
+        lib.darts_load_table.argtypes = [vp, sc_p, sp_p, vp]
         lib.darts_table_row_stride.argtypes = [C.c_int32]
         lib.darts_table_row_stride.restype = C.c_int32
         lib.darts_render.argtypes = [vp, sc_p, sp_p, vp, vp, C.c_uint64, C.POINTER(darts_probe)]
@@ -254,6 +256,11 @@ def darts_table_row_stride(n_mu: int) -> int:
 def darts_build_table(h, scene, sampling, cdf: torch.Tensor):
     cs, keep = to_c_scene(scene)
     _check(h, load().darts_build_table(h, C.byref(cs), C.byref(to_c_sampling(sampling)), _ptr(cdf)))
+
+
+def darts_load_table(h, scene, sampling, cdf: torch.Tensor):
+    cs, keep = to_c_scene(scene)
+    _check(h, load().darts_load_table(h, C.byref(cs), C.byref(to_c_sampling(sampling)), _ptr(cdf)))
 
 
 def darts_render(h, scene, sampling, hist: torch.Tensor, sumsq: Optional[torch.Tensor] = None,
@@ -472,6 +479,17 @@ class Context:
         cdf = out if out is not None else torch.empty(rows, stride, dtype=torch.float32, device=self._dev())
         darts_build_table(self.h, scene, sampling, cdf)
         return cdf
+
+    def load_table(self, scene, sampling, cdf: torch.Tensor):
+        """Install a precomputed direction table (float32 [rows][row stride]
+        on this context's device, the layout of build_table) as the cached
+        table of the scene's medium; renders without FLAG_REBUILD_TABLE use it."""
+        rows = sampling.table_n_rho * sampling.table_n_s
+        stride = darts_table_row_stride(sampling.table_n_mu)
+        if (cdf.dtype != torch.float32 or tuple(cdf.shape) != (rows, stride) or not cdf.is_contiguous()
+                or cdf.device != self._dev()):
+            raise ValueError(f"the table must be a contiguous float32 [{rows}][{stride}] tensor on {self._dev()}")
+        darts_load_table(self.h, scene, sampling, cdf)
 
     def adjoint(self, scene, sampling, dLdh: torch.Tensor, sumsq: bool = False, path_offset: int = 0):
         """Gradient of sum_b dLdh[b] h_b w.r.t. (sigma_s, sigma_a, g) by path replay."""

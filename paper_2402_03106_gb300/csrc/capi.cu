@@ -858,6 +858,22 @@ darts_status darts_build_table(darts_ctx* ctx, const darts_scene* scene,
   return DARTS_OK;
 }
 
+darts_status darts_load_table(darts_ctx* ctx, const darts_scene* scene, const darts_sampling* sampling,
+                              const float* cdf_dev) {
+  if (!ctx) return DARTS_ERR_INVALID_ARG;
+  darts_status s = validate(ctx, scene, sampling);
+  if (s != DARTS_OK) return s;
+  if (!cdf_dev) return fail(ctx, DARTS_ERR_INVALID_ARG, "cdf_dev must not be NULL");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const size_t bytes = (size_t)sampling->table_n_rho * sampling->table_n_s *
+                       row_stride_of(sampling->table_n_mu) * sizeof(float);
+  CK(ensure((void**)&ctx->table, &ctx->table_bytes, bytes), "table allocation");
+  CK(cudaMemcpyAsync(ctx->table, cdf_dev, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "table copy");
+  table_key(scene, sampling, ctx->table_key);
+  ctx->table_valid = true;
+  return DARTS_OK;
+}
+
 darts_status darts_render(darts_ctx* ctx, const darts_scene* scene, const darts_sampling* sampling,
                           double* hist_dev, double* sumsq_dev, uint64_t path_offset,
                           const darts_probe* probe) {

@@ -18,6 +18,49 @@ EXACT_TIE = 1e-6
 # <= 9e-7), which moves the throughput of a path by at most half that times
 # the oracle's per-path table sensitivity (two CDF entries per p_EDA)
 TABLE_EPS = 1e-6
+# When the GPU renders with the oracle's own table rounded to FP32
+# (Context.load_table), a bin mass differs from the oracle's by at most one
+# FP32 unit of a CDF value below 1 (2^-24), half of which multiplies the
+# per-path table sensitivity as above.
+SHARED_TABLE_EPS = 3e-8
+
+
+def share_oracle_table(ctx, sc, sp):
+    """Install the oracle's FP64 direction table, rounded to FP32, as the GPU
+    context's table for this scene: both sides then sample directions from
+    the same table data (the oracle in FP64, the GPU in FP32), and the
+    GPU's own quadrature drops out of the per-path comparison.  Renders and
+    debug traces that follow must not set FLAG_REBUILD_TABLE.  Returns the
+    oracle table (for O.trace_paths(cdf=...))."""
+    import torch
+    from paper_2402_03106_gb300 import capi
+    cdf = O.build_table(sc, sp)
+    rows, nb1 = cdf.shape
+    t = np.ones((rows, capi.darts_table_row_stride(sp.table_n_mu)), np.float32)
+    t[:, :nb1] = cdf.astype(np.float32)
+    ctx.load_table(sc, sp, torch.from_numpy(t).to(ctx._dev()))
+    return cdf
+
+
+def report(name, same, rel, ref, tol, rel_tol=REL_PATH):
+    """Summary of one per-path comparison: paths whose traces agree, how many
+    of them differ by more than the plain tolerance, the worst relative
+    error, and how many needed a conditioning allowance.  Appended as one
+    JSON line to $DARTS_PARITY_REPORT when that is set."""
+    import json
+    import os
+    ok = same & ((ref["flags"] & O.FLAG_NEAR_DEGENERATE) == 0)
+    r = rel[ok]
+    out = {"test": name, "paths": int(len(same)), "same_trace": int(same.sum()),
+           "beyond_1e-4": int(np.sum(r > rel_tol)), "frac_beyond_1e-4": float(np.mean(r > rel_tol)) if len(r) else 0.0,
+           "worst_rel": float(r.max()) if len(r) else 0.0,
+           "worst_path": int(np.nonzero(ok)[0][np.argmax(r)]) if len(r) else -1,
+           "needing_allowance": int(np.sum(tol[ok] > rel_tol)), "near_degenerate": int(np.sum(same & ~ok))}
+    path = os.environ.get("DARTS_PARITY_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(out) + "\n")
+    return out
 
 
 def compare_paths(gpu, ref, K):
@@ -68,7 +111,8 @@ def displaced_sensitivity(sc, sp, first, n, method, ref, shift=1e-6):
     return s
 
 
-def check_paths(gpu, ref, K, rel_tol=REL_PATH, max_flip_frac=0.01, extra_tol=None):
+def check_paths(gpu, ref, K, rel_tol=REL_PATH, max_flip_frac=0.01, extra_tol=None, table_eps=TABLE_EPS,
+                name=None):
     """Flips must sit at a decision the oracle met within NEAR_TIE of its
     threshold.  Flips at an exact tie (margin below FP32 resolution, e.g. a
     bin edge that coincides with a table cell edge, rho = C/S_M = 1/2) may be
@@ -84,9 +128,11 @@ def check_paths(gpu, ref, K, rel_tol=REL_PATH, max_flip_frac=0.01, extra_tol=Non
     # decision the trace does not record (the table cell of an EDA sample)
     tie = ref["margin"].min(axis=1) < EXACT_TIE
     ok = same & ~nd & ~tie
-    tol = np.maximum(rel_tol, COND_EPS * ref["cond"] + TABLE_EPS * ref["tabcond"])
+    tol = np.maximum(rel_tol, COND_EPS * ref["cond"] + table_eps * ref["tabcond"])
     if extra_tol is not None:
         tol = np.maximum(tol, extra_tol)
+    if name is not None:
+        report(name, same & ~tie, rel, ref, tol, rel_tol)
     bad = np.nonzero(ok & (rel > tol))[0]
     assert len(bad) == 0, (f"{len(bad)} paths beyond their tolerance: rel {rel[bad][:5]}, "
                            f"tol {tol[bad][:5]}, cond {ref['cond'][bad][:5]}")
