@@ -13,6 +13,13 @@ REL_PATH = 1e-4
 COND_EPS = 4e-7
 # a decision this close to its threshold is a tie at FP32 resolution
 EXACT_TIE = 1e-6
+# In scenes with surfaces a surface vertex's direct connection is kept only
+# when its path time falls in the path's bin; that test is not part of the
+# decision record.  After tens of vertices the FP32 position and length
+# carry errors of order 1e-5 relative, so a path that met such a test (or
+# any decision) within SURFACE_TIE of its threshold may keep a connection on
+# one side and drop it on the other with identical traces: it is a tie.
+SURFACE_TIE = 1e-5
 # the GPU builds its own FP32 direction table: its bin masses may differ from
 # the oracle's by up to 2e-6 (asserted by the table parity test; measured
 # <= 9e-7), which moves the throughput of a path by at most half that times
@@ -112,7 +119,7 @@ def displaced_sensitivity(sc, sp, first, n, method, ref, shift=1e-6):
 
 
 def check_paths(gpu, ref, K, rel_tol=REL_PATH, max_flip_frac=0.01, extra_tol=None, table_eps=TABLE_EPS,
-                name=None):
+                name=None, tie_margin=EXACT_TIE):
     """Flips must sit at a decision the oracle met within NEAR_TIE of its
     threshold.  Flips at an exact tie (margin below FP32 resolution, e.g. a
     bin edge that coincides with a table cell edge, rho = C/S_M = 1/2) may be
@@ -126,7 +133,7 @@ def check_paths(gpu, ref, K, rel_tol=REL_PATH, max_flip_frac=0.01, extra_tol=Non
     nd = (ref["flags"] & O.FLAG_NEAR_DEGENERATE) != 0
     # a path that met an exact tie may have taken the other branch of a
     # decision the trace does not record (the table cell of an EDA sample)
-    tie = ref["margin"].min(axis=1) < EXACT_TIE
+    tie = ref["margin"].min(axis=1) < tie_margin
     ok = same & ~nd & ~tie
     tol = np.maximum(rel_tol, COND_EPS * ref["cond"] + table_eps * ref["tabcond"])
     if extra_tol is not None:

@@ -19,14 +19,14 @@ def bench():
     return mod
 
 
-@pytest.mark.parametrize("workload,paths", [("box_camera", 65536), ("cube", 1 << 24)])
+@pytest.mark.parametrize("workload,paths", [("spheres_512", 1 << 24), ("box_camera", 65536), ("cube", 1 << 24)])
 def test_profiles_match_the_current_kernels(bench, workload, paths):
     """bench.py reports DRAM traffic only from an ncu summary taken on the
     current path-kernel sources; a kernel change without a new capture
     shows up here."""
     t = bench.profiled_traffic(workload, paths)
     assert t is not None, f"profiles/darts_trace_kernel_{workload}.md is stale or missing"
-    assert 0 < t < 16e6
+    assert 0 < t < 1e9
 
 
 @pytest.mark.parametrize("workload", ["spheres_512", "box_camera", "cube"])

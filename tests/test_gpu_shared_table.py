@@ -21,8 +21,8 @@ torch = pytest.importorskip("torch")
 
 import oracle as O  # noqa: E402
 from paper_2402_03106_gb300 import scenes as S  # noqa: E402
-from parity_util import (REL_PATH, SHARED_TABLE_EPS, check_paths, displaced_sensitivity,  # noqa: E402
-                         report, share_oracle_table)
+from parity_util import (REL_PATH, SHARED_TABLE_EPS, SURFACE_TIE, check_paths,  # noqa: E402
+                         displaced_sensitivity, report, share_oracle_table)
 
 pytestmark = pytest.mark.gpu
 
@@ -129,7 +129,11 @@ def test_shared_table_camera_scenes(ctx, scene):
     """The two camera workloads of the benchmark at their full resolution,
     2048 paths from the middle of the frame, with the shared table; grazing
     surface hits keep their measured allowance (5x the FP64 change under a
-    1e-6 displacement of the camera), which stays the exception."""
+    1e-6 displacement of the camera), which stays the exception.  A
+    surface connection's in-bin test is not in the decision record, so a
+    path that met any decision within 1e-5 of its threshold is a tie (one
+    such path of the box frame keeps a connection in FP32 that the oracle
+    drops, 2e-6 from a bin edge after 21 vertices)."""
     if scene == "box_camera":
         sc, sp = S.box_camera_workload(seed=0)
         first = 32 * 64 * 16
@@ -143,6 +147,6 @@ def test_shared_table_camera_scenes(ctx, scene):
     ref = O.trace_paths(sc, sp, first, n, cdf=cdf)
     sens = 5.0 * displaced_sensitivity(sc, sp, first, n, S.DARTS, ref)
     check_paths(gpu, ref, sp.max_bounces, extra_tol=sens, table_eps=SHARED_TABLE_EPS,
-                name=f"shared_table_{scene}")
+                name=f"shared_table_{scene}", tie_margin=SURFACE_TIE)
     assert np.count_nonzero(ref["contrib"]) > n // 50
     assert np.mean(sens > REL_PATH) < 0.05
