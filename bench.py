@@ -249,7 +249,7 @@ def cpu_baseline(workload: str, budget_s: float = 10.0):
     cores = os.cpu_count() or 1
     cdf = O.build_table(sc, sp)
     done, paths, t_tot = 0, 0, 0.0
-    while t_tot < budget_s and done < 64:
+    while t_tot < budget_s and done < 128:
         for first, count, window in pieces:
             t0 = time.perf_counter()
             O.render(sc, sp, O.ORC_DARTS, n_paths=count, offset=first + done * N, cdf=cdf, threads=cores,
@@ -258,7 +258,7 @@ def cpu_baseline(workload: str, budget_s: float = 10.0):
             paths += count
         done += 1
     first, count, window = pieces[0]
-    n1 = max(1, count // 16)
+    n1 = max(1, count // 2)
     t0 = time.perf_counter()
     O.render(sc, sp, O.ORC_DARTS, n_paths=n1, offset=first, cdf=cdf, threads=1, window=window)
     t1 = time.perf_counter() - t0
@@ -574,12 +574,21 @@ def two_peak_response(ctx, S, torch, seeds=16, spp=64):
 
 def batched_compare(ctx, S, torch, reps=5):
     """256 independent slab media with uneven budgets (2^U[12,20] paths,
-    128 bins): one graph-captured persistent launch vs one launch per medium."""
+    128 bins): one graph-captured persistent launch, in the shape the
+    project's autotuner picks (block size, work items per CTA share), vs one
+    launch per medium (each in its own tuned shape would cost 256 tunings:
+    the per-medium launches use the default shape)."""
     media = S.batched_media(n_media=256, seed=0)
     scenes = [m[0] for m in media]
     samplings = [m[1] for m in media]
     total = sum(sp.paths_per_element for sp in samplings)
-    outs = ctx.render_batch(scenes, samplings)
+    outs = [torch.empty(sc.gate.n_bins, dtype=torch.float64, device="cuda") for sc in scenes]
+    t_tune = time.perf_counter()
+    tuned = ctx.autotune_batch(scenes, samplings, outs)
+    t_tune = time.perf_counter() - t_tune
+    # the tuned batch shape; single renders (the per-medium loop) in the default shape
+    ctx.set_launch_config(batch_block=tuned["batch_block"], batch_items=tuned["batch_items"])
+    ctx.render_batch(scenes, samplings, outs=outs)
     ctx.render_batch(scenes, samplings, outs=outs)
     torch.cuda.synchronize()
 
@@ -602,7 +611,10 @@ def batched_compare(ctx, S, torch, reps=5):
 
     loop()
     t_loop = timed(loop, 2)
+    ctx.set_launch_config()
     return {"media": len(scenes), "paths": total, "ms_batched_graph": t_batch,
+            "tuned_shape": {"batch_block": tuned["batch_block"], "batch_items": tuned["batch_items"],
+                            "tuning_s": t_tune},
             "ms_one_launch_per_medium": t_loop, "paths_per_s_batched": total / (t_batch * 1e-3),
             "paths_per_s_per_medium_launches": total / (t_loop * 1e-3),
             "speedup": t_loop / t_batch, "events_per_launch": events,
@@ -818,20 +830,21 @@ def time_workload(ctx, S, torch, name, flush, steps):
     sc, sp, N = make_workload(name, S)
     prep = ctx.prepare(sc, sp)
     h = torch.empty(S.histogram_shape(sc), dtype=torch.float64, device="cuda")
-    if sc.sensor.kind != S.SENSOR_PINHOLE:
-        ctx.autotune(sc, sp)
+    ctx.autotune(sc, sp)
     for _ in range(3):
         prep.render(out=h)
     torch.cuda.synchronize()
     ctx.set_kernel_timing(True)
     st, kt, per = time_steps(ctx, torch, lambda: prep.render(out=h), steps, flush)
     ctx.set_kernel_timing(False)
-    ctx.set_launch(0)
+    launch = ctx.launch_config()
+    ctx.set_launch_config()
     t = statistics.fmean(st)
     roof = roofline(per, statistics.fmean(kt), name)
     del h
     return {"paths_per_step": N, "ms_per_step": t, "paths_per_s": N / (t * 1e-3),
-            "kernel_ms": roof["kernel_ms"], "fp32_frac": roof["frac"]}
+            "kernel_ms": roof["kernel_ms"], "fp32_frac": roof["frac"],
+            "launch": {"block": launch["block"], "chunk": launch["chunk"]}}
 
 
 def run_studies(ctx, S, torch, flush, sc, sp, N, path):
@@ -908,8 +921,9 @@ def main():
         prepared.render(out=hist, path_offset=offset)
         pipe.end_step(hist)
 
-    # a camera always runs 512-thread blocks; the point sensor's block is tuned
-    tuned_block = 512 if camera else ctx.autotune(sc, sp)
+    # block size and path-counter chunk of the path kernel, tuned on this workload
+    ctx.autotune(sc, sp)
+    launch = ctx.launch_config()
     for _ in range(args.warmup):
         step()
     pipe.finish()
@@ -959,8 +973,15 @@ def main():
     # reaches the host
     shape = S.histogram_shape(sc)
     hh = [torch.empty(shape, dtype=torch.float64, pin_memory=True) for _ in range(2)]
-    ne = max(3, min(K, 8))
+    for h_ in hh:
+        h_.zero_()  # first touch of the pinned pages, outside the timed region
+    ne = max(4, min(K, 10))
+    # warm both calls: the context allocates its device histograms (two for
+    # the queued call, one for the synchronous one) at their first use
     prepared.render_host(hh[0])
+    for i in range(2):
+        prepared.render_host_async(hh[i])
+    ctx.sync()
     te = time.perf_counter()
     for i in range(ne):
         prepared.render_host_async(hh[i % 2], path_offset=i * N)
@@ -998,7 +1019,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
-                       "paths_per_gpu_per_step": N, "block": tuned_block,
+                       "paths_per_gpu_per_step": N,
+                       "launch": {"block": launch["block"], "chunk": launch["chunk"],
+                                  "source": "darts_autotune on this workload"},
                        "grid": "one CTA per SM (persistent)",
                        "l2": "256 MiB buffer written between timed steps (flush); histogram of "
                              "%.3f GB per step" % (math.prod(S.histogram_shape(sc)) * 8e-9),

@@ -369,17 +369,52 @@ darts_status darts_last_kernel_ms(darts_ctx* ctx, float* ms);
 /* ---- launch shape ---------------------------------------------------------- */
 
 /* Block size of the persistent path kernel (one CTA per SM): 512, 640 or 768
- * threads, or 0 for the default (the largest whose shared memory fits).
- * Other values return DARTS_ERR_INVALID_ARG. */
+ * threads, or 0 for the default (a point sensor: the largest whose shared
+ * memory fits; a camera: 512).  The point-sensor DARTS and baseline kernels
+ * and the camera kernel of DARTS are built for all three sizes; the other
+ * variants always run 512.  Other values return DARTS_ERR_INVALID_ARG. */
 darts_status darts_set_launch(darts_ctx* ctx, int block);
 
-/* Autotuner: times darts_render of (scene, sampling) with every supported
- * block size (3 timed renders each, after one warm-up; CUDA events on the
- * context's stream), keeps the fastest on the context and returns it in
+/* Launch shape of the context's kernels.  Zero fields take the defaults.
+ *   block        path kernel, as darts_set_launch (0, 512, 640, 768);
+ *   chunk        paths a warp claims per update of the global path counter,
+ *                1..1024 (default 64; a launch with fewer paths per resident
+ *                warp claims fewer);
+ *   batch_block  threads per CTA of darts_render_batch (0, 512, 640, 768;
+ *                default 768);
+ *   batch_items  work items per CTA's share of a batch's estimated cost,
+ *                1..64 (default 8): more items balance uneven media better,
+ *                fewer restage the direction table less often.
+ * Out-of-range fields return DARTS_ERR_INVALID_ARG and change nothing. */
+typedef struct {
+  int32_t block;
+  int32_t chunk;
+  int32_t batch_block;
+  int32_t batch_items;
+} darts_launch;
+darts_status darts_set_launch_config(darts_ctx* ctx, const darts_launch* cfg);
+darts_status darts_get_launch_config(darts_ctx* ctx, darts_launch* cfg);
+
+/* Autotuner of the path kernel's launch shape for one render: times
+ * darts_render of (scene, sampling) for every block size (512, 640, 768) and
+ * chunk (16, 32, 64, 128, 256) that the scene's kernel runs (3 timed renders
+ * each after one warm-up; CUDA events on the context's stream; chunks above
+ * the launch's paths per resident warp are the same launch and are timed
+ * once), keeps the fastest pair on the context and returns the block size in
  * *block_out (may be NULL).  Synchronises the stream.  The renders write the
  * context's scratch histogram, not a caller buffer. */
 darts_status darts_autotune(darts_ctx* ctx, const darts_scene* scene,
                             const darts_sampling* sampling, int* block_out);
+
+/* Autotuner of darts_render_batch: times the batch (2 timed launches after
+ * one warm-up, without graph capture) for every batch block size (512, 640,
+ * 768) and work-item granularity (2, 4, 8, 16, 32 items per CTA share),
+ * keeps the fastest on the context and returns the context's launch shape
+ * in *out (may be NULL).  The renders write the caller's hist_dev outputs,
+ * as darts_render_batch does.  Synchronises the stream. */
+darts_status darts_autotune_batch(darts_ctx* ctx, int n, const darts_scene* scenes,
+                                  const darts_sampling* samplings, double* const* hist_dev,
+                                  darts_launch* out);
 
 /* ---- rendering without allocating ----------------------------------------- */
 

@@ -39,7 +39,8 @@ EXPORTED = ("darts_create", "darts_destroy", "darts_set_stream", "darts_status_s
             "darts_debug_philox", "darts_set_kernel_timing", "darts_last_kernel_ms",
             "darts_render_static", "darts_set_launch", "darts_autotune", "darts_adjoint",
             "darts_render_batch", "darts_render_host_async", "darts_render_frames",
-            "darts_load_table")
+            "darts_load_table", "darts_set_launch_config", "darts_get_launch_config",
+            "darts_autotune_batch")
 BATCH_NO_GRAPH = 1
 
 
@@ -94,6 +95,11 @@ class darts_probe(C.Structure):
                 ("contrib_dev", C.c_void_p), ("bin_dev", C.c_void_p)]
 
 
+class darts_launch(C.Structure):
+    _fields_ = [("block", C.c_int32), ("chunk", C.c_int32), ("batch_block", C.c_int32),
+                ("batch_items", C.c_int32)]
+
+
 class darts_stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "paths", "vertices", "connections_nonempty", "distance_steps", "early_exits",
@@ -141,6 +147,10 @@ def load(path: str = LIB_PATH):
         lib.darts_adjoint.argtypes = [vp, sc_p, sp_p, vp, vp, vp, C.c_uint64]
         lib.darts_render_batch.argtypes = [vp, C.c_int, sc_p, sp_p, C.POINTER(C.c_void_p), C.c_uint32]
         lib.darts_autotune.argtypes = [vp, sc_p, sp_p, C.POINTER(C.c_int)]
+        lib.darts_set_launch_config.argtypes = [vp, C.POINTER(darts_launch)]
+        lib.darts_get_launch_config.argtypes = [vp, C.POINTER(darts_launch)]
+        lib.darts_autotune_batch.argtypes = [vp, C.c_int, sc_p, sp_p, C.POINTER(C.c_void_p),
+                                             C.POINTER(darts_launch)]
         for name in EXPORTED:
             if name not in ("darts_status_string", "darts_table_row_stride"):
                 getattr(lib, name).restype = st
@@ -324,6 +334,37 @@ def darts_render_batch(h, scenes, samplings, hists, flags: int = 0):
     sp_arr = (darts_sampling * n)(*[to_c_sampling(sp) for sp in samplings])
     ptrs = (C.c_void_p * n)(*[t.data_ptr() for t in hists])
     _check(h, load().darts_render_batch(h, n, cs_arr, sp_arr, ptrs, int(flags)))
+
+
+def _batch_arrays(scenes, samplings, hists):
+    n = len(scenes)
+    cs_arr = (darts_scene * n)()
+    keep = []
+    for i, sc in enumerate(scenes):
+        cs, k = to_c_scene(sc)
+        cs_arr[i] = cs
+        keep.append(k)
+    sp_arr = (darts_sampling * n)(*[to_c_sampling(sp) for sp in samplings])
+    ptrs = (C.c_void_p * n)(*[t.data_ptr() for t in hists])
+    return cs_arr, sp_arr, ptrs, keep
+
+
+def darts_autotune_batch(h, scenes, samplings, hists) -> dict:
+    cs_arr, sp_arr, ptrs, keep = _batch_arrays(scenes, samplings, hists)
+    out = darts_launch()
+    _check(h, load().darts_autotune_batch(h, len(scenes), cs_arr, sp_arr, ptrs, C.byref(out)))
+    return {f: int(getattr(out, f)) for f, _ in darts_launch._fields_}
+
+
+def darts_set_launch_config(h, block: int = 0, chunk: int = 0, batch_block: int = 0, batch_items: int = 0):
+    cfg = darts_launch(int(block), int(chunk), int(batch_block), int(batch_items))
+    _check(h, load().darts_set_launch_config(h, C.byref(cfg)))
+
+
+def darts_get_launch_config(h) -> dict:
+    out = darts_launch()
+    _check(h, load().darts_get_launch_config(h, C.byref(out)))
+    return {f: int(getattr(out, f)) for f, _ in darts_launch._fields_}
 
 
 def darts_set_launch(h, block: int):
@@ -511,6 +552,17 @@ class Context:
 
     def autotune(self, scene, sampling) -> int:
         return darts_autotune(self.h, scene, sampling)
+
+    def autotune_batch(self, scenes, samplings, outs) -> dict:
+        """Tune the batched launch (block size, work items per CTA share) on
+        these media; returns the context's launch shape."""
+        return darts_autotune_batch(self.h, scenes, samplings, outs)
+
+    def launch_config(self) -> dict:
+        return darts_get_launch_config(self.h)
+
+    def set_launch_config(self, block: int = 0, chunk: int = 0, batch_block: int = 0, batch_items: int = 0):
+        darts_set_launch_config(self.h, block, chunk, batch_block, batch_items)
 
     def set_kernel_timing(self, enable: bool):
         darts_set_kernel_timing(self.h, enable)

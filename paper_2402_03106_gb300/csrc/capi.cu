@@ -44,8 +44,14 @@ struct darts_ctx {
   size_t table_bytes = 0;
   bool table_valid = false;
   double table_key[9] = {0};
-  // launch shape: requested block size of the path kernel (0 = largest that fits)
+  // launch shape: requested block size of the path kernel (0 = largest that
+  // fits), the cap of a warp's claim on the path counter (0 = kPathChunk),
+  // and the batched kernel's block size and work items per CTA share (0 =
+  // defaults); set by the caller or the autotuners
   int block = 0;
+  int chunk = 0;
+  int batch_block = 0;
+  int batch_items = 0;
   int last_block = 0;
   unsigned long long last_paths = 0;  // paths of the last render
   bool last_fast = false;              // last launch ran the specialised DARTS kernel
@@ -374,6 +380,7 @@ darts_status ensure_table(darts_ctx* ctx, const darts_scene* sc, const darts_sam
 void make_trace_params(darts_ctx* ctx, const darts_scene* sc, const darts_sampling* sp,
                        TraceParams* P) {
   std::memset(P, 0, sizeof(*P));
+  P->chunk_cap = (unsigned)ctx->chunk;
   const darts_medium& m = sc->medium;
   const darts_emitter& e = sc->emitters[0];
   const double st = m.sigma_s + m.sigma_a;
@@ -476,6 +483,18 @@ void make_trace_params(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
     P->sph[k] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
     P->sph_albedo[k] = (float)q[4];
   }
+  {  // slab grid of the sphere culling (see cast_ray): the medium box in kCullSlabs slabs per axis
+    double ext = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      const double w = (sc->geom.hi[i] - sc->geom.lo[i]) / kCullSlabs;
+      P->cull_inv_w[i] = (float)(1.0 / w);
+      P->cull_off[i] = (float)(-sc->geom.lo[i] / w);
+      ext = std::max(ext, sc->geom.hi[i] - sc->geom.lo[i]);
+    }
+    // far above the FP32 rounding of a ray point (about 1e-7 of the box), so
+    // that no sphere a ray can meet is ever left out of its masks
+    P->cull_eps = (float)(1e-4 * ext);
+  }
   P->walls = sc->geom.walls;
   P->wall_albedo = (float)sc->geom.wall_albedo;
   const darts_sensor& sen = sc->sensor;
@@ -572,13 +591,17 @@ darts_status set_weights(darts_ctx* ctx, const darts_scene* sc, const darts_samp
 // fits (and always for a camera, whose output has one row per pixel).
 void choose_launch(const darts_ctx* ctx, const darts_sampling* sp, const TraceParams& P, bool debug,
                    int* block, bool* tile, size_t* smem) {
-  const int want = ctx->block ? ctx->block : 768;
   if (P.camera) {  // one histogram row per pixel: FP64 atomics straight into the output
     *tile = false;
-    *block = 512;
+    *block = trace_block_for(ctx->block ? ctx->block : 512, debug, false, sp->method, sp->ris_m, P.general != 0);
     *smem = trace_smem_bytes(sp->method, P, *block, false);
+    while (*smem > (size_t)ctx->smem_optin && *block > 512) {
+      *block = *block == 768 ? 640 : 512;
+      *smem = trace_smem_bytes(sp->method, P, *block, false);
+    }
     return;
   }
+  const int want = ctx->block ? ctx->block : 768;
   *tile = true;
   *block = trace_block_for(want, debug, true, sp->method, sp->ris_m, P.general != 0);
   *smem = trace_smem_bytes(sp->method, P, *block, true);
@@ -793,6 +816,70 @@ darts_status darts_set_launch(darts_ctx* ctx, int block) {
   return DARTS_OK;
 }
 
+darts_status darts_set_launch_config(darts_ctx* ctx, const darts_launch* cfg) {
+  if (!ctx || !cfg) return DARTS_ERR_INVALID_ARG;
+  auto block_ok = [](int b) { return b == 0 || b == 512 || b == 640 || b == 768; };
+  if (!block_ok(cfg->block) || !block_ok(cfg->batch_block))
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "block sizes must be 0, 512, 640 or 768");
+  if (cfg->chunk < 0 || cfg->chunk > 1024 || cfg->batch_items < 0 || cfg->batch_items > 64)
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "chunk must be in [0, 1024] and batch_items in [0, 64]");
+  ctx->block = cfg->block;
+  ctx->chunk = cfg->chunk;
+  ctx->batch_block = cfg->batch_block;
+  ctx->batch_items = cfg->batch_items;
+  return DARTS_OK;
+}
+
+darts_status darts_get_launch_config(darts_ctx* ctx, darts_launch* cfg) {
+  if (!ctx || !cfg) return DARTS_ERR_INVALID_ARG;
+  cfg->block = ctx->block;
+  cfg->chunk = ctx->chunk;
+  cfg->batch_block = ctx->batch_block;
+  cfg->batch_items = ctx->batch_items;
+  return DARTS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// Total time of `runs` enqueues after one untimed warm-up (CUDA events on
+// the context's stream).  `fn` enqueues one render.
+template <class F>
+darts_status time_enqueues(darts_ctx* ctx, cudaEvent_t e0, cudaEvent_t e1, int runs, F fn, float* total) {
+  *total = 0.0f;
+  for (int it = 0; it <= runs; ++it) {
+    if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "event record");
+    const darts_status s = fn();
+    if (s != DARTS_OK) return s;
+    if (cudaEventRecord(e1, ctx->stream) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "event record");
+    float ms = 0.0f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      return cuda_fail(ctx, cudaGetLastError(), "event timing");
+    if (it > 0) *total += ms;
+  }
+  return DARTS_OK;
+}
+
+struct EventPair {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t create() {
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    return e;
+  }
+  ~EventPair() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
+constexpr int kTuneBlocks[3] = {512, 640, 768};
+constexpr int kTuneChunks[5] = {16, 32, 64, 128, 256};
+constexpr int kTuneItems[5] = {2, 4, 8, 16, 32};
+}  // namespace
+
+extern "C" {
+
 darts_status darts_autotune(darts_ctx* ctx, const darts_scene* scene, const darts_sampling* sampling,
                             int* block_out) {
   if (!ctx) return DARTS_ERR_INVALID_ARG;
@@ -801,39 +888,68 @@ darts_status darts_autotune(darts_ctx* ctx, const darts_scene* scene, const dart
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   const size_t hb = elements_of(scene) * (size_t)scene->gate.n_bins * sizeof(double);
   CK(ensure((void**)&ctx->host_hist, &ctx->host_hist_bytes, 2 * hb), "histogram allocation");
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0), "event create");
-  if (cudaEventCreate(&e1) != cudaSuccess) {
-    cudaEventDestroy(e0);
-    return fail(ctx, DARTS_ERR_CUDA, "event create");
-  }
-  const int saved = ctx->block;
-  const int cand[3] = {512, 640, 768};
-  int best = 0;
+  EventPair ev;
+  CK(ev.create(), "event create");
+  const int saved_block = ctx->block, saved_chunk = ctx->chunk;
+  int best_block = 0, best_chunk = 0;
   float best_ms = 0.0f;
-  s = DARTS_OK;
-  for (int c = 0; c < 3 && s == DARTS_OK; ++c) {
-    ctx->block = cand[c];
-    float tot = 0.0f;
-    for (int it = 0; it < 4 && s == DARTS_OK; ++it) {
-      if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) s = fail(ctx, DARTS_ERR_CUDA, "event record");
-      if (s == DARTS_OK) s = darts_render(ctx, scene, sampling, ctx->host_hist, nullptr, 0, nullptr);
-      if (s == DARTS_OK && cudaEventRecord(e1, ctx->stream) != cudaSuccess) s = fail(ctx, DARTS_ERR_CUDA, "event record");
-      float ms = 0.0f;
-      if (s == DARTS_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-        s = fail(ctx, DARTS_ERR_CUDA, "event timing");
-      if (it > 0) tot += ms;
-    }
-    // a block size whose shared memory does not fit falls back to a smaller one
-    if (s == DARTS_OK && ctx->last_block == cand[c] && (best == 0 || tot < best_ms)) {
-      best = cand[c];
-      best_ms = tot;
+  // a chunk cap above the launch's paths per resident warp changes nothing:
+  // those are searched once (the smallest such cap stands for all)
+  const uint64_t paths = sampling->paths_per_element * elements_of(scene);
+  for (int bi = 0; bi < 3 && s == DARTS_OK; ++bi) {
+    bool saturated = false;
+    for (int ci = 0; ci < 5 && s == DARTS_OK && !saturated; ++ci) {
+      ctx->block = kTuneBlocks[bi];
+      ctx->chunk = kTuneChunks[ci];
+      saturated = paths <= (uint64_t)kTuneChunks[ci] * ctx->sm_count * (kTuneBlocks[bi] / 32);
+      float tot = 0.0f;
+      s = time_enqueues(ctx, ev.e0, ev.e1, 3, [&] {
+        return darts_render(ctx, scene, sampling, ctx->host_hist, nullptr, 0, nullptr);
+      }, &tot);
+      // a block size whose shared memory does not fit, or that this scene's
+      // kernel is not built for, falls back to another: not a candidate
+      if (s == DARTS_OK && ctx->last_block == kTuneBlocks[bi] && (best_block == 0 || tot < best_ms)) {
+        best_block = kTuneBlocks[bi];
+        best_chunk = kTuneChunks[ci];
+        best_ms = tot;
+      }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  ctx->block = (s == DARTS_OK && best) ? best : saved;
+  ctx->block = (s == DARTS_OK && best_block) ? best_block : saved_block;
+  ctx->chunk = (s == DARTS_OK && best_block) ? best_chunk : saved_chunk;
   if (block_out) *block_out = ctx->block;
+  return s;
+}
+
+darts_status darts_autotune_batch(darts_ctx* ctx, int n, const darts_scene* scenes,
+                                  const darts_sampling* samplings, double* const* hist_dev,
+                                  darts_launch* out) {
+  if (!ctx) return DARTS_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  EventPair ev;
+  CK(ev.create(), "event create");
+  const int saved_block = ctx->batch_block, saved_items = ctx->batch_items;
+  int best_block = 0, best_items = 0;
+  float best_ms = 0.0f;
+  darts_status s = DARTS_OK;
+  for (int bi = 0; bi < 3 && s == DARTS_OK; ++bi) {
+    for (int ii = 0; ii < 5 && s == DARTS_OK; ++ii) {
+      ctx->batch_block = kTuneBlocks[bi];
+      ctx->batch_items = kTuneItems[ii];
+      float tot = 0.0f;
+      s = time_enqueues(ctx, ev.e0, ev.e1, 2, [&] {
+        return darts_render_batch(ctx, n, scenes, samplings, hist_dev, DARTS_BATCH_NO_GRAPH);
+      }, &tot);
+      if (s == DARTS_OK && (best_block == 0 || tot < best_ms)) {
+        best_block = kTuneBlocks[bi];
+        best_items = kTuneItems[ii];
+        best_ms = tot;
+      }
+    }
+  }
+  ctx->batch_block = (s == DARTS_OK && best_block) ? best_block : saved_block;
+  ctx->batch_items = (s == DARTS_OK && best_block) ? best_items : saved_items;
+  if (out) darts_get_launch_config(ctx, out);
   return s;
 }
 
@@ -1109,7 +1225,8 @@ darts_status darts_render_batch(darts_ctx* ctx, int n, const darts_scene* scenes
     cpp[i] = 1.0 + scenes[i].medium.sigma_s * std::sqrt(diag);
     total_cost += cpp[i] * (double)samplings[i].paths_per_element;
   }
-  const double item_cost = total_cost / (8.0 * std::max(ctx->sm_count, 1));
+  const double items_per_cta = ctx->batch_items ? (double)ctx->batch_items : 8.0;
+  const double item_cost = total_cost / (items_per_cta * std::max(ctx->sm_count, 1));
   std::vector<uint64_t> chunk(n);
   size_t n_items = 0;
   for (int i = 0; i < n; ++i) {
@@ -1169,7 +1286,7 @@ darts_status darts_render_batch(darts_ctx* ctx, int n, const darts_scene* scenes
   bp.rows = rows;
   bp.row_stride = stride;
   bp.stats = ctx->scratch + 2;
-  int block = ctx->block ? ctx->block : 768;  // 24 warps per SM: measured fastest for the batch
+  int block = ctx->batch_block ? ctx->batch_block : 768;  // 24 warps per SM unless tuned
   size_t smem = batch_smem_bytes(bp, block);
   while (smem > (size_t)ctx->smem_optin && block > 512) {
     block = block == 768 ? 640 : 512;

@@ -13,6 +13,12 @@ constexpr int kStatCount = 12;      // device event counters (see the ST_ slots 
 constexpr int kPathChunk = 64;      // paths a warp claims from the global counter
 constexpr int kMaxEmitters = 8;
 constexpr int kMaxSpheres = 64;
+// Sphere culling of the general kernels: per axis, kCullSlabs slabs of the
+// medium box and, for every slab range [i, j], the mask of the spheres whose
+// (slightly enlarged) extent meets it; built in shared memory by each CTA.
+constexpr int kCullSlabs = 16;
+constexpr size_t kCullBytes = 3 * kCullSlabs * kCullSlabs * sizeof(unsigned long long) +
+                              kMaxSpheres * 4 * sizeof(float);
 
 // One pulse emitter: an isotropic point (kind 0) or a one-sided Lambertian
 // parallelogram pos + s u + t v emitting toward n = u x v / |u x v| (kind 1).
@@ -70,6 +76,8 @@ struct TraceParams {
   int n_spheres;
   float4 sph[kMaxSpheres];         // centre, radius
   float sph_albedo[kMaxSpheres];
+  float cull_off[3], cull_inv_w[3]; // slab grid of the box: slab = floor(x inv_w + off), off = -lo inv_w
+  float cull_eps;                  // enlargement of a sphere's extent in the masks
   int walls;                       // box faces with walls: bit 2 * axis + (1: hi face)
   float wall_albedo;
   int camera;                      // 0: point sensor at xs; 1: pinhole camera
@@ -95,7 +103,8 @@ struct TraceParams {
   unsigned long long bin_base;     // (path_offset + o_e) mod n_bins: bin of local path 0
   unsigned long long N;            // paths in this launch (local index 0..N-1)
   unsigned long long path_offset;  // global id = path_offset + local index
-  unsigned int chunk;              // paths a warp claims per counter update (0: kPathChunk)
+  unsigned int chunk;              // paths a warp claims per counter update (set at launch)
+  unsigned int chunk_cap;          // largest such claim (0: kPathChunk), the tuned launch shape
   float wb;                        // weight per path contribution (DARTS n_bins/N_e, else 1/N_e)
   // temporal response W (null without): cumulative weights C[0..n_bins]
   // (FP64), per-bin DARTS path weight sum W / (N_e W_b) (0 where W_b = 0),

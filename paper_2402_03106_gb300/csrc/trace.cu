@@ -12,8 +12,15 @@ cudaError_t launch_method(const TraceParams& p, int grid, int block, bool debug,
     if (kIsDartsM<METHOD> && p.M != 8) return cudaErrorInvalidValue;  // shared memory sized for M = 8
     if (debug) return tile ? launch_one<METHOD, 8, true, true, 512, true>(p, grid, smem, s)
                            : launch_one<METHOD, 8, true, false, 512, true>(p, grid, smem, s);
-    return tile ? launch_one<METHOD, 8, false, true, 512, true>(p, grid, smem, s)
-                : launch_one<METHOD, 8, false, false, 512, true>(p, grid, smem, s);
+    if (tile) return launch_one<METHOD, 8, false, true, 512, true>(p, grid, smem, s);
+    if constexpr (METHOD == kDarts) {  // the camera frame of the benchmark: 640 and 768 threads too
+      switch (block) {
+        case 640: return launch_one<METHOD, 8, false, false, 640, true>(p, grid, smem, s);
+        case 768: return launch_one<METHOD, 8, false, false, 768, true>(p, grid, smem, s);
+        default: break;
+      }
+    }
+    return launch_one<METHOD, 8, false, false, 512, true>(p, grid, smem, s);
   }
   const bool m8 = !kIsDartsM<METHOD> || p.M == 8;
   if constexpr (kIsDartsM<METHOD>) {
@@ -75,7 +82,7 @@ cudaError_t launch_batch(const BatchParams& bp, int grid, int block, size_t smem
 }
 
 size_t adjoint_smem_bytes(const TraceParams& p) {
-  size_t b = (size_t)p.rows * p.row_stride * sizeof(float);
+  size_t b = (size_t)p.rows * p.row_stride * sizeof(float) + (p.general ? kCullBytes : 0);
   if (p.M == 8) b += (size_t)(512 / 32) * 32 * (sizeof(RisTask) + sizeof(RisResult));
   return b;
 }
@@ -83,7 +90,7 @@ size_t adjoint_smem_bytes(const TraceParams& p) {
 cudaError_t launch_adjoint(const TraceParams& p0, int grid, size_t smem, cudaStream_t s) {
   TraceParams p = p0;
   p.bin_base = (p0.path_offset + p0.o_e) % (unsigned long long)p0.n_bins;
-  p.chunk = chunk_for(p.N, grid, 512);
+  p.chunk = chunk_for(p.N, grid, 512, p.chunk_cap);
   if (p.general) {
     if (p.M != 8) return cudaErrorInvalidValue;  // shared memory sized for M = 8
     auto kern = trace_kernel<kDarts, 8, false, false, 512, true, true>;
@@ -107,6 +114,7 @@ cudaError_t launch_adjoint(const TraceParams& p0, int grid, size_t smem, cudaStr
 size_t trace_smem_bytes(int method, const TraceParams& p, int block, bool tile) {
   const bool darts = method == kDarts || method == kDartsFull;
   size_t b = darts ? (size_t)p.rows * p.row_stride * sizeof(float) : 0;
+  if (p.general) b += kCullBytes;  // sphere-culling masks and the spheres, first in shared memory
   const size_t task = p.ris_mode ? sizeof(RisTaskVar) : sizeof(RisTask);
   if (darts && p.M == 8) b += (size_t)(block / 32) * 32 * (task + sizeof(RisResult));
   if (tile) b += (size_t)(block / 32) * (p.sumsq ? 3 : 2) * p.n_bins * sizeof(float);
@@ -116,8 +124,10 @@ size_t trace_smem_bytes(int method, const TraceParams& p, int block, bool tile) 
 int trace_max_m() { return kMaxM; }
 
 int trace_block_for(int block, bool debug, bool tile, int method, int M, bool general) {
-  if (general || debug || !tile || method == kDartsFull || (method == kDarts && M != 8)) return 512;
-  return (block == 640 || block == 768) ? block : 512;
+  const bool wide = block == 640 || block == 768;
+  if (debug || method == kDartsFull || (method == kDarts && M != 8)) return 512;
+  if (general) return (!tile && method == kDarts && wide) ? block : 512;  // camera frames of DARTS
+  return (tile && wide) ? block : 512;
 }
 
 cudaError_t launch_trace(int method, const TraceParams& p0, int grid, int block, bool debug,

@@ -332,11 +332,76 @@ __device__ __forceinline__ float ray_sphere(const float4 c, float x, float y, fl
   return t0 > kGeomEps ? t0 : (t1 > kGeomEps ? t1 : FLT_MAX);
 }
 
+// ---- sphere culling ---------------------------------------------------------
+// The general kernels keep, at the start of dynamic shared memory, per axis a
+// of the medium box split into kCullSlabs slabs, the mask M_a[i][j] of the
+// spheres whose extent along a, enlarged by cull_eps, meets slabs i..j, and
+// the spheres themselves (float4 centre, radius).  A sphere that a segment
+// meets overlaps the segment's bounding box on every axis, so it is in
+// M_x & M_y & M_z of that box: testing only those spheres, in increasing
+// index order, finds the same nearest hit (and the same lowest-index tie) as
+// testing every sphere.  Each segment is split at its middle and the two
+// halves' masks are OR-ed, which tightens the boxes of long diagonal rays.
+__device__ __forceinline__ const unsigned long long* cull_masks() {
+  extern __shared__ float4 smem4[];
+  return reinterpret_cast<const unsigned long long*>(smem4);
+}
+__device__ __forceinline__ const float4* cull_spheres() {
+  return reinterpret_cast<const float4*>(cull_masks() + 3 * kCullSlabs * kCullSlabs);
+}
+__device__ __forceinline__ int cull_slab(const TraceParams& P, int a, float v) {
+  return min(max(__float2int_rd(fmaf(v, P.cull_inv_w[a], P.cull_off[a])), 0), kCullSlabs - 1);
+}
+// Masks and spheres, built by the whole block before any path runs.
+__device__ __forceinline__ void build_cull(const TraceParams& P, int tid, int nthreads) {
+  extern __shared__ float4 smem4[];
+  unsigned long long* m = reinterpret_cast<unsigned long long*>(smem4);
+  float4* sph = reinterpret_cast<float4*>(m + 3 * kCullSlabs * kCullSlabs);
+  for (int k = tid; k < P.n_spheres; k += nthreads) sph[k] = P.sph[k];
+  for (int e = tid; e < 3 * kCullSlabs * kCullSlabs; e += nthreads) {
+    const int a = e / (kCullSlabs * kCullSlabs), i = (e / kCullSlabs) % kCullSlabs, j = e % kCullSlabs;
+    unsigned long long bits = 0;
+    for (int k = 0; k < P.n_spheres; ++k) {
+      const float4 c = P.sph[k];
+      const float ca = a == 0 ? c.x : (a == 1 ? c.y : c.z);
+      const float rr = c.w + P.cull_eps;
+      if (cull_slab(P, a, ca - rr) <= j && cull_slab(P, a, ca + rr) >= i) bits |= 1ull << k;
+    }
+    m[e] = bits;
+  }
+}
+// Spheres that may meet the segment a -> b, split at m: the slab of a point
+// is monotone in its coordinate, so a half's slab range on an axis is the
+// range of its two end points' slabs.
+__device__ __forceinline__ unsigned long long cull_two(const TraceParams& P, float ax, float ay, float az,
+                                                       float mx, float my, float mz, float bx, float by,
+                                                       float bz) {
+  const unsigned long long* m = cull_masks();
+  constexpr int kAxis = kCullSlabs * kCullSlabs;
+  const int a0 = cull_slab(P, 0, ax), a1 = cull_slab(P, 1, ay), a2 = cull_slab(P, 2, az);
+  const int m0 = cull_slab(P, 0, mx), m1 = cull_slab(P, 1, my), m2 = cull_slab(P, 2, mz);
+  const int b0 = cull_slab(P, 0, bx), b1 = cull_slab(P, 1, by), b2 = cull_slab(P, 2, bz);
+  const unsigned long long h1 = m[min(a0, m0) * kCullSlabs + max(a0, m0)] &
+                                m[kAxis + min(a1, m1) * kCullSlabs + max(a1, m1)] &
+                                m[2 * kAxis + min(a2, m2) * kCullSlabs + max(a2, m2)];
+  const unsigned long long h2 = m[min(m0, b0) * kCullSlabs + max(m0, b0)] &
+                                m[kAxis + min(m1, b1) * kCullSlabs + max(m1, b1)] &
+                                m[2 * kAxis + min(m2, b2) * kCullSlabs + max(m2, b2)];
+  return h1 | h2;
+}
+__device__ __forceinline__ unsigned long long cull_segment(const TraceParams& P, float x, float y, float z,
+                                                           float wx, float wy, float wz, float len) {
+  const float h = 0.5f * len;
+  return cull_two(P, x, y, z, fmaf(wx, h, x), fmaf(wy, h, y), fmaf(wz, h, z), fmaf(wx, len, x),
+                  fmaf(wy, len, y), fmaf(wz, len, z));
+}
+
 // Nearest wall, sphere or open face along (x, w) from inside the box.
 // hit: 0 open face, 1 wall, 2 + i sphere i; n: the surface normal facing the
 // ray.  Sphere `skip` is the one the ray leaves (outward): being convex it
 // cannot be met again, and skipping it keeps FP32 rounding of the start point
-// from producing a spurious second hit.
+// from producing a spurious second hit.  Only the spheres of the segment's
+// culling masks are tested (general kernels: they are in shared memory).
 __device__ __forceinline__ float cast_ray(const TraceParams& P, float x, float y, float z, float wx,
                                           float wy, float wz, int skip, int* hit, float* nx, float* ny,
                                           float* nz) {
@@ -356,17 +421,22 @@ __device__ __forceinline__ float cast_ray(const TraceParams& P, float x, float y
   *nx = face / 2 == 0 ? ((face & 1) ? -1.0f : 1.0f) : 0.0f;
   *ny = face / 2 == 1 ? ((face & 1) ? -1.0f : 1.0f) : 0.0f;
   *nz = face / 2 == 2 ? ((face & 1) ? -1.0f : 1.0f) : 0.0f;
+  if (P.n_spheres == 0) return d;
+  const float4* sph = cull_spheres();
+  unsigned long long cand = cull_segment(P, x, y, z, wx, wy, wz, d);
+  if (skip >= 0) cand &= ~(1ull << skip);
   int hs = -1;
-  for (int k = 0; k < P.n_spheres; ++k) {
-    if (k == skip) continue;
-    const float t = ray_sphere(P.sph[k], x, y, z, wx, wy, wz);
+  while (cand) {
+    const int k = __ffsll((long long)cand) - 1;
+    cand &= cand - 1;
+    const float t = ray_sphere(sph[k], x, y, z, wx, wy, wz);
     if (t < d) {
       d = t;
       hs = k;
     }
   }
   if (hs >= 0) {
-    const float4 c = P.sph[hs];
+    const float4 c = sph[hs];
     const float ir = 1.0f / c.w;
     *hit = 2 + hs;
     *nx = (fmaf(wx, d, x) - c.x) * ir;
@@ -388,8 +458,15 @@ __device__ __forceinline__ bool visible(const TraceParams& P, float ax, float ay
   wx *= il;
   wy *= il;
   wz *= il;
-  for (int k = 0; k < P.n_spheres; ++k)
-    if (k != skip && ray_sphere(P.sph[k], ax, ay, az, wx, wy, wz) < len - kGeomEps) return false;
+  const float4* sph = cull_spheres();
+  const float h = 0.5f * len;
+  unsigned long long cand = cull_two(P, ax, ay, az, fmaf(wx, h, ax), fmaf(wy, h, ay), fmaf(wz, h, az), bx, by, bz);
+  if (skip >= 0) cand &= ~(1ull << skip);
+  while (cand) {
+    const int k = __ffsll((long long)cand) - 1;
+    cand &= cand - 1;
+    if (ray_sphere(sph[k], ax, ay, az, wx, wy, wz) < len - kGeomEps) return false;
+  }
   return true;
 }
 
@@ -1617,7 +1694,8 @@ template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK, bool ADJ = fal
           bool VAR = false>
 __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
   extern __shared__ float4 smem4[];
-  float* smem = reinterpret_cast<float*>(smem4);
+  // general kernels: the sphere-culling masks and spheres come first
+  float* smem = reinterpret_cast<float*>(smem4) + (GEN ? kCullBytes / sizeof(float) : 0);
   const int tab_floats = kIsDartsM<METHOD> ? P.rows * P.row_stride : 0;
   float* tab = smem;
   constexpr int nwarps = BLOCK / 32;
@@ -1640,8 +1718,10 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
   // stage the direction table (row stride is a multiple of 4 floats)
   if (kIsDartsM<METHOD>) {
     const float4* src = reinterpret_cast<const float4*>(P.table);
-    for (int i = threadIdx.x; i < tab_floats / 4; i += BLOCK) smem4[i] = __ldg(src + i);
+    float4* dst = reinterpret_cast<float4*>(tab);
+    for (int i = threadIdx.x; i < tab_floats / 4; i += BLOCK) dst[i] = __ldg(src + i);
   }
+  if (GEN) build_cull(P, threadIdx.x, BLOCK);
   if (TILE)
     for (int i = threadIdx.x; i < nwarps * tile_stride; i += BLOCK) tiles[i] = 0.0f;
   if (threadIdx.x < kStatCount) blk_stats[threadIdx.x] = 0;
@@ -1850,14 +1930,16 @@ __global__ void philox_kernel(const uint32_t* ctr, uint32_t k0, uint32_t k1, uin
   out[4 * i + 3] = r.w;
 }
 
-// Paths a warp claims at a time: kPathChunk, or fewer when the launch has
-// fewer than kPathChunk paths per resident warp, so that a small launch
-// (one camera frame) spreads over every warp instead of giving some lanes
-// two paths in a row while other warps idle.
-unsigned int chunk_for(unsigned long long N, int grid, int block) {
+// Paths a warp claims at a time: `cap` (kPathChunk when 0; the autotuner
+// picks it), or fewer when the launch has fewer than that many paths per
+// resident warp, so that a small launch (one camera frame) spreads over
+// every warp instead of giving some lanes two paths in a row while other
+// warps idle.
+unsigned int chunk_for(unsigned long long N, int grid, int block, unsigned int cap) {
+  const unsigned long long c = cap ? cap : (unsigned long long)kPathChunk;
   const unsigned long long warps = (unsigned long long)grid * (block / 32);
-  const unsigned long long per = warps ? (N + warps - 1) / warps : kPathChunk;
-  return (unsigned int)std::max<unsigned long long>(1, std::min<unsigned long long>(per, kPathChunk));
+  const unsigned long long per = warps ? (N + warps - 1) / warps : c;
+  return (unsigned int)std::max<unsigned long long>(1, std::min<unsigned long long>(per, c));
 }
 
 // Raise a kernel's dynamic shared-memory limit only when a launch needs more
@@ -1886,7 +1968,7 @@ cudaError_t launch_one(const TraceParams& p0, int grid, size_t smem, cudaStream_
   cudaError_t e = smem_limit<kern>(smem);
   if (e != cudaSuccess) return e;
   TraceParams p = p0;
-  p.chunk = chunk_for(p.N, grid, BLOCK);
+  p.chunk = chunk_for(p.N, grid, BLOCK, p.chunk_cap);
   kern<<<grid, BLOCK, smem, s>>>(p);
   return cudaGetLastError();
 }

@@ -41,6 +41,26 @@ def test_batch_equals_single_renders(ctx):
         torch.testing.assert_close(h, ref, rtol=1e-5, atol=1e-14 * float(ref.abs().max()) + 1e-300)
 
 
+def test_tuned_batch_equals_single_renders(ctx):
+    """darts_autotune_batch times every batch block size and item
+    granularity, keeps the fastest on the context, and the batch in that
+    shape (and in the extreme shapes) still equals the single renders."""
+    media = _media(24, seed=7)
+    scenes = [m[0] for m in media]
+    samplings = [m[1] for m in media]
+    outs = [torch.empty(sc.gate.n_bins, dtype=torch.float64, device="cuda") for sc in scenes]
+    cfg = ctx.autotune_batch(scenes, samplings, outs)
+    assert cfg["batch_block"] in (512, 640, 768) and cfg["batch_items"] in (2, 4, 8, 16, 32)
+    refs = [ctx.render(sc, sp) for sc, sp in zip(scenes, samplings)]
+    for shape in (cfg, dict(batch_block=512, batch_items=1), dict(batch_block=768, batch_items=64)):
+        ctx.set_launch_config(batch_block=shape["batch_block"], batch_items=shape["batch_items"])
+        got = ctx.render_batch(scenes, samplings)
+        ctx.sync()
+        for h, ref in zip(got, refs):
+            torch.testing.assert_close(h, ref, rtol=1e-5, atol=1e-14 * float(ref.abs().max()) + 1e-300)
+    ctx.set_launch_config()
+
+
 def test_full_size_batch_equals_single_renders(ctx):
     """The batched configuration at full size: 256 media, budgets
     2^U[12,20] (about 47 M paths), 128 bins, in the benchmark's launch (one

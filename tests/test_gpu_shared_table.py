@@ -149,4 +149,5 @@ def test_shared_table_camera_scenes(ctx, scene):
     check_paths(gpu, ref, sp.max_bounces, extra_tol=sens, table_eps=SHARED_TABLE_EPS,
                 name=f"shared_table_{scene}", tie_margin=SURFACE_TIE)
     assert np.count_nonzero(ref["contrib"]) > n // 50
-    assert np.mean(sens > REL_PATH) < 0.05
+    # the grazing allowance stays the exception: under 2 % of the paths get more than 1e-3
+    assert np.mean(sens > 1e-3) < 0.02
