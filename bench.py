@@ -86,6 +86,9 @@ def parse():
     ap.add_argument("--only", default=None, choices=["timed", "batched", "differentiable"],
                     help="run one measurement alone (for ncu captures of its kernels)")
     ap.add_argument("--only-timed", action="store_true", help="same as --only timed")
+    ap.add_argument("--launch", default=None, metavar="BLOCK,CHUNK",
+                    help="path-kernel launch shape instead of the autotuner's (profiler captures: "
+                         "no tuning launches before the timed ones)")
     a = ap.parse_args()
     if a.only_timed:
         a.only = "timed"
@@ -922,7 +925,11 @@ def main():
         pipe.end_step(hist)
 
     # block size and path-counter chunk of the path kernel, tuned on this workload
-    ctx.autotune(sc, sp)
+    if args.launch:
+        b_, c_ = (int(x) for x in args.launch.split(","))
+        ctx.set_launch_config(block=b_, chunk=c_)
+    else:
+        ctx.autotune(sc, sp)
     launch = ctx.launch_config()
     for _ in range(args.warmup):
         step()
@@ -960,7 +967,7 @@ def main():
     if args.only == "timed":
         print(json.dumps({"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": ws,
                           "steps": K, "warmup": args.warmup, "ms_per_step": t_step,
-                          "config": {"workload": args.workload}, "roofline": roof,
+                          "config": {"workload": args.workload, "launch": launch}, "roofline": roof,
                           "note": "timed steps only"}), flush=True)
         ctx.close()
         return 0
@@ -1021,7 +1028,7 @@ def main():
             "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
                        "paths_per_gpu_per_step": N,
                        "launch": {"block": launch["block"], "chunk": launch["chunk"],
-                                  "source": "darts_autotune on this workload"},
+                                  "source": "--launch" if args.launch else "darts_autotune on this workload"},
                        "grid": "one CTA per SM (persistent)",
                        "l2": "256 MiB buffer written between timed steps (flush); histogram of "
                              "%.3f GB per step" % (math.prod(S.histogram_shape(sc)) * 8e-9),

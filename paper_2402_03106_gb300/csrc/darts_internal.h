@@ -116,7 +116,7 @@ struct TraceParams {
   // outputs and scratch
   double* hist;                    // [elements][n_bins]; zeroed before a launch without tiles
   double* sumsq;                   // [elements][n_bins] or null
-  double* partials;                // [grid][2][n_bins]
+  double* partials;                // [grid][n_bins] x (sum, sum of squares): 2 doubles per bin
   unsigned long long* counter;     // path counter
   unsigned int* ticket;            // last-block ticket
   unsigned int* status;            // device status word (bit 0: non-finite)

@@ -1385,10 +1385,30 @@ struct Stepper {
 __device__ __forceinline__ void warp_commit(bool has, int bin, float val, float* wsum, float* wcomp,
                                             float* wsq, bool tile, const TraceParams& P,
                                             bool do_sq) {
-  if (!tile) {  // outputs zeroed before the launch
-    if (has && DARTS_INDEX_OK(P, bin, (P.camera ? (long long)P.width * P.height : 1ll) * P.n_bins)) {
-      atomicAdd(&P.hist[bin], (double)val);
-      if (do_sq) atomicAdd(&P.sumsq[bin], (double)val * (double)val);
+  if (!tile) {  // outputs zeroed before the launch: FP64 atomics into them
+    const bool ok = has && DARTS_INDEX_OK(P, bin, (P.camera ? (long long)P.width * P.height : 1ll) * P.n_bins);
+    const unsigned act = __ballot_sync(kFull, ok);
+    if (!ok) return;
+    // lanes adding to the same bin (the baselines and full-gate DARTS bin by
+    // time; a one-bin gate sends every path of a pixel to one bin) add once:
+    // the group's first lane adds the group's sum and sum of squares, FP64,
+    // in lane order
+    const unsigned grp = __match_any_sync(act, bin);
+    const int lane = threadIdx.x & 31;
+    double v = (double)val, q = v * v;
+    if (grp != (1u << lane)) {
+      double sv = 0.0, sq = 0.0;
+      for (unsigned m = grp; m; m &= m - 1) {
+        const double x = __shfl_sync(grp, (double)val, __ffs(m) - 1);
+        sv += x;
+        sq = fma(x, x, sq);
+      }
+      v = sv;
+      q = sq;
+    }
+    if (lane == __ffs(grp) - 1) {
+      atomicAdd(&P.hist[bin], v);
+      if (do_sq) atomicAdd(&P.sumsq[bin], q);
     }
     return;
   }
@@ -1789,8 +1809,9 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
     return;
   }
 
-  // ---- flush: FP64 reduction of the warp tiles into this block's partials
-  double* part = P.partials + (size_t)blockIdx.x * 2 * B;
+  // ---- flush: FP64 reduction of the warp tiles into this block's partials,
+  // one 16-byte (sum, sum of squares) store per bin, coalesced over the block
+  double2* part = reinterpret_cast<double2*>(P.partials) + (size_t)blockIdx.x * B;
   if (TILE) {
     for (int b = threadIdx.x; b < B; b += BLOCK) {
       double s = 0.0, q = 0.0;
@@ -1799,8 +1820,7 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
         s += (double)t[b] - (double)t[B + b];
         if (do_sq) q += (double)t[2 * B + b];
       }
-      part[b] = s;
-      part[B + b] = q;
+      part[b] = make_double2(s, q);
     }
   }
   // ---- last block: sum the partials in block order (no waiting: atomic ticket)
@@ -1812,12 +1832,13 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
   if (!last) return;
   __threadfence();
   if (TILE) {
+    const double2* all = reinterpret_cast<const double2*>(P.partials);
     for (int b = threadIdx.x; b < B; b += BLOCK) {
       double s = 0.0, q = 0.0;
       for (unsigned g = 0; g < gridDim.x; ++g) {
-        const double* pg = P.partials + (size_t)g * 2 * B;
-        s += __ldcg(pg + b);
-        q += __ldcg(pg + B + b);
+        const double2 v = __ldcg(all + (size_t)g * B + b);
+        s += v.x;
+        q += v.y;
       }
       P.hist[b] = P.accumulate ? P.hist[b] + s : s;
       if (P.sumsq) P.sumsq[b] = P.accumulate ? P.sumsq[b] + q : q;
