@@ -84,6 +84,13 @@ typedef enum {
  * estimates (divide by k for their average).  Device outputs of darts_render
  * only; the host, batched, static and adjoint calls refuse it. */
 #define DARTS_FLAG_ACCUMULATE (1u << 7)
+/* EDA directions at surface vertices: the direction that leaves a Lambertian
+ * wall or sphere is drawn by the one-sample MIS of Eq. 19 from the EDA table
+ * and the cosine lobe about the normal (f = albedo cos / pi) instead of the
+ * cosine lobe alone (Sec. 5.1's direction sampler at a surface scattering
+ * vertex).  DARTS and full-gate DARTS in general scenes; a direction into the
+ * surface ends the path (zero throughput). */
+#define DARTS_FLAG_SURFACE_EDA (1u << 8)
 
 typedef struct darts_ctx darts_ctx;
 

@@ -173,7 +173,7 @@ def make_scene(scene, sampling) -> OrcScene:
     s.paths_per_element = sampling.paths_per_element
     f = sampling.flags
     s.ablation = ((1 if f & (1 << 2) else 0) | (2 if f & (1 << 3) else 0) | (4 if f & (1 << 4) else 0)
-                  | (8 if f & (1 << 5) else 0) | (16 if f & (1 << 6) else 0))
+                  | (8 if f & (1 << 5) else 0) | (16 if f & (1 << 6) else 0) | (32 if f & (1 << 8) else 0))
     return s
 
 

@@ -564,11 +564,15 @@ static void rec_margin_at(path_rec* pr, int k, double m) {
 
 /* Direction at vertex k (Sec. 5.1): one-sample MIS (balance heuristic) of the
  * EDA table and the base strategy -- HG about the previous direction for
- * k >= 1, the uniform sphere at the sensor vertex.  gamma = (C/S)/(C/S + alpha)
- * (Eq. 19).  Returns the throughput factor f/p and writes the direction. */
+ * k >= 1, the uniform sphere at the sensor vertex, and, with surf_alb > 0
+ * (EDA at a Lambertian surface vertex, the direction sampler of Sec. 5.1
+ * applied where the local scattering is the BRDF), the cosine lobe about the
+ * surface normal held in wprev, with f = albedo / pi * cos.
+ * gamma = (C/S)/(C/S + alpha) (Eq. 19).  Returns the throughput factor f/p
+ * and writes the direction. */
 static double darts_direction(const orc_scene* sc, const double* cdf, int k, uint64_t id,
                               const double a[3], double C, double SM, const double wprev[3],
-                              double w[3], double* mu_base_out, path_rec* pr) {
+                              double w[3], double* mu_base_out, path_rec* pr, double surf_alb) {
   int nb = sc->n_mu;
   double tab_margin;
   int row = orc_table_row(sc, C, SM, &tab_margin);
@@ -601,15 +605,15 @@ static double darts_direction(const orc_scene* sc, const double* cdf, int k, uin
     frame_dir(a, mu, phi, w);
     pE = (hi - lo) * (nb / 2.0) / (2.0 * M_PI);
     mu_b = dot3(w, axis);
-    pB = orc_hg_pdf(mu_b, gb);
+    pB = surf_alb > 0.0 ? dmax(mu_b, 0.0) / M_PI : orc_hg_pdf(mu_b, gb);
     mis_choice = 1;
     mu_bin = i;
   } else {
-    mu_b = orc_hg_sample(gb, u1);
+    mu_b = surf_alb > 0.0 ? sqrt(u1) : orc_hg_sample(gb, u1); /* cosine lobe: cos^2 uniform */
     double phi = 2.0 * M_PI * u2;
     rec_margin(pr, k, fabs(axis[2]));
     frame_dir(axis, mu_b, phi, w);
-    pB = orc_hg_pdf(mu_b, gb);
+    pB = surf_alb > 0.0 ? mu_b / M_PI : orc_hg_pdf(mu_b, gb);
     double mua = dot3(w, a);
     double y = (mua + 1.0) * (nb / 2.0);
     int i = (int)floor(y);
@@ -622,7 +626,7 @@ static double darts_direction(const orc_scene* sc, const double* cdf, int k, uin
   }
   double p_mix = gamma * pE + (1.0 - gamma) * pB;
   if (gamma > 0.0) ORC_NOT_COUNTED(pr->tabcond += (orc_tally)(gamma * nb / (2.0 * M_PI) / p_mix));
-  double f = (k == 0) ? 1.0 : orc_hg_pdf(mu_b, sc->g);
+  double f = (k == 0) ? 1.0 : (surf_alb > 0.0 ? surf_alb / M_PI * dmax(mu_b, 0.0) : orc_hg_pdf(mu_b, sc->g));
   if (pr->dec) {
     pr->dec[k * 4 + 2] = (uint8_t)mis_choice;
     pr->dec[k * 4 + 3] = (uint8_t)(mu_bin & 0xFF);
@@ -996,6 +1000,7 @@ static void trace_darts(const orc_scene* sc, const double* cdf, uint64_t id, pat
   if (!path_start(sc, id, elem, x, w, &L, &fixed)) return;
   double wprev[3] = {w[0], w[1], w[2]};
   double beta = E.wsel;
+  double surf_alb = 0.0; /* albedo of the surface this vertex sits on (EDA at surfaces) */
   double gsum = 0.0;  /* sum of d log HG / dg over medium walk vertices */
   int n_med = 0;      /* medium scattering vertices of the walk */
   double wb = pr->wpath;
@@ -1016,9 +1021,15 @@ static void trace_darts(const orc_scene* sc, const double* cdf, uint64_t id, pat
     }
     if (!fixed) {
       double wn[3], mu_b;
-      beta *= darts_direction(sc, cdf, k, id, a, C, SM, wprev, wn, &mu_b, pr);
-      if (k >= 1) ORC_NOT_COUNTED(gsum += hg_dlog_dg(mu_b, sc->g));
+      beta *= darts_direction(sc, cdf, k, id, a, C, SM, wprev, wn, &mu_b, pr, surf_alb);
+      if (k >= 1 && surf_alb == 0.0) ORC_NOT_COUNTED(gsum += hg_dlog_dg(mu_b, sc->g));
       for (int i = 0; i < 3; ++i) w[i] = wn[i];
+      if (surf_alb > 0.0 && !(beta > 0.0)) { /* an EDA direction into the surface: nothing follows */
+        if (pr->dec) pr->dec[k * 4] = ORC_EV_INVALID;
+        pr->n_invalid += 1.0;
+        return;
+      }
+      surf_alb = 0.0;
     }
     int32_t hit;
     double nrm[3];
@@ -1092,6 +1103,12 @@ static void trace_darts(const orc_scene* sc, const double* cdf, uint64_t id, pat
         }
       }
       if (pr->dec) pr->dec[k * 4] = ORC_EV_SURFACE | ne;
+      if (sc->ablation & 32) { /* EDA at surfaces: the next vertex samples its direction */
+        for (int i = 0; i < 3; ++i) wprev[i] = nrm[i];
+        surf_alb = alb;
+        fixed = 0;
+        continue;
+      }
       uint32_t us[4];
       orc_rng4(sc, id, (uint32_t)(k + 1), 1, us);
       double wn[3];

@@ -77,7 +77,9 @@ typedef struct {
                                    weights all 1, no DA target); bit 1: no EDA
                                    direction sampling (gamma = 0); bit 2:
                                    i.i.d. RIS candidates; bit 3: equiangular
-                                   candidates; bit 4: reservoir selection     */
+                                   candidates; bit 4: reservoir selection;
+                                   bit 5: EDA directions at surface vertices
+                                   (MIS with the cosine lobe)                 */
   /* emitters (em[0] repeats xe/t0/energy for the single point emitter) */
   int32_t n_emitters;
   orc_emitter em[ORC_MAX_EMITTERS];

@@ -430,6 +430,7 @@ void make_trace_params(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
   P->mis_alpha = (float)sp->mis_alpha;
   P->uniform_sensor = (sp->flags & DARTS_FLAG_SENSOR_UNIFORM_ONLY) ? 1 : 0;
   P->no_eda = (sp->flags & DARTS_FLAG_NO_EDA) ? 1 : 0;
+  P->surface_eda = (sp->flags & DARTS_FLAG_SURFACE_EDA) ? 1 : 0;
   P->no_da = (sp->flags & DARTS_FLAG_NO_DA_DISTANCE) ? 1 : 0;
   P->accumulate = (sp->flags & DARTS_FLAG_ACCUMULATE) ? 1 : 0;
   P->ris_mode = ((sp->flags & DARTS_FLAG_IID_CANDIDATES) ? 1 : 0) | ((sp->flags & DARTS_FLAG_EQUIANGULAR) ? 2 : 0) |

@@ -92,6 +92,7 @@ struct TraceParams {
   float mis_alpha;
   int uniform_sensor;
   int no_eda;                      // ablation: phase-function directions only
+  int surface_eda;                 // EDA/cosine-lobe MIS directions at surface vertices
   int no_da;                       // ablation: truncated-exponential distances (RIS weights 1)
   int ris_mode;                    // bit 0: i.i.d. candidates, 1: equiangular candidates, 2: reservoir
   int accumulate;                  // add the estimate into hist / sumsq instead of overwriting

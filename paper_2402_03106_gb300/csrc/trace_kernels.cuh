@@ -83,6 +83,8 @@ struct Path {
   float ey0, ey1, ey2, en0, en1, en2, ie, s_hi_e;
   int elem, nmed;
   int surf;          // sphere the current vertex lies on, -1 otherwise
+  float salb;        // EDA at surfaces: albedo of the surface the vertex lies on (0: none);
+                     // the previous direction (wx, wy, wz) then holds its normal
   bool fixed, miss;
   // full-gate DARTS: the step's control-vertex and surface contributions
   // (flat bin, value; bin -1 when none)
@@ -591,6 +593,7 @@ struct Stepper {
     p.a0 = p.a1 = p.a2 = p.gsum = 0.0f;
     p.miss = false;
     p.surf = -1;
+    p.salb = 0.0f;
     // emitter point
     const U4 ue = rng(P, j, 0xFFFFFFu, 2);
     const float target = u01(ue.x);
@@ -718,6 +721,14 @@ struct Stepper {
     p.surf = hit >= 2 ? hit - 2 : -1;
     const float alb = hit == 1 ? P.wall_albedo : P.sph_albedo[hit - 2];
     const float c = p.beta * surface_connect(P, p, nx, ny, nz, alb, r_out);
+    if (P.surface_eda) {  // the next vertex draws its direction (EDA / cosine-lobe MIS)
+      p.wx = nx;
+      p.wy = ny;
+      p.wz = nz;
+      p.salb = alb;
+      p.fixed = false;
+      return c;
+    }
     const U4 us = rng(P, p.j, (uint32_t)(p.k + 1), 1);
     float sn, cs;
     sincos_2pi(u01(us.z), &sn, &cs);
@@ -767,6 +778,7 @@ struct Stepper {
       float sphi, cphi;
       sincos_2pi(u01(u1.z), &sphi, &cphi);
       const bool eda = v0 < gamma;
+      const bool lobe = p.salb > 0.0f;  // base strategy: the cosine lobe about a surface normal
       const int lo = row_search(row, P.n_mu, v1);
       const float c_lo = row[lo], c_hi = row[lo + 1];
       const float fr = __fdividef(v1 - c_lo, c_hi - c_lo);
@@ -774,8 +786,8 @@ struct Stepper {
       // 1 -+ mu of the table sample from the bin index: no cancellation near +-1
       const float st_eda = sqrtf(fmaxf(0.0f, ((float)(P.n_mu - lo) - fr) * P.inv_mu_scale *
                                                  (((float)lo + fr) * P.inv_mu_scale)));
-      const float mu_hg = hg_sample(gb, v1);
-      const float st_hg = hg_sin(gb, v1);
+      const float mu_hg = lobe ? sqrtf(v1) : hg_sample(gb, v1);
+      const float st_hg = lobe ? sqrtf(1.0f - v1) : hg_sin(gb, v1);
       frame_dir(eda ? ax : bx, eda ? ay : by, eda ? az : bz, eda ? mu_eda : mu_hg, eda ? st_eda : st_hg, sphi,
                 cphi, &wx, &wy, &wz);
       const float mu_b = eda ? fmaf(wx, bx, fmaf(wy, by, wz * bz)) : mu_hg;
@@ -786,13 +798,22 @@ struct Stepper {
       }
       const float pE = (eda ? c_hi - c_lo : row[bin + 1] - row[bin]) * P.mu_scale * (1.0f / kTwoPi);
       const float hg = hg_eval(mu_b, P.hg_a, P.hg_b, P.hg_c);
-      const float pB = sensor ? kInv4Pi : hg;
-      const float f = sensor ? 1.0f : hg;
+      const float cl = fmaxf(mu_b, 0.0f) * (1.0f / kPi);  // cosine lobe density; BRDF cos = albedo * cl
+      const float pB = sensor ? kInv4Pi : (lobe ? cl : hg);
+      const float f = sensor ? 1.0f : (lobe ? p.salb * cl : hg);
       p.beta *= __fdividef(f, fmaf(gamma, pE - pB, pB));
-      if (ADJ && !sensor) p.gsum += hg_dlog_dg(P, mu_b);
+      if (ADJ && !sensor && !lobe) p.gsum += hg_dlog_dg(P, mu_b);
       if (DEBUG) {
         record(P, p, 2, eda ? 1 : 0);
         record(P, p, 3, (uint8_t)(bin & 0xFF));
+      }
+      if (lobe) {
+        p.salb = 0.0f;
+        if (!(p.beta > 0.0f)) {  // an EDA direction into the surface: nothing follows
+          cnt.add(ST_INVALID);
+          record(P, p, 0, EV_INVALID);
+          return 1;
+        }
       }
     }
     // control vertex, capped at the first surface (case II of Sec. 5.2)

@@ -36,6 +36,7 @@ FLAG_IID_CANDIDATES = 1 << 4  # RIS candidates from independent uniforms (not th
 FLAG_EQUIANGULAR = 1 << 5     # RIS candidates from the equiangular density about the emitter
 FLAG_RESERVOIR = 1 << 6       # RIS selection by weighted reservoir sampling
 FLAG_ACCUMULATE = 1 << 7      # darts_render adds into its outputs instead of overwriting them
+FLAG_SURFACE_EDA = 1 << 8     # EDA / cosine-lobe MIS directions at surface vertices
 
 Vec3 = Tuple[float, float, float]
 

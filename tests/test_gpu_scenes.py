@@ -125,6 +125,33 @@ def test_general_histogram_parity(ctx, name, method):
         np.testing.assert_allclose(sq.cpu().numpy().reshape(-1), sqref, rtol=2e-3, atol=1e-9 * sqref.max())
 
 
+@pytest.mark.parametrize("name", sorted(SCENES))
+@pytest.mark.parametrize("method", [S.DARTS, S.DARTS_FULL_GATE])
+def test_surface_eda_parity(ctx, name, method):
+    """EDA directions at surface vertices (FLAG_SURFACE_EDA): per-path
+    parity with the oracle (bins, decision traces, contributions within the
+    per-path bound) and matched-seed histograms within relative L2 1e-3."""
+    sc = SCENES[name]()
+    sp = S.Sampling(seed=5, paths_per_element=8 if sc.sensor.kind == S.SENSOR_PINHOLE else 1 << 14,
+                    max_bounces=30, method=method, flags=S.FLAG_SURFACE_EDA)
+    n, first = 2048, 300
+    gpu = ctx.debug_paths(sc, sp, first, n)
+    ref = O.trace_paths(sc, sp, first, n, method=method)
+    sens = 5.0 * displaced_sensitivity(sc, sp, first, n, method, ref)
+    check_paths(gpu, ref, sp.max_bounces, extra_tol=sens)
+    assert np.count_nonzero(ref["contrib"]) > n // 20
+    if sc.sensor.kind == S.SENSOR_PINHOLE:
+        sc.sensor.width, sc.sensor.height = 8, 8
+        sp.paths_per_element = 64
+    else:
+        sp.paths_per_element = 1 << 15
+    sp.max_bounces = 20
+    h = ctx.render(sc, sp).cpu().numpy().reshape(-1)
+    ctx.sync()
+    href, _, _ = O.render(sc, sp, method)
+    assert np.linalg.norm(h - href) <= 1e-3 * np.linalg.norm(href)
+
+
 def test_camera_rows_are_pixels(ctx):
     """Pixel p of a W x H camera is row [p // W, p % W] of the output: a
     render restricted (by the debug path) to pixel p's ids puts its

@@ -652,6 +652,45 @@ def test_estimators_agree_with_surfaces_and_camera(scene):
     assert abs(hv - hp) < 4.5 * math.sqrt(sv ** 2 + spp ** 2), res
 
 
+FLAG_SURFACE_EDA = 1 << 8
+
+
+@pytest.mark.parametrize("scene", ["box", "spheres"])
+def test_surface_eda_stays_unbiased(scene):
+    """EDA directions at surface vertices (one-sample MIS with the cosine
+    lobe, f = albedo cos / pi) change the sampling, not the estimate: the
+    DARTS render with them agrees with the uniform-temporal tracer on the
+    walled box (walls on five faces) and on the sphere scene, over all bins
+    and per bin."""
+    if scene == "box":
+        sc = S.box_camera_scene(seed=1, width=2, height=2, n_bins=8, t_max=10.0)
+    else:
+        sc = S.spheres_camera_scene(seed=1, width=2, height=2, n_spheres=16, n_bins=8)
+        sc.gate.t_min, sc.gate.t_max = 1.0, 9.0
+    n, K = 1 << 15, 6
+    hd, sqd, _ = O.render(sc, S.Sampling(seed=21, paths_per_element=n, max_bounces=K, flags=FLAG_SURFACE_EDA),
+                          O.ORC_DARTS)
+    hp, sqp, _ = O.render(sc, S.Sampling(seed=22, paths_per_element=n, max_bounces=K), O.ORC_PLAIN_UNIFORM_T)
+    sd, sp_ = O.standard_error(hd, sqd, n / 8), O.standard_error(hp, sqp, n)
+    assert abs(hd.sum() - hp.sum()) < 4.5 * math.sqrt(np.sum(sd ** 2) + np.sum(sp_ ** 2))
+    assert np.all(np.abs(hd - hp) <= 5.0 * np.sqrt(sd ** 2 + sp_ ** 2) + 1e-12)
+
+
+def test_surface_eda_without_eda_is_the_cosine_bounce():
+    """With the EDA share gamma forced to 0 (the EDA ablation) the surface
+    vertex's MIS reduces to the cosine lobe drawn from the same uniforms
+    (vertex k + 1, group 1) and f / p = albedo: every path's contribution
+    equals the one of the plain cosine bounce to rounding."""
+    sc = S.box_camera_scene(seed=0, width=8, height=8, n_bins=64)
+    base = S.Sampling(seed=3, paths_per_element=16, max_bounces=20, flags=S.FLAG_NO_EDA)
+    with_flag = S.Sampling(seed=3, paths_per_element=16, max_bounces=20, flags=S.FLAG_NO_EDA | FLAG_SURFACE_EDA)
+    a = O.trace_paths(sc, base, 0, 1024)
+    b = O.trace_paths(sc, with_flag, 0, 1024)
+    assert np.array_equal(a["nvert"], b["nvert"]) and np.array_equal(a["bin"], b["bin"])
+    np.testing.assert_allclose(b["contrib"], a["contrib"], rtol=1e-12, atol=0)
+    assert np.count_nonzero(a["contrib"]) > 100
+
+
 def test_camera_ids_wrap_with_continuing_sample_index():
     """Ids one frame apart fall on the same pixel with DARTS bins N_e apart
     (mod B): shards of a camera render cover further bins, not the same ones."""
