@@ -813,7 +813,9 @@ def roofline(per, kms, workload, traffic_workload=None, paths=None):
            "kernel": "trace_kernel (persistent path kernel)", "kernel_ms": kms,
            "peak_note": f"derived nominal: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                         f"{clock_mhz:.0f} MHz (measured max SM clock)",
-           "vertices_per_launch": per.get("vertices")}
+           "vertices_per_launch": per.get("vertices"),
+           "events_per_launch": {k: per[k] for k in ("paths", "vertices", "connections_nonempty", "distance_steps",
+                                                     "fp64_ellipse", "fp64_phi") if k in per}}
     if w is None or not kms:
         out["note"] = "no op-count summary for this workload"
         return out
