@@ -725,7 +725,8 @@ def time_steps(ctx, torch, step, steps, flush, kernel_timing=True, finish=None):
 def mse_time_spheres(ctx, S, torch, seeds=16, spps=(64, 256)):
     """MSE x time on the largest configuration (512x512 camera, 32 spheres,
     two emitters, 1000 bins, K = 100): DARTS, full-gate DARTS, the plain
-    uniform-temporal tracer and the vanilla tracer, `seeds` seeds at 64 and
+    uniform-temporal tracer, the vanilla tracer, and DARTS without EDA
+    directions and with EDA at surface vertices, `seeds` seeds at 64 and
     256 spp.  The reference is the path-weighted mean of every DARTS and
     uniform-temporal render (both unbiased; 160x the paths of one 64-spp
     render), formed on the device in a first pass; a second pass re-renders
@@ -734,13 +735,14 @@ def mse_time_spheres(ctx, S, torch, seeds=16, spps=(64, 256)):
     ratio = (MSE x time)_base / (MSE x time)_darts with the median render
     time (table build + trace, CUDA events)."""
     sc = S.spheres_camera_scene(seed=0)
-    methods = (("darts", S.DARTS), ("darts_full_gate", S.DARTS_FULL_GATE),
-               ("plain_uniform_t", S.PLAIN_UNIFORM_T), ("vanilla_direct", S.VANILLA_DIRECT))
+    methods = (("darts", S.DARTS, 0), ("darts_full_gate", S.DARTS_FULL_GATE, 0),
+               ("plain_uniform_t", S.PLAIN_UNIFORM_T, 0), ("vanilla_direct", S.VANILLA_DIRECT, 0),
+               ("darts_no_eda", S.DARTS, S.FLAG_NO_EDA), ("darts_surface_eda", S.DARTS, S.FLAG_SURFACE_EDA))
     out = {"workload": "512x512 spheres frame of the benchmark, 1000 bins on [0,20), K=100", "seeds": seeds}
 
-    def render(scene, m, spp, seed, buf):
+    def render(scene, m, fl, spp, seed, buf):
         sp = S.Sampling(seed=seed, paths_per_element=spp, max_bounces=100, method=m,
-                        flags=S.FLAG_REBUILD_TABLE if m in (S.DARTS, S.DARTS_FULL_GATE) else 0)
+                        flags=fl | (S.FLAG_REBUILD_TABLE if m in (S.DARTS, S.DARTS_FULL_GATE) else 0))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         ctx.render(scene, sp, out=buf)
@@ -754,25 +756,25 @@ def mse_time_spheres(ctx, S, torch, seeds=16, spps=(64, 256)):
         ref = torch.zeros(shape, dtype=torch.float64, device="cuda")
         wsum = 0.0
         for spp in spps_:  # pass 1: the pooled reference
-            for name, m in methods[:3:2]:
+            for name, m, fl in methods[:3:2]:
                 for s_ in range(seeds):
-                    render(scene, m, spp, seed0 + s_, buf)
+                    render(scene, m, fl, spp, seed0 + s_, buf)
                     ref.add_(buf, alpha=float(spp))
                     wsum += spp
         ref.div_(wsum)
         res = {"reference_paths_per_pixel": int(wsum)}
         for spp in spps_:  # pass 2: per-seed MSE
             rows = {}
-            for name, m in methods:
+            for name, m, fl in methods:
                 mse, ts = [], []
                 for s_ in range(seeds):
-                    ts.append(render(scene, m, spp, seed0 + s_, buf))
+                    ts.append(render(scene, m, fl, spp, seed0 + s_, buf))
                     buf.sub_(ref)
                     mse.append(float(torch.mean(buf * buf)))
                 mse.sort()
                 rows[name] = {"seconds_per_render": statistics.median(ts),
                               "mse_mean": statistics.fmean(mse), "mse_median": statistics.median(mse)}
-            for base in ("plain_uniform_t", "vanilla_direct", "darts_full_gate"):
+            for base in ("plain_uniform_t", "vanilla_direct", "darts_full_gate", "darts_no_eda", "darts_surface_eda"):
                 b, d = rows[base], rows["darts"]
                 rows[f"ratio_{base}_over_darts"] = {
                     "mse_mean_time": b["mse_mean"] * b["seconds_per_render"] /

@@ -527,6 +527,12 @@ void make_trace_params(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
     P->width = sen.width;
     P->height = sen.height;
   }
+  {  // the lean camera kernel: every branch it drops is one this scene never takes
+    bool points = true;
+    for (int k = 0; k < sc->n_emitters; ++k) points = points && sc->emitters[k].kind == DARTS_EMITTER_POINT;
+    P->lean = (P->general && P->camera && P->cam_inside && points && !sc->gate.weights &&
+               !(sp->flags & DARTS_FLAG_SURFACE_EDA)) ? 1 : 0;
+  }
   P->stats = ctx->scratch + 2;
   P->counter = ctx->scratch;
   P->ticket = reinterpret_cast<unsigned int*>(ctx->scratch + 1);

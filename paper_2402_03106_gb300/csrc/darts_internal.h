@@ -71,6 +71,9 @@ struct TraceParams {
   int n_bins;
   // general scenes: several / area emitters, surfaces, a pinhole camera
   int general;                     // run the general variant of the path kernel
+  int lean;                        // general scene with point emitters only, a camera inside the
+                                   // medium, no temporal response, no EDA at surfaces: the lean
+                                   // camera kernel of DARTS
   int n_emitters;
   EmitterParams em[kMaxEmitters];
   int n_spheres;

@@ -13,7 +13,14 @@ cudaError_t launch_method(const TraceParams& p, int grid, int block, bool debug,
     if (debug) return tile ? launch_one<METHOD, 8, true, true, 512, true>(p, grid, smem, s)
                            : launch_one<METHOD, 8, true, false, 512, true>(p, grid, smem, s);
     if (tile) return launch_one<METHOD, 8, false, true, 512, true>(p, grid, smem, s);
-    if constexpr (METHOD == kDarts) {  // the camera frame of the benchmark: 640 and 768 threads too
+    if constexpr (METHOD == kDarts) {  // camera frames: 640 and 768 threads too, and the lean kernels
+      if (p.lean) {
+        switch (block) {
+          case 640: return launch_one<METHOD, 8, false, false, 640, true, false, true>(p, grid, smem, s);
+          case 768: return launch_one<METHOD, 8, false, false, 768, true, false, true>(p, grid, smem, s);
+          default: return launch_one<METHOD, 8, false, false, 512, true, false, true>(p, grid, smem, s);
+        }
+      }
       switch (block) {
         case 640: return launch_one<METHOD, 8, false, false, 640, true>(p, grid, smem, s);
         case 768: return launch_one<METHOD, 8, false, false, 768, true>(p, grid, smem, s);

@@ -532,8 +532,22 @@ __device__ __forceinline__ int w_bin(const TraceParams& P, unsigned long long s,
   return min(lo, P.n_bins - 1);
 }
 
-template <int METHOD, int MAXM, bool DEBUG, bool ADJ = false, bool GEN = false, bool VAR = false>
+// LEAN (general kernels only): the scene has point emitters only, a point
+// sensor or a camera inside the medium, no temporal response and no EDA at
+// surfaces, so those branches are compiled out (the host picks it).
+template <int METHOD, int MAXM, bool DEBUG, bool ADJ = false, bool GEN = false, bool VAR = false,
+          bool LEAN = false>
 struct Stepper {
+  // Radiant intensity of the path's emitter point toward x, and the zero
+  // temporal weight test, without the branches a lean scene never takes.
+  __device__ __forceinline__ static float intensity(const Path& p, float x, float y, float z) {
+    if constexpr (LEAN) return p.ie;
+    else return emit_intensity(p, x, y, z);
+  }
+  __device__ __forceinline__ static bool zero_weight(const TraceParams& P, int b) {
+    if constexpr (LEAN) return b < 0 || b >= P.n_bins;
+    else return zero_w(P, b);
+  }
   // Initialise a path with local index j.
   __device__ static void init(const TraceParams& P, Path& p, unsigned long long j, int bin) {
     p.x = P.xs[0];
@@ -614,7 +628,7 @@ struct Stepper {
     if (METHOD == kDarts) {
       const U4 uo = philox4x32_10((uint32_t)p.elem, 0u, P.stream, (kVertexElement << 8) | 0u, P.key0, P.key1);
       int b;
-      if (P.wcdf) {
+      if (!LEAN && P.wcdf) {
         const unsigned long long oe = (unsigned long long)floor((double)u01(uo.x) * (double)P.spp);
         b = w_bin(P, s, min(oe, P.spp - 1), (double)u01(uo.y));
       } else {
@@ -642,7 +656,7 @@ struct Stepper {
       p.wy = wy * iw;
       p.wz = wz * iw;
       p.fixed = true;
-      if (P.cam_inside) {
+      if (LEAN || P.cam_inside) {
         p.x = P.cam_pos[0];
         p.y = P.cam_pos[1];
         p.z = P.cam_pos[2];
@@ -707,7 +721,7 @@ struct Stepper {
     const float cs = fmaf(dx, nx, fmaf(dy, ny, dz * nz)) * ir;
     if (!(cs > 0.0f)) return 0.0f;
     if (!visible(P, p.x, p.y, p.z, p.ey0, p.ey1, p.ey2, p.surf)) return 0.0f;
-    return albedo * (1.0f / kPi) * cs * __expf(-P.sigma_t * r) * emit_intensity(p, p.x, p.y, p.z) / r2;
+    return albedo * (1.0f / kPi) * cs * __expf(-P.sigma_t * r) * intensity(p, p.x, p.y, p.z) / r2;
   }
 
   // Surface vertex: move onto the surface, connect, then a cosine-weighted
@@ -721,7 +735,7 @@ struct Stepper {
     p.surf = hit >= 2 ? hit - 2 : -1;
     const float alb = hit == 1 ? P.wall_albedo : P.sph_albedo[hit - 2];
     const float c = p.beta * surface_connect(P, p, nx, ny, nz, alb, r_out);
-    if (P.surface_eda) {  // the next vertex draws its direction (EDA / cosine-lobe MIS)
+    if (!LEAN && P.surface_eda) {  // the next vertex draws its direction (EDA / cosine-lobe MIS)
       p.wx = nx;
       p.wy = ny;
       p.wz = nz;
@@ -778,7 +792,7 @@ struct Stepper {
       float sphi, cphi;
       sincos_2pi(u01(u1.z), &sphi, &cphi);
       const bool eda = v0 < gamma;
-      const bool lobe = p.salb > 0.0f;  // base strategy: the cosine lobe about a surface normal
+      const bool lobe = !LEAN && p.salb > 0.0f;  // base strategy: the cosine lobe about a surface normal
       const int lo = row_search(row, P.n_mu, v1);
       const float c_lo = row[lo], c_hi = row[lo + 1];
       const float fr = __fdividef(v1 - c_lo, c_hi - c_lo);
@@ -829,7 +843,7 @@ struct Stepper {
       float cc = connect(P, wx, wy, wz, C, ax, ay, az, S_lo, S_hi, u01(u1.w), false, &S, cnt, &cos_s,
                          &tctl, 1.0f);
       const float qx = fmaf(wx, tctl, p.x), qy = fmaf(wy, tctl, p.y), qz = fmaf(wz, tctl, p.z);
-      cc *= emit_intensity(p, qx, qy, qz);
+      cc *= intensity(p, qx, qy, qz);
       if (!visible(P, qx, qy, qz, p.ey0, p.ey1, p.ey2, -1)) cc = 0.0f;
       p.c = fmaf(p.beta, cc, p.c);
       cnt.add(ST_CONN);
@@ -838,7 +852,7 @@ struct Stepper {
         const int b = min(max((int)floorf(((p.L + S) - p.Sm0) * P.inv_S_bin), 0), P.n_bins - 1);
         p.cb = p.elem * P.n_bins + b;
         p.cv = p.beta * cc;
-        if (zero_w(P, b)) cnt.add(ST_REJECT);
+        if (zero_weight(P, b)) cnt.add(ST_REJECT);
       }
       if (ADJ) {
         const float cv = p.beta * cc, ell = p.L + S;
@@ -871,7 +885,7 @@ struct Stepper {
         if (METHOD == kDartsFull) {
           const float y = (Lt - p.Sm0) * P.inv_S_bin;
           const int b = (y >= 0.0f && y < (float)P.n_bins) ? min((int)y, P.n_bins - 1) : -1;
-          if (zero_w(P, b)) cnt.add(ST_REJECT2);
+          if (zero_weight(P, b)) cnt.add(ST_REJECT2);
           if (b >= 0) {
             p.cb2 = p.elem * P.n_bins + b;
             p.cv2 = cs;
@@ -941,13 +955,13 @@ struct Stepper {
         float cc = connect(P, p.wx, p.wy, p.wz, C, ex * invC, ey * invC, ez * invC, S_lo, S_hi,
                            u01(u1.w), true, &S, cnt, &cos_s, &tctl, 1.0f);
         const float qx = fmaf(p.wx, tctl, p.x), qy = fmaf(p.wy, tctl, p.y), qz = fmaf(p.wz, tctl, p.z);
-        cc *= emit_intensity(p, qx, qy, qz);
+        cc *= intensity(p, qx, qy, qz);
         if (!visible(P, qx, qy, qz, p.ey0, p.ey1, p.ey2, -1)) cc = 0.0f;
         cnt.add(ST_CONN);
         const float y = ((p.L + S) - p.Sm0) * P.inv_S_bin;
         const int b = min(max((int)floorf(y), 0), P.n_bins - 1);
         cnt.add(ST_SAMPLE);
-        if (zero_w(P, b)) cnt.add(ST_REJECT);
+        if (zero_weight(P, b)) cnt.add(ST_REJECT);
         *out_bin = row + b;
         *out_c = p.beta * cc;
         p.c += *out_c;
@@ -970,7 +984,7 @@ struct Stepper {
         if (cs > 0.0f) {
           const float y = ((p.L + r) - p.Sm0) * P.inv_S_bin;
           cnt.add(ST_SAMPLE2);
-          if (zero_w(P, (y >= 0.0f && y < (float)P.n_bins) ? min((int)y, P.n_bins - 1) : -1)) cnt.add(ST_REJECT2);
+          if (zero_weight(P, (y >= 0.0f && y < (float)P.n_bins) ? min((int)y, P.n_bins - 1) : -1)) cnt.add(ST_REJECT2);
           if (y >= 0.0f && y < (float)P.n_bins) {
             *out_bin2 = row + min((int)y, P.n_bins - 1);
             *out_c2 = cs;
@@ -1014,7 +1028,7 @@ struct Stepper {
           cnt.add(ST_CONN);
           const float y = ((p.L + r) - p.Sm0) * P.inv_S_bin;
           cnt.add(ST_SAMPLE);
-          if (zero_w(P, (y >= 0.0f && y < (float)P.n_bins) ? min((int)y, P.n_bins - 1) : -1)) cnt.add(ST_REJECT);
+          if (zero_weight(P, (y >= 0.0f && y < (float)P.n_bins) ? min((int)y, P.n_bins - 1) : -1)) cnt.add(ST_REJECT);
           if (y >= 0.0f && y < (float)P.n_bins) {
             *out_bin = row + min((int)y, P.n_bins - 1);
             *out_c = cs;
@@ -1048,11 +1062,11 @@ struct Stepper {
       const float cos_s = -__fdividef(ex * p.wx + ey * p.wy + ez * p.wz, C);
       const float y = ((p.L + C) - p.Sm0) * P.inv_S_bin;
       cnt.add(ST_SAMPLE);
-      if (zero_w(P, (y >= 0.0f && y < (float)P.n_bins) ? min((int)y, P.n_bins - 1) : -1)) cnt.add(ST_REJECT);
+      if (zero_weight(P, (y >= 0.0f && y < (float)P.n_bins) ? min((int)y, P.n_bins - 1) : -1)) cnt.add(ST_REJECT);
       if (y >= 0.0f && y < (float)P.n_bins) {
         cnt.add(ST_CONN);
         float c = p.beta * hg_eval(cos_s, P.hg_a, P.hg_b, P.hg_c) * __expf(-P.sigma_t * C) *
-                  emit_intensity(p, p.x, p.y, p.z) / C2;
+                  intensity(p, p.x, p.y, p.z) / C2;
         if (!visible(P, p.x, p.y, p.z, p.ey0, p.ey1, p.ey2, -1)) c = 0.0f;
         *out_bin = row + min((int)y, P.n_bins - 1);
         *out_c = c;
@@ -1172,7 +1186,7 @@ struct Stepper {
         p.cb = b;
         p.cv = p.beta * cc;
         cnt.add(ST_SAMPLE);
-        if (zero_w(P, b)) cnt.add(ST_REJECT);
+        if (zero_weight(P, b)) cnt.add(ST_REJECT);
       }
       if (ADJ) {
         // score of log f: k walk vertices + the control vertex scatter (sigma_s),
@@ -1325,7 +1339,7 @@ struct Stepper {
         int b = (int)floorf(y);
         b = min(max(b, 0), P.n_bins - 1);
         cnt.add(ST_SAMPLE);
-        if (zero_w(P, b)) cnt.add(ST_REJECT);
+        if (zero_weight(P, b)) cnt.add(ST_REJECT);
         *out_bin = b;
         *out_c = p.beta * cc;
         p.c += *out_c;
@@ -1367,7 +1381,7 @@ struct Stepper {
       const float cos_s = -__fdividef(ex * p.wx + ey * p.wy + ez * p.wz, C);
       const float y = ((p.L + C) - P.S_gate_lo) * P.inv_S_bin;
       cnt.add(ST_SAMPLE);
-      if (zero_w(P, (y >= 0.0f && y < (float)P.n_bins) ? min((int)y, P.n_bins - 1) : -1)) cnt.add(ST_REJECT);
+      if (zero_weight(P, (y >= 0.0f && y < (float)P.n_bins) ? min((int)y, P.n_bins - 1) : -1)) cnt.add(ST_REJECT);
       if (y >= 0.0f && y < (float)P.n_bins) {
         cnt.add(ST_CONN);
         *out_bin = min((int)y, P.n_bins - 1);
@@ -1561,7 +1575,8 @@ __device__ __forceinline__ float path_weight(const TraceParams& P, const Path& p
   return __ldg(P.wbin + b);
 }
 
-template <int METHOD, int MAXM, bool DEBUG, bool TILE, bool ADJ, bool GEN = false, bool VAR = false>
+template <int METHOD, int MAXM, bool DEBUG, bool TILE, bool ADJ, bool GEN = false, bool VAR = false,
+          bool LEAN = false>
 __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab,
                                           unsigned long long* counter, unsigned long long N,
                                           float* wsum, float* wcomp, float* wsq, RisTaskT<VAR>* wtasks,
@@ -1592,8 +1607,8 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
       const int n_dead = __popc(dead);
       const unsigned long long avail = pool_end - pool_next;
       if (!alive && (unsigned long long)rank < avail) {
-        if constexpr (GEN) Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR>::init_gen(P, p, pool_next + rank);
-        else Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR>::init(P, p, pool_next + rank, add_mod(pool_bin, rank, B));
+        if constexpr (GEN) Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR, LEAN>::init_gen(P, p, pool_next + rank);
+        else Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR, LEAN>::init(P, p, pool_next + rank, add_mod(pool_bin, rank, B));
         alive = true;
       }
       if ((unsigned long long)n_dead > avail) {
@@ -1610,8 +1625,8 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
           const int base_bin = (int)((P.bin_base + base) % (unsigned long long)B);
           const long long r2 = (long long)rank - (long long)avail;
           if (!alive && r2 >= 0 && (unsigned long long)r2 < end - base) {
-            if constexpr (GEN) Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR>::init_gen(P, p, base + (unsigned long long)r2);
-            else Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR>::init(P, p, base + (unsigned long long)r2,
+            if constexpr (GEN) Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR, LEAN>::init_gen(P, p, base + (unsigned long long)r2);
+            else Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR, LEAN>::init(P, p, base + (unsigned long long)r2,
                                                          add_mod(base_bin, (int)r2, B));
             alive = true;
           }
@@ -1641,11 +1656,11 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
       bool need = false;
       if (alive) {
         if constexpr (GEN) {
-          const int st = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR>::vertex_gen(P, p, tab, cnt, task);
+          const int st = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR, LEAN>::vertex_gen(P, p, tab, cnt, task);
           fin = st == 1;
           need = st == 0;
         } else {
-          fin = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR>::vertex_darts(P, p, tab, cnt, task);
+          fin = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR, LEAN>::vertex_darts(P, p, tab, cnt, task);
           need = !fin;
         }
       }
@@ -1653,9 +1668,9 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
       if (kCoop) {
         ris_warp<VAR>(P, need, task, wtasks, wresults, r, cnt);
       } else if (need) {
-        r = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR>::ris_lane(P, task, cnt);
+        r = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR, LEAN>::ris_lane(P, task, cnt);
       }
-      if (need) fin = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR>::finish_ris(P, p, r, task.nonempty, cnt);
+      if (need) fin = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR, LEAN>::finish_ris(P, p, r, task.nonempty, cnt);
       if constexpr (METHOD == kDartsFull) {
         if (alive) {
           cbin = p.cb;
@@ -1669,10 +1684,10 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
       }
     } else if (alive) {
       if constexpr (GEN) {
-        fin = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR>::step_base_gen(P, p, cnt, &cbin, &cval, &cbin2, &cval2);
+        fin = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR, LEAN>::step_base_gen(P, p, cnt, &cbin, &cval, &cbin2, &cval2);
         cval2 *= P.wb;
       } else {
-        fin = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR>::step_base(P, p, cnt, &cbin, &cval);
+        fin = Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR, LEAN>::step_base(P, p, cnt, &cbin, &cval);
       }
       cval *= P.wb;
     }
@@ -1732,7 +1747,7 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
 }
 
 template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK, bool ADJ = false, bool GEN = false,
-          bool VAR = false>
+          bool VAR = false, bool LEAN = false>
 __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
   extern __shared__ float4 smem4[];
   // general kernels: the sphere-culling masks and spheres come first
@@ -1776,7 +1791,7 @@ __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
   const unsigned long long chunk = P.chunk ? P.chunk : (unsigned long long)kPathChunk;
   const unsigned long long first = ((unsigned long long)blockIdx.x * nwarps + warp) * chunk;
   const unsigned long long dyn_base = (unsigned long long)gridDim.x * nwarps * chunk;
-  path_loop<METHOD, MAXM, DEBUG, TILE, ADJ, GEN, VAR>(P, tab, P.counter, P.N, wsum, wcomp, wsq, wtasks,
+  path_loop<METHOD, MAXM, DEBUG, TILE, ADJ, GEN, VAR, LEAN>(P, tab, P.counter, P.N, wsum, wcomp, wsq, wtasks,
                                                  wresults, warp_events[warp], do_sq, g_s, g_c, g_q, first,
                                                  first + chunk, dyn_base);
 
@@ -2004,9 +2019,10 @@ cudaError_t smem_limit(size_t smem) {
   return e;
 }
 
-template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK, bool GEN = false, bool VAR = false>
+template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK, bool GEN = false, bool VAR = false,
+          bool LEAN = false>
 cudaError_t launch_one(const TraceParams& p0, int grid, size_t smem, cudaStream_t s) {
-  constexpr auto kern = trace_kernel<METHOD, MAXM, DEBUG, TILE, BLOCK, false, GEN, VAR>;
+  constexpr auto kern = trace_kernel<METHOD, MAXM, DEBUG, TILE, BLOCK, false, GEN, VAR, LEAN>;
   cudaError_t e = smem_limit<kern>(smem);
   if (e != cudaSuccess) return e;
   TraceParams p = p0;

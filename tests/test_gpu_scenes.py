@@ -152,6 +152,34 @@ def test_surface_eda_parity(ctx, name, method):
     assert np.linalg.norm(h - href) <= 1e-3 * np.linalg.norm(href)
 
 
+def test_lean_camera_kernel_equals_the_general_one(ctx):
+    """The sphere frame (point emitters, camera inside the medium, no
+    temporal response) runs the lean camera kernel.  A zero-energy area
+    emitter appended to the scene is never picked, so every path is the
+    same, but it makes the scene run the full general kernel: the two
+    frames agree up to the FP64 order of their atomics and the FP32
+    rounding of two compilations, at every block size; the probed paths
+    land in the same bins with the same contributions to FP32 rounding."""
+    sc = S.spheres_camera_scene(seed=0, width=64, height=64, n_bins=250)
+    sp = S.Sampling(seed=8, paths_per_element=32, max_bounces=60)
+    full = dataclasses.replace(sc, emitters=sc.emitters + [
+        S.Emitter((2.0, 3.9, 2.0), 0.0, 0.0, S.EMITTER_AREA, (0.2, 0.0, 0.0), (0.0, 0.0, 0.2))])
+    n = S.total_paths(sc, sp)
+    for block in (512, 640, 768):
+        ctx.set_launch_config(block=block)
+        outs, probes = [], []
+        for scene in (sc, full):
+            probe, pc, pb = ctx.probe(first=3, stride=n // 1024, count=1024)
+            h = ctx.render(scene, sp, probe=probe)
+            ctx.sync()
+            outs.append(h.cpu())
+            probes.append((pc.cpu().clone(), pb.cpu().clone()))
+        torch.testing.assert_close(outs[0], outs[1], rtol=1e-5, atol=1e-12 * float(outs[0].abs().max()))
+        assert torch.equal(probes[0][1], probes[1][1])
+        torch.testing.assert_close(probes[0][0], probes[1][0], rtol=1e-5, atol=0.0)
+    ctx.set_launch_config()
+
+
 def test_camera_rows_are_pixels(ctx):
     """Pixel p of a W x H camera is row [p // W, p % W] of the output: a
     render restricted (by the debug path) to pixel p's ids puts its
