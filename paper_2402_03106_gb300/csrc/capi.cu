@@ -484,10 +484,12 @@ void make_trace_params(darts_ctx* ctx, const darts_scene* sc, const darts_sampli
     P->sph[k] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
     P->sph_albedo[k] = (float)q[4];
   }
-  {  // slab grid of the sphere culling (see cast_ray): the medium box in kCullSlabs slabs per axis
+  {  // slab grid of the sphere culling (see cast_ray): the medium box in cull_slabs slabs per axis;
+     // 32 for a camera (its kernel keeps no histogram tiles in shared memory), else 16
+    P->cull_slabs = sc->sensor.kind == DARTS_SENSOR_PINHOLE ? kMaxCullSlabs : 16;
     double ext = 0.0;
     for (int i = 0; i < 3; ++i) {
-      const double w = (sc->geom.hi[i] - sc->geom.lo[i]) / kCullSlabs;
+      const double w = (sc->geom.hi[i] - sc->geom.lo[i]) / P->cull_slabs;
       P->cull_inv_w[i] = (float)(1.0 / w);
       P->cull_off[i] = (float)(-sc->geom.lo[i] / w);
       ext = std::max(ext, sc->geom.hi[i] - sc->geom.lo[i]);

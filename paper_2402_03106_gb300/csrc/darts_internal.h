@@ -13,12 +13,15 @@ constexpr int kStatCount = 12;      // device event counters (see the ST_ slots 
 constexpr int kPathChunk = 64;      // paths a warp claims from the global counter
 constexpr int kMaxEmitters = 8;
 constexpr int kMaxSpheres = 64;
-// Sphere culling of the general kernels: per axis, kCullSlabs slabs of the
-// medium box and, for every slab range [i, j], the mask of the spheres whose
-// (slightly enlarged) extent meets it; built in shared memory by each CTA.
-constexpr int kCullSlabs = 16;
-constexpr size_t kCullBytes = 3 * kCullSlabs * kCullSlabs * sizeof(unsigned long long) +
-                              kMaxSpheres * 4 * sizeof(float);
+// Sphere culling of the general kernels: per axis, cull_slabs slabs of the
+// medium box (16, or 32 where shared memory allows: camera kernels) and, for
+// every slab range [i, j], the mask of the spheres whose (slightly enlarged)
+// extent meets it; built in shared memory by each CTA, followed by the
+// spheres themselves.
+constexpr int kMaxCullSlabs = 32;
+__host__ __device__ inline size_t cull_bytes(int slabs) {
+  return 3 * (size_t)slabs * slabs * sizeof(unsigned long long) + kMaxSpheres * 4 * sizeof(float);
+}
 
 // One pulse emitter: an isotropic point (kind 0) or a one-sided Lambertian
 // parallelogram pos + s u + t v emitting toward n = u x v / |u x v| (kind 1).
@@ -81,6 +84,7 @@ struct TraceParams {
   float sph_albedo[kMaxSpheres];
   float cull_off[3], cull_inv_w[3]; // slab grid of the box: slab = floor(x inv_w + off), off = -lo inv_w
   float cull_eps;                  // enlargement of a sphere's extent in the masks
+  int cull_slabs;                  // slabs per axis of the culling grid
   int walls;                       // box faces with walls: bit 2 * axis + (1: hi face)
   float wall_albedo;
   int camera;                      // 0: point sensor at xs; 1: pinhole camera

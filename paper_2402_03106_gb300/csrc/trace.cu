@@ -89,7 +89,7 @@ cudaError_t launch_batch(const BatchParams& bp, int grid, int block, size_t smem
 }
 
 size_t adjoint_smem_bytes(const TraceParams& p) {
-  size_t b = (size_t)p.rows * p.row_stride * sizeof(float) + (p.general ? kCullBytes : 0);
+  size_t b = (size_t)p.rows * p.row_stride * sizeof(float) + (p.general ? cull_bytes(p.cull_slabs) : 0);
   if (p.M == 8) b += (size_t)(512 / 32) * 32 * (sizeof(RisTask) + sizeof(RisResult));
   return b;
 }
@@ -121,7 +121,7 @@ cudaError_t launch_adjoint(const TraceParams& p0, int grid, size_t smem, cudaStr
 size_t trace_smem_bytes(int method, const TraceParams& p, int block, bool tile) {
   const bool darts = method == kDarts || method == kDartsFull;
   size_t b = darts ? (size_t)p.rows * p.row_stride * sizeof(float) : 0;
-  if (p.general) b += kCullBytes;  // sphere-culling masks and the spheres, first in shared memory
+  if (p.general) b += cull_bytes(p.cull_slabs);  // sphere-culling masks and the spheres, first in shared memory
   const size_t task = p.ris_mode ? sizeof(RisTaskVar) : sizeof(RisTask);
   if (darts && p.M == 8) b += (size_t)(block / 32) * 32 * (task + sizeof(RisResult));
   if (tile) b += (size_t)(block / 32) * (p.sumsq ? 3 : 2) * p.n_bins * sizeof(float);

@@ -336,7 +336,7 @@ __device__ __forceinline__ float ray_sphere(const float4 c, float x, float y, fl
 
 // ---- sphere culling ---------------------------------------------------------
 // The general kernels keep, at the start of dynamic shared memory, per axis a
-// of the medium box split into kCullSlabs slabs, the mask M_a[i][j] of the
+// of the medium box split into G = cull_slabs slabs, the mask M_a[i][j] of the
 // spheres whose extent along a, enlarged by cull_eps, meets slabs i..j, and
 // the spheres themselves (float4 centre, radius).  A sphere that a segment
 // meets overlaps the segment's bounding box on every axis, so it is in
@@ -348,20 +348,21 @@ __device__ __forceinline__ const unsigned long long* cull_masks() {
   extern __shared__ float4 smem4[];
   return reinterpret_cast<const unsigned long long*>(smem4);
 }
-__device__ __forceinline__ const float4* cull_spheres() {
-  return reinterpret_cast<const float4*>(cull_masks() + 3 * kCullSlabs * kCullSlabs);
+__device__ __forceinline__ const float4* cull_spheres(const TraceParams& P) {
+  return reinterpret_cast<const float4*>(cull_masks() + 3 * P.cull_slabs * P.cull_slabs);
 }
 __device__ __forceinline__ int cull_slab(const TraceParams& P, int a, float v) {
-  return min(max(__float2int_rd(fmaf(v, P.cull_inv_w[a], P.cull_off[a])), 0), kCullSlabs - 1);
+  return min(max(__float2int_rd(fmaf(v, P.cull_inv_w[a], P.cull_off[a])), 0), P.cull_slabs - 1);
 }
 // Masks and spheres, built by the whole block before any path runs.
 __device__ __forceinline__ void build_cull(const TraceParams& P, int tid, int nthreads) {
   extern __shared__ float4 smem4[];
   unsigned long long* m = reinterpret_cast<unsigned long long*>(smem4);
-  float4* sph = reinterpret_cast<float4*>(m + 3 * kCullSlabs * kCullSlabs);
+  const int G = P.cull_slabs;
+  float4* sph = reinterpret_cast<float4*>(m + 3 * G * G);
   for (int k = tid; k < P.n_spheres; k += nthreads) sph[k] = P.sph[k];
-  for (int e = tid; e < 3 * kCullSlabs * kCullSlabs; e += nthreads) {
-    const int a = e / (kCullSlabs * kCullSlabs), i = (e / kCullSlabs) % kCullSlabs, j = e % kCullSlabs;
+  for (int e = tid; e < 3 * G * G; e += nthreads) {
+    const int a = e / (G * G), i = (e / G) % G, j = e % G;
     unsigned long long bits = 0;
     for (int k = 0; k < P.n_spheres; ++k) {
       const float4 c = P.sph[k];
@@ -379,16 +380,16 @@ __device__ __forceinline__ unsigned long long cull_two(const TraceParams& P, flo
                                                        float mx, float my, float mz, float bx, float by,
                                                        float bz) {
   const unsigned long long* m = cull_masks();
-  constexpr int kAxis = kCullSlabs * kCullSlabs;
+  const int G = P.cull_slabs, kAxis = G * G;
   const int a0 = cull_slab(P, 0, ax), a1 = cull_slab(P, 1, ay), a2 = cull_slab(P, 2, az);
   const int m0 = cull_slab(P, 0, mx), m1 = cull_slab(P, 1, my), m2 = cull_slab(P, 2, mz);
   const int b0 = cull_slab(P, 0, bx), b1 = cull_slab(P, 1, by), b2 = cull_slab(P, 2, bz);
-  const unsigned long long h1 = m[min(a0, m0) * kCullSlabs + max(a0, m0)] &
-                                m[kAxis + min(a1, m1) * kCullSlabs + max(a1, m1)] &
-                                m[2 * kAxis + min(a2, m2) * kCullSlabs + max(a2, m2)];
-  const unsigned long long h2 = m[min(m0, b0) * kCullSlabs + max(m0, b0)] &
-                                m[kAxis + min(m1, b1) * kCullSlabs + max(m1, b1)] &
-                                m[2 * kAxis + min(m2, b2) * kCullSlabs + max(m2, b2)];
+  const unsigned long long h1 = m[min(a0, m0) * G + max(a0, m0)] &
+                                m[kAxis + min(a1, m1) * G + max(a1, m1)] &
+                                m[2 * kAxis + min(a2, m2) * G + max(a2, m2)];
+  const unsigned long long h2 = m[min(m0, b0) * G + max(m0, b0)] &
+                                m[kAxis + min(m1, b1) * G + max(m1, b1)] &
+                                m[2 * kAxis + min(m2, b2) * G + max(m2, b2)];
   return h1 | h2;
 }
 __device__ __forceinline__ unsigned long long cull_segment(const TraceParams& P, float x, float y, float z,
@@ -424,7 +425,7 @@ __device__ __forceinline__ float cast_ray(const TraceParams& P, float x, float y
   *ny = face / 2 == 1 ? ((face & 1) ? -1.0f : 1.0f) : 0.0f;
   *nz = face / 2 == 2 ? ((face & 1) ? -1.0f : 1.0f) : 0.0f;
   if (P.n_spheres == 0) return d;
-  const float4* sph = cull_spheres();
+  const float4* sph = cull_spheres(P);
   unsigned long long cand = cull_segment(P, x, y, z, wx, wy, wz, d);
   if (skip >= 0) cand &= ~(1ull << skip);
   int hs = -1;
@@ -460,7 +461,7 @@ __device__ __forceinline__ bool visible(const TraceParams& P, float ax, float ay
   wx *= il;
   wy *= il;
   wz *= il;
-  const float4* sph = cull_spheres();
+  const float4* sph = cull_spheres(P);
   const float h = 0.5f * len;
   unsigned long long cand = cull_two(P, ax, ay, az, fmaf(wx, h, ax), fmaf(wy, h, ay), fmaf(wz, h, az), bx, by, bz);
   if (skip >= 0) cand &= ~(1ull << skip);
@@ -1751,7 +1752,7 @@ template <int METHOD, int MAXM, bool DEBUG, bool TILE, int BLOCK, bool ADJ = fal
 __global__ void __launch_bounds__(BLOCK, 1) trace_kernel(const TraceParams P) {
   extern __shared__ float4 smem4[];
   // general kernels: the sphere-culling masks and spheres come first
-  float* smem = reinterpret_cast<float*>(smem4) + (GEN ? kCullBytes / sizeof(float) : 0);
+  float* smem = reinterpret_cast<float*>(smem4) + (GEN ? cull_bytes(P.cull_slabs) / sizeof(float) : 0);
   const int tab_floats = kIsDartsM<METHOD> ? P.rows * P.row_stride : 0;
   float* tab = smem;
   constexpr int nwarps = BLOCK / 32;
