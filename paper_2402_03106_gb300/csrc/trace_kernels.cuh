@@ -533,6 +533,15 @@ __device__ __forceinline__ int w_bin(const TraceParams& P, unsigned long long s,
   return min(lo, P.n_bins - 1);
 }
 
+// The per-element Philox block (vertex 0xFFFFFE, group 0) and the DARTS bin
+// offset o_e = floor(u01(x) B) of a sensor element (R1, R28).
+__device__ __forceinline__ U4 element_block(const TraceParams& P, int elem) {
+  return philox4x32_10((uint32_t)elem, 0u, P.stream, (kVertexElement << 8) | 0u, P.key0, P.key1);
+}
+__device__ __forceinline__ unsigned element_offset(const TraceParams& P, int elem) {
+  return (unsigned)(((unsigned long long)(element_block(P, elem).x >> 8) * (unsigned)P.n_bins) >> 24);
+}
+
 // LEAN (general kernels only): the scene has point emitters only, a point
 // sensor or a camera inside the medium, no temporal response and no EDA at
 // surfaces, so those branches are compiled out (the host picks it).
@@ -589,13 +598,16 @@ struct Stepper {
   // Path start: sensor element and (DARTS) bin, the emitter point (chosen by
   // energy, a uniform point on an area emitter), then the point sensor or
   // the camera ray entering the medium (p.miss when it never does).
-  __device__ static void init_gen(const TraceParams& P, Path& p, unsigned long long j) {
+  // oe_pre: the element's bin offset o_e when the caller has it (else -1),
+  // e_pre: gid / spp when the caller has it (cameras).
+  __device__ static void init_gen(const TraceParams& P, Path& p, unsigned long long j, int oe_pre = -1,
+                                  unsigned long long e_pre = ~0ull) {
     const unsigned long long gid = P.path_offset + j;
     const int B = P.n_bins;
     unsigned long long s = gid;
     p.elem = 0;
     if (P.camera) {  // sample s of pixel elem; ids past the last pixel wrap with s continuing
-      const unsigned long long e = gid / P.spp;
+      const unsigned long long e = e_pre != ~0ull ? e_pre : gid / P.spp;
       const unsigned long long pixels = (unsigned long long)P.width * (unsigned long long)P.height;
       const unsigned long long wrap = e / pixels;
       s = wrap * P.spp + (gid - e * P.spp);
@@ -627,13 +639,15 @@ struct Stepper {
     p.s_hi_e = E.s_hi;
     p.beta = E.wsel;
     if (METHOD == kDarts) {
-      const U4 uo = philox4x32_10((uint32_t)p.elem, 0u, P.stream, (kVertexElement << 8) | 0u, P.key0, P.key1);
       int b;
-      if (!LEAN && P.wcdf) {
+      if (oe_pre >= 0) {
+        b = (int)((s % (unsigned long long)B + (unsigned)oe_pre) % (unsigned)B);
+      } else if (!LEAN && P.wcdf) {
+        const U4 uo = element_block(P, p.elem);
         const unsigned long long oe = (unsigned long long)floor((double)u01(uo.x) * (double)P.spp);
         b = w_bin(P, s, min(oe, P.spp - 1), (double)u01(uo.y));
       } else {
-        const unsigned oe = (unsigned)(((unsigned long long)(uo.x >> 8) * (unsigned)B) >> 24);
+        const unsigned oe = element_offset(P, p.elem);
         b = (int)((s % (unsigned long long)B + oe) % (unsigned)B);
       }
       p.bin = p.elem * B + b;
@@ -1599,6 +1613,11 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
   constexpr unsigned kSpread = 0x108421u, kFields = 0x1041041u;
   unsigned ev0 = 0, ev1 = 0;  // packed per-lane event counts (6-bit fields)
   int ev_steps = 0;
+  // general DARTS kernels: bin offsets o_e of the 32 consecutive sensor
+  // elements from cache_e0 on, one per lane (a pixel's paths share o_e, so
+  // a refill need not draw the element's Philox block for every path)
+  unsigned long long cache_e0 = ~0ull;
+  unsigned cache_oe = 0;
 
   for (;;) {
     // ---- refill lanes whose path ended (ballot + popc, warp-private id pool)
@@ -1607,10 +1626,14 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
       const int rank = __popc(dead & ((1u << lane) - 1u));
       const int n_dead = __popc(dead);
       const unsigned long long avail = pool_end - pool_next;
+      long long jn = -1;  // general kernels: the path this lane takes (initialised below)
       if (!alive && (unsigned long long)rank < avail) {
-        if constexpr (GEN) Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR, LEAN>::init_gen(P, p, pool_next + rank);
-        else Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR, LEAN>::init(P, p, pool_next + rank, add_mod(pool_bin, rank, B));
-        alive = true;
+        if constexpr (GEN) {
+          jn = (long long)(pool_next + rank);
+        } else {
+          Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR, LEAN>::init(P, p, pool_next + rank, add_mod(pool_bin, rank, B));
+          alive = true;
+        }
       }
       if ((unsigned long long)n_dead > avail) {
         unsigned long long base = N;
@@ -1625,11 +1648,14 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
           const unsigned long long end = min(base + chunk, N);
           const int base_bin = (int)((P.bin_base + base) % (unsigned long long)B);
           const long long r2 = (long long)rank - (long long)avail;
-          if (!alive && r2 >= 0 && (unsigned long long)r2 < end - base) {
-            if constexpr (GEN) Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR, LEAN>::init_gen(P, p, base + (unsigned long long)r2);
-            else Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR, LEAN>::init(P, p, base + (unsigned long long)r2,
-                                                         add_mod(base_bin, (int)r2, B));
-            alive = true;
+          if (!alive && jn < 0 && r2 >= 0 && (unsigned long long)r2 < end - base) {
+            if constexpr (GEN) {
+              jn = (long long)(base + (unsigned long long)r2);
+            } else {
+              Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR, LEAN>::init(P, p, base + (unsigned long long)r2,
+                                                                      add_mod(base_bin, (int)r2, B));
+              alive = true;
+            }
           }
           const int used = (int)min((unsigned long long)n_dead - avail, end - base);
           pool_next = base + used;
@@ -1639,6 +1665,32 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
       } else {
         pool_next += (unsigned long long)n_dead;
         pool_bin = add_mod(pool_bin, n_dead, B);
+      }
+      if constexpr (GEN) {  // the whole warp is here (dead and drained are warp-uniform)
+        int oe_pre = -1;
+        unsigned long long e_pre = ~0ull;
+        if constexpr (METHOD == kDarts) {
+          if (LEAN || !P.wcdf) {
+            const bool take = jn >= 0;
+            const unsigned long long e =
+                (take && P.camera) ? (P.path_offset + (unsigned long long)jn) / P.spp : 0ull;
+            const bool miss = take && (e < cache_e0 || e - cache_e0 >= 32ull);
+            const unsigned mm = __ballot_sync(kFull, miss);
+            if (mm) {  // restart the cache at the first missing lane's element
+              cache_e0 = __shfl_sync(kFull, e, __ffs(mm) - 1);
+              const unsigned long long pixels = P.camera ? (unsigned long long)P.width * P.height : 1ull;
+              cache_oe = element_offset(P, (int)((cache_e0 + (unsigned long long)lane) % pixels));
+            }
+            const bool in = take && e >= cache_e0 && e - cache_e0 < 32ull;
+            const unsigned v = __shfl_sync(kFull, cache_oe, in ? (int)(e - cache_e0) : lane);
+            if (in) oe_pre = (int)v;
+            if (take && P.camera) e_pre = e;
+          }
+        }
+        if (jn >= 0) {
+          Stepper<METHOD, MAXM, DEBUG, ADJ, GEN, VAR, LEAN>::init_gen(P, p, (unsigned long long)jn, oe_pre, e_pre);
+          alive = true;
+        }
       }
     }
     if (!__any_sync(kFull, alive)) break;
