@@ -621,8 +621,11 @@ struct Stepper {
     p.miss = false;
     p.surf = -1;
     p.salb = 0.0f;
-    // emitter point
+    // emitter point; the camera's jitter block is drawn beside it (two
+    // independent Philox chains whose latencies overlap)
     const U4 ue = rng(P, j, 0xFFFFFFu, 2);
+    U4 uc = U4{0u, 0u, 0u, 0u};
+    if (LEAN || P.camera) uc = rng(P, j, 0xFFFFFFu, 3);
     const float target = u01(ue.x);
     int pick = P.n_emitters - 1;
     for (int k = P.n_emitters - 1; k >= 0; --k)
@@ -659,7 +662,6 @@ struct Stepper {
       p.SM0 = E.s_hi;
     }
     if (P.camera) {
-      const U4 uc = rng(P, j, 0xFFFFFFu, 3);
       const int px = p.elem % P.width, py = p.elem / P.width;
       const float sx = (2.0f * ((float)px + u01(uc.x)) / (float)P.width - 1.0f) * P.cam_th * P.cam_aspect;
       const float sy = (1.0f - 2.0f * ((float)py + u01(uc.y)) / (float)P.height) * P.cam_th;
