@@ -1529,16 +1529,14 @@ __device__ __forceinline__ void ris_warp(const TraceParams& P, bool need, const 
       const unsigned gbits = (gt >> seg) & 0xFFu;
       sel = gbits ? __ffs(gbits) - 1 : (vbits ? 31 - __clz(vbits) : 0);
     }
-    const float wsel = __shfl_sync(kFull, w, sel, 8);
-    const float dsel = __shfl_sync(kFull, d, sel, 8);
-    if (act && j == 0) {
+    if (act && j == sel) {  // the selected candidate's lane writes the task's result
       RisResult r;
       r.ok = vbits != 0;
       r.sel = sel;
-      r.dsel = dsel;
-      r.factor = P.albedo * __fdividef(tot, wsel * 8.0f);
+      r.dsel = d;
+      r.factor = P.albedo * __fdividef(tot, w * 8.0f);
       if constexpr (VAR) {
-        if (P.ris_mode & 2) r.factor *= __expf(equi_lcorr(P, T, dsel));
+        if (P.ris_mode & 2) r.factor *= __expf(equi_lcorr(P, T, d));
       }
       results[t] = r;
     }
