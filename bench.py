@@ -993,22 +993,28 @@ def main():
     for i in range(2):
         prepared.render_host_async(hh[i])
     ctx.sync()
-    te = time.perf_counter()
-    for i in range(ne):
-        prepared.render_host_async(hh[i % 2], path_offset=i * N)
-    ctx.sync()
-    te = time.perf_counter() - te
-    # the synchronous call (render, copy back, synchronise per frame) beside it
-    ts_ = time.perf_counter()
-    for i in range(ne):
-        prepared.render_host(hh[0], path_offset=i * N)
-    ts_ = time.perf_counter() - ts_
+    # three repetitions of ne frames each, the median kept (one repetition
+    # on one box once ran without its copy/render overlap)
+    t_async, t_sync = [], []
+    for rep in range(3):
+        te = time.perf_counter()
+        for i in range(ne):
+            prepared.render_host_async(hh[i % 2], path_offset=(rep * ne + i) * N)
+        ctx.sync()
+        t_async.append(time.perf_counter() - te)
+        # the synchronous call (render, copy back, synchronise per frame) beside it
+        ts_ = time.perf_counter()
+        for i in range(ne):
+            prepared.render_host(hh[0], path_offset=(rep * ne + i) * N)
+        t_sync.append(time.perf_counter() - ts_)
+    te, ts_ = statistics.median(t_async), statistics.median(t_sync)
     cs, keep = capi.to_c_scene(sc)
     import ctypes
     h2d = (ctypes.sizeof(cs) + ctypes.sizeof(capi.darts_sampling)
            + len(sc.emitters) * ctypes.sizeof(capi.darts_emitter) + 40 * len(sc.geometry.spheres))
     e2e = {"value": N * ne / te, "unit": "paths/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": hh[0].numel() * 8, "frames": ne,
+           "d2h_bytes_per_step": hh[0].numel() * 8, "frames": ne, "repetitions": 3,
+           "ms_per_frame_each": [round(1e3 * t / ne, 3) for t in t_async],
            "synchronous_value": N * ne / ts_,
            "call": "darts_render_host_async (queued; one darts_sync after the last frame); "
                    "synchronous_value: darts_render_host"}
