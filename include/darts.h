@@ -377,7 +377,9 @@ darts_status darts_last_kernel_ms(darts_ctx* ctx, float* ms);
 
 /* Block size of the persistent path kernel (one CTA per SM): 512, 640 or 768
  * threads, or 0 for the default (a point sensor: the largest whose shared
- * memory fits; a camera: 512).  The point-sensor DARTS and baseline kernels
+ * memory fits; a camera: 640 below 2^21 paths per render and 768 from there,
+ * each as far as its shared memory fits; camera kernels other than DARTS's
+ * run 512).  The point-sensor DARTS and baseline kernels
  * and the camera kernel of DARTS are built for all three sizes; the other
  * variants always run 512.  Other values return DARTS_ERR_INVALID_ARG. */
 darts_status darts_set_launch(darts_ctx* ctx, int block);

@@ -23,6 +23,19 @@ __host__ __device__ inline size_t cull_bytes(int slabs) {
   return 3 * (size_t)slabs * slabs * sizeof(unsigned long long) + kMaxSpheres * 4 * sizeof(float);
 }
 
+// Guide of each direction-table row in shared memory: for k = 0..kGuide-1
+// the largest bin lo with cdf[lo] <= k / kGuide, and n_mu - 1 at k = kGuide
+// (uint16 entries, after the rows).  An inverse-CDF search for v then starts
+// from the bins [guide[floor(v kGuide)], guide[floor(v kGuide) + 1]].
+constexpr int kGuide = 32;
+__host__ __device__ inline size_t guide_bytes(int rows) {
+  return ((size_t)rows * (kGuide + 1) * sizeof(uint16_t) + 15) / 16 * 16;
+}
+// Shared memory of a staged direction table: its rows, then their guides.
+__host__ __device__ inline size_t table_smem_bytes(int rows, int row_stride) {
+  return (size_t)rows * row_stride * sizeof(float) + guide_bytes(rows);
+}
+
 // One pulse emitter: an isotropic point (kind 0) or a one-sided Lambertian
 // parallelogram pos + s u + t v emitting toward n = u x v / |u x v| (kind 1).
 struct EmitterParams {

@@ -56,7 +56,7 @@ cudaError_t launch_method(const TraceParams& p, int grid, int block, bool debug,
 }  // namespace
 
 size_t batch_smem_bytes(const BatchParams& bp, int block) {
-  return (size_t)bp.rows * bp.row_stride * sizeof(float) +
+  return table_smem_bytes(bp.rows, bp.row_stride) +
          (size_t)(block / 32) * 32 * (sizeof(RisTask) + sizeof(RisResult)) +
          (size_t)(block / 32) * 2 * bp.max_bins * sizeof(float);
 }
@@ -89,7 +89,7 @@ cudaError_t launch_batch(const BatchParams& bp, int grid, int block, size_t smem
 }
 
 size_t adjoint_smem_bytes(const TraceParams& p) {
-  size_t b = (size_t)p.rows * p.row_stride * sizeof(float) + (p.general ? cull_bytes(p.cull_slabs) : 0);
+  size_t b = table_smem_bytes(p.rows, p.row_stride) + (p.general ? cull_bytes(p.cull_slabs) : 0);
   if (p.M == 8) b += (size_t)(512 / 32) * 32 * (sizeof(RisTask) + sizeof(RisResult));
   return b;
 }
@@ -120,7 +120,7 @@ cudaError_t launch_adjoint(const TraceParams& p0, int grid, size_t smem, cudaStr
 
 size_t trace_smem_bytes(int method, const TraceParams& p, int block, bool tile) {
   const bool darts = method == kDarts || method == kDartsFull;
-  size_t b = darts ? (size_t)p.rows * p.row_stride * sizeof(float) : 0;
+  size_t b = darts ? table_smem_bytes(p.rows, p.row_stride) : 0;
   if (p.general) b += cull_bytes(p.cull_slabs);  // sphere-culling masks and the spheres, first in shared memory
   const size_t task = p.ris_mode ? sizeof(RisTaskVar) : sizeof(RisTask);
   if (darts && p.M == 8) b += (size_t)(block / 32) * 32 * (task + sizeof(RisResult));
