@@ -986,15 +986,28 @@ def main():
     hh = [torch.empty(shape, dtype=torch.float64, pin_memory=True) for _ in range(2)]
     for h_ in hh:
         h_.zero_()  # first touch of the pinned pages, outside the timed region
-    ne = max(4, min(K, 10))
+    ne = max(4, min(K, 30))
     # warm both calls: the context allocates its device histograms (two for
     # the queued call, one for the synchronous one) at their first use
     prepared.render_host(hh[0])
     for i in range(2):
         prepared.render_host_async(hh[i])
     ctx.sync()
-    # three repetitions of ne frames each, the median kept (one repetition
-    # on one box once ran without its copy/render overlap)
+    # the host link's bandwidth for one frame's histogram (a plain copy), the
+    # bound of the queued call when the copy outlasts the render
+    dev_h = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    t_copy = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hh[1].copy_(dev_h, non_blocking=True)
+        torch.cuda.synchronize()
+        t_copy.append(time.perf_counter() - t0)
+    d2h_gbs = hh[1].numel() * 8 / min(t_copy) / 1e9
+    del dev_h
+    # three repetitions of ne frames each, the median kept: the copies share
+    # the host link with other work on the machine, and a repetition now and
+    # then loses one copy's length to it
     t_async, t_sync = [], []
     for rep in range(3):
         te = time.perf_counter()
@@ -1015,6 +1028,7 @@ def main():
     e2e = {"value": N * ne / te, "unit": "paths/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": hh[0].numel() * 8, "frames": ne, "repetitions": 3,
            "ms_per_frame_each": [round(1e3 * t / ne, 3) for t in t_async],
+           "d2h_gbs": round(d2h_gbs, 1), "copy_ms_per_frame": round(hh[0].numel() * 8 / d2h_gbs / 1e6, 3),
            "synchronous_value": N * ne / ts_,
            "call": "darts_render_host_async (queued; one darts_sync after the last frame); "
                    "synchronous_value: darts_render_host"}
