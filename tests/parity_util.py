@@ -39,14 +39,43 @@ def share_oracle_table(ctx, sc, sp):
     GPU's own quadrature drops out of the per-path comparison.  Renders and
     debug traces that follow must not set FLAG_REBUILD_TABLE.  Returns the
     oracle table (for O.trace_paths(cdf=...))."""
+    return install_table(ctx, sc, sp, O.build_table(sc, sp))
+
+
+def install_table(ctx, sc, sp, cdf):
+    """Install the FP64 table cdf [rows][n_mu + 1], rounded to FP32, as the
+    GPU context's table for this scene; returns cdf."""
     import torch
     from paper_2402_03106_gb300 import capi
-    cdf = O.build_table(sc, sp)
     rows, nb1 = cdf.shape
     t = np.ones((rows, capi.darts_table_row_stride(sp.table_n_mu)), np.float32)
     t[:, :nb1] = cdf.astype(np.float32)
     ctx.load_table(sc, sp, torch.from_numpy(t).to(ctx._dev()))
     return cdf
+
+
+def plateau_table(rows, n_mu, seed, zero_frac=0.6):
+    """A direction table whose rows are CDFs with runs of zero-probability
+    bins (plateaus), including leading and trailing ones: every bin density
+    is drawn, most are set to zero, and each row is normalised in FP64.
+    Exercises the inverse-CDF search where many bins share one CDF value."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((rows, n_mu + 1))
+    for r in range(rows):
+        d = rng.random(n_mu) * (rng.random(n_mu) >= zero_frac)
+        if r % 4 == 1:
+            d[: n_mu // 3] = 0.0  # leading plateau at 0
+        if r % 4 == 2:
+            d[-n_mu // 3:] = 0.0  # trailing plateau at 1
+        if r % 4 == 3:
+            d[:] = 0.0
+            d[rng.integers(0, n_mu, 3)] = 1.0  # three bins carry everything
+        if d.sum() == 0.0:
+            d[rng.integers(0, n_mu)] = 1.0
+        c = np.concatenate(([0.0], np.cumsum(d)))
+        out[r] = c / c[-1]
+        out[r, -1] = 1.0
+    return out
 
 
 def report(name, same, rel, ref, tol, rel_tol=REL_PATH):

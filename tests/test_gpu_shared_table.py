@@ -22,7 +22,8 @@ torch = pytest.importorskip("torch")
 import oracle as O  # noqa: E402
 from paper_2402_03106_gb300 import scenes as S  # noqa: E402
 from parity_util import (REL_PATH, SHARED_TABLE_EPS, SURFACE_TIE, check_paths,  # noqa: E402
-                         displaced_sensitivity, report, share_oracle_table)
+                         displaced_sensitivity, install_table, plateau_table, report,
+                         share_oracle_table)
 
 pytestmark = pytest.mark.gpu
 
@@ -199,3 +200,29 @@ def test_shared_table_full_size_frames(ctx, name):
     assert np.mean(beyond) <= 0.01, (np.sort(rel[beyond])[-10:], np.count_nonzero(beyond))
     assert np.count_nonzero(c_ref) > 50
     report(f"shared_table_full_size_{name}", ~beyond & ~tie, rel, {"flags": flags}, tol)
+
+
+@pytest.mark.parametrize("scene", ["cube", "box_camera"])
+def test_plateau_table_per_path_parity(ctx, scene):
+    """Direction sampling from a table whose rows have runs of zero-probability
+    bins (leading, trailing and inner plateaus; rows with three live bins),
+    loaded on both sides.  The GPU's inverse-CDF search starts from a coarse
+    guide of each row, whose entries coincide on plateaus; the oracle takes
+    the first bin whose upper CDF edge exceeds the uniform.  Bins and traces
+    must agree path by path, contributions within the shared-table bar."""
+    if scene == "cube":
+        sc, sp = S.cube_workload(paths=1 << 16, seed=3)
+        sp.max_bounces = 50
+        first, n = 0, 4096
+    else:
+        sc, sp = S.box_camera_workload(seed=0)
+        first, n = 32 * 64 * 16, 2048
+    cdf = install_table(ctx, sc, sp, plateau_table(sp.table_n_rho * sp.table_n_s, sp.table_n_mu, seed=11))
+    gpu = ctx.debug_paths(sc, sp, first, n)
+    torch.cuda.synchronize()
+    ref = O.trace_paths(sc, sp, first, n, cdf=cdf)
+    kw = {}
+    if scene != "cube":  # grazing surface hits: as in the camera tests above
+        kw = {"extra_tol": 5.0 * displaced_sensitivity(sc, sp, first, n, S.DARTS, ref), "tie_margin": SURFACE_TIE}
+    check_paths(gpu, ref, sp.max_bounces, table_eps=SHARED_TABLE_EPS, name=f"plateau_table_{scene}", **kw)
+    assert np.count_nonzero(ref["contrib"]) > n // 50
