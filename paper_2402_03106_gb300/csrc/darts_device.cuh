@@ -22,9 +22,13 @@ struct U4 {
 };
 
 // Philox4x32-10: ten rounds of two 32x32 -> 64-bit multiplies, Weyl key bumps.
+// UNROLL: rounds per iteration of the round loop in the generated code (the
+// same ten rounds and the same result for every value; kernels short of
+// instruction cache take a shorter body).
+template <int UNROLL = 10>
 __host__ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
                                                       uint32_t c3, uint32_t k0, uint32_t k1) {
-#pragma unroll
+#pragma unroll UNROLL
   for (int r = 0; r < 10; ++r) {
 #ifdef __CUDA_ARCH__
     const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
