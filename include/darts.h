@@ -375,17 +375,18 @@ darts_status darts_last_kernel_ms(darts_ctx* ctx, float* ms);
 
 /* ---- launch shape ---------------------------------------------------------- */
 
-/* Block size of the persistent path kernel (one CTA per SM): 512, 640 or 768
- * threads, or 0 for the default (a point sensor: the largest whose shared
- * memory fits; a camera: 640 below 2^21 paths per render and 768 from there,
- * each as far as its shared memory fits; camera kernels other than DARTS's
- * run 512).  The point-sensor DARTS and baseline kernels
- * and the camera kernel of DARTS are built for all three sizes; the other
- * variants always run 512.  Other values return DARTS_ERR_INVALID_ARG. */
+/* Block size of the persistent path kernel (one CTA per SM): 512, 640, 768
+ * or 896 threads, or 0 for the default (a point sensor: the largest whose
+ * shared memory fits; a camera: 640 below 2^21 paths per render and 768
+ * from there, each as far as its shared memory fits; camera kernels other
+ * than DARTS's run 512).  The point-sensor DARTS and baseline kernels are
+ * built for 512, 640 and 768, the camera kernels of DARTS for all four
+ * sizes; the other variants always run 512, and a size a kernel is not
+ * built for runs as 512.  Other values return DARTS_ERR_INVALID_ARG. */
 darts_status darts_set_launch(darts_ctx* ctx, int block);
 
 /* Launch shape of the context's kernels.  Zero fields take the defaults.
- *   block        path kernel, as darts_set_launch (0, 512, 640, 768);
+ *   block        path kernel, as darts_set_launch (0, 512, 640, 768, 896);
  *   chunk        paths a warp claims per update of the global path counter,
  *                1..1024 (default 64; a launch with fewer paths per resident
  *                warp claims fewer);
@@ -405,7 +406,8 @@ darts_status darts_set_launch_config(darts_ctx* ctx, const darts_launch* cfg);
 darts_status darts_get_launch_config(darts_ctx* ctx, darts_launch* cfg);
 
 /* Autotuner of the path kernel's launch shape for one render: times
- * darts_render of (scene, sampling) for every block size (512, 640, 768) and
+ * darts_render of (scene, sampling) for every block size (512, 640, 768; 896
+ * for a camera render of DARTS) and
  * chunk (16, 32, 64, 128, 256) that the scene's kernel runs (3 timed renders
  * each after one warm-up; CUDA events on the context's stream; chunks above
  * the launch's paths per resident warp are the same launch and are timed

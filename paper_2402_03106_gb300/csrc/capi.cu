@@ -610,7 +610,7 @@ void choose_launch(const darts_ctx* ctx, const darts_sampling* sp, const TracePa
     *block = trace_block_for(ctx->block ? ctx->block : dflt, debug, false, sp->method, sp->ris_m, P.general != 0);
     *smem = trace_smem_bytes(sp->method, P, *block, false);
     while (*smem > (size_t)ctx->smem_optin && *block > 512) {
-      *block = *block == 768 ? 640 : 512;
+      *block = *block == 896 ? 768 : (*block == 768 ? 640 : 512);
       *smem = trace_smem_bytes(sp->method, P, *block, false);
     }
     return;
@@ -824,17 +824,17 @@ darts_status darts_last_kernel_ms(darts_ctx* ctx, float* ms) {
 
 darts_status darts_set_launch(darts_ctx* ctx, int block) {
   if (!ctx) return DARTS_ERR_INVALID_ARG;
-  if (block != 0 && block != 512 && block != 640 && block != 768)
-    return fail(ctx, DARTS_ERR_INVALID_ARG, "block must be 0, 512, 640 or 768");
+  if (block != 0 && block != 512 && block != 640 && block != 768 && block != 896)
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "block must be 0, 512, 640, 768 or 896");
   ctx->block = block;
   return DARTS_OK;
 }
 
 darts_status darts_set_launch_config(darts_ctx* ctx, const darts_launch* cfg) {
   if (!ctx || !cfg) return DARTS_ERR_INVALID_ARG;
-  auto block_ok = [](int b) { return b == 0 || b == 512 || b == 640 || b == 768; };
-  if (!block_ok(cfg->block) || !block_ok(cfg->batch_block))
-    return fail(ctx, DARTS_ERR_INVALID_ARG, "block sizes must be 0, 512, 640 or 768");
+  auto batch_ok = [](int b) { return b == 0 || b == 512 || b == 640 || b == 768; };
+  if (!(batch_ok(cfg->block) || cfg->block == 896) || !batch_ok(cfg->batch_block))
+    return fail(ctx, DARTS_ERR_INVALID_ARG, "block must be 0, 512, 640, 768 or 896; batch_block 0, 512, 640 or 768");
   if (cfg->chunk < 0 || cfg->chunk > 1024 || cfg->batch_items < 0 || cfg->batch_items > 64)
     return fail(ctx, DARTS_ERR_INVALID_ARG, "chunk must be in [0, 1024] and batch_items in [0, 64]");
   ctx->block = cfg->block;
@@ -887,7 +887,7 @@ struct EventPair {
   }
 };
 
-constexpr int kTuneBlocks[3] = {512, 640, 768};
+constexpr int kTuneBlocks[4] = {512, 640, 768, 896};  // 896: the DARTS camera kernels only
 constexpr int kTuneChunks[5] = {16, 32, 64, 128, 256};
 constexpr int kTuneItems[5] = {2, 4, 8, 16, 32};
 }  // namespace
@@ -910,7 +910,10 @@ darts_status darts_autotune(darts_ctx* ctx, const darts_scene* scene, const dart
   // a chunk cap above the launch's paths per resident warp changes nothing:
   // those are searched once (the smallest such cap stands for all)
   const uint64_t paths = sampling->paths_per_element * elements_of(scene);
-  for (int bi = 0; bi < 3 && s == DARTS_OK; ++bi) {
+  const bool camera_darts =
+      scene->sensor.kind == DARTS_SENSOR_PINHOLE && sampling->method == DARTS_METHOD_DARTS;
+  for (int bi = 0; bi < 4 && s == DARTS_OK; ++bi) {
+    if (kTuneBlocks[bi] == 896 && !camera_darts) continue;
     bool saturated = false;
     for (int ci = 0; ci < 5 && s == DARTS_OK && !saturated; ++ci) {
       ctx->block = kTuneBlocks[bi];

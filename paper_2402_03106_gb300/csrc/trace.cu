@@ -18,12 +18,14 @@ cudaError_t launch_method(const TraceParams& p, int grid, int block, bool debug,
         switch (block) {
           case 640: return launch_one<METHOD, 8, false, false, 640, true, false, true>(p, grid, smem, s);
           case 768: return launch_one<METHOD, 8, false, false, 768, true, false, true>(p, grid, smem, s);
+          case 896: return launch_one<METHOD, 8, false, false, 896, true, false, true>(p, grid, smem, s);
           default: return launch_one<METHOD, 8, false, false, 512, true, false, true>(p, grid, smem, s);
         }
       }
       switch (block) {
         case 640: return launch_one<METHOD, 8, false, false, 640, true>(p, grid, smem, s);
         case 768: return launch_one<METHOD, 8, false, false, 768, true>(p, grid, smem, s);
+        case 896: return launch_one<METHOD, 8, false, false, 896, true>(p, grid, smem, s);
         default: break;
       }
     }
@@ -133,7 +135,8 @@ int trace_max_m() { return kMaxM; }
 int trace_block_for(int block, bool debug, bool tile, int method, int M, bool general) {
   const bool wide = block == 640 || block == 768;
   if (debug || method == kDartsFull || (method == kDarts && M != 8)) return 512;
-  if (general) return (!tile && method == kDarts && wide) ? block : 512;  // camera frames of DARTS
+  // camera frames of DARTS: 896 threads too (72 registers a thread)
+  if (general) return (!tile && method == kDarts && (wide || block == 896)) ? block : 512;
   return (tile && wide) ? block : 512;
 }
 

@@ -10,6 +10,8 @@ Tolerances:
   * histograms at matched seeds: relative L2 <= 1e-3 and every bin within
     3 standard errors.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -261,26 +263,33 @@ def test_block_sizes_agree_and_autotune(ctx, method):
 
 
 def test_launch_shapes_of_the_camera_kernel_agree(ctx):
-    """The camera kernel of DARTS at 512, 640 and 768 threads and with
+    """The camera kernel of DARTS at 512, 640, 768 and 896 threads and with
     chunk caps from 1 to 1024 paths renders the same frame (the same paths
-    with their FP64 atomics in another order); the autotuner keeps one of
-    the shapes it timed; out-of-range shapes are refused and change nothing."""
+    with their FP64 atomics in another order), the lean kernel (camera in
+    the medium, point emitters) and the general one (a zero-energy area
+    emitter forces it); the autotuner keeps one of the shapes it timed;
+    out-of-range shapes (896 for the batch kernel among them) are refused
+    and change nothing."""
     sc = S.spheres_camera_scene(seed=0, width=64, height=64, n_bins=200)
     sp = S.Sampling(seed=4, paths_per_element=64, max_bounces=40)
-    ref = None
-    for block, chunk in ((512, 0), (640, 0), (768, 0), (512, 1), (640, 7), (768, 1024)):
-        ctx.set_launch_config(block=block, chunk=chunk)
-        h = ctx.render(sc, sp).cpu()
-        if ref is None:
-            ref = h
-        else:
-            torch.testing.assert_close(h, ref, rtol=1e-9, atol=1e-15)
+    general = dataclasses.replace(sc, emitters=sc.emitters + [
+        S.Emitter((2.0, 3.9, 2.0), 0.0, 0.0, S.EMITTER_AREA, (0.2, 0.0, 0.0), (0.0, 0.0, 0.2))])
+    for scene in (sc, general):
+        ref = None
+        for block, chunk in ((512, 0), (640, 0), (768, 0), (896, 0), (512, 1), (640, 7), (768, 1024), (896, 128)):
+            ctx.set_launch_config(block=block, chunk=chunk)
+            h = ctx.render(scene, sp).cpu()
+            if ref is None:
+                ref = h
+            else:
+                torch.testing.assert_close(h, ref, rtol=1e-9, atol=1e-15)
     ctx.set_launch_config()
     best = ctx.autotune(sc, sp)
     cfg = ctx.launch_config()
-    assert best in (512, 640, 768) and cfg["block"] == best and cfg["chunk"] in (16, 32, 64, 128, 256)
+    assert best in (512, 640, 768, 896) and cfg["block"] == best and cfg["chunk"] in (16, 32, 64, 128, 256)
     from paper_2402_03106_gb300 import capi
-    for bad in (dict(block=100), dict(chunk=-1), dict(chunk=2000), dict(batch_items=65), dict(batch_block=1)):
+    for bad in (dict(block=100), dict(chunk=-1), dict(chunk=2000), dict(batch_items=65), dict(batch_block=1),
+                dict(batch_block=896)):
         with pytest.raises(capi.DartsError):
             ctx.set_launch_config(**bad)
     assert ctx.launch_config() == cfg

@@ -165,7 +165,7 @@ def test_lean_camera_kernel_equals_the_general_one(ctx):
     full = dataclasses.replace(sc, emitters=sc.emitters + [
         S.Emitter((2.0, 3.9, 2.0), 0.0, 0.0, S.EMITTER_AREA, (0.2, 0.0, 0.0), (0.0, 0.0, 0.2))])
     n = S.total_paths(sc, sp)
-    for block in (512, 640, 768):
+    for block in (512, 640, 768, 896):
         ctx.set_launch_config(block=block)
         outs, probes = [], []
         for scene in (sc, full):
