@@ -49,6 +49,39 @@ __host__ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, u
   return U4{c0, c1, c2, c3};
 }
 
+// Two Philox4x32-10 blocks whose counters differ only in the last word,
+// advanced in one loop: two independent chains in one loop body (the same
+// results as two calls).
+template <int UNROLL = 10>
+__host__ __device__ __forceinline__ void philox4x32_10_pair(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                           uint32_t c3a, uint32_t c3b, uint32_t k0,
+                                                           uint32_t k1, U4* a, U4* b) {
+  uint32_t a0 = c0, a1 = c1, a2 = c2, a3 = c3a;
+  uint32_t b0 = c0, b1 = c1, b2 = c2, b3 = c3b;
+#pragma unroll UNROLL
+  for (int r = 0; r < 10; ++r) {
+#ifdef __CUDA_ARCH__
+    const uint32_t ha0 = __umulhi(0xD2511F53u, a0), la0 = 0xD2511F53u * a0;
+    const uint32_t ha1 = __umulhi(0xCD9E8D57u, a2), la1 = 0xCD9E8D57u * a2;
+    const uint32_t hb0 = __umulhi(0xD2511F53u, b0), lb0 = 0xD2511F53u * b0;
+    const uint32_t hb1 = __umulhi(0xCD9E8D57u, b2), lb1 = 0xCD9E8D57u * b2;
+#else
+    const uint64_t pa0 = uint64_t(0xD2511F53u) * a0, pa1 = uint64_t(0xCD9E8D57u) * a2;
+    const uint64_t pb0 = uint64_t(0xD2511F53u) * b0, pb1 = uint64_t(0xCD9E8D57u) * b2;
+    const uint32_t ha0 = uint32_t(pa0 >> 32), la0 = uint32_t(pa0), ha1 = uint32_t(pa1 >> 32), la1 = uint32_t(pa1);
+    const uint32_t hb0 = uint32_t(pb0 >> 32), lb0 = uint32_t(pb0), hb1 = uint32_t(pb1 >> 32), lb1 = uint32_t(pb1);
+#endif
+    const uint32_t na0 = ha1 ^ a1 ^ k0, na2 = ha0 ^ a3 ^ k1;
+    const uint32_t nb0 = hb1 ^ b1 ^ k0, nb2 = hb0 ^ b3 ^ k1;
+    a0 = na0; a1 = la1; a2 = na2; a3 = la0;
+    b0 = nb0; b1 = lb1; b2 = nb2; b3 = lb0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  *a = U4{a0, a1, a2, a3};
+  *b = U4{b0, b1, b2, b3};
+}
+
 // Counter layout shared by every kernel: (path lo, path hi, stream,
 // vertex << 8 | group); group 0 = distance step, group 1 = direction and
 // control vertex; vertex 0xFFFFFE = per sensor element.

@@ -129,6 +129,15 @@ __device__ __forceinline__ U4 rng(const TraceParams& P, unsigned long long id, u
                        P.key0, P.key1);
 }
 
+// The blocks of groups ga and gb at one vertex of a path (see rng).
+template <int UNROLL = 10>
+__device__ __forceinline__ void rng_pair(const TraceParams& P, unsigned long long id, uint32_t vertex,
+                                         uint32_t ga, uint32_t gb, U4* a, U4* b) {
+  const unsigned long long gid = P.path_offset + id;
+  philox4x32_10_pair<UNROLL>((uint32_t)gid, (uint32_t)(gid >> 32), P.stream, (vertex << 8) | ga,
+                             (vertex << 8) | gb, P.key0, P.key1, a, b);
+}
+
 __device__ __forceinline__ void kahan_add(float& sum, float& comp, float v) {
   const float y = v - comp;
   const float t = sum + y;
@@ -584,6 +593,8 @@ struct Stepper {
   // code least fits the instruction cache, takes two (1.3 % faster on the
   // 512x512 sphere frame); the others unroll all ten (two cost them 5 %).
   static constexpr int kPU = LEAN ? 2 : 10;
+  // the same for the two blocks a lean vertex or refill draws side by side
+  static constexpr int kPUP = LEAN ? 2 : 10;
   // Radiant intensity of the path's emitter point toward x, and the zero
   // temporal weight test, without the branches a lean scene never takes.
   __device__ __forceinline__ static float intensity(const Path& p, float x, float y, float z) {
@@ -659,9 +670,13 @@ struct Stepper {
     p.salb = 0.0f;
     // emitter point; the camera's jitter block is drawn beside it (two
     // independent Philox chains whose latencies overlap)
-    const U4 ue = rng<kPU>(P, j, 0xFFFFFFu, 2);
-    U4 uc = U4{0u, 0u, 0u, 0u};
-    if (LEAN || P.camera) uc = rng<kPU>(P, j, 0xFFFFFFu, 3);
+    U4 ue, uc = U4{0u, 0u, 0u, 0u};
+    if (LEAN) {
+      rng_pair<kPUP>(P, j, 0xFFFFFFu, 2, 3, &ue, &uc);
+    } else {
+      ue = rng<kPU>(P, j, 0xFFFFFFu, 2);
+      if (P.camera) uc = rng<kPU>(P, j, 0xFFFFFFu, 3);
+    }
     const float target = u01(ue.x);
     int pick = P.n_emitters - 1;
     for (int k = P.n_emitters - 1; k >= 0; --k)
@@ -826,8 +841,13 @@ struct Stepper {
     }
     float wx = p.wx, wy = p.wy, wz = p.wz;
     // both draws of the vertex up front: two independent Philox chains
-    const U4 u1 = rng<kPU>(P, p.j, (uint32_t)p.k, 1);
-    const U4 u0 = rng<kPU>(P, p.j, (uint32_t)p.k, 0);
+    U4 u1, u0;
+    if (LEAN) {
+      rng_pair<kPUP>(P, p.j, (uint32_t)p.k, 1, 0, &u1, &u0);
+    } else {
+      u1 = rng<kPU>(P, p.j, (uint32_t)p.k, 1);
+      u0 = rng<kPU>(P, p.j, (uint32_t)p.k, 0);
+    }
     if (!p.fixed) {
       // MIS of the EDA table and HG (uniform sphere at the point sensor), Eq. 19
       const float rho = __fdividef(C, SM);
