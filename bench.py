@@ -1005,11 +1005,11 @@ def main():
         t_copy.append(time.perf_counter() - t0)
     d2h_gbs = hh[1].numel() * 8 / min(t_copy) / 1e9
     del dev_h
-    # three repetitions of ne frames each, the median kept: the copies share
+    # five repetitions of ne frames each, the median kept: the copies share
     # the host link with other work on the machine, and a repetition now and
     # then loses one copy's length to it
     t_async, t_sync = [], []
-    for rep in range(3):
+    for rep in range(5):
         te = time.perf_counter()
         for i in range(ne):
             prepared.render_host_async(hh[i % 2], path_offset=(rep * ne + i) * N)
@@ -1026,7 +1026,7 @@ def main():
     h2d = (ctypes.sizeof(cs) + ctypes.sizeof(capi.darts_sampling)
            + len(sc.emitters) * ctypes.sizeof(capi.darts_emitter) + 40 * len(sc.geometry.spheres))
     e2e = {"value": N * ne / te, "unit": "paths/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": hh[0].numel() * 8, "frames": ne, "repetitions": 3,
+           "d2h_bytes_per_step": hh[0].numel() * 8, "frames": ne, "repetitions": 5,
            "ms_per_frame_each": [round(1e3 * t / ne, 3) for t in t_async],
            "d2h_gbs": round(d2h_gbs, 1), "copy_ms_per_frame": round(hh[0].numel() * 8 / d2h_gbs / 1e6, 3),
            "synchronous_value": N * ne / ts_,
