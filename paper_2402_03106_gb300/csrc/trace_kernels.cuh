@@ -1497,9 +1497,16 @@ struct Stepper {
 // bins are serialised (one lane per distinct bin per round).
 __device__ __forceinline__ void warp_commit(bool has, int bin, float val, float* wsum, float* wcomp,
                                             float* wsq, bool tile, const TraceParams& P,
-                                            bool do_sq) {
+                                            bool do_sq, bool merge = true) {
   if (!tile) {  // outputs zeroed before the launch: FP64 atomics into them
     const bool ok = has && DARTS_INDEX_OK(P, bin, (P.camera ? (long long)P.width * P.height : 1ll) * P.n_bins);
+    if (!merge) {  // lanes rarely share a bin: each adds its own contribution
+      if (ok) {
+        atomicAdd(&P.hist[bin], (double)val);
+        if (do_sq) atomicAdd(&P.sumsq[bin], (double)val * (double)val);
+      }
+      return;
+    }
     const unsigned act = __ballot_sync(kFull, ok);
     if (!ok) return;
     // lanes adding to the same bin (the baselines and full-gate DARTS bin by
@@ -1836,7 +1843,12 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
         }
       }
     } else {
-      warp_commit(has, cbin, cval, wsum, wcomp, wsq, TILE, P, do_sq);
+      // DARTS dedicates the paths of one sensor element to distinct bins
+      // (sample index + offset mod B): two lanes meet in a bin only with
+      // more samples per element than bins, so the general DARTS kernels do
+      // not merge lanes (the sums are the same; the baselines and full-gate
+      // DARTS bin by time and merge)
+      warp_commit(has, cbin, cval, wsum, wcomp, wsq, TILE, P, do_sq, !(GEN && METHOD == kDarts));
       if constexpr ((GEN && METHOD == kPlain) || METHOD == kDartsFull) {
         if (cbin2 >= 0 && !isfinite(cval2)) {
           atomicOr(P.status, 1u);
