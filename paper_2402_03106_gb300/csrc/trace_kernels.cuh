@@ -98,6 +98,11 @@ struct Path {
 // shared memory.
 __shared__ unsigned long long s_rare[2];
 
+// Branches a path takes at most once (early exits, the last vertex) or
+// almost never (non-finite values, probes, FP64 fallbacks): laid out away
+// from the hot loop so that its instructions stay dense in the cache.
+#define DARTS_RARE(x) __builtin_expect(!!(x), 0)
+
 // Checked builds (-DDARTS_CHECKS, libdarts_checked.so): every index into an
 // output, a tile or the table is tested; one out of range sets status bit 2
 // (reported as DARTS_ERR_BOUNDS by darts_sync) and the access is skipped.
@@ -305,7 +310,7 @@ __device__ __forceinline__ float ris_candidate(const TraceParams& P, const RisTa
   *d_out = d;
   if (P.no_da) return 0.0f;  // ablation: the target equals the candidate density
   if (!(s > 0.0f && r2 < s * s)) return -FLT_MAX;
-  if (act && s < P.tiny_s) {
+  if (DARTS_RARE(act && s < P.tiny_s)) {
     cnt.add_rare(ST_FP64P);
     return log_phi_fp64(P, r2, T.SM, T.SMlo, d) + lc;
   }
@@ -829,7 +834,7 @@ struct Stepper {
   // surface vertex (no distance step).
   __device__ static int vertex_gen(const TraceParams& P, Path& p, const float* tab, Counters& cnt,
                                    RisTaskT<VAR>& task) {
-    if (p.miss) return 1;  // camera ray that never enters the medium
+    if (DARTS_RARE(p.miss)) return 1;  // camera ray that never enters the medium
     cnt.add(ST_VERT);
     const float ex = p.ey0 - p.x, ey = p.ey1 - p.y, ez = p.ey2 - p.z;
     const float C2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
@@ -837,7 +842,7 @@ struct Stepper {
     const float invC = __frcp_rn(C);
     const float ax = ex * invC, ay = ey * invC, az = ez * invC;
     const float SM = p.SM0 - p.L, Sm = p.Sm0 - p.L;
-    if (!(SM > C)) {
+    if (DARTS_RARE(!(SM > C))) {
       cnt.add(ST_EARLY);
       record(P, p, 0, EV_EARLY);
       return 1;
@@ -942,7 +947,7 @@ struct Stepper {
     p.wx = wx;
     p.wy = wy;
     p.wz = wz;
-    if (p.k + 1 == P.K) {
+    if (DARTS_RARE(p.k + 1 == P.K)) {
       record(P, p, 0, EV_MAXDEPTH | nonempty);
       return 1;
     }
@@ -1018,7 +1023,7 @@ struct Stepper {
       const float C = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
       const float invC = __frcp_rn(C);
       const float SM = p.SM0 - p.L, Sm = p.Sm0 - p.L;
-      if (!(SM > C)) {
+      if (DARTS_RARE(!(SM > C))) {
         cnt.add(ST_EARLY);
         record(P, p, 0, EV_EARLY);
         return true;
@@ -1043,7 +1048,7 @@ struct Stepper {
         *out_c = p.beta * cc;
         p.c += *out_c;
       }
-      if (p.k + 1 == P.K) {
+      if (DARTS_RARE(p.k + 1 == P.K)) {
         record(P, p, 0, EV_MAXDEPTH);
         return true;
       }
@@ -1154,7 +1159,7 @@ struct Stepper {
         record(P, p, 0, EV_EARLY);
         return true;
       }
-      if (p.k + 1 == P.K) {
+      if (DARTS_RARE(p.k + 1 == P.K)) {
         record(P, p, 0, EV_MAXDEPTH);
         return true;
       }
@@ -1190,7 +1195,7 @@ struct Stepper {
     const float invC = __frcp_rn(C);
     const float ax = ex * invC, ay = ey * invC, az = ez * invC;
     const float SM = p.SM0 - p.L, Sm = p.Sm0 - p.L;
-    if (!(SM > C)) {  // Sec. 5.2 early exit
+    if (DARTS_RARE(!(SM > C))) {  // Sec. 5.2 early exit
       cnt.add(ST_EARLY);
       record(P, p, 0, EV_EARLY);
       return true;
@@ -1279,7 +1284,7 @@ struct Stepper {
     p.wx = wx;  // the walk continues along the connection direction (Eq. 20)
     p.wy = wy;
     p.wz = wz;
-    if (p.k + 1 == P.K) {
+    if (DARTS_RARE(p.k + 1 == P.K)) {
       record(P, p, 0, EV_MAXDEPTH | nonempty);
       return true;
     }
@@ -1397,7 +1402,7 @@ struct Stepper {
       const float C = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
       const float invC = 1.0f / C;
       const float SM = P.S_gate_hi - p.L, Sm = P.S_gate_lo - p.L;
-      if (!(SM > C)) {
+      if (DARTS_RARE(!(SM > C))) {
         cnt.add(ST_EARLY);
         record(P, p, 0, EV_EARLY);
         return true;
@@ -1422,7 +1427,7 @@ struct Stepper {
         *out_c = p.beta * cc;
         p.c += *out_c;
       }
-      if (p.k + 1 == P.K) {
+      if (DARTS_RARE(p.k + 1 == P.K)) {
         record(P, p, 0, EV_MAXDEPTH);
         return true;
       }
@@ -1472,7 +1477,7 @@ struct Stepper {
         record(P, p, 0, EV_EARLY);
         return true;
       }
-      if (p.k + 1 == P.K) {
+      if (DARTS_RARE(p.k + 1 == P.K)) {
         record(P, p, 0, EV_MAXDEPTH);
         return true;
       }
@@ -1812,13 +1817,13 @@ __device__ __forceinline__ void path_loop(const TraceParams& P, const float* tab
       }
       cval *= P.wb;
     }
-    if (cbin >= 0 && !isfinite(cval)) {
+    if (DARTS_RARE(cbin >= 0 && !isfinite(cval))) {
       atomicOr(P.status, 1u);
       cval = 0.0f;
     }
     const bool has = alive && cbin >= 0;
     if (alive && fin) {
-      if (P.probe_stride && p.j >= P.probe_first && (p.j - P.probe_first) % P.probe_stride == 0) {
+      if (DARTS_RARE(P.probe_stride && p.j >= P.probe_first && (p.j - P.probe_first) % P.probe_stride == 0)) {
         const unsigned long long slot = (p.j - P.probe_first) / P.probe_stride;
         if (slot < P.probe_count) {
           P.probe_c[slot] = p.c;
